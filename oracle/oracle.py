@@ -1,0 +1,417 @@
+"""CPU oracle for the mesh-embedding hot path of arXiv 2512.01251.
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py``.  The product package never imports
+it, and it never imports the product package.  It is plain and slow on
+purpose: every result is the definition evaluated by brute force over all
+triangles (C core in ``emb_oracle.c``), driven by numpy.
+
+Parity status of each function (see also the module functions' docstrings):
+  * ``build_forest``, ``masks``, ``refine_flags``, ``cut_links`` — pinned by
+    closed forms, half-space representations, clipping and invariants
+    (tests/test_oracle_pins.py).
+  * ``mex_force``/``mex_force_dq``/``dq_dverts`` — the derivative formulas are
+    pinned by finite differences and a closed form; the Bouzidi branch rule for
+    a missing interpolation partner and the momentum-exchange sign convention
+    are readings of the paper (it prints neither formula): parity unpinned for
+    that branch rule.
+
+Integer frame.  With R = r_o 2^k root blocks per axis (r_o odd), a vertex
+coordinate v (a multiple of 2^-20 in (0,1)) maps to X = v 2^20 r_o.  At level L
+the cell size is h_L = 2^(18-k-L) units and cell i has its centre at
+(2 i + 1) 2^(17-k-L), so every query point is an integer.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from fractions import Fraction
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_SRC = os.path.join(_HERE, "emb_oracle.c")
+
+
+def build(force: bool = False) -> str:
+    """Compile the C core with gcc (OpenMP) into oracle/liboracle.so."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        i64 = ctypes.c_int64
+        L.orc_solid.argtypes = [P, i64, P, i64, ctypes.c_int, P]
+        L.orc_links.argtypes = [P, i64, P, P, i64, i64, P, P, P]
+        L.orc_boxes_any.argtypes = [P, i64, P, P, i64, P]
+        L.orc_sat.argtypes = [P, P, P]
+        L.orc_sat.restype = ctypes.c_int
+        L.orc_segment_hit.argtypes = [P, P, ctypes.c_int, i64, P]
+        L.orc_segment_hit.restype = ctypes.c_int
+        L.orc_line_hits.argtypes = [P, P, ctypes.c_int]
+        L.orc_line_hits.restype = ctypes.c_int
+        L.orc_directions.argtypes = [P]
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.int64)
+
+
+# --------------------------------------------------------------------------- #
+# frame
+# --------------------------------------------------------------------------- #
+def frame(R: int):
+    """(r_o, k) with R = r_o 2^k, r_o odd."""
+    if R < 1:
+        raise ValueError("R must be positive")
+    k = 0
+    while R % 2 == 0:
+        R //= 2
+        k += 1
+    return R, k
+
+
+def h_units(R: int, L: int) -> int:
+    _, k = frame(R)
+    if k + L > 17:
+        raise ValueError("level too fine for the integer frame")
+    return 1 << (18 - k - L)
+
+
+def domain_units(R: int) -> int:
+    return (1 << 20) * frame(R)[0]
+
+
+def int_coords(verts: np.ndarray, R: int) -> np.ndarray:
+    """Vertex coordinates in frame units (int64); raises on unsnapped input."""
+    m = np.asarray(verts, dtype=np.float64) * float(1 << 20)
+    if not np.all(m == np.round(m)):
+        raise ValueError("vertices are not on the 2^-20 grid")
+    if not (np.all(m > 0) and np.all(m < (1 << 20))):
+        raise ValueError("vertices must lie strictly inside (0, 1)")
+    return m.astype(np.int64) * frame(R)[0]
+
+
+def tri_coords(X: np.ndarray, tris: np.ndarray) -> np.ndarray:
+    """(T, 9) int64 records A, B, C."""
+    t = np.asarray(tris, dtype=np.int64)
+    return _c64(np.concatenate([X[t[:, 0]], X[t[:, 1]], X[t[:, 2]]], axis=1))
+
+
+def directions() -> np.ndarray:
+    out = np.zeros((27, 3), dtype=np.int32)
+    lib().orc_directions(_p(out))
+    return out.astype(np.int64)
+
+
+def opposite(i: int) -> int:
+    """Index of -c_i (pairs (1,2), (3,4), ... , (25,26))."""
+    return i + 1 if i % 2 == 1 else i - 1
+
+
+def watertight(tris: np.ndarray) -> bool:
+    """Every directed edge appears exactly once and its reverse exactly once."""
+    t = np.asarray(tris, dtype=np.int64)
+    e = np.concatenate([t[:, [0, 1]], t[:, [1, 2]], t[:, [2, 0]]])
+    if np.any(e[:, 0] == e[:, 1]):
+        return False
+    key = e[:, 0] * (1 << 32) + e[:, 1]
+    rkey = e[:, 1] * (1 << 32) + e[:, 0]
+    u, cnt = np.unique(key, return_counts=True)
+    if np.any(cnt != 1):
+        return False
+    return bool(np.all(np.isin(rkey, u)))
+
+
+# --------------------------------------------------------------------------- #
+# primitive queries (brute force over all triangles, C core)
+# --------------------------------------------------------------------------- #
+def solid(tri9: np.ndarray, pts: np.ndarray, dir: int = 1) -> np.ndarray:
+    """Parity of crossings of the perturbed ray from each point along DIR[dir]."""
+    tri9, pts = _c64(tri9), _c64(pts).reshape(-1, 3)
+    out = np.zeros(len(pts), dtype=np.uint8)
+    if len(pts):
+        lib().orc_solid(_p(tri9), len(tri9), _p(pts), len(pts), int(dir), _p(out))
+    return out
+
+
+def links(tri9: np.ndarray, pts: np.ndarray, dirs: np.ndarray, h: int):
+    """Nearest crossing of each segment P -> P + h c: (q float64, argmin tri, number of crossings)."""
+    tri9, pts = _c64(tri9), _c64(pts).reshape(-1, 3)
+    d = np.ascontiguousarray(dirs, dtype=np.int32)
+    q = np.zeros(len(pts), dtype=np.float64)
+    arg = np.zeros(len(pts), dtype=np.int64)
+    nc = np.zeros(len(pts), dtype=np.int32)
+    if len(pts):
+        lib().orc_links(_p(tri9), len(tri9), _p(pts), _p(d), len(pts), int(h), _p(q), _p(arg), _p(nc))
+    return q, arg, nc
+
+
+def boxes_any(tri9: np.ndarray, lo: np.ndarray, hi: np.ndarray) -> np.ndarray:
+    tri9 = _c64(tri9)
+    lo, hi = _c64(lo).reshape(-1, 3), _c64(hi).reshape(-1, 3)
+    out = np.zeros(len(lo), dtype=np.uint8)
+    if len(lo):
+        lib().orc_boxes_any(_p(tri9), len(tri9), _p(lo), _p(hi), len(lo), _p(out))
+    return out
+
+
+def sat(tri9_one, lo, hi) -> bool:
+    return bool(lib().orc_sat(_p(_c64(tri9_one)), _p(_c64(lo)), _p(_c64(hi))))
+
+
+# --------------------------------------------------------------------------- #
+# forest, refinement, masks, links
+# --------------------------------------------------------------------------- #
+def rho_schedule(levels: int, band: int):
+    """Near-wall distance rho_L (in level-L cells) for L = 0 .. levels-1.
+
+    rho at the level below the finest equals ``band``; coarser levels use
+    rho_L = max(band, rho_{L+1}/2 + 5/2), which makes every neighbour of a
+    refined block exist (2:1 balance, Sec. 3.2) and every unrefined block's
+    closed box free of the surface.
+    """
+    rho = [Fraction(0)] * levels
+    for L in range(levels - 1, -1, -1):
+        rho[L] = Fraction(band) if L == levels - 1 else max(Fraction(band), rho[L + 1] / 2 + Fraction(5, 2))
+    return rho
+
+
+def dilation(R: int, L: int, levels: int, band: int) -> int:
+    """(rho_L - 1/2) h_L in frame units: the box dilation of the refine test at level L."""
+    d = (rho_schedule(levels, band)[L] - Fraction(1, 2)) * h_units(R, L)
+    if d.denominator != 1:
+        raise ValueError("dilation is not an integer in this frame")
+    return int(d)
+
+
+def sort_blocks(b: np.ndarray) -> np.ndarray:
+    b = np.asarray(b, dtype=np.int64).reshape(-1, 3)
+    order = np.lexsort((b[:, 0], b[:, 1], b[:, 2]))
+    return b[order]
+
+
+def root_blocks(R: int) -> np.ndarray:
+    g = np.stack(np.meshgrid(np.arange(R), np.arange(R), np.arange(R), indexing="ij"), -1).reshape(-1, 3)
+    return sort_blocks(g)
+
+
+def refine_flags(tri9, R, L, levels, band, blocks) -> np.ndarray:
+    """flag(b) = some triangle overlaps the closed block box dilated by (rho_L - 1/2) h_L."""
+    W = 4 * h_units(R, L)
+    D = dilation(R, L, levels, band)
+    lo = blocks * W - D
+    hi = (blocks + 1) * W + D
+    return boxes_any(tri9, lo, hi)
+
+
+def children(blocks: np.ndarray, flags: np.ndarray) -> np.ndarray:
+    p = blocks[flags.astype(bool)]
+    off = np.array([[dx, dy, dz] for dz in (0, 1) for dy in (0, 1) for dx in (0, 1)], dtype=np.int64)
+    ch = (2 * p[:, None, :] + off[None, :, :]).reshape(-1, 3)
+    return sort_blocks(ch)
+
+
+def build_forest(tri9, R: int, levels: int, band: int):
+    """Top-down forest: blocks per level (sorted by z, y, x) and flags for levels < finest."""
+    blocks = [root_blocks(R)]
+    flags = []
+    for L in range(levels):
+        f = refine_flags(tri9, R, L, levels, band, blocks[L])
+        flags.append(f)
+        blocks.append(children(blocks[L], f))
+    return blocks, flags
+
+
+def cell_centres(R: int, L: int, blocks: np.ndarray) -> np.ndarray:
+    """(n*64, 3) integer centres; cell t = x + 4 y + 16 z inside each block."""
+    _, k = frame(R)
+    half = 1 << (17 - k - L)
+    t = np.arange(64)
+    loc = np.stack([t % 4, (t // 4) % 4, t // 16], axis=1)
+    g = 4 * blocks[:, None, :] + loc[None, :, :]
+    return ((2 * g + 1) * half).reshape(-1, 3)
+
+
+def pack_masks(bits: np.ndarray) -> np.ndarray:
+    b = bits.reshape(-1, 64).astype(np.uint64)
+    return (b << np.arange(64, dtype=np.uint64)[None, :]).sum(axis=1, dtype=np.uint64)
+
+
+def unpack_masks(words: np.ndarray) -> np.ndarray:
+    w = np.asarray(words, dtype=np.uint64)
+    return ((w[:, None] >> np.arange(64, dtype=np.uint64)[None, :]) & np.uint64(1)).astype(np.uint8)
+
+
+def masks(tri9, R, L, blocks, dir: int = 1) -> np.ndarray:
+    """Solid mask word per block: bit t set iff the centre of cell t is inside."""
+    return pack_masks(solid(tri9, cell_centres(R, L, blocks), dir))
+
+
+def cut_links(tri9, R, levels, blocks_f, mask_f, lattice: int):
+    """Flat cut-link table at the finest level, sorted by (cell, dir).
+
+    For every fluid cell P and every lattice direction i != 0 whose neighbour
+    P + h c_i is solid (decided by the same point predicate; a neighbour outside
+    the domain is fluid): q = min over crossed triangles of the crossing
+    parameter t in [0, 1].  Returns dict(cell, dir, q, tri, ncross).
+    """
+    h = h_units(R, levels)
+    dom = domain_units(R)
+    C = directions()
+    P = cell_centres(R, levels, blocks_f)
+    fluid = unpack_masks(mask_f).reshape(-1) == 0
+    cells = np.nonzero(fluid)[0]
+    dirs = np.arange(1, lattice)
+    cand_cell = np.repeat(cells, len(dirs))
+    cand_dir = np.tile(dirs, len(cells))
+    Q = P[cand_cell] + h * C[cand_dir]
+    inside = np.all((Q > 0) & (Q < dom), axis=1)
+    s = np.zeros(len(Q), dtype=np.uint8)
+    if np.any(inside):
+        uq, inv = np.unique(Q[inside], axis=0, return_inverse=True)
+        s[inside] = solid(tri9, uq)[inv.reshape(-1)]
+    keep = s.astype(bool)
+    cell = cand_cell[keep]
+    d = cand_dir[keep]
+    q, arg, ncross = links(tri9, P[cell], d, h)
+    return dict(cell=cell.astype(np.int64), dir=d.astype(np.int64), q=q, tri=arg, ncross=ncross)
+
+
+def embed(verts, tris, R: int, levels: int, band: int = 2, lattice: int = 19):
+    """Whole path: forest, masks per level, refine flags, cut links."""
+    X = int_coords(verts, R)
+    tri9 = tri_coords(X, tris)
+    blocks, flags = build_forest(tri9, R, levels, band)
+    m = [masks(tri9, R, L, blocks[L]) for L in range(levels + 1)]
+    lk = cut_links(tri9, R, levels, blocks[levels], m[levels], lattice)
+    return dict(X=X, tri9=tri9, blocks=blocks, flags=flags, masks=m, links=lk)
+
+
+# --------------------------------------------------------------------------- #
+# Bouzidi interpolated bounce-back, momentum exchange, and their derivatives
+# --------------------------------------------------------------------------- #
+def _block_index(blocks: np.ndarray):
+    return {tuple(b): i for i, b in enumerate(blocks.tolist())}
+
+
+def partner_cells(R, levels, blocks_f, mask_f, cell, dir):
+    """Cell id of x_f - c_i at the finest level, or -1 if that cell is absent or solid."""
+    C = directions()
+    idx = _block_index(blocks_f)
+    b = cell // 64
+    t = cell % 64
+    loc = np.stack([t % 4, (t // 4) % 4, t // 16], axis=1)
+    g = 4 * blocks_f[b] + loc - C[dir]
+    bb = np.floor_divide(g, 4)
+    ll = g - 4 * bb
+    bits = unpack_masks(mask_f)
+    out = np.full(len(cell), -1, dtype=np.int64)
+    for k in range(len(cell)):
+        j = idx.get(tuple(bb[k].tolist()))
+        if j is None:
+            continue
+        tt = int(ll[k, 0] + 4 * ll[k, 1] + 16 * ll[k, 2])
+        if bits[j, tt] == 0:
+            out[k] = j * 64 + tt
+    return out
+
+
+def bouzidi_incoming(q, f_i, f_i_partner, f_opp, has_partner):
+    """Interpolated population entering x_f along -c_i (linear Bouzidi rule).
+
+    q < 1/2 with a fluid partner x_f - c_i:  2q f_i(x_f) + (1-2q) f_i(x_f - c_i)
+    q >= 1/2:                                f_i(x_f)/(2q) + (2q-1)/(2q) f_-i(x_f)
+    q < 1/2 without a fluid partner:         f_i(x_f)   (simple bounce-back)
+    """
+    q = np.asarray(q, dtype=np.float64)
+    lo = q < 0.5
+    qs = np.where(lo, 1.0, q)
+    hi_val = f_i / (2 * qs) + (2 * qs - 1) / (2 * qs) * f_opp
+    lo_val = np.where(has_partner, 2 * q * f_i + (1 - 2 * q) * f_i_partner, f_i)
+    return np.where(lo, lo_val, hi_val)
+
+
+def _link_pops(links_, pop, partner):
+    C = directions()
+    d = links_["dir"]
+    opp = np.array([opposite(int(i)) for i in d], dtype=np.int64)
+    cell = links_["cell"]
+    f_i = pop[d, cell].astype(np.float64)
+    f_opp = pop[opp, cell].astype(np.float64)
+    has = partner >= 0
+    f_p = np.where(has, pop[d, np.where(has, partner, 0)].astype(np.float64), 0.0)
+    return C[d].astype(np.float64), f_i, f_opp, f_p, has
+
+
+def mex_force(links_, pop, partner) -> np.ndarray:
+    """Momentum-exchange force on the body: sum over links of c_i (f_i(x_f) + f~_-i(x_f))."""
+    c, f_i, f_opp, f_p, has = _link_pops(links_, pop, partner)
+    inc = bouzidi_incoming(links_["q"], f_i, f_p, f_opp, has)
+    return (c * (f_i + inc)[:, None]).sum(axis=0)
+
+
+def mex_force_dq(links_, pop, partner) -> np.ndarray:
+    """dF/dq_k (n_links, 3): c_i 2(f_i - f_i(partner)) for q < 1/2 with a partner,
+    0 for the bounce-back fallback, c_i (f_-i - f_i) / (2 q^2) for q >= 1/2."""
+    c, f_i, f_opp, f_p, has = _link_pops(links_, pop, partner)
+    q = links_["q"]
+    lo = q < 0.5
+    qs = np.where(lo, 1.0, q)
+    g = np.where(lo, np.where(has, 2 * (f_i - f_p), 0.0), (f_opp - f_i) / (2 * qs * qs))
+    return c * g[:, None]
+
+
+def dq_dverts(links_, X, tris, R, levels):
+    """Per link: the three vertex ids of the nearest crossed triangle and dq/dV (n, 3, 3).
+
+    Moving vertex j of the crossed triangle by dV moves the hit point's plane
+    by lambda_j (n . dV)/|n|, with lambda the barycentric coordinates of the
+    hit; along the link (length h, direction c) this changes q by
+    lambda_j n . dV / (h n . c).  World units: coordinates are X / (2^20 r_o).
+    """
+    scale = float(domain_units(R))
+    h = h_units(R, levels) / scale
+    C = directions().astype(np.float64)
+    Xw = X.astype(np.float64) / scale
+    t = np.asarray(tris, dtype=np.int64)[links_["tri"]]
+    A, B, Cc = Xw[t[:, 0]], Xw[t[:, 1]], Xw[t[:, 2]]
+    cell = links_["cell"]
+    c = C[links_["dir"]]
+    n = np.cross(B - A, Cc - A)
+    nn = np.einsum("ij,ij->i", n, n)
+    return t, n, nn, A, B, Cc, c, h
+
+
+def grad_verts_from_gq(links_, gq, X, tris, R, levels, blocks_f, n_verts):
+    """sum_k gq_k dq_k/dV  (float64, (V, 3))."""
+    t, n, nn, A, B, Cc, c, h = dq_dverts(links_, X, tris, R, levels)
+    scale = float(domain_units(R))
+    P = cell_centres(R, levels, blocks_f)[links_["cell"]].astype(np.float64) / scale
+    Xh = P + (links_["q"] * h)[:, None] * c
+    lamA = np.einsum("ij,ij->i", n, np.cross(B - Xh, Cc - Xh)) / nn
+    lamB = np.einsum("ij,ij->i", n, np.cross(Cc - Xh, A - Xh)) / nn
+    lamC = np.einsum("ij,ij->i", n, np.cross(A - Xh, B - Xh)) / nn
+    base = n / (h * np.einsum("ij,ij->i", n, c))[:, None]
+    g = np.zeros((n_verts, 3), dtype=np.float64)
+    for j, lam in enumerate((lamA, lamB, lamC)):
+        np.add.at(g, t[:, j], (gq * lam)[:, None] * base)
+    return g
