@@ -1,0 +1,426 @@
+#!/usr/bin/env python3
+"""Throughput of the embedding path on one GB300 (or N replicas, one per GPU).
+
+One step = the whole path on the ~7.2M-triangle radial mesh (root 32^3 blocks,
+levels 0..4, band 2, D3Q27): triangle records, then per level binning, solid
+voxelization, refine flags and the forest refinement, then the cut-link table.
+Metric: cells (64 per block, all levels) plus cut links embedded per second.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+`--impl reference` times the CPU oracle (exact brute force over every triangle)
+on bounded samples of the same workload on this host's cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from synth import workload  # noqa: E402
+
+METRIC = "cells+cut links embedded/s at 7.2M tris; batched & fwd+bwd vs plain, same GPU"
+UNIT = "units/s"
+WORKLOAD = "star_7m"
+# Nominal 32-bit ALU instruction slots charged per (link, triangle) exact segment test
+# (three Pluecker signs in 64-bit arithmetic plus the normal dot product).
+KAPPA_SEG = 48
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-extras", action="store_true", help="skip the e2e leg and the CPU baseline")
+    return ap.parse_args()
+
+
+def workload_config(w, lattice):
+    v, t = w.build_mesh()
+    return v, t, dict(workload=f"{w.name}: radial star mesh, {len(t)} triangles, root {w.R}^3 blocks of 4^3 "
+                                f"cells, levels 0..{w.levels}, band {w.band}, D3Q{lattice}",
+                      triangles=int(len(t)), root=w.R, levels=w.levels, band=w.band, lattice=lattice,
+                      l2="flushed between steps (256 MB write)")
+
+
+# --------------------------------------------------------------------------- #
+# CPU oracle sample (reference arm and cpu_baseline)
+# --------------------------------------------------------------------------- #
+def oracle_sample(v, t, w, lattice, n_blocks, seed):
+    """Brute-force work for n_blocks finest-level blocks that hold the surface:
+    the solid state of their 64 cells and of every lattice neighbour of their
+    fluid cells, then q for each cut link.  Returns (units, seconds)."""
+    from oracle import oracle as O
+    O.lib()
+    X = O.int_coords(v, w.R)
+    tri9 = O.tri_coords(X, t)
+    rng = np.random.default_rng(seed)
+    h = O.h_units(w.R, w.levels)
+    W = 4 * h
+    C = O.directions()
+    picks = rng.choice(len(t), n_blocks, replace=False)
+    t0 = time.perf_counter()
+    units = 0
+    for p in picks:
+        cen = tri9[p].reshape(3, 3).mean(axis=0)
+        blk = (cen // W).astype(np.int64)[None, :]
+        P = O.cell_centres(w.R, w.levels, blk)
+        s = O.solid(tri9, P)
+        fluid = np.nonzero(s == 0)[0]
+        cand = (P[fluid][:, None, :] + h * C[None, 1:lattice, :]).reshape(-1, 3)
+        cdir = np.tile(np.arange(1, lattice), len(fluid))
+        ccell = np.repeat(fluid, lattice - 1)
+        uq, inv = np.unique(cand, axis=0, return_inverse=True)
+        sn = O.solid(tri9, uq)[inv.reshape(-1)]
+        sel = sn == 1
+        O.links(tri9, P[ccell[sel]], cdir[sel], h)
+        units += 64 + int(sel.sum())
+    return units, time.perf_counter() - t0
+
+
+def omp_threads():
+    n = os.environ.get("OMP_NUM_THREADS")
+    return int(n) if n else os.cpu_count()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w = workload(args.workload)
+    lattice = max(w.lattices)
+    v, t, cfg = workload_config(w, lattice)
+    per_step = 1
+    for i in range(args.warmup):
+        oracle_sample(v, t, w, lattice, per_step, seed=1000 + i)
+    units = 0
+    secs = 0.0
+    for i in range(args.steps):
+        u, s = oracle_sample(v, t, w, lattice, per_step, seed=2000 + i)
+        units += u
+        secs += s
+    val = units / secs
+    sample = (f"{per_step} surface block(s) of the finest level per step: 64 cell states, the states of all "
+              f"lattice neighbours of their fluid cells, and q of every cut link, each by brute force over all "
+              f"{len(t)} triangles")
+    line = dict(impl="reference", metric=METRIC, value=val, unit=UNIT, n_gpus=args.gpus, steps=args.steps,
+                warmup=args.warmup, ms_per_step=1e3 * secs / args.steps, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="int64", data="synthetic", config=cfg,
+                cpu_baseline=dict(value=val, unit=UNIT, cores=omp_threads(), kind="oracle", sample=sample),
+                e2e=dict(value=val, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------- #
+# GPU arm
+# --------------------------------------------------------------------------- #
+class ClockSampler:
+    """nvidia-smi samples during the timed region (median SM clock, throttle reasons)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in out.strip().splitlines():
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return dict(sm_mhz=statistics.median(sm), sm_max_mhz=mx, reasons=sorted(reasons), samples=len(sm))
+
+
+def source_hash(*names):
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_2512_01251_gb300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    with open(os.path.join(ROOT, "paper_2512_01251_gb300", "csrc", "emb_internal.cuh"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel, src_files):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the source is unchanged."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(p))[kernel]
+    except (OSError, KeyError, ValueError):
+        return None
+    if d.get("source_hash") != source_hash(*src_files):
+        return None
+    return d
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def run_ours(args):
+    import torch
+
+    import paper_2512_01251_gb300 as P
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    w = workload(args.workload)
+    lattice = max(w.lattices)
+    v, t, cfg = workload_config(w, lattice)
+    cfg["parallelism"] = f"replicas x{world}" if world > 1 else "single GPU"
+    verts = torch.from_numpy(v).cuda()
+    tris = torch.from_numpy(t).cuda()
+    stream = torch.cuda.current_stream()
+    # one-time validation of the input (watertight, snapped)
+    P.emb_mesh_create(verts, tris, w.R, check_watertight=True).close()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    names = ["mesh", "bin", "voxelize", "refine_flags", "forest_refine", "cutlinks"]
+
+    def step(timed=None):
+        ev = []
+
+        def mark(name):
+            if timed is not None:
+                e = torch.cuda.Event(enable_timing=True)
+                e.record(stream)
+                ev.append((name, e))
+
+        mark("start")
+        mesh = P.emb_mesh_create(verts, tris, w.R, check_watertight=False)
+        mark("mesh")
+        forest = P.emb_forest_root(w.R, w.levels)
+        masks, links, stats = [], None, []
+        for L in range(w.levels + 1):
+            bins = P.emb_bin(mesh, forest, L, lattice)
+            mark(f"bin{L}")
+            masks.append(P.emb_voxelize(forest, bins, L))
+            mark(f"voxelize{L}")
+            if L < w.levels:
+                fl = P.emb_refine_flags(forest, bins, L, w.band)
+                mark(f"refine_flags{L}")
+                P.emb_forest_refine(forest, L, fl)
+                mark(f"forest_refine{L}")
+            else:
+                n = P.emb_cutlinks_count(forest, lattice)
+                mark("cutlinks_count")
+                links = P.emb_cutlinks(forest, bins, lattice, capacity=n)
+                mark("cutlinks_emit")
+                if timed is not None and timed.get("want_bins"):
+                    timed["bins"] = P.emb_bins_copy(bins, forest)
+            stats.append(P.emb_bins_stats(bins))
+            bins.close()
+        if timed is not None:
+            timed["events"] = ev
+        return mesh, forest, masks, links, stats
+
+    def units_of(forest, links):
+        return sum(64 * P.emb_forest_num_blocks(forest, L) for L in range(w.levels + 1)) + links["q"].numel()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if P.emb_status_get() != P.EMB_OK:
+        raise RuntimeError("device status error during warm-up")
+
+    # ---- timed region: K steps, L2 flushed (untimed) before each
+    clocks = ClockSampler(local)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    l0 = P.emb_launch_count()
+    step_ms, per_call = [], {}
+    units = 0
+    last = None
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        info = dict(want_bins=(i == args.steps - 1))
+        mesh, forest, masks, links, stats = step(info)
+        torch.cuda.synchronize()
+        ev = info["events"]
+        step_ms.append(ev[0][1].elapsed_time(ev[-1][1]))
+        for (a, ea), (b, eb) in zip(ev[:-1], ev[1:]):
+            per_call.setdefault(b, []).append(ea.elapsed_time(eb))
+        units += units_of(forest, links)
+        last = (mesh, forest, masks, links, stats, info.get("bins"))
+    launches = P.emb_launch_count() - l0
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if dist is not None:
+        dist.barrier()
+    st = P.emb_status_get()
+    if st != P.EMB_OK:
+        raise RuntimeError(f"device status {st} in the timed region")
+    total_ms = sum(step_ms)
+    if dist is not None:
+        tt = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+        uu = torch.tensor([units], dtype=torch.float64, device="cuda")
+        dist.all_reduce(uu)
+        units = float(uu.item())
+    value = units / (total_ms / 1e3)
+
+    # ---- breakdown, roofline of the dominant call
+    mesh, forest, masks, links, stats, bins = last
+    med = {k: statistics.median(v_) for k, v_ in per_call.items()}
+    groups = {}
+    for k, ms in med.items():
+        g = k.rstrip("0123456789")
+        groups[g] = groups.get(g, 0.0) + ms
+    pk, pk_src = peaks()
+    n_links = int(links["q"].numel())
+    lf = w.levels
+    off = bins["off"].cpu().numpy().astype(np.int64)
+    blk_links = np.bincount(links["cell"].cpu().numpy().astype(np.int64) // 64, minlength=len(off) - 1)
+    tests = int((blk_links * np.diff(off)).sum())
+    emit_ms = med["cutlinks_emit"]
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    clk_mhz = (clk or {}).get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
+    alu_peak = sm_count * 128 * clk_mhz * 1e6 / 1e12  # Tops/s of 32-bit ALU slots
+    achieved = tests * KAPPA_SEG / (emit_ms / 1e3) / 1e12
+    traffic = measured_traffic("k_link_emit", ["emb_cutlinks.cu"])
+    roofline = dict(kernel="k_link_emit (emb_cutlinks)", bound="alu", achieved=achieved, peak=alu_peak,
+                    unit="Tops/s", frac=achieved / alu_peak,
+                    traffic=(traffic or {}).get("bytes_per_launch"),
+                    basis=(f"{tests} (link, bin triangle) exact segment tests x {KAPPA_SEG} 32-bit ALU slots / "
+                           f"median launch time; peak = {sm_count} SMs x 128 lanes x {clk_mhz:.0f} MHz "
+                           f"(SM clock sampled under load; {pk_src} peaks file for HBM)"))
+    hbm = pk.get("hbm_gbs", 6800.0)
+    T = len(t)
+    level_blocks = [P.emb_forest_num_blocks(forest, L) for L in range(lf + 1)]
+    # HBM view of the triangle-parallel passes: each reads every 48-byte record once
+    hbm_view = {}
+    for L in range(lf):
+        ms = med.get(f"refine_flags{L}")
+        if ms:
+            by = 48 * T + level_blocks[L]
+            hbm_view[f"refine_flags{L}"] = dict(GBps=by / (ms / 1e3) / 1e9, frac=by / (ms / 1e3) / 1e9 / hbm)
+    for L in range(lf + 1):
+        ms = med.get(f"bin{L}")
+        if ms:
+            by = 48 * T + 8 * T + 4 * stats[L][0]
+            hbm_view[f"bin{L}"] = dict(GBps=by / (ms / 1e3) / 1e9, frac=by / (ms / 1e3) / 1e9 / hbm)
+
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+                ms_per_step=total_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="int64", data="synthetic", config=cfg, roofline=roofline, gpu_launches=launches,
+                clocks=clk,
+                units_per_step=dict(cells=64 * sum(level_blocks), links=n_links, blocks_per_level=level_blocks),
+                breakdown_ms={k: round(v_, 4) for k, v_ in groups.items()},
+                breakdown_hbm=hbm_view)
+
+    if rank == 0 and not args.no_extras:
+        line["e2e"] = e2e_leg(P, v, t, w, lattice, args, stream)
+        units_s, secs = oracle_sample(v, t, w, lattice, 6, seed=7)
+        line["cpu_baseline"] = dict(value=units_s / secs, unit=UNIT, cores=omp_threads(), kind="oracle",
+                                    sample=("6 surface blocks of the finest level: 64 cell states each, the states "
+                                            "of all lattice neighbours of their fluid cells and q of every cut link, "
+                                            f"each by brute force over all {len(t)} triangles; {units_s} units in "
+                                            f"{secs:.1f} s"))
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def e2e_leg(P, v, t, w, lattice, args, stream):
+    """Same metric through the public API with host inputs and a host copy of the result:
+    pinned host -> device copies of the mesh, the embedding, and device -> pinned host copies of
+    the cut-link table and the finest solid mask, all inside the timed region."""
+    import torch
+
+    hv = torch.from_numpy(v).pin_memory()
+    ht = torch.from_numpy(t).pin_memory()
+    h2d = hv.numel() * 4 + ht.numel() * 4
+    d2h = 0
+    times, units = [], 0
+    for i in range(args.warmup + max(3, args.steps // 2)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dv = hv.to("cuda", non_blocking=True)
+        dt = ht.to("cuda", non_blocking=True)
+        E = P.embed(dv, dt, w.R, w.levels, w.band, lattice, check_watertight=False, check_status=False)
+        L = E.links
+        n = L["q"].numel()
+        out = [torch.empty(n, dtype=torch.int32, pin_memory=True), torch.empty(n, dtype=torch.uint8, pin_memory=True),
+               torch.empty(n, dtype=torch.float32, pin_memory=True),
+               torch.empty(E.masks[-1].numel(), dtype=torch.int64, pin_memory=True)]
+        for o, s in zip(out, [L["cell"], L["dir"], L["q"], E.masks[-1]]):
+            o.copy_(s, non_blocking=True)
+        torch.cuda.synchronize()
+        dt_s = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt_s)
+            units += E.units()
+            d2h = sum(o.numel() * o.element_size() for o in out)
+    return dict(value=units / sum(times), unit=UNIT, h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h,
+                ms_per_step=1e3 * statistics.mean(times))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

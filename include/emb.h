@@ -1,0 +1,218 @@
+/*
+ * emb.h -- C ABI of libemb: GB300 embedding of a closed triangle mesh into a
+ * block-structured forest of octrees (arXiv 2512.01251).
+ *
+ * The library implements the data-parallel path of the paper's geometry module:
+ * hierarchical spatial binning (Sec. 3.3), solid voxelization by ray casting
+ * (Sec. 3.4, "Partial Surface Voxelization" and "External Cell Flag
+ * Propagation"), near-wall refinement flags (Sec. 3.4, "Refinement Flagging"),
+ * and the flattened link-length table for interpolated bounce-back (Sec. 3.4,
+ * "Link-Length Computation"), plus the momentum-exchange force with Bouzidi
+ * interpolation and the adjoint of q with respect to the vertices.
+ *
+ * Conventions shared by every call
+ *   - Pointers named d_* are CUDA device pointers owned by the caller; the
+ *     library never frees them.  Handles (emb_mesh, emb_forest, emb_bins) own
+ *     library-allocated device memory, released by the matching *_destroy.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Calls enqueue work on it and return an immediate status for argument and
+ *     launch errors; errors detected inside kernels are recorded in a device
+ *     status word read (and cleared) by emb_status_get.  Calls that must size a
+ *     library allocation (mesh creation, forest refinement, binning, link
+ *     counting) synchronise the stream once to read a count back.
+ *   - Integer frame: with R = r_o 2^k root blocks per axis (r_o odd), vertex
+ *     coordinate v (a multiple of 2^-20 in (0,1)) maps to v 2^20 r_o.  Level L
+ *     cells have size 2^(18-k-L) and centres at odd multiples of 2^(17-k-L);
+ *     k + L <= 17 is required (EMB_ERR_RANGE otherwise).
+ *   - Blocks of 4x4x4 cells; cell t = x + 4y + 16z inside a block (the LINEAR
+ *     map of Alg. 3).  The blocks of a level are numbered in (z, y, x) order
+ *     of their block coordinates; the global cell id at the finest level is
+ *     block_id * 64 + t.
+ *   - Lattice directions (index: vector), opposite pairs adjacent:
+ *     0 rest; 1 +x, 2 -x, 3 +y, 4 -y, 5 +z, 6 -z;
+ *     7 (1,1,0), 8 (-1,-1,0), 9 (1,-1,0), 10 (-1,1,0), 11 (1,0,1), 12 (-1,0,-1),
+ *     13 (1,0,-1), 14 (-1,0,1), 15 (0,1,1), 16 (0,-1,-1), 17 (0,1,-1), 18 (0,-1,1);
+ *     19 (1,1,1), 20 (-1,-1,-1), 21 (1,1,-1), 22 (-1,-1,1), 23 (1,-1,1),
+ *     24 (-1,1,-1), 25 (-1,1,1), 26 (1,-1,-1).  D3Q19 uses 0..18, D3Q27 0..26.
+ *   - Every inside/outside, crossing and overlap decision is exact (integer
+ *     predicates with a fixed symbolic perturbation of the query points), so
+ *     masks, flags, forests and link sets are deterministic and bit-exact.
+ */
+#ifndef EMB_H
+#define EMB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t emb_status;
+#define EMB_OK 0
+#define EMB_ERR_BAD_INPUT (-1)      /* argument out of range, unsnapped vertex, bad triangle id */
+#define EMB_ERR_NOT_WATERTIGHT (-2) /* an edge is not shared by exactly two oppositely oriented faces */
+#define EMB_ERR_CAPACITY (-3)       /* caller buffer too small; the required size was written */
+#define EMB_ERR_CUDA (-4)           /* a CUDA runtime call failed */
+#define EMB_ERR_TIMEOUT (-5)        /* a bounded device wait gave up */
+#define EMB_ERR_RANGE (-6)          /* the level is too fine for the integer frame */
+#define EMB_ERR_STATE (-7)          /* call order violated, or an internal invariant failed */
+
+typedef struct emb_mesh_s *emb_mesh;
+typedef struct emb_forest_s *emb_forest;
+typedef struct emb_bins_s *emb_bins;
+
+/* Human-readable name of a status code (static string). */
+const char *emb_status_string(emb_status s);
+
+/* Synchronises `stream`, then returns in *out the first error recorded by a
+ * kernel since the last call (EMB_OK if none) and clears it. */
+emb_status emb_status_get(void *stream, emb_status *out);
+
+/* Writes the 27 lattice vectors (27 x 3 int32, host memory) in the order above. */
+emb_status emb_directions(int32_t *h_out);
+
+/* Diagnostics (no counterpart in the paper): number of kernels this library has
+ * launched in the process so far, counted on the host at each launch site. */
+emb_status emb_launch_count(int64_t *h_out);
+
+/* ---------------------------------------------------------------- mesh ---- */
+/* Geometry input (Sec. 3.1): a closed, oriented triangle mesh given as an index
+ * list.  d_verts: V x 3 float32, each coordinate a multiple of 2^-20 strictly
+ * inside (0,1); d_tris: T x 3 int32 vertex ids, counter-clockwise seen from
+ * outside.  R: root blocks per axis of the forests this mesh will be embedded
+ * in (fixes the integer frame).  check_watertight != 0 verifies on the GPU that
+ * every directed edge occurs once and its reverse once (Sec. 3.4 requires a
+ * watertight, non-self-intersecting surface).  Builds library-owned 48-byte
+ * records {X,Y,Z,vertex id} x 3 per triangle.  Synchronises the stream.
+ * Errors: EMB_ERR_BAD_INPUT, EMB_ERR_NOT_WATERTIGHT, EMB_ERR_RANGE, EMB_ERR_CUDA. */
+emb_status emb_mesh_create(const float *d_verts, const int32_t *d_tris, int64_t V, int64_t T, int32_t R,
+                           int32_t check_watertight, void *stream, emb_mesh *out);
+void emb_mesh_destroy(emb_mesh m);
+
+/* -------------------------------------------------------------- forest ---- */
+/* Root grid of R^3 blocks (Sec. 3.2) with room for levels 0..max_level.
+ * Errors: EMB_ERR_BAD_INPUT (R < 1, max_level < 0 or > 15), EMB_ERR_RANGE. */
+emb_status emb_forest_root(int32_t R, int32_t max_level, void *stream, emb_forest *out);
+void emb_forest_destroy(emb_forest f);
+
+/* Creates level+1 from the refinement flags of `level` (d_flags: one uint8 per
+ * level block, nonzero = refine): 8 children per flagged block, numbered in
+ * (z, y, x) order, plus their coordinate hash.  This is the forest harness
+ * (the paper delegates it to its AMR pipeline, Sec. 3.2 steps 1-8); it keeps no
+ * ghost/interface metadata.  Synchronises once to read the child count.
+ * Errors: EMB_ERR_STATE (level not the current finest, or beyond max_level). */
+emb_status emb_forest_refine(emb_forest f, int32_t level, const uint8_t *d_flags, void *stream);
+
+/* Number of blocks at `level` (host value; 0 if the level does not exist). */
+emb_status emb_forest_num_blocks(emb_forest f, int32_t level, int64_t *h_out);
+
+/* Copies the block coordinates (n x 3 int32: bx, by, bz) of `level` into d_out. */
+emb_status emb_forest_blocks(emb_forest f, int32_t level, int32_t *d_out, void *stream);
+
+/* Copies the neighbour table of `level` into d_out (n x 26 int32): entry
+ * [b*26 + i-1] is the id of the block at offset c_i from block b, or -1 if it
+ * does not exist at this level (Sec. 3.2: neighbour links over the full halo). */
+emb_status emb_forest_neighbors(emb_forest f, int32_t level, int32_t *d_out, void *stream);
+
+/* Copies the solid mask words of `level` (written by emb_voxelize) into d_out. */
+emb_status emb_forest_masks(emb_forest f, int32_t level, uint64_t *d_out, void *stream);
+
+/* ---------------------------------------------------------------- bins ---- */
+/* Spatial binning on `level` (Sec. 3.3, steps 1-9 and Alg. 1-2):
+ *  (1) filter: keeps the triangles crossed by at least one x-line through level
+ *      cell centres (the 1-D ray-indicator filter, exact), as a compact id list
+ *      in ascending order;
+ *  (2) at the finest level of the forest (level == max_level): per-block bins in
+ *      CSR form holding every non-degenerate triangle that overlaps the block box
+ *      dilated by half a cell (Alg. 2 dilates bins by the cell size; a link from
+ *      a cell centre, itself half a cell inside the block, reaches at most one
+ *      cell further, so half a cell suffices), built by count, exclusive scan and
+ *      fill; ids within a bin are unordered.
+ * `lattice` (19 or 27) is recorded for emb_cutlinks.  Synchronises once.
+ * Errors: EMB_ERR_BAD_INPUT, EMB_ERR_STATE (level missing, mesh/forest frame mismatch). */
+emb_status emb_bin(emb_mesh m, emb_forest f, int32_t level, int32_t lattice, void *stream, emb_bins *out);
+void emb_bins_destroy(emb_bins b);
+
+/* Host statistics: filtered triangles and (at the finest level) bin entries. */
+emb_status emb_bins_stats(emb_bins b, int64_t *h_filtered, int64_t *h_pairs);
+
+/* Copies the bins out (Sec. 3.3's bins_face_ids / _N arrays): d_filtered gets the
+ * filtered triangle ids (h_filtered entries), d_off the CSR offsets (blocks + 1
+ * entries) and d_ent the triangle ids of every bin (h_pairs entries, unordered
+ * within a bin).  Any pointer may be NULL; offsets exist only at the finest level. */
+emb_status emb_bins_copy(emb_bins b, uint32_t *d_filtered, uint32_t *d_off, uint32_t *d_ent, void *stream);
+
+/* ------------------------------------------------------------ voxelize ---- */
+/* Solid voxelization of `level` (Sec. 3.4): a cell is solid iff its centre is
+ * inside the surface.  Each filtered triangle casts the +x lines through the
+ * level's cell centres that cross it; the crossing's block records which of its
+ * four cells on that line lie before the hit and flips the line's block parity.
+ * A segmented suffix-XOR of the line parities along each (y, z) row of blocks
+ * then completes every line (the role of the external propagation of Alg. 4).
+ * Writes one uint64 per level block (bit t = cell t solid) into d_solid_mask
+ * (may be NULL) and keeps a copy in the forest.
+ * Errors: EMB_ERR_STATE (bins of another level, missing level);
+ * device status EMB_ERR_STATE if a crossing falls outside every block. */
+emb_status emb_voxelize(emb_forest f, emb_bins b, int32_t level, uint64_t *d_solid_mask, void *stream);
+
+/* -------------------------------------------------------------- refine ---- */
+/* Near-wall refinement flags of `level` < max_level (Sec. 3.4, "Refinement
+ * Flagging"; near-wall criterion d_spec): flag = some triangle overlaps the
+ * closed block box dilated by (rho_L - 1/2) cells, where rho = band at level
+ * max_level-1 and rho_L = max(band, rho_{L+1}/2 + 5/2) above it.  This keeps the
+ * 2:1 balance of Sec. 3.2 and leaves every unrefined block free of the surface.
+ * d_flags: one uint8 per level block (1 = refine), overwritten.
+ * Errors: EMB_ERR_BAD_INPUT (band < 1), EMB_ERR_STATE, EMB_ERR_RANGE. */
+emb_status emb_refine_flags(emb_forest f, emb_bins b, int32_t level, int32_t band, uint8_t *d_flags,
+                            void *stream);
+
+/* ------------------------------------------------------------ cut links ---- */
+/* Number of cut links at the finest level for `lattice` (19 or 27): pairs
+ * (fluid cell, direction i) whose neighbour along c_i is solid (Sec. 3.4,
+ * "Boundary Cell Identification").  Needs emb_voxelize of the finest level.
+ * Synchronises; the count is returned in *h_count. */
+emb_status emb_cutlinks_count(emb_forest f, int32_t lattice, int64_t *h_count, void *stream);
+
+/* The flat link-length table (Sec. 3.4, "Link-Length Computation"): for every
+ * cut link, d_cell = finest cell id, d_dir = direction, d_q = distance from the
+ * cell centre to the nearest crossed face along the link divided by the link
+ * length (in [0,1]), d_tri = that face's triangle id (lowest id on exact ties).
+ * Ordered by (cell, dir).  `b` must be the bins of the finest level.  If the
+ * count exceeds `capacity`, nothing is written, *d_count (device int64) still
+ * receives the required size and the device status becomes EMB_ERR_CAPACITY. */
+emb_status emb_cutlinks(emb_forest f, emb_bins b, int32_t lattice, int32_t *d_cell, uint8_t *d_dir,
+                        float *d_q, int32_t *d_tri, int64_t capacity, int64_t *d_count, void *stream);
+
+/* -------------------------------------------------- force and adjoints ---- */
+/* Momentum-exchange force on the body (Sec. 2.2 cites momentum exchange and
+ * Bouzidi interpolated bounce-back; linear rule): per link (x_f, i, q),
+ *   F += c_i (f_i(x_f) + g),  g = 2q f_i(x_f) + (1-2q) f_i(x_f - c_i)       (q < 1/2)
+ *                             g = f_i(x_f)/(2q) + (2q-1)/(2q) f_-i(x_f)     (q >= 1/2)
+ *                             g = f_i(x_f)  when q < 1/2 and x_f - c_i is not a
+ *                                           fluid cell of the finest level.
+ * d_pop: D3Q19/D3Q27 populations (post-collision), layout [Q][pop_stride]
+ * indexed by finest cell id (pop_stride >= 64 * blocks).  d_F: 3 floats.
+ * Deterministic fixed-order reduction (no float atomics). */
+emb_status emb_mex_force(emb_forest f, int32_t lattice, const int32_t *d_cell, const uint8_t *d_dir,
+                         const float *d_q, int64_t n, const float *d_pop, int64_t pop_stride, float *d_F,
+                         void *stream);
+
+/* d_gq[k] = d_gF . dF/dq_k for the force above (d_gF: 3 floats). */
+emb_status emb_mex_force_backward(emb_forest f, int32_t lattice, const int32_t *d_cell, const uint8_t *d_dir,
+                                  const float *d_q, int64_t n, const float *d_pop, int64_t pop_stride,
+                                  const float *d_gF, float *d_gq, void *stream);
+
+/* Adjoint of the link table with respect to the vertex positions (world
+ * units): d_gverts (V x 3 float32, overwritten) = sum_k d_gq[k] dq_k/dV with
+ * dq/dV_j = lambda_j n / (h n.c) for the three vertices of link k's triangle
+ * (lambda: barycentric coordinates of the hit point, n: face normal, h: cell
+ * size).  Summed per vertex in link order (segmented, no float atomics). */
+emb_status emb_cutlinks_backward(emb_mesh m, emb_forest f, const int32_t *d_cell, const uint8_t *d_dir,
+                                 const float *d_q, const int32_t *d_tri, int64_t n, const float *d_gq,
+                                 float *d_gverts, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EMB_H */

@@ -1,0 +1,250 @@
+// Spatial binning (Sec. 3.3).
+//
+// Step 1, the filter (the 1-D ray indicator of Alg. 1): a triangle takes part
+// in voxelizing level L only if some +x line through level-L cell centres
+// crosses it.  The test is exact and the survivors are compacted into an
+// ascending id list by flag / exclusive scan / scatter (no sort).
+//
+// Steps 2-9 at the finest level (Alg. 2): every triangle is paired with the
+// existing blocks whose box, dilated by half a cell, it overlaps (exact
+// separating-axis test).  A link P -> P + h c starts at a cell centre, at least
+// h/2 inside the block, and has L-infinity length h, so it stays inside the box
+// dilated by h/2.  Pairs are counted per block with integer atomics, offsets
+// come from an exclusive scan, and a second pass fills the CSR bins.
+#include <stdlib.h>
+
+#include "emb_internal.cuh"
+
+__global__ void k_xfilter(const int4 *__restrict__ rec, int64_t T, LevelGeom g, uint32_t *__restrict__ flag)
+{
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    int4 A = rec[3 * t], B = rec[3 * t + 1], C = rec[3 * t + 2];
+    long long nx = ((long long)B.y - A.y) * ((long long)C.z - A.z) - ((long long)B.z - A.z) * ((long long)C.y - A.y);
+    uint32_t hit = 0;
+    if (nx != 0) {
+        int sx = nx > 0 ? 1 : -1;
+        long long j0, j1, k0, k1;
+        line_range(min(A.y, min(B.y, C.y)), max(A.y, max(B.y, C.y)), g.h, g.half, g.ncell, j0, j1);
+        line_range(min(A.z, min(B.z, C.z)), max(A.z, max(B.z, C.z)), g.h, g.half, g.ncell, k0, k1);
+        for (long long k = k0; k <= k1 && !hit; ++k) {
+            int pz = (int)((2 * k + 1) * g.half);
+            for (long long j = j0; j <= j1; ++j) {
+                int py = (int)((2 * j + 1) * g.half);
+                if (emb_orient_yz(A.y, A.z, B.y, B.z, py, pz) == sx && emb_orient_yz(B.y, B.z, C.y, C.z, py, pz) == sx &&
+                    emb_orient_yz(C.y, C.z, A.y, A.z, py, pz) == sx) {
+                    hit = 1;
+                    break;
+                }
+            }
+        }
+    }
+    flag[t] = hit;
+}
+
+__global__ void k_compact(const uint32_t *__restrict__ flag, const uint32_t *__restrict__ pos, int64_t n,
+                          uint32_t *__restrict__ out)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && flag[i]) out[pos[i]] = (uint32_t)i;
+}
+
+// The (triangle, block) pairs of 32 consecutive triangles, visited warp-cooperatively
+// over the union of their candidate blocks (see emb_internal.cuh).
+// MODE 0: count pairs per block; MODE 1: fill the CSR bins.  Degenerate
+// triangles (zero normal) are never crossed by a link and are left out.
+template <int MODE>
+__global__ void __launch_bounds__(EMB_WU_WARPS * 32) k_bin_pairs(const int4 *__restrict__ rec, int64_t T, LevelGeom g,
+                                                                 long long dil, EmbLookup lk, uint32_t *__restrict__ cnt,
+                                                                 const uint32_t *__restrict__ off,
+                                                                 uint32_t *__restrict__ ent)
+{
+    __shared__ WuTri tiles[EMB_WU_WARPS];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WuTri &S = tiles[w];
+    const int64_t t0 = ((int64_t)blockIdx.x * EMB_WU_WARPS + w) * 32;
+    const int64_t t = t0 + lane;
+    bool valid = t < T;
+    long long b0[3] = {1ll << 40, 1ll << 40, 1ll << 40}, b1[3] = {-1, -1, -1};
+    int4 A = make_int4(0, 0, 0, 0), B = A, C = A;
+    if (valid) {
+        A = rec[3 * t];
+        B = rec[3 * t + 1];
+        C = rec[3 * t + 2];
+        long long ux = (long long)B.x - A.x, uy = (long long)B.y - A.y, uz = (long long)B.z - A.z;
+        long long vx = (long long)C.x - A.x, vy = (long long)C.y - A.y, vz = (long long)C.z - A.z;
+        if (uy * vz - uz * vy == 0 && uz * vx - ux * vz == 0 && ux * vy - uy * vx == 0) valid = false;
+    }
+    if (valid) {
+        emb_block_range(min(A.x, min(B.x, C.x)), max(A.x, max(B.x, C.x)), g.W, dil, g.nb, b0[0], b1[0]);
+        emb_block_range(min(A.y, min(B.y, C.y)), max(A.y, max(B.y, C.y)), g.W, dil, g.nb, b0[1], b1[1]);
+        emb_block_range(min(A.z, min(B.z, C.z)), max(A.z, max(B.z, C.z)), g.W, dil, g.nb, b0[2], b1[2]);
+    }
+    S.A[lane] = A;
+    S.B[lane] = B;
+    S.C[lane] = C;
+    S.lo[0][lane] = valid ? min(A.x, min(B.x, C.x)) : 0x7fffffff;
+    S.hi[0][lane] = valid ? max(A.x, max(B.x, C.x)) : -0x7fffffff;
+    S.lo[1][lane] = min(A.y, min(B.y, C.y));
+    S.hi[1][lane] = max(A.y, max(B.y, C.y));
+    S.lo[2][lane] = min(A.z, min(B.z, C.z));
+    S.hi[2][lane] = max(A.z, max(B.z, C.z));
+    __syncwarp();
+    int u0[3], u1[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        u0[d] = __reduce_min_sync(0xffffffffu, (int)min(b0[d], (long long)0x7fffffff));
+        u1[d] = __reduce_max_sync(0xffffffffu, (int)b1[d]);
+    }
+    const long long nx = u1[0] - u0[0] + 1, ny = u1[1] - u0[1] + 1, nz = u1[2] - u0[2] + 1;
+    if (nx <= 0 || ny <= 0 || nz <= 0) return;
+    const long long total = nx * ny * nz;
+    // per-triangle candidates summed over the warp: the union pays off only when it is much smaller
+    const long long own = valid ? (b1[0] >= b0[0] && b1[1] >= b0[1] && b1[2] >= b0[2]
+                                       ? (b1[0] - b0[0] + 1) * (b1[1] - b0[1] + 1) * (b1[2] - b0[2] + 1)
+                                       : 0)
+                                : 0;
+    const unsigned own_sum = __reduce_add_sync(0xffffffffu, (unsigned)min(own, 1ll << 20));
+    if (total <= EMB_WU_MAX && 4 * total <= (long long)own_sum) {
+        for (long long c = lane; c < total; c += 32) {
+            const long long bx = u0[0] + c % nx, by = u0[1] + (c / nx) % ny, bz = u0[2] + c / (nx * ny);
+            const int32_t id = emb_lookup(lk, bx, by, bz);
+            if (id < 0) continue;
+            const long long lx = bx * g.W - dil, ly = by * g.W - dil, lz = bz * g.W - dil;
+            const long long hx = lx + g.W + 2 * dil, hy = ly + g.W + 2 * dil, hz = lz + g.W + 2 * dil;
+            uint32_t hits = 0;
+            for (int j = 0; j < 32; ++j)
+                if (wu_overlap(S, j, lx, ly, lz, hx, hy, hz)) hits |= 1u << j;
+            if (!hits) continue;
+            if (MODE == 0) {
+                atomicAdd(cnt + id, (uint32_t)__popc(hits));
+            } else {
+                uint32_t p = off[id] + atomicAdd(cnt + id, (uint32_t)__popc(hits));
+                while (hits) {
+                    const int j = __ffs(hits) - 1;
+                    hits &= hits - 1;
+                    ent[p++] = (uint32_t)(t0 + j);
+                }
+            }
+        }
+        return;
+    }
+    // large or loose union: each lane enumerates the blocks of its own triangle
+    if (!valid) return;
+    for (long long bz = b0[2]; bz <= b1[2]; ++bz)
+        for (long long by = b0[1]; by <= b1[1]; ++by)
+            for (long long bx = b0[0]; bx <= b1[0]; ++bx) {
+                int32_t id = emb_lookup(lk, bx, by, bz);
+                if (id < 0) continue;
+                long long lx = bx * g.W - dil, ly = by * g.W - dil, lz = bz * g.W - dil;
+                long long hx = lx + g.W + 2 * dil, hy = ly + g.W + 2 * dil, hz = lz + g.W + 2 * dil;
+                bool ov = emb_point_in_box(A, lx, ly, lz, hx, hy, hz) || emb_point_in_box(B, lx, ly, lz, hx, hy, hz) ||
+                          emb_point_in_box(C, lx, ly, lz, hx, hy, hz) || emb_tri_box(A, B, C, lx, ly, lz, hx, hy, hz);
+                if (!ov) continue;
+                if (MODE == 0) {
+                    atomicAdd(cnt + id, 1u);
+                } else {
+                    uint32_t p = atomicAdd(cnt + id, 1u);
+                    ent[off[id] + p] = (uint32_t)t;
+                }
+            }
+}
+
+extern "C" emb_status emb_bin(emb_mesh m, emb_forest f, int32_t level, int32_t lattice, void *stream, emb_bins *out)
+{
+    if (!m || !f || !out) return EMB_ERR_BAD_INPUT;
+    if (lattice != 19 && lattice != 27) return EMB_ERR_BAD_INPUT;
+    if (level < 0 || level > f->top) return EMB_ERR_STATE;
+    if (m->R != f->R) return EMB_ERR_STATE;
+    *out = nullptr;
+    cudaStream_t s = emb_stream(stream);
+    emb_bins b = new emb_bins_s();
+    b->m = m;
+    b->f = f;
+    b->level = level;
+    b->lattice = lattice;
+    LevelGeom g = level_geom(f, level);
+    const EmbLevel &lv = f->lv[level];
+    emb_status rc = EMB_OK;
+    uint32_t *flag = nullptr, *pos = nullptr;
+    uint64_t nf = 0;
+    // step 1: exact x-line filter, compacted in ascending order
+    if (cudaMallocAsync(&flag, (m->T + 1) * sizeof(uint32_t), s) != cudaSuccess ||
+        cudaMallocAsync(&pos, (m->T + 1) * sizeof(uint32_t), s) != cudaSuccess) {
+        emb_bins_destroy(b);
+        return EMB_ERR_CUDA;
+    }
+    EMB_LAUNCH((k_xfilter), emb_grid(m->T, 256), 256, 0, s)(m->rec, m->T, g, flag);
+    rc = emb_scan_u32(flag, pos, m->T, &nf, s);
+    if (rc == EMB_OK) {
+        b->nf = (int64_t)nf;
+        if (cudaMalloc(&b->flist, (nf + 1) * sizeof(uint32_t)) != cudaSuccess) rc = EMB_ERR_CUDA;
+    }
+    if (rc == EMB_OK && nf > 0) EMB_LAUNCH((k_compact), emb_grid(m->T, 256), 256, 0, s)(flag, pos, m->T, b->flist);
+    cudaFreeAsync(flag, s);
+    cudaFreeAsync(pos, s);
+    // steps 2-9 at the finest level: CSR bins of link-relevant triangles per block
+    if (rc == EMB_OK && level == f->max_level && lv.n > 0) {
+        uint32_t *cnt = nullptr;
+        uint64_t np = 0;
+        long long dil = g.half;
+        if (cudaMallocAsync(&cnt, (lv.n + 1) * sizeof(uint32_t), s) != cudaSuccess ||
+            cudaMalloc(&b->off, (lv.n + 1) * sizeof(uint32_t)) != cudaSuccess) {
+            emb_bins_destroy(b);
+            return EMB_ERR_CUDA;
+        }
+        cudaMemsetAsync(cnt, 0, (lv.n + 1) * sizeof(uint32_t), s);
+        EMB_LAUNCH((k_bin_pairs<0>), emb_grid(m->T, 32 * EMB_WU_WARPS), 32 * EMB_WU_WARPS, 0, s)(m->rec, m->T, g, dil, emb_lookup_of(lv), cnt, nullptr,
+                                                           nullptr);
+        rc = emb_scan_u32(cnt, b->off, lv.n, &np, s);
+        if (rc == EMB_OK) {
+            b->npairs = (int64_t)np;
+            if (cudaMalloc(&b->ent, (np + 1) * sizeof(uint32_t)) != cudaSuccess) rc = EMB_ERR_CUDA;
+        }
+        if (rc == EMB_OK) {
+            cudaMemsetAsync(cnt, 0, (lv.n + 1) * sizeof(uint32_t), s);
+            EMB_LAUNCH((k_bin_pairs<1>), emb_grid(m->T, 32 * EMB_WU_WARPS), 32 * EMB_WU_WARPS, 0, s)(m->rec, m->T, g, dil, emb_lookup_of(lv), cnt,
+                                                               b->off, b->ent);
+        }
+        cudaFreeAsync(cnt, s);
+    }
+    if (rc == EMB_OK && cudaGetLastError() != cudaSuccess) rc = EMB_ERR_CUDA;
+    if (rc != EMB_OK) {
+        emb_bins_destroy(b);
+        return rc;
+    }
+    *out = b;
+    return EMB_OK;
+}
+
+extern "C" void emb_bins_destroy(emb_bins b)
+{
+    if (!b) return;
+    cudaDeviceSynchronize();
+    if (b->flist) cudaFree(b->flist);
+    if (b->off) cudaFree(b->off);
+    if (b->ent) cudaFree(b->ent);
+    delete b;
+}
+
+extern "C" emb_status emb_bins_stats(emb_bins b, int64_t *h_filtered, int64_t *h_pairs)
+{
+    if (!b) return EMB_ERR_BAD_INPUT;
+    if (h_filtered) *h_filtered = b->nf;
+    if (h_pairs) *h_pairs = b->npairs;
+    return EMB_OK;
+}
+
+extern "C" emb_status emb_bins_copy(emb_bins b, uint32_t *d_filtered, uint32_t *d_off, uint32_t *d_ent, void *stream)
+{
+    if (!b) return EMB_ERR_BAD_INPUT;
+    cudaStream_t s = emb_stream(stream);
+    if (d_filtered && b->nf > 0)
+        EMB_CUDA_TRY(cudaMemcpyAsync(d_filtered, b->flist, b->nf * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    if ((d_off || d_ent) && !b->off) return EMB_ERR_STATE;
+    if (d_off)
+        EMB_CUDA_TRY(cudaMemcpyAsync(d_off, b->off, (b->f->lv[b->level].n + 1) * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    if (d_ent && b->npairs > 0)
+        EMB_CUDA_TRY(cudaMemcpyAsync(d_ent, b->ent, b->npairs * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    return EMB_OK;
+}

@@ -1,0 +1,306 @@
+// Shared plumbing of libemb: device status word, exclusive scan, level hash,
+// neighbour tables, and the small query entry points of the C ABI.
+#include <stdio.h>
+#include <stdlib.h>
+
+#include <atomic>
+#include <mutex>
+
+#include "emb_internal.cuh"
+
+// ---------------------------------------------------------------------------
+// status word and error notes
+// ---------------------------------------------------------------------------
+static std::mutex g_status_mu;
+static int *g_status_dev[64] = {nullptr};
+
+void emb_note_cuda_error(cudaError_t e, const char *what, const char *file, int line)
+{
+    if (getenv("EMB_VERBOSE")) fprintf(stderr, "libemb: %s failed (%s) at %s:%d\n", what, cudaGetErrorString(e), file, line);
+}
+
+int *emb_status_word()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(g_status_mu);
+    if (!g_status_dev[dev]) {
+        int *p = nullptr;
+        if (cudaMalloc(&p, sizeof(int)) != cudaSuccess) return nullptr;
+        if (cudaMemset(p, 0, sizeof(int)) != cudaSuccess) return nullptr;
+        g_status_dev[dev] = p;
+    }
+    return g_status_dev[dev];
+}
+
+cudaStream_t emb_stream(void *s) { return (cudaStream_t)s; }
+
+static std::atomic<long long> g_launches{0};
+
+void emb_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+extern "C" emb_status emb_launch_count(int64_t *h_out)
+{
+    if (!h_out) return EMB_ERR_BAD_INPUT;
+    *h_out = g_launches.load(std::memory_order_relaxed);
+    return EMB_OK;
+}
+
+int emb_grid(int64_t n, int block)
+{
+    int64_t g = (n + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > 2147483647ll) g = 2147483647ll;
+    return (int)g;
+}
+
+extern "C" const char *emb_status_string(emb_status s)
+{
+    switch (s) {
+    case EMB_OK: return "EMB_OK";
+    case EMB_ERR_BAD_INPUT: return "EMB_ERR_BAD_INPUT";
+    case EMB_ERR_NOT_WATERTIGHT: return "EMB_ERR_NOT_WATERTIGHT";
+    case EMB_ERR_CAPACITY: return "EMB_ERR_CAPACITY";
+    case EMB_ERR_CUDA: return "EMB_ERR_CUDA";
+    case EMB_ERR_TIMEOUT: return "EMB_ERR_TIMEOUT";
+    case EMB_ERR_RANGE: return "EMB_ERR_RANGE";
+    case EMB_ERR_STATE: return "EMB_ERR_STATE";
+    default: return "EMB_ERR_UNKNOWN";
+    }
+}
+
+extern "C" emb_status emb_status_get(void *stream, emb_status *out)
+{
+    if (!out) return EMB_ERR_BAD_INPUT;
+    int *st = emb_status_word();
+    if (!st) return EMB_ERR_CUDA;
+    EMB_CUDA_TRY(cudaStreamSynchronize(emb_stream(stream)));
+    int v = 0;
+    EMB_CUDA_TRY(cudaMemcpy(&v, st, sizeof(int), cudaMemcpyDeviceToHost));
+    EMB_CUDA_TRY(cudaMemset(st, 0, sizeof(int)));
+    *out = v;
+    return EMB_OK;
+}
+
+extern "C" emb_status emb_directions(int32_t *h_out)
+{
+    if (!h_out) return EMB_ERR_BAD_INPUT;
+    for (int i = 0; i < 27; ++i) {
+        int cx, cy, cz;
+        emb_dir(i, cx, cy, cz);
+        h_out[3 * i + 0] = cx;
+        h_out[3 * i + 1] = cy;
+        h_out[3 * i + 2] = cz;
+    }
+    return EMB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// exclusive scan of uint32 values (three phases: tile sums, scan of sums, apply)
+// ---------------------------------------------------------------------------
+#define SCAN_BLOCK 512
+#define SCAN_ITEMS 8
+#define SCAN_TILE (SCAN_BLOCK * SCAN_ITEMS)
+
+// Block-wide exclusive scan of one uint64 per thread; returns the block total in *total.
+__device__ __forceinline__ uint64_t block_excl_scan(uint64_t v, uint64_t *total)
+{
+    __shared__ uint64_t warp_sums[SCAN_BLOCK / 32];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint64_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint64_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) warp_sums[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        uint64_t s = lane < SCAN_BLOCK / 32 ? warp_sums[lane] : 0;
+        uint64_t si = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint64_t t = __shfl_up_sync(0xffffffffu, si, o);
+            if (lane >= o) si += t;
+        }
+        if (lane < SCAN_BLOCK / 32) warp_sums[lane] = si - s;  // exclusive warp offsets
+        if (lane == SCAN_BLOCK / 32 - 1) *total = si;
+    }
+    __syncthreads();
+    uint64_t r = warp_sums[w] + inc - v;
+    __syncthreads();
+    return r;
+}
+
+__global__ void k_scan_tile_sums(const uint32_t *__restrict__ in, int64_t n, uint64_t *__restrict__ tile_sum)
+{
+    __shared__ uint64_t tot;
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    uint64_t s = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i)
+        if (base + i < n) s += in[base + i];
+    block_excl_scan(s, &tot);
+    if (threadIdx.x == 0) tile_sum[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_sums(uint64_t *__restrict__ tile_sum, int64_t ntiles, uint64_t *__restrict__ total)
+{
+    __shared__ uint64_t tot;
+    uint64_t carry = 0;
+    for (int64_t b = 0; b < ntiles; b += SCAN_BLOCK) {
+        int64_t i = b + threadIdx.x;
+        uint64_t v = i < ntiles ? tile_sum[i] : 0;
+        uint64_t ex = block_excl_scan(v, &tot);
+        if (i < ntiles) tile_sum[i] = carry + ex;
+        carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void k_scan_apply(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int64_t n,
+                             const uint64_t *__restrict__ tile_off, int *st)
+{
+    __shared__ uint64_t tot;
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    uint32_t v[SCAN_ITEMS];
+    uint64_t s = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        v[i] = base + i < n ? in[base + i] : 0u;
+        s += v[i];
+    }
+    uint64_t run = tile_off[blockIdx.x] + block_excl_scan(s, &tot);
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        if (base + i <= n) {  // entry n receives the total
+            if (run > 0xFFFFFFFFull) emb_set_status(st, EMB_ERR_CAPACITY);
+            out[base + i] = (uint32_t)run;
+        }
+        run += v[i];
+    }
+}
+
+// d_out gets n + 1 entries: exclusive prefix sums and, at index n, the total.
+emb_status emb_scan_u32(const uint32_t *d_in, uint32_t *d_out, int64_t n, uint64_t *h_total, cudaStream_t s)
+{
+    int *st = emb_status_word();
+    if (!st) return EMB_ERR_CUDA;
+    int64_t ntiles = (n + 1 + SCAN_TILE - 1) / SCAN_TILE;
+    uint64_t *tmp = nullptr;
+    EMB_CUDA_TRY(cudaMallocAsync(&tmp, (ntiles + 1) * sizeof(uint64_t), s));
+    EMB_LAUNCH((k_scan_tile_sums), (int)ntiles, SCAN_BLOCK, 0, s)(d_in, n, tmp);
+    EMB_LAUNCH((k_scan_sums), 1, SCAN_BLOCK, 0, s)(tmp, ntiles, tmp + ntiles);
+    EMB_LAUNCH((k_scan_apply), (int)ntiles, SCAN_BLOCK, 0, s)(d_in, d_out, n, tmp, st);
+    EMB_CUDA_TRY(cudaGetLastError());
+    if (h_total) {
+        EMB_CUDA_TRY(cudaMemcpyAsync(h_total, tmp + ntiles, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+        EMB_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    EMB_CUDA_TRY(cudaFreeAsync(tmp, s));
+    return EMB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// level hash and neighbour table
+// ---------------------------------------------------------------------------
+__global__ void k_hash_insert(const uint64_t *__restrict__ key, int64_t n, uint64_t *hkey, int32_t *hval, int64_t hcap,
+                              int *st)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint64_t k = key[i];
+    uint64_t m = (uint64_t)hcap - 1, s = emb_hash_mix(k) & m;
+    for (int64_t it = 0; it < hcap; ++it) {
+        unsigned long long prev = atomicCAS((unsigned long long *)(hkey + s), (unsigned long long)EMB_HASH_EMPTY,
+                                            (unsigned long long)k);
+        if (prev == EMB_HASH_EMPTY || prev == k) {
+            hval[s] = (int32_t)i;
+            return;
+        }
+        s = (s + 1) & m;
+    }
+    emb_set_status(st, EMB_ERR_STATE);  // table full: cannot happen with capacity >= 2n
+}
+
+__global__ void k_bits_set(const uint64_t *__restrict__ key, int64_t n, int64_t nb, unsigned long long *__restrict__ bits)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint64_t k = key[i];
+    int64_t bx = (int64_t)(k & EMB_KEY_MASK), by = (int64_t)((k >> EMB_KEY_BITS) & EMB_KEY_MASK),
+            bz = (int64_t)(k >> (2 * EMB_KEY_BITS));
+    int64_t lin = (bz * nb + by) * nb + bx;
+    atomicOr(bits + (lin >> 6), 1ull << (lin & 63));
+}
+
+__global__ void k_word_popc(const uint64_t *__restrict__ bits, int64_t nw, uint32_t *__restrict__ out)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nw) out[i] = (uint32_t)__popcll(bits[i]);
+}
+
+emb_status emb_build_hash(EmbLevel &lv, cudaStream_t s)
+{
+    int *st = emb_status_word();
+    if (!st) return EMB_ERR_CUDA;
+    int64_t cap = 1024;
+    while (cap < 2 * lv.n) cap <<= 1;
+    if (lv.hkey) EMB_CUDA_TRY(cudaFreeAsync(lv.hkey, s));
+    if (lv.hval) EMB_CUDA_TRY(cudaFreeAsync(lv.hval, s));
+    EMB_CUDA_TRY(cudaMallocAsync(&lv.hkey, cap * sizeof(uint64_t), s));
+    EMB_CUDA_TRY(cudaMallocAsync(&lv.hval, cap * sizeof(int32_t), s));
+    EMB_CUDA_TRY(cudaMemsetAsync(lv.hkey, 0xFF, cap * sizeof(uint64_t), s));
+    lv.hcap = cap;
+    if (lv.n > 0) EMB_LAUNCH((k_hash_insert), emb_grid(lv.n, 256), 256, 0, s)(lv.key, lv.n, lv.hkey, lv.hval, cap, st);
+    if (lv.bits) EMB_CUDA_TRY(cudaFreeAsync(lv.bits, s));
+    if (lv.wpre) EMB_CUDA_TRY(cudaFreeAsync(lv.wpre, s));
+    lv.bits = nullptr;
+    lv.wpre = nullptr;
+    int64_t cells = lv.nb_axis * lv.nb_axis * lv.nb_axis;
+    if (cells <= EMB_BITMAP_MAX_BITS) {
+        int64_t nw = (cells + 63) / 64;
+        uint32_t *pc = nullptr;
+        EMB_CUDA_TRY(cudaMallocAsync(&lv.bits, nw * sizeof(uint64_t), s));
+        EMB_CUDA_TRY(cudaMallocAsync(&lv.wpre, (nw + 1) * sizeof(uint32_t), s));
+        EMB_CUDA_TRY(cudaMallocAsync(&pc, (nw + 1) * sizeof(uint32_t), s));
+        EMB_CUDA_TRY(cudaMemsetAsync(lv.bits, 0, nw * sizeof(uint64_t), s));
+        if (lv.n > 0)
+            EMB_LAUNCH((k_bits_set), emb_grid(lv.n, 256), 256, 0, s)(lv.key, lv.n, lv.nb_axis,
+                                                                    (unsigned long long *)lv.bits);
+        EMB_LAUNCH((k_word_popc), emb_grid(nw, 256), 256, 0, s)(lv.bits, nw, pc);
+        emb_status rc = emb_scan_u32(pc, lv.wpre, nw, nullptr, s);
+        EMB_CUDA_TRY(cudaFreeAsync(pc, s));
+        if (rc != EMB_OK) return rc;
+    }
+    EMB_CUDA_TRY(cudaGetLastError());
+    return EMB_OK;
+}
+
+__global__ void k_neighbors(const uint64_t *__restrict__ key, int64_t n, int64_t nb, EmbLookup lk, int32_t *__restrict__ nbr)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * 26) return;
+    int64_t b = i / 26;
+    int d = (int)(i % 26) + 1;
+    uint64_t k = key[b];
+    int64_t bx = (int64_t)(k & EMB_KEY_MASK), by = (int64_t)((k >> EMB_KEY_BITS) & EMB_KEY_MASK),
+            bz = (int64_t)(k >> (2 * EMB_KEY_BITS));
+    int cx, cy, cz;
+    emb_dir(d, cx, cy, cz);
+    int64_t x = bx + cx, y = by + cy, z = bz + cz;
+    int32_t r = -1;
+    if (x >= 0 && y >= 0 && z >= 0 && x < nb && y < nb && z < nb) r = emb_lookup(lk, x, y, z);
+    nbr[i] = r;
+}
+
+emb_status emb_build_neighbors(EmbLevel &lv, cudaStream_t s)
+{
+    if (lv.nbr) return EMB_OK;
+    EMB_CUDA_TRY(cudaMallocAsync(&lv.nbr, (lv.n * 26 + 1) * sizeof(int32_t), s));
+    if (lv.n > 0)
+        EMB_LAUNCH((k_neighbors), emb_grid(lv.n * 26, 256), 256, 0, s)(lv.key, lv.n, lv.nb_axis, emb_lookup_of(lv), lv.nbr);
+    EMB_CUDA_TRY(cudaGetLastError());
+    return EMB_OK;
+}

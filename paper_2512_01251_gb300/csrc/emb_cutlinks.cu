@@ -1,0 +1,665 @@
+// Boundary-cell identification and the flat link-length table (Sec. 3.4,
+// "Boundary Cell Identification", "Memory Allocations for Boundary Cells",
+// "Link-Length Computation").
+//
+// k_link_cand: per finest block and direction, the 64-bit word of fluid cells
+//   whose neighbour along that direction is solid, from the 27 mask words of the
+//   block and its 26 neighbours by 3-D bit shifts.
+// Counts per block -> exclusive scan -> link offsets (block-granular, in block
+//   order, so the table is sorted by (cell, direction)).
+// k_link_emit: one warp per block with links (details at the kernel).  Exact
+//   Pluecker sides for the line, exact plane sides for the two segment ends
+//   (query points pushed by (e, e^2, e^3)), and an exact rational comparison of
+//   t = N / (h M) between crossings (lowest triangle id on equality).  q = t is
+//   rounded to float once.
+#include "emb_internal.cuh"
+
+#define LINK_TILE 64
+
+// Neighbour-solid words by 3-D bit shifts.  A block's 64 cells are bit t =
+// x + 4y + 16z of its mask word; shifting the 4x4x4 bit cube by one cell along an
+// axis takes three cell layers from the block itself and the fourth from the
+// neighbouring block on that side.
+#define EMB_X0 0x1111111111111111ull
+#define EMB_X3 0x8888888888888888ull
+#define EMB_Y0 0x000F000F000F000Full
+#define EMB_Y3 0xF000F000F000F000ull
+#define EMB_Z0 0x000000000000FFFFull
+#define EMB_Z3 0xFFFF000000000000ull
+
+// bit t of the result = bit of cell (t + e_axis * s) where the cell lies in `cur`
+// or, across the face, in `nxt` (the neighbour block on the +s side).
+__device__ __forceinline__ uint64_t shift_axis(uint64_t cur, uint64_t nxt, int axis, int s)
+{
+    if (axis == 0) return s > 0 ? (((cur >> 1) & ~EMB_X3) | ((nxt << 3) & EMB_X3)) : (((cur << 1) & ~EMB_X0) | ((nxt >> 3) & EMB_X0));
+    if (axis == 1) return s > 0 ? (((cur >> 4) & ~EMB_Y3) | ((nxt << 12) & EMB_Y3)) : (((cur << 4) & ~EMB_Y0) | ((nxt >> 12) & EMB_Y0));
+    return s > 0 ? (((cur >> 16) & ~EMB_Z3) | ((nxt << 48) & EMB_Z3)) : (((cur << 16) & ~EMB_Z0) | ((nxt >> 48) & EMB_Z0));
+}
+
+// Per finest block: word d-1 (d = 1 .. lattice-1) has bit t set iff cell t is fluid
+// and its neighbour along c_d is solid.  A missing neighbour block counts as fluid:
+// a fluid cell with a solid neighbour is within one link of the surface, and the
+// refine rule makes every block within that reach exist.
+__global__ void k_link_cand(const uint64_t *__restrict__ mask, const int32_t *__restrict__ nbr, int64_t n, int lattice,
+                            uint64_t *__restrict__ cand, uint32_t *__restrict__ blk_cnt)
+{
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n) return;
+    uint64_t W[27];  // mask words by offset code (ox+1) + 3(oy+1) + 9(oz+1)
+    W[13] = mask[b];
+#pragma unroll
+    for (int i = 1; i < 27; ++i) {
+        int cx, cy, cz;
+        emb_dir(i, cx, cy, cz);
+        const int32_t id = nbr[b * 26 + i - 1];
+        W[(cx + 1) + 3 * (cy + 1) + 9 * (cz + 1)] = id >= 0 ? mask[id] : 0ull;
+    }
+    const uint64_t fluid = ~W[13];
+    uint32_t count = 0;
+#pragma unroll
+    for (int d = 1; d < 27; ++d) {
+        if (d >= lattice) {
+            cand[b * 26 + d - 1] = 0;
+            continue;
+        }
+        int cx, cy, cz;
+        emb_dir(d, cx, cy, cz);
+        // shift along x for every (y, z) block layer touched, then along y, then along z
+        uint64_t Y[2][2];
+#pragma unroll
+        for (int jy = 0; jy < 2; ++jy)
+#pragma unroll
+            for (int jz = 0; jz < 2; ++jz) {
+                const int oy = jy ? cy : 0, oz = jz ? cz : 0;
+                const uint64_t cur = W[1 + 3 * (oy + 1) + 9 * (oz + 1)];
+                Y[jy][jz] = cx ? shift_axis(cur, W[(cx + 1) + 3 * (oy + 1) + 9 * (oz + 1)], 0, cx) : cur;
+            }
+        uint64_t Z[2];
+#pragma unroll
+        for (int jz = 0; jz < 2; ++jz) Z[jz] = cy ? shift_axis(Y[0][jz], Y[1][jz], 1, cy) : Y[0][jz];
+        const uint64_t nb_solid = cz ? shift_axis(Z[0], Z[1], 2, cz) : Z[0];
+        const uint64_t c = fluid & nb_solid;
+        cand[b * 26 + d - 1] = c;
+        count += __popcll(c);
+    }
+    blk_cnt[b] = count;
+}
+
+// One warp per finest block.  The block's cells that have cut links are taken in
+// chunks of up to 32 (slot j = the j-th such cell of the chunk).  The block's bin
+// is staged 32 triangles at a time into the warp's shared-memory tile.  A
+// triangle can only cross a link from cell centre P if its bounding box meets the
+// cube [P - h, P + h]; because the cells form a 4x4x4 lattice, the set of cells
+// passing that test is a sub-box, built as a 64-bit mask with a few bit
+// operations.  The surviving (triangle, cell) pairs of a tile are spread over the
+// 32 lanes with a prefix sum, so the exact tests run with full lanes.  Each pair
+// gets its three edge moments (U - P) x (V - P) once; every candidate direction
+// c of the cell then costs the dot products c . m (entries of c in {-1,0,1}).
+// Crossings are appended to a per-cell bucket; afterwards the owner lane of each
+// cell resolves the nearest crossing per direction with exact rational
+// comparisons and writes the links.  A bucket that overflows sends its cell
+// through an exact per-cell scan of the whole bin instead.
+#define LE_WARPS 4
+#define LE_TILE 32
+#define LE_BCAP 28
+
+struct TriT {
+    int ax, ay, az, bx, by, bz, cx, cy, cz, id;
+    int lox, loy, loz, hix, hiy, hiz;
+    long long nx, ny, nz;
+};
+
+struct LeWarp {
+    TriT tile[LE_TILE];
+    uint2 hit[32][LE_BCAP];  // (triangle id, direction)
+    int best[27][32];        // nearest crossed triangle per (direction, slot) during resolution
+    int hcnt[32];
+    uint32_t cm[32];         // candidate directions of each slot's cell
+};
+
+// Directions whose component on one axis lies in an allowed subset of {-1, 0, +1}.
+__device__ __forceinline__ uint32_t dirs_allowed(int axis, bool neg, bool zero, bool pos)
+{
+    const uint32_t N = axis == 0 ? emb_dirs_with(0, -1) : (axis == 1 ? emb_dirs_with(1, -1) : emb_dirs_with(2, -1));
+    const uint32_t Z = axis == 0 ? emb_dirs_with(0, 0) : (axis == 1 ? emb_dirs_with(1, 0) : emb_dirs_with(2, 0));
+    const uint32_t P = axis == 0 ? emb_dirs_with(0, 1) : (axis == 1 ? emb_dirs_with(1, 1) : emb_dirs_with(2, 1));
+    return (neg ? N : 0u) | (zero ? Z : 0u) | (pos ? P : 0u);
+}
+
+__device__ __forceinline__ long long cdot(int cx, int cy, int cz, long long x, long long y, long long z)
+{
+    long long s = 0;
+    if (cx) s = cx > 0 ? s + x : s - x;
+    if (cy) s = cy > 0 ? s + y : s - y;
+    if (cz) s = cz > 0 ? s + z : s - z;
+    return s;
+}
+
+// Perturbed Pluecker sign for edge U -> V given s = c . ((U-P) x (V-P)) and the edge vector d = V - U:
+// a zero is resolved by e . (c x d), e = (e, e^2, e^3).
+__device__ __forceinline__ int plk_resolve(long long s, int cx, int cy, int cz, long long dx, long long dy, long long dz)
+{
+    if (s != 0) return s > 0 ? 1 : -1;
+    long long w0 = cy * dz - cz * dy;
+    if (w0) return w0 > 0 ? 1 : -1;
+    long long w1 = cz * dx - cx * dz;
+    if (w1) return w1 > 0 ? 1 : -1;
+    long long w2 = cx * dy - cy * dx;
+    return w2 > 0 ? 1 : (w2 < 0 ? -1 : 0);
+}
+
+// Sign of (X - n . e): X when nonzero, else minus the first nonzero normal component.
+__device__ __forceinline__ int side_sign(i128 X, long long nx, long long ny, long long nz)
+{
+    if (X != 0) return X > 0 ? 1 : -1;
+    if (nx) return nx > 0 ? -1 : 1;
+    if (ny) return ny > 0 ? -1 : 1;
+    return nz > 0 ? -1 : 1;
+}
+
+// Position of the r-th (0-based) set bit of m (m has more than r set bits).
+__device__ __forceinline__ int select64(unsigned long long m, int r)
+{
+    int pos = 0;
+#pragma unroll
+    for (int w = 32; w >= 1; w >>= 1) {
+        unsigned long long lowm = m & ((1ull << w) - 1ull);
+        int c = __popcll(lowm);
+        if (r >= c) {
+            r -= c;
+            m >>= w;
+            pos += w;
+        } else {
+            m = lowm;
+        }
+    }
+    return pos;
+}
+
+// Bits [lo, hi] of a 64-bit word (0 <= lo <= hi <= 63).
+__device__ __forceinline__ unsigned long long bit_range(int lo, int hi)
+{
+    unsigned long long top = hi >= 63 ? ~0ull : ((1ull << (hi + 1)) - 1ull);
+    return top & ~((1ull << lo) - 1ull);
+}
+
+// Exact crossing parameter t = N / (h M) of the segment P -> P + h c with a triangle
+// already known to be crossed (recomputed from its record).
+__device__ __forceinline__ void tri_NM(const int4 *__restrict__ rec, int tr, long long px, long long py, long long pz,
+                                       int cx, int cy, int cz, i128 &N, long long &M)
+{
+    int4 A = rec[3 * (int64_t)tr], B = rec[3 * (int64_t)tr + 1], C = rec[3 * (int64_t)tr + 2];
+    long long ux = (long long)B.x - A.x, uy = (long long)B.y - A.y, uz = (long long)B.z - A.z;
+    long long vx = (long long)C.x - A.x, vy = (long long)C.y - A.y, vz = (long long)C.z - A.z;
+    long long nx = uy * vz - uz * vy, ny = uz * vx - ux * vz, nz = ux * vy - uy * vx;
+    long long nc = cdot(cx, cy, cz, nx, ny, nz);
+    i128 D = mul128(nx, A.x - px) + mul128(ny, A.y - py) + mul128(nz, A.z - pz);
+    N = nc > 0 ? D : -D;
+    M = nc > 0 ? nc : -nc;
+}
+
+// Exact test of the segment P -> P + h c (perturbed) against a triangle given its
+// vertices relative to P, its normal and the edge moments; fills D on first use.
+__device__ __forceinline__ bool seg_cross(int cx, int cy, int cz, long long h, long long ax, long long ay, long long az,
+                                          long long bx, long long by, long long bz, long long qx, long long qy,
+                                          long long qz, long long nx, long long ny, long long nz, long long m1x,
+                                          long long m1y, long long m1z, long long m2x, long long m2y, long long m2z,
+                                          long long m3x, long long m3y, long long m3z, i128 &D, bool &haveD)
+{
+    const long long nc = cdot(cx, cy, cz, nx, ny, nz);
+    if (nc == 0) return false;
+    const int sn = nc > 0 ? 1 : -1;
+    if (plk_resolve(cdot(cx, cy, cz, m1x, m1y, m1z), cx, cy, cz, bx - ax, by - ay, bz - az) != sn) return false;
+    if (plk_resolve(cdot(cx, cy, cz, m2x, m2y, m2z), cx, cy, cz, qx - bx, qy - by, qz - bz) != sn) return false;
+    if (plk_resolve(cdot(cx, cy, cz, m3x, m3y, m3z), cx, cy, cz, ax - qx, ay - qy, az - qz) != sn) return false;
+    if (!haveD) {
+        D = mul128(nx, ax) + mul128(ny, ay) + mul128(nz, az);
+        haveD = true;
+    }
+    if (side_sign(D, nx, ny, nz) != sn) return false;                 // t <= 0
+    if (side_sign(D - mul128(h, nc), nx, ny, nz) != -sn) return false;  // t >= 1
+    return true;
+}
+
+// Nearest crossed triangle of every candidate direction in `cm` for cell centre P,
+// by a plain exact scan of the whole bin (used for cells whose bucket overflowed).
+__device__ __noinline__ void scan_cell_slow(const uint32_t *__restrict__ bin_ent, uint32_t e0, uint32_t e1,
+                                            const int4 *__restrict__ rec, long long px, long long py, long long pz,
+                                            long long h, uint32_t cm, int *bestT)
+{
+    for (int d = 0; d < 27; ++d) bestT[d] = -1;
+    for (uint32_t e = e0; e < e1; ++e) {
+        const int id = (int)bin_ent[e];
+        const int4 A = rec[3 * (int64_t)id], B = rec[3 * (int64_t)id + 1], C = rec[3 * (int64_t)id + 2];
+        const long long ax = A.x - px, ay = A.y - py, az = A.z - pz;
+        const long long bx = B.x - px, by = B.y - py, bz = B.z - pz;
+        const long long qx = C.x - px, qy = C.y - py, qz = C.z - pz;
+        const long long ux = bx - ax, uy = by - ay, uz = bz - az, vx = qx - ax, vy = qy - ay, vz = qz - az;
+        const long long nx = uy * vz - uz * vy, ny = uz * vx - ux * vz, nz = ux * vy - uy * vx;
+        const long long m1x = ay * bz - az * by, m1y = az * bx - ax * bz, m1z = ax * by - ay * bx;
+        const long long m2x = by * qz - bz * qy, m2y = bz * qx - bx * qz, m2z = bx * qy - by * qx;
+        const long long m3x = qy * az - qz * ay, m3y = qz * ax - qx * az, m3z = qx * ay - qy * ax;
+        i128 D = 0;
+        bool haveD = false;
+        uint32_t mm = cm;
+        while (mm) {
+            const int d = __ffs(mm) - 1;
+            mm &= mm - 1;
+            int cx, cy, cz;
+            emb_dir(d, cx, cy, cz);
+            if (!seg_cross(cx, cy, cz, h, ax, ay, az, bx, by, bz, qx, qy, qz, nx, ny, nz, m1x, m1y, m1z, m2x, m2y, m2z,
+                           m3x, m3y, m3z, D, haveD))
+                continue;
+            bool better = bestT[d] < 0;
+            if (!better) {
+                i128 No, Nn;
+                long long Mo, Mn;
+                tri_NM(rec, bestT[d], px, py, pz, cx, cy, cz, No, Mo);
+                tri_NM(rec, id, px, py, pz, cx, cy, cz, Nn, Mn);
+                const i128 l = Nn * (i128)Mo, r = No * (i128)Mn;
+                better = l < r || (l == r && id < bestT[d]);
+            }
+            if (better) bestT[d] = id;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(LE_WARPS * 32, 4) k_link_emit(const uint64_t *__restrict__ key, const uint32_t *__restrict__ work,
+                                                                const uint32_t *__restrict__ work_n, unsigned int *__restrict__ next, LevelGeom g,
+                                                                const uint64_t *__restrict__ cand,
+                                                                const uint32_t *__restrict__ blk_off,
+                                                                const uint32_t *__restrict__ bin_off,
+                                                                const uint32_t *__restrict__ bin_ent,
+                                                                const int4 *__restrict__ rec, int32_t *__restrict__ o_cell,
+                                                                uint8_t *__restrict__ o_dir, float *__restrict__ o_q,
+                                                                int32_t *__restrict__ o_tri, int *st)
+{
+    extern __shared__ __align__(16) unsigned char le_smem[];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    LeWarp &S = reinterpret_cast<LeWarp *>(le_smem)[w];
+    // persistent warps: take the next block with links from the work list
+    for (;;) {
+    unsigned int widx = 0;
+    if (lane == 0) widx = atomicAdd(next, 1u);
+    widx = __shfl_sync(0xffffffffu, widx, 0);
+    if (widx >= *work_n) return;
+    const int64_t b = work[widx];
+    const uint32_t base = blk_off[b];
+    // candidate directions of cells lane and 32 + lane from the block's direction words
+    const uint64_t wd = lane < 26 ? cand[b * 26 + lane] : 0ull;
+    uint32_t c0 = 0, c1 = 0;
+    unsigned long long bmask = 0;
+#pragma unroll
+    for (int d = 0; d < 26; ++d) {
+        const uint64_t wdd = ((unsigned long long)__shfl_sync(0xffffffffu, (unsigned)(wd >> 32), d) << 32) |
+                             (unsigned long long)__shfl_sync(0xffffffffu, (unsigned)wd, d);
+        bmask |= wdd;
+        c0 |= (uint32_t)((wdd >> lane) & 1ull) << (d + 1);
+        c1 |= (uint32_t)((wdd >> (32 + lane)) & 1ull) << (d + 1);
+    }
+    const int nbc = __popcll(bmask);
+    // exclusive link offsets of cells lane and 32 + lane, in cell order
+    uint32_t k0 = __popc(c0), k1 = __popc(c1), i0 = k0, i1 = k1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t0 = __shfl_up_sync(0xffffffffu, i0, o), t1 = __shfl_up_sync(0xffffffffu, i1, o);
+        if (lane >= o) {
+            i0 += t0;
+            i1 += t1;
+        }
+    }
+    const uint32_t tot0 = __shfl_sync(0xffffffffu, i0, 31);
+    const uint32_t ex0 = i0 - k0, ex1 = tot0 + i1 - k1;
+    const uint64_t bk = key[b];
+    const long long X0 = 4 * (long long)(bk & EMB_KEY_MASK) * g.h, Y0 = 4 * (long long)((bk >> EMB_KEY_BITS) & EMB_KEY_MASK) * g.h,
+                    Z0 = 4 * (long long)(bk >> (2 * EMB_KEY_BITS)) * g.h;
+    const uint32_t e0 = bin_off[b], e1 = bin_off[b + 1];
+    const long long h = g.h, half = g.half;
+    const int lh = __ffsll(h) - 1;  // h is a power of two
+    for (int chunk = 0; chunk * 32 < nbc; ++chunk) {
+        // the chunk's cells: set bits 32*chunk .. 32*chunk+31 of bmask
+        const int lo_bit = select64(bmask, chunk * 32);
+        const int ncc = min(32, nbc - chunk * 32);
+        const int hi_bit = select64(bmask, chunk * 32 + ncc - 1);
+        const unsigned long long cmask = bmask & bit_range(lo_bit, hi_bit);
+        // slot lane: its cell, candidates and link offset
+        const bool active = lane < ncc;
+        const int t = active ? select64(cmask, lane) : 0;
+        const uint32_t cm_lo = __shfl_sync(0xffffffffu, c0, t & 31), cm_hi = __shfl_sync(0xffffffffu, c1, t & 31);
+        const uint32_t ex_lo = __shfl_sync(0xffffffffu, ex0, t & 31), ex_hi = __shfl_sync(0xffffffffu, ex1, t & 31);
+        const uint32_t cm = active ? (t < 32 ? cm_lo : cm_hi) : 0u;
+        const uint32_t off = t < 32 ? ex_lo : ex_hi;
+        S.cm[lane] = cm;
+        S.hcnt[lane] = 0;
+        __syncwarp();
+        for (uint32_t e = e0; e < e1; e += LE_TILE) {
+            // stage triangle `lane` of this tile and the chunk cells its reach box touches
+            unsigned long long pm = 0;
+            if (e + lane < e1) {
+                const uint32_t id = bin_ent[e + lane];
+                const int4 A = rec[3 * (int64_t)id], B = rec[3 * (int64_t)id + 1], C = rec[3 * (int64_t)id + 2];
+                TriT s;
+                s.ax = A.x; s.ay = A.y; s.az = A.z;
+                s.bx = B.x; s.by = B.y; s.bz = B.z;
+                s.cx = C.x; s.cy = C.y; s.cz = C.z;
+                s.id = (int)id;
+                s.lox = min(A.x, min(B.x, C.x)); s.hix = max(A.x, max(B.x, C.x));
+                s.loy = min(A.y, min(B.y, C.y)); s.hiy = max(A.y, max(B.y, C.y));
+                s.loz = min(A.z, min(B.z, C.z)); s.hiz = max(A.z, max(B.z, C.z));
+                const long long ux = (long long)B.x - A.x, uy = (long long)B.y - A.y, uz = (long long)B.z - A.z;
+                const long long vx = (long long)C.x - A.x, vy = (long long)C.y - A.y, vz = (long long)C.z - A.z;
+                s.nx = uy * vz - uz * vy;
+                s.ny = uz * vx - ux * vz;
+                s.nz = ux * vy - uy * vx;
+                S.tile[lane] = s;
+                // cell i (centre X0 + (2i+1) half) reaches the box iff lo - h <= centre <= hi + h
+                int r0[3], r1[3];
+                const long long lo3[3] = {s.lox - X0, s.loy - Y0, s.loz - Z0};
+                const long long hi3[3] = {s.hix - X0, s.hiy - Y0, s.hiz - Z0};
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    long long a = lo3[d] - h - half;  // ceil(a / h)
+                    long long c = hi3[d] + h - half;  // floor(c / h)
+                    long long i0_ = -((-a) >> lh), i1_ = c >> lh;
+                    r0[d] = (int)(i0_ < 0 ? 0 : (i0_ > 4 ? 4 : i0_));
+                    r1[d] = (int)(i1_ > 3 ? 3 : (i1_ < -1 ? -1 : i1_));
+                }
+                if (r0[0] <= r1[0] && r0[1] <= r1[1] && r0[2] <= r1[2]) {
+                    const unsigned long long X = (unsigned long long)(((1u << (r1[0] + 1)) - 1u) & ~((1u << r0[0]) - 1u)) *
+                                                 0x1111111111111111ull;
+                    const unsigned long long Y = (((1ull << (4 * r1[1] + 4)) - 1ull) & ~((1ull << (4 * r0[1])) - 1ull)) *
+                                                 0x0001000100010001ull;
+                    const unsigned long long Z = bit_range(16 * r0[2], 16 * r1[2] + 15);
+                    pm = X & Y & Z & cmask;
+                }
+            }
+            __syncwarp();
+            // spread the tile's (triangle, cell) pairs over the lanes
+            const int np = __popcll(pm);
+            int incl = np;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int tt = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += tt;
+            }
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            for (int s0 = 0; s0 < total; s0 += 32) {
+                // ---- level 1: lane -> one (triangle, cell) pair of this tile
+                const int gidx = s0 + lane;
+                int lo = 0;
+#pragma unroll
+                for (int step = 16; step >= 1; step >>= 1) {
+                    int v = __shfl_sync(0xffffffffu, incl, lo + step - 1);
+                    if (v <= gidx) lo += step;
+                }
+                const int ti = lo > 31 ? 31 : lo;
+                const int excl_i = __shfl_sync(0xffffffffu, incl - np, ti);
+                const unsigned long long pmi = ((unsigned long long)__shfl_sync(0xffffffffu, (unsigned)(pm >> 32), ti) << 32) |
+                                               (unsigned long long)__shfl_sync(0xffffffffu, (unsigned)pm, ti);
+                uint32_t ok = 0;
+                int cell = 0;
+                if (gidx < total) {
+                    cell = select64(pmi, gidx - excl_i);
+                    const int slot = __popcll(cmask & ((1ull << cell) - 1ull));
+                    const TriT &T = S.tile[ti];
+                    const long long px = X0 + (2 * (cell & 3) + 1) * half, py = Y0 + (2 * ((cell >> 2) & 3) + 1) * half,
+                                    pz = Z0 + (2 * (cell >> 4) + 1) * half;
+                    // directions whose segment box meets the triangle box: along each axis the
+                    // segment covers [-h, 0], {0} or [0, h] relative to P
+                    const long long l0 = T.lox - px, h0 = T.hix - px, l1 = T.loy - py, h1 = T.hiy - py,
+                                    l2 = T.loz - pz, h2 = T.hiz - pz;
+                    ok = S.cm[slot];
+                    ok &= dirs_allowed(0, l0 <= 0 && h0 >= -h, l0 <= 0 && h0 >= 0, l0 <= h && h0 >= 0);
+                    ok &= dirs_allowed(1, l1 <= 0 && h1 >= -h, l1 <= 0 && h1 >= 0, l1 <= h && h1 >= 0);
+                    ok &= dirs_allowed(2, l2 <= 0 && h2 >= -h, l2 <= 0 && h2 >= 0, l2 <= h && h2 >= 0);
+                }
+                // ---- level 2: lane -> one (pair, direction) item of this batch
+                const int nk = __popc(ok);
+                int kincl = nk;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    int tt = __shfl_up_sync(0xffffffffu, kincl, o);
+                    if (lane >= o) kincl += tt;
+                }
+                const int ktotal = __shfl_sync(0xffffffffu, kincl, 31);
+                for (int k0 = 0; k0 < ktotal; k0 += 32) {
+                    const int gk = k0 + lane;
+                    int pl = 0;
+#pragma unroll
+                    for (int step = 16; step >= 1; step >>= 1) {
+                        int v = __shfl_sync(0xffffffffu, kincl, pl + step - 1);
+                        if (v <= gk) pl += step;
+                    }
+                    const int src = pl > 31 ? 31 : pl;
+                    const int kex = __shfl_sync(0xffffffffu, kincl - nk, src);
+                    const uint32_t okp = __shfl_sync(0xffffffffu, ok, src);
+                    const int tip = __shfl_sync(0xffffffffu, ti, src);
+                    const int cellp = __shfl_sync(0xffffffffu, cell, src);
+                    if (gk >= ktotal) continue;
+                    const int d = select64((unsigned long long)okp, gk - kex);
+                    const int slot = __popcll(cmask & ((1ull << cellp) - 1ull));
+                    const TriT &T = S.tile[tip];
+                    const long long px = X0 + (2 * (cellp & 3) + 1) * half, py = Y0 + (2 * ((cellp >> 2) & 3) + 1) * half,
+                                    pz = Z0 + (2 * (cellp >> 4) + 1) * half;
+                    int cx, cy, cz;
+                    emb_dir(d, cx, cy, cz);
+                    const long long nc = cdot(cx, cy, cz, T.nx, T.ny, T.nz);
+                    if (nc == 0) continue;
+                    const int sn = nc > 0 ? 1 : -1;
+                    const long long ax = T.ax - px, ay = T.ay - py, az = T.az - pz;
+                    const long long bxx = T.bx - px, byy = T.by - py, bzz = T.bz - pz;
+                    const long long qx = T.cx - px, qy = T.cy - py, qz = T.cz - pz;
+                    int s1, s2, s3;
+                    const long long lim = 1ll << 14;
+                    if (T.lox - px > -lim && T.hix - px < lim && T.loy - py > -lim && T.hiy - py < lim && T.loz - pz > -lim &&
+                        T.hiz - pz < lim) {
+                        // every coordinate below 2^14 in magnitude: products < 2^28, sums < 2^31
+                        const int ax32 = (int)ax, ay32 = (int)ay, az32 = (int)az, bx32 = (int)bxx, by32 = (int)byy,
+                                  bz32 = (int)bzz, qx32 = (int)qx, qy32 = (int)qy, qz32 = (int)qz;
+                        int v1 = 0, v2 = 0, v3 = 0;
+                        if (cx) {
+                            const int e1 = ay32 * bz32 - az32 * by32, e2 = by32 * qz32 - bz32 * qy32, e3 = qy32 * az32 - qz32 * ay32;
+                            v1 += cx * e1; v2 += cx * e2; v3 += cx * e3;
+                        }
+                        if (cy) {
+                            const int e1 = az32 * bx32 - ax32 * bz32, e2 = bz32 * qx32 - bx32 * qz32, e3 = qz32 * ax32 - qx32 * az32;
+                            v1 += cy * e1; v2 += cy * e2; v3 += cy * e3;
+                        }
+                        if (cz) {
+                            const int e1 = ax32 * by32 - ay32 * bx32, e2 = bx32 * qy32 - by32 * qx32, e3 = qx32 * ay32 - qy32 * ax32;
+                            v1 += cz * e1; v2 += cz * e2; v3 += cz * e3;
+                        }
+                        s1 = plk_resolve(v1, cx, cy, cz, bxx - ax, byy - ay, bzz - az);
+                        if (s1 != sn) continue;
+                        s2 = plk_resolve(v2, cx, cy, cz, qx - bxx, qy - byy, qz - bzz);
+                        if (s2 != sn) continue;
+                        s3 = plk_resolve(v3, cx, cy, cz, ax - qx, ay - qy, az - qz);
+                        if (s3 != sn) continue;
+                    } else {
+                        const long long m1x = ay * bzz - az * byy, m1y = az * bxx - ax * bzz, m1z = ax * byy - ay * bxx;
+                        const long long m2x = byy * qz - bzz * qy, m2y = bzz * qx - bxx * qz, m2z = bxx * qy - byy * qx;
+                        const long long m3x = qy * az - qz * ay, m3y = qz * ax - qx * az, m3z = qx * ay - qy * ax;
+                        if (plk_resolve(cdot(cx, cy, cz, m1x, m1y, m1z), cx, cy, cz, bxx - ax, byy - ay, bzz - az) != sn) continue;
+                        if (plk_resolve(cdot(cx, cy, cz, m2x, m2y, m2z), cx, cy, cz, qx - bxx, qy - byy, qz - bzz) != sn) continue;
+                        if (plk_resolve(cdot(cx, cy, cz, m3x, m3y, m3z), cx, cy, cz, ax - qx, ay - qy, az - qz) != sn) continue;
+                    }
+                    const i128 D = mul128(T.nx, ax) + mul128(T.ny, ay) + mul128(T.nz, az);
+                    if (side_sign(D, T.nx, T.ny, T.nz) != sn) continue;                   // t <= 0
+                    if (side_sign(D - mul128(h, nc), T.nx, T.ny, T.nz) != -sn) continue;  // t >= 1
+                    const int kk = atomicAdd(&S.hcnt[slot], 1);
+                    if (kk < LE_BCAP) S.hit[slot][kk] = make_uint2((unsigned)T.id, (unsigned)d);
+                }
+            }
+            __syncwarp();
+        }
+        // resolve: the owner lane of each cell picks, per direction, the nearest crossing
+        if (active) {
+            const long long px = X0 + (2 * (t & 3) + 1) * half, py = Y0 + (2 * ((t >> 2) & 3) + 1) * half,
+                            pz = Z0 + (2 * (t >> 4) + 1) * half;
+            const int nh = S.hcnt[lane];
+            int slowT[27];
+            const bool slow = nh > LE_BCAP;
+            if (slow) scan_cell_slow(bin_ent, e0, e1, rec, px, py, pz, h, cm, slowT);
+            if (!slow) {
+                for (int d = 0; d < 27; ++d) S.best[d][lane] = -1;
+                for (int k = 0; k < nh; ++k) {
+                    const uint2 hv = S.hit[lane][k];
+                    const int d = (int)hv.y, tr = (int)hv.x, prev = S.best[d][lane];
+                    bool better = prev < 0;
+                    if (!better) {
+                        int cx, cy, cz;
+                        emb_dir(d, cx, cy, cz);
+                        i128 Nn, No;
+                        long long Mn, Mo;
+                        tri_NM(rec, tr, px, py, pz, cx, cy, cz, Nn, Mn);
+                        tri_NM(rec, prev, px, py, pz, cx, cy, cz, No, Mo);
+                        const i128 l = Nn * (i128)Mo, rr = No * (i128)Mn;
+                        better = l < rr || (l == rr && tr < prev);
+                    }
+                    if (better) S.best[d][lane] = tr;
+                }
+            }
+            uint32_t mm = cm;
+            int r = 0;
+            while (mm) {
+                const int d = __ffs(mm) - 1;
+                mm &= mm - 1;
+                int cx, cy, cz;
+                emb_dir(d, cx, cy, cz);
+                const int bT = slow ? slowT[d] : S.best[d][lane];
+                i128 bN = 0;
+                long long bM = 1;
+                if (bT >= 0) tri_NM(rec, bT, px, py, pz, cx, cy, cz, bN, bM);
+                const uint32_t o = base + off + r;
+                ++r;
+                o_cell[o] = (int32_t)(b * 64 + t);
+                o_dir[o] = (uint8_t)d;
+                if (bT >= 0) {
+                    o_q[o] = __fdiv_rn(i128_to_float(bN), (float)bM * (float)h);
+                    o_tri[o] = bT;
+                } else {
+                    o_q[o] = -1.0f;
+                    o_tri[o] = -1;
+                    emb_set_status(st, EMB_ERR_STATE);  // a fluid-to-solid link must cross the surface
+                }
+            }
+        }
+        __syncwarp();
+    }
+    }
+}
+
+__global__ void k_store_count(const uint32_t *__restrict__ blk_off, int64_t n, int64_t *__restrict__ d_count)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) *d_count = (int64_t)blk_off[n];
+}
+
+__global__ void k_set_status(int *st, int code) { emb_set_status(st, code); }
+
+__global__ void k_nonempty(const uint32_t *__restrict__ cnt, int64_t n, uint32_t *__restrict__ flag)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) flag[i] = cnt[i] ? 1u : 0u;
+}
+
+__global__ void k_compact_ids(const uint32_t *__restrict__ flag, const uint32_t *__restrict__ pos, int64_t n,
+                              uint32_t *__restrict__ out)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && flag[i]) out[pos[i]] = (uint32_t)i;
+}
+
+static void free_candidates(emb_forest f, cudaStream_t s)
+{
+    if (f->cand) cudaFreeAsync(f->cand, s);
+    f->cand = nullptr;
+    uint32_t **bufs[] = {&f->blk_off, &f->work, &f->work_n};
+    for (uint32_t **p : bufs) {
+        if (*p) cudaFreeAsync(*p, s);
+        *p = nullptr;
+    }
+}
+
+static emb_status build_candidates(emb_forest f, int lattice, cudaStream_t s)
+{
+    int L = f->max_level;
+    if (f->top != L || !f->lv[L].mask_valid) return EMB_ERR_STATE;
+    if (f->n_links >= 0 && f->cand_lattice == lattice && f->cand) return EMB_OK;
+    EmbLevel &lv = f->lv[L];
+    emb_status rc = emb_build_neighbors(lv, s);
+    if (rc != EMB_OK) return rc;
+    free_candidates(f, s);
+    EMB_CUDA_TRY(cudaMallocAsync(&f->cand, (lv.n * 26 + 1) * sizeof(uint64_t), s));
+    EMB_CUDA_TRY(cudaMallocAsync(&f->blk_off, (lv.n + 1) * sizeof(uint32_t), s));
+    EMB_CUDA_TRY(cudaMallocAsync(&f->work_n, (lv.n + 1) * sizeof(uint32_t), s));
+    EMB_CUDA_TRY(cudaMallocAsync(&f->work, (lv.n + 1) * sizeof(uint32_t), s));
+    if (!f->next) EMB_CUDA_TRY(cudaMalloc(&f->next, sizeof(unsigned int)));
+    uint32_t *cnt = nullptr, *flag = nullptr;
+    EMB_CUDA_TRY(cudaMallocAsync(&cnt, (lv.n + 1) * sizeof(uint32_t), s));
+    EMB_CUDA_TRY(cudaMallocAsync(&flag, (lv.n + 1) * sizeof(uint32_t), s));
+    EMB_CUDA_TRY(cudaMemsetAsync(cnt, 0, (lv.n + 1) * sizeof(uint32_t), s));
+    if (lv.n > 0)
+        EMB_LAUNCH((k_link_cand), emb_grid(lv.n, 128), 128, 0, s)(lv.mask, lv.nbr, lv.n, lattice, f->cand, cnt);
+    // work list: blocks with links, ascending; the count ends up at pos[n]
+    if (lv.n > 0) EMB_LAUNCH((k_nonempty), emb_grid(lv.n, 256), 256, 0, s)(cnt, lv.n, flag);
+    rc = emb_scan_u32(flag, f->work_n, lv.n, nullptr, s);
+    if (rc != EMB_OK) return rc;
+    if (lv.n > 0) EMB_LAUNCH((k_compact_ids), emb_grid(lv.n, 256), 256, 0, s)(flag, f->work_n, lv.n, f->work);
+    EMB_CUDA_TRY(cudaGetLastError());
+    uint64_t total = 0;
+    rc = emb_scan_u32(cnt, f->blk_off, lv.n, &total, s);
+    EMB_CUDA_TRY(cudaFreeAsync(cnt, s));
+    EMB_CUDA_TRY(cudaFreeAsync(flag, s));
+    if (rc != EMB_OK) return rc;
+    f->n_links = (int64_t)total;
+    f->cand_lattice = lattice;
+    return EMB_OK;
+}
+
+extern "C" emb_status emb_cutlinks_count(emb_forest f, int32_t lattice, int64_t *h_count, void *stream)
+{
+    if (!f || !h_count || (lattice != 19 && lattice != 27)) return EMB_ERR_BAD_INPUT;
+    emb_status rc = build_candidates(f, lattice, emb_stream(stream));
+    if (rc != EMB_OK) return rc;
+    *h_count = f->n_links;
+    return EMB_OK;
+}
+
+extern "C" emb_status emb_cutlinks(emb_forest f, emb_bins b, int32_t lattice, int32_t *d_cell, uint8_t *d_dir, float *d_q,
+                                   int32_t *d_tri, int64_t capacity, int64_t *d_count, void *stream)
+{
+    if (!f || !b || (lattice != 19 && lattice != 27) || capacity < 0) return EMB_ERR_BAD_INPUT;
+    if (b->f != f || b->level != f->max_level || !b->off) return EMB_ERR_STATE;
+    cudaStream_t s = emb_stream(stream);
+    int *st = emb_status_word();
+    if (!st) return EMB_ERR_CUDA;
+    emb_status rc = build_candidates(f, lattice, s);
+    if (rc != EMB_OK) return rc;
+    EmbLevel &lv = f->lv[f->max_level];
+    if (d_count) EMB_LAUNCH((k_store_count), 1, 32, 0, s)(f->blk_off, lv.n, d_count);
+    if (f->n_links > capacity) {
+        EMB_LAUNCH((k_set_status), 1, 1, 0, s)(st, EMB_ERR_CAPACITY);
+        EMB_CUDA_TRY(cudaGetLastError());
+        return EMB_ERR_CAPACITY;
+    }
+    if (f->n_links == 0) return EMB_OK;
+    if (!d_cell || !d_dir || !d_q || !d_tri) return EMB_ERR_BAD_INPUT;
+    LevelGeom g = level_geom(f, f->max_level);
+    static int grid = 0;
+    const size_t smem = LE_WARPS * sizeof(LeWarp);
+    if (!grid) {
+        EMB_CUDA_TRY(cudaFuncSetAttribute(k_link_emit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per_sm = 0, dev = 0, sms = 0;
+        EMB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_link_emit, LE_WARPS * 32, smem));
+        EMB_CUDA_TRY(cudaGetDevice(&dev));
+        EMB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        grid = (per_sm > 0 ? per_sm : 1) * sms;
+    }
+    // the work list sits in work_n[0 .. n) with its length at work_n[n]
+    EMB_CUDA_TRY(cudaMemsetAsync(f->next, 0, sizeof(unsigned int), s));
+    EMB_LAUNCH((k_link_emit), grid, LE_WARPS * 32, smem, s)(lv.key, f->work, f->work_n + lv.n, f->next, g,
+                                                           f->cand, f->blk_off,
+                                                           b->off, b->ent, b->m->rec, d_cell, d_dir, d_q, d_tri, st);
+    EMB_CUDA_TRY(cudaGetLastError());
+    return EMB_OK;
+}

@@ -1,0 +1,363 @@
+// Internal definitions shared by the translation units of libemb (sm_103a).
+//
+// Holds the handle layouts, the device status word, the level hash and the
+// exact integer predicates used by the kernels.  Predicates evaluate signs in
+// int64 / __int128 with the query point pushed by (e, e^2, e^3), e -> 0+
+// (simulation of simplicity), so that no query point ever lies on a plane,
+// edge or vertex of the mesh and every decision has one answer.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/emb.h"
+
+#define EMB_MAX_LEVELS 16
+
+typedef __int128 i128;
+
+// ---------------------------------------------------------------------------
+// error plumbing
+// ---------------------------------------------------------------------------
+#define EMB_CUDA_TRY(expr)                                 \
+    do {                                                   \
+        cudaError_t _e = (expr);                           \
+        if (_e != cudaSuccess) {                           \
+            emb_note_cuda_error(_e, #expr, __FILE__, __LINE__); \
+            return EMB_ERR_CUDA;                           \
+        }                                                  \
+    } while (0)
+
+void emb_note_cuda_error(cudaError_t e, const char *what, const char *file, int line);
+
+// Every kernel launch goes through EMB_LAUNCH((kernel), grid, block, smem, stream)(args), which
+// bumps a host-side counter read by emb_launch_count.
+void emb_count_launch();
+#define EMB_STRIP(...) __VA_ARGS__
+#define EMB_LAUNCH(kern, ...) emb_count_launch(), EMB_STRIP kern<<<__VA_ARGS__>>>
+int *emb_status_word();  // device pointer of the current device's status word (lazily created)
+cudaStream_t emb_stream(void *s);
+
+__device__ __forceinline__ void emb_set_status(int *st, int code)
+{
+    atomicCAS(st, 0, code);
+}
+
+// ---------------------------------------------------------------------------
+// handles
+// ---------------------------------------------------------------------------
+struct emb_mesh_s {
+    int32_t R, r_o, k;
+    int64_t V, T;
+    int4 *rec;      // T x 3 records {X, Y, Z, vertex id}
+    int device;
+};
+
+struct EmbLevel {
+    int64_t n = 0;
+    int64_t nb_axis = 0;       // blocks per axis at this level (R << L)
+    uint64_t *key = nullptr;   // block keys, ascending ((bz << 42) | (by << 21) | bx)
+    uint64_t *hkey = nullptr;  // open-addressing hash: key -> block id
+    int32_t *hval = nullptr;
+    int64_t hcap = 0;          // power of two
+    uint64_t *mask = nullptr;  // solid mask per block (after emb_voxelize)
+    int32_t *nbr = nullptr;    // n x 26 neighbour ids (built on demand)
+    // rank bitmap over the dense (bz, by, bx) positions of the level: bit = block exists;
+    // blocks are numbered in that linear order, so a block's id is the rank of its bit
+    uint64_t *bits = nullptr;
+    uint32_t *wpre = nullptr;  // exclusive popcount prefix per 64-bit word
+    int mask_valid = 0;
+};
+
+#define EMB_BITMAP_MAX_BITS (1ll << 32)
+
+// Block lookup of one level, passed by value to kernels: the rank bitmap when it
+// exists (two loads, L2-resident at the sizes used here), else the hash.
+struct EmbLookup {
+    const uint64_t *hkey;
+    const int32_t *hval;
+    int64_t hcap;
+    const uint64_t *bits;
+    const uint32_t *wpre;
+    int64_t nb;
+};
+
+static inline EmbLookup emb_lookup_of(const EmbLevel &lv)
+{
+    EmbLookup l;
+    l.hkey = lv.hkey;
+    l.hval = lv.hval;
+    l.hcap = lv.hcap;
+    l.bits = lv.bits;
+    l.wpre = lv.wpre;
+    l.nb = lv.nb_axis;
+    return l;
+}
+
+struct emb_forest_s {
+    int32_t R, r_o, k, max_level, top;
+    EmbLevel lv[EMB_MAX_LEVELS];
+    // cut-link candidates at the finest level (built by emb_cutlinks_count / emb_cutlinks)
+    uint64_t *cand = nullptr;     // per finest block x 26 directions: fluid cells whose neighbour along c_d is solid
+    uint32_t *blk_off = nullptr;  // per finest block: exclusive link offset (n+1 entries)
+    uint32_t *work = nullptr;     // ids of finest blocks with at least one link; count at work_n[0]
+    uint32_t *work_n = nullptr;
+    unsigned int *next = nullptr; // work-queue cursor of the persistent link kernel
+    int32_t cand_lattice = 0;
+    int64_t n_links = -1;
+    int device;
+};
+
+struct emb_bins_s {
+    emb_mesh m;
+    emb_forest f;
+    int32_t level, lattice;
+    uint32_t *flist = nullptr;  // filtered triangle ids (ascending)
+    int64_t nf = 0;
+    uint32_t *off = nullptr;    // finest level only: CSR offsets (n_blocks + 1)
+    uint32_t *ent = nullptr;    // triangle ids
+    int64_t npairs = 0;
+};
+
+// Geometry of one level in frame units.
+struct LevelGeom {
+    long long h, half, W;  // cell size, half cell, block width
+    long long ncell;       // cells per axis
+    long long nb;          // blocks per axis
+};
+
+static inline LevelGeom level_geom(const emb_forest_s *f, int L)
+{
+    LevelGeom g;
+    g.h = 1ll << (18 - f->k - L);
+    g.half = g.h >> 1;
+    g.W = 4 * g.h;
+    g.nb = (long long)f->R << L;
+    g.ncell = 4 * g.nb;
+    return g;
+}
+
+// ---------------------------------------------------------------------------
+// small host helpers (defined in emb_common.cu)
+// ---------------------------------------------------------------------------
+emb_status emb_scan_u32(const uint32_t *d_in, uint32_t *d_out, int64_t n, uint64_t *h_total, cudaStream_t s);
+emb_status emb_build_hash(EmbLevel &lv, cudaStream_t s);
+emb_status emb_build_neighbors(EmbLevel &lv, cudaStream_t s);
+int emb_grid(int64_t n, int block);
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+#define EMB_KEY_BITS 21
+#define EMB_KEY_MASK ((1ull << EMB_KEY_BITS) - 1ull)
+#define EMB_HASH_EMPTY 0xFFFFFFFFFFFFFFFFull
+
+__host__ __device__ __forceinline__ uint64_t emb_key(int64_t bx, int64_t by, int64_t bz)
+{
+    return ((uint64_t)bz << (2 * EMB_KEY_BITS)) | ((uint64_t)by << EMB_KEY_BITS) | (uint64_t)bx;
+}
+
+__host__ __device__ __forceinline__ uint64_t emb_hash_mix(uint64_t k)
+{
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdull;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ull;
+    k ^= k >> 33;
+    return k;
+}
+
+// Block id of key in a level hash, or -1.  Probing is bounded by the table size.
+__device__ __forceinline__ int32_t emb_hash_find(const uint64_t *__restrict__ hkey, const int32_t *__restrict__ hval,
+                                                 int64_t hcap, uint64_t key)
+{
+    uint64_t m = (uint64_t)hcap - 1;
+    uint64_t s = emb_hash_mix(key) & m;
+    for (int64_t i = 0; i < hcap; ++i) {
+        uint64_t k = __ldg(hkey + s);
+        if (k == key) return __ldg(hval + s);
+        if (k == EMB_HASH_EMPTY) return -1;
+        s = (s + 1) & m;
+    }
+    return -1;
+}
+
+// Block id at (bx, by, bz) of a level, or -1 (coordinates must lie in [0, nb)).
+__device__ __forceinline__ int32_t emb_lookup(const EmbLookup &l, int64_t bx, int64_t by, int64_t bz)
+{
+    if (l.bits) {
+        const int64_t lin = (bz * l.nb + by) * l.nb + bx;
+        const uint64_t w = __ldg(l.bits + (lin >> 6));
+        const int sh = (int)(lin & 63);
+        if (!((w >> sh) & 1ull)) return -1;
+        return (int32_t)(__ldg(l.wpre + (lin >> 6)) + __popcll(w & ((1ull << sh) - 1ull)));
+    }
+    return emb_hash_find(l.hkey, l.hval, l.hcap, emb_key(bx, by, bz));
+}
+
+__device__ __forceinline__ int64_t emb_floordiv(int64_t a, int64_t b)  // b > 0
+{
+    int64_t q = a / b;
+    return (a % b != 0 && a < 0) ? q - 1 : q;
+}
+
+__device__ __forceinline__ int sgn_ll(long long v) { return (v > 0) - (v < 0); }
+__device__ __forceinline__ int sgn_i128(i128 v) { return (v > 0) - (v < 0); }
+
+// Lattice vectors in the order documented in emb.h.  Component d of c_i is
+// ((K_d >> 2i) & 3) - 1 with the three packed constants below (pure ALU, so a
+// divergent index costs no memory access).
+#define EMB_DIR_KX 0x20889548889549ull
+#define EMB_DIR_KY 0xa088895609495ull
+#define EMB_DIR_KZ 0x8a0a0a0954955ull
+__host__ __device__ __forceinline__ void emb_dir(int i, int &cx, int &cy, int &cz)
+{
+    cx = (int)((EMB_DIR_KX >> (2 * i)) & 3ull) - 1;
+    cy = (int)((EMB_DIR_KY >> (2 * i)) & 3ull) - 1;
+    cz = (int)((EMB_DIR_KZ >> (2 * i)) & 3ull) - 1;
+}
+
+// Set of directions (bit i = direction i) whose component on `axis` equals `val`.
+__host__ __device__ constexpr uint32_t emb_dirs_with(int axis, int val)
+{
+    uint32_t m = 0;
+    for (int i = 0; i < 27; ++i) {
+        unsigned long long K = axis == 0 ? EMB_DIR_KX : (axis == 1 ? EMB_DIR_KY : EMB_DIR_KZ);
+        if ((int)((K >> (2 * i)) & 3ull) - 1 == val) m |= 1u << i;
+    }
+    return m;
+}
+
+// Orientation of the perturbed query (py + e^2, pz + e^3) against the yz
+// projection of edge U -> V:  (V-U)_y (P-U)_z - (V-U)_z (P-U)_y, with the
+// e^2 coefficient -(V-U)_z and the e^3 coefficient (V-U)_y deciding ties.
+__device__ __forceinline__ int emb_orient_yz(int uy, int uz, int vy, int vz, int py, int pz)
+{
+    long long ey = (long long)vy - uy, ez = (long long)vz - uz;
+    long long o = ey * ((long long)pz - uz) - ez * ((long long)py - uy);
+    if (o != 0) return o > 0 ? 1 : -1;
+    if (ez != 0) return ez > 0 ? -1 : 1;
+    return ey > 0 ? 1 : (ey < 0 ? -1 : 0);
+}
+
+// i128 from the product of two int64.
+__device__ __forceinline__ i128 mul128(long long a, long long b) { return (i128)a * (i128)b; }
+
+// Float approximation of a non-negative i128 (relative error below 2^-23).
+__device__ __forceinline__ float i128_to_float(i128 v)
+{
+    unsigned long long hi = (unsigned long long)(v >> 64);
+    unsigned long long lo = (unsigned long long)v;
+    return (float)hi * 18446744073709551616.0f + (float)lo;
+}
+
+// Exact overlap of a triangle with the closed box [lo, hi] (separating axes:
+// the box normals, the face normal and the 9 edge x axis products), computed
+// in coordinates relative to the box's low corner.
+static __device__ __noinline__ bool emb_tri_box(const int4 &A, const int4 &B, const int4 &C, long long lx, long long ly,
+                                            long long lz, long long hx, long long hy, long long hz)
+{
+    long long v[3][3] = {{A.x - lx, A.y - ly, A.z - lz}, {B.x - lx, B.y - ly, B.z - lz}, {C.x - lx, C.y - ly, C.z - lz}};
+    long long E[3] = {hx - lx, hy - ly, hz - lz};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        long long mn = min(v[0][d], min(v[1][d], v[2][d]));
+        long long mx = max(v[0][d], max(v[1][d], v[2][d]));
+        if (mn > E[d] || mx < 0) return false;
+    }
+    long long f[3][3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        f[0][d] = v[1][d] - v[0][d];
+        f[1][d] = v[2][d] - v[1][d];
+        f[2][d] = v[0][d] - v[2][d];
+    }
+    // face normal: the triangle projects to the single value n.v0
+    long long n0 = f[0][1] * f[1][2] - f[0][2] * f[1][1];
+    long long n1 = f[0][2] * f[1][0] - f[0][0] * f[1][2];
+    long long n2 = f[0][0] * f[1][1] - f[0][1] * f[1][0];
+    {
+        i128 p = mul128(n0, v[0][0]) + mul128(n1, v[0][1]) + mul128(n2, v[0][2]);
+        i128 t0 = mul128(n0, E[0]), t1 = mul128(n1, E[1]), t2 = mul128(n2, E[2]);
+        i128 bmin = (t0 < 0 ? t0 : 0) + (t1 < 0 ? t1 : 0) + (t2 < 0 ? t2 : 0);
+        i128 bmax = (t0 > 0 ? t0 : 0) + (t1 > 0 ? t1 : 0) + (t2 > 0 ? t2 : 0);
+        if (p < bmin || p > bmax) return false;
+    }
+    // edge axes e_d x f_j: (e_x x f) = (0, -f_z, f_y), (e_y x f) = (f_z, 0, -f_x), (e_z x f) = (-f_y, f_x, 0)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            long long a[3];
+            if (d == 0) { a[0] = 0; a[1] = -f[j][2]; a[2] = f[j][1]; }
+            else if (d == 1) { a[0] = f[j][2]; a[1] = 0; a[2] = -f[j][0]; }
+            else { a[0] = -f[j][1]; a[1] = f[j][0]; a[2] = 0; }
+            long long p0 = a[0] * v[0][0] + a[1] * v[0][1] + a[2] * v[0][2];
+            long long p1 = a[0] * v[1][0] + a[1] * v[1][1] + a[2] * v[1][2];
+            long long p2 = a[0] * v[2][0] + a[1] * v[2][1] + a[2] * v[2][2];
+            long long pmin = min(p0, min(p1, p2)), pmax = max(p0, max(p1, p2));
+            long long t0 = a[0] * E[0], t1 = a[1] * E[1], t2 = a[2] * E[2];
+            long long bmin = min(t0, 0ll) + min(t1, 0ll) + min(t2, 0ll);
+            long long bmax = max(t0, 0ll) + max(t1, 0ll) + max(t2, 0ll);
+            if (pmax < bmin || pmin > bmax) return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ bool emb_point_in_box(const int4 &P, long long lx, long long ly, long long lz, long long hx,
+                                                 long long hy, long long hz)
+{
+    return P.x >= lx && P.x <= hx && P.y >= ly && P.y <= hy && P.z >= lz && P.z <= hz;
+}
+
+// Enumerate the block range [b0, b1] along one axis whose boxes dilated by dil
+// meet the interval [mn, mx] (block width W, nb blocks on the axis).
+__device__ __forceinline__ void emb_block_range(long long mn, long long mx, long long W, long long dil, long long nb,
+                                                long long &b0, long long &b1)
+{
+    b0 = -emb_floordiv(-(mn - dil - W), W);  // ceil((mn - dil - W) / W)
+    b1 = emb_floordiv(mx + dil, W);
+    if (b0 < 0) b0 = 0;
+    if (b1 > nb - 1) b1 = nb - 1;
+}
+
+// Range of line indices j with centre (2j+1) half inside [mn, mx], clamped.
+__device__ __forceinline__ void line_range(long long mn, long long mx, long long h, long long half, long long ncell,
+                                           long long &j0, long long &j1)
+{
+    j0 = -emb_floordiv(-(mn - half), h);
+    j1 = emb_floordiv(mx - half, h);
+    if (j0 < 0) j0 = 0;
+    if (j1 > ncell - 1) j1 = ncell - 1;
+}
+
+// ---------------------------------------------------------------------------
+// warp-cooperative visit of (triangle, block) overlaps
+// ---------------------------------------------------------------------------
+// A warp takes 32 consecutive triangles (neighbours in a mesh's storage order
+// are usually neighbours in space), forms the union of the block ranges their
+// dilated boxes can touch, and lets each lane test whole blocks of that union
+// against all 32 triangles.  This trades 32 independent lookups per candidate
+// block for one.  When the union is large (above EMB_WU_MAX blocks) or loose
+// (more than a quarter of the warp's summed per-triangle candidates), the warp
+// falls back to the per-triangle enumeration.
+#define EMB_WU_WARPS 4
+#define EMB_WU_MAX 2048
+
+struct WuTri {
+    int4 A[32], B[32], C[32];
+    int lo[3][32], hi[3][32];
+};
+
+// Overlap of triangle j of the tile with the closed box [l, u] (exact).
+__device__ __forceinline__ bool wu_overlap(const WuTri &S, int j, long long lx, long long ly, long long lz, long long ux,
+                                           long long uy, long long uz)
+{
+    if (S.lo[0][j] > ux || S.hi[0][j] < lx || S.lo[1][j] > uy || S.hi[1][j] < ly || S.lo[2][j] > uz || S.hi[2][j] < lz)
+        return false;
+    const int4 A = S.A[j], B = S.B[j], C = S.C[j];
+    return emb_point_in_box(A, lx, ly, lz, ux, uy, uz) || emb_point_in_box(B, lx, ly, lz, ux, uy, uz) ||
+           emb_point_in_box(C, lx, ly, lz, ux, uy, uz) || emb_tri_box(A, B, C, lx, ly, lz, ux, uy, uz);
+}
+

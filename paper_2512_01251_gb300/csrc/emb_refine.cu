@@ -1,0 +1,123 @@
+// Near-wall refinement flags (Sec. 3.4, "Refinement Flagging and Propagation").
+//
+// The paper marks solid-boundary blocks and propagates flags block by block a
+// number of layers set by the near-wall distance (Eq. N_prop).  Here the
+// criterion is evaluated directly and exactly: block B of level L is flagged iff
+// some triangle overlaps B's closed box dilated by (rho_L - 1/2) h_L, i.e. iff a
+// cell centre of B lies within L-infinity distance rho_L h_L of the surface.
+// rho equals `band` one level above the finest and grows towards the root as
+// rho_L = max(band, rho_{L+1}/2 + 5/2), which keeps all 26 neighbours of every
+// refined block present (2:1 balance) and leaves unrefined blocks surface-free.
+//
+// Warp-cooperative over 32 consecutive triangles (see emb_internal.cuh): each
+// candidate block of the warp's union range is looked up once and tested
+// against the 32 triangles; flags are idempotent byte stores.
+#include "emb_internal.cuh"
+
+__global__ void __launch_bounds__(EMB_WU_WARPS * 32) k_refine(const int4 *__restrict__ rec, int64_t T, LevelGeom g,
+                                                              long long dil, EmbLookup lk, uint8_t *__restrict__ flags)
+{
+    __shared__ WuTri tiles[EMB_WU_WARPS];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WuTri &S = tiles[w];
+    const int64_t t = ((int64_t)blockIdx.x * EMB_WU_WARPS + w) * 32 + lane;
+    const bool valid = t < T;
+    long long b0[3] = {1ll << 40, 1ll << 40, 1ll << 40}, b1[3] = {-1, -1, -1};
+    int4 A = make_int4(0, 0, 0, 0), B = A, C = A;
+    if (valid) {
+        A = rec[3 * t];
+        B = rec[3 * t + 1];
+        C = rec[3 * t + 2];
+        emb_block_range(min(A.x, min(B.x, C.x)), max(A.x, max(B.x, C.x)), g.W, dil, g.nb, b0[0], b1[0]);
+        emb_block_range(min(A.y, min(B.y, C.y)), max(A.y, max(B.y, C.y)), g.W, dil, g.nb, b0[1], b1[1]);
+        emb_block_range(min(A.z, min(B.z, C.z)), max(A.z, max(B.z, C.z)), g.W, dil, g.nb, b0[2], b1[2]);
+    }
+    S.A[lane] = A;
+    S.B[lane] = B;
+    S.C[lane] = C;
+    S.lo[0][lane] = valid ? min(A.x, min(B.x, C.x)) : 0x7fffffff;
+    S.hi[0][lane] = valid ? max(A.x, max(B.x, C.x)) : -0x7fffffff;
+    S.lo[1][lane] = min(A.y, min(B.y, C.y));
+    S.hi[1][lane] = max(A.y, max(B.y, C.y));
+    S.lo[2][lane] = min(A.z, min(B.z, C.z));
+    S.hi[2][lane] = max(A.z, max(B.z, C.z));
+    __syncwarp();
+    int u0[3], u1[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        u0[d] = __reduce_min_sync(0xffffffffu, (int)min(b0[d], (long long)0x7fffffff));
+        u1[d] = __reduce_max_sync(0xffffffffu, (int)b1[d]);
+    }
+    const long long nx = u1[0] - u0[0] + 1, ny = u1[1] - u0[1] + 1, nz = u1[2] - u0[2] + 1;
+    if (nx <= 0 || ny <= 0 || nz <= 0) return;
+    const long long total = nx * ny * nz;
+    // per-triangle candidates summed over the warp: the union pays off only when it is much smaller
+    const long long own = valid ? (b1[0] >= b0[0] && b1[1] >= b0[1] && b1[2] >= b0[2]
+                                       ? (b1[0] - b0[0] + 1) * (b1[1] - b0[1] + 1) * (b1[2] - b0[2] + 1)
+                                       : 0)
+                                : 0;
+    const unsigned own_sum = __reduce_add_sync(0xffffffffu, (unsigned)min(own, 1ll << 20));
+    if (total <= EMB_WU_MAX && 4 * total <= (long long)own_sum) {
+        for (long long c = lane; c < total; c += 32) {
+            const long long bx = u0[0] + c % nx, by = u0[1] + (c / nx) % ny, bz = u0[2] + c / (nx * ny);
+            const int32_t id = emb_lookup(lk, bx, by, bz);
+            if (id < 0 || flags[id]) continue;
+            const long long lx = bx * g.W - dil, ly = by * g.W - dil, lz = bz * g.W - dil;
+            const long long hx = lx + g.W + 2 * dil, hy = ly + g.W + 2 * dil, hz = lz + g.W + 2 * dil;
+            for (int j = 0; j < 32; ++j) {
+                if (wu_overlap(S, j, lx, ly, lz, hx, hy, hz)) {
+                    flags[id] = 1;
+                    break;
+                }
+            }
+        }
+        return;
+    }
+    // large or loose union: each lane enumerates the blocks of its own triangle
+    if (!valid) return;
+    for (long long bz = b0[2]; bz <= b1[2]; ++bz)
+        for (long long by = b0[1]; by <= b1[1]; ++by)
+            for (long long bx = b0[0]; bx <= b1[0]; ++bx) {
+                int32_t id = emb_lookup(lk, bx, by, bz);
+                if (id < 0) continue;
+                if (*((volatile uint8_t *)flags + id)) continue;
+                long long lx = bx * g.W - dil, ly = by * g.W - dil, lz = bz * g.W - dil;
+                long long hx = lx + g.W + 2 * dil, hy = ly + g.W + 2 * dil, hz = lz + g.W + 2 * dil;
+                if (emb_point_in_box(A, lx, ly, lz, hx, hy, hz) || emb_point_in_box(B, lx, ly, lz, hx, hy, hz) ||
+                    emb_point_in_box(C, lx, ly, lz, hx, hy, hz) || emb_tri_box(A, B, C, lx, ly, lz, hx, hy, hz))
+                    flags[id] = 1;
+            }
+}
+
+// (rho_L - 1/2) h_L in frame units, or -1 if it is not an integer.
+static long long refine_dilation(const emb_forest_s *f, int L, int band)
+{
+    const int sh = 16;  // rho is kept as an integer multiple of 2^-16
+    long long rho = (long long)band << sh;
+    for (int l = f->max_level - 1; l > L; --l) {
+        long long cand = rho / 2 + (5ll << (sh - 1));
+        rho = cand > ((long long)band << sh) ? cand : ((long long)band << sh);
+    }
+    long long h = 1ll << (18 - f->k - L);
+    long long num = (rho - (1ll << (sh - 1))) * h;
+    if (num % (1ll << sh) != 0) return -1;
+    return num >> sh;
+}
+
+extern "C" emb_status emb_refine_flags(emb_forest f, emb_bins b, int32_t level, int32_t band, uint8_t *d_flags,
+                                       void *stream)
+{
+    if (!f || !b || band < 1 || band > (1 << 20)) return EMB_ERR_BAD_INPUT;
+    if (b->f != f || level < 0 || level > f->top || level >= f->max_level) return EMB_ERR_STATE;
+    const EmbLevel &lv = f->lv[level];
+    if (lv.n == 0) return EMB_OK;
+    if (!d_flags) return EMB_ERR_BAD_INPUT;
+    long long dil = refine_dilation(f, level, band);
+    if (dil < 0) return EMB_ERR_RANGE;
+    cudaStream_t s = emb_stream(stream);
+    LevelGeom g = level_geom(f, level);
+    EMB_CUDA_TRY(cudaMemsetAsync(d_flags, 0, lv.n, s));
+    EMB_LAUNCH((k_refine), emb_grid(b->m->T, 32 * EMB_WU_WARPS), 32 * EMB_WU_WARPS, 0, s)(b->m->rec, b->m->T, g, dil, emb_lookup_of(lv), d_flags);
+    EMB_CUDA_TRY(cudaGetLastError());
+    return EMB_OK;
+}

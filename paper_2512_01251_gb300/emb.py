@@ -1,0 +1,317 @@
+"""Python binding of libemb: the C ABI calls under the same names, taking torch
+CUDA tensors (argument marshalling only), plus ``embed``, which chains the calls
+of the whole path (bin -> voxelize -> refine flags -> refine, per level, then the
+cut-link table) the way Sec. 3.4 orders them.
+
+Status codes other than EMB_OK raise ``EmbError``.  Device-side errors are
+collected by ``emb_status_get`` (``embed`` checks it once at the end).
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass, field
+
+import torch
+
+from ._lib import load
+
+EMB_OK = 0
+EMB_ERR_BAD_INPUT = -1
+EMB_ERR_NOT_WATERTIGHT = -2
+EMB_ERR_CAPACITY = -3
+EMB_ERR_CUDA = -4
+EMB_ERR_TIMEOUT = -5
+EMB_ERR_RANGE = -6
+EMB_ERR_STATE = -7
+
+
+class EmbError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        name = load().emb_status_string(code).decode()
+        super().__init__(f"{where}: {name} ({code})")
+
+
+def _check(code: int, where: str):
+    if code != EMB_OK:
+        raise EmbError(code, where)
+
+
+def _ptr(t: torch.Tensor | None):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class _Handle:
+    _destroy = None
+
+    def __init__(self, h, keep=()):
+        self.h = h
+        self._keep = keep
+
+    def close(self):
+        if self.h:
+            getattr(load(), self._destroy)(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Mesh(_Handle):
+    _destroy = "emb_mesh_destroy"
+
+
+class Forest(_Handle):
+    _destroy = "emb_forest_destroy"
+
+
+class Bins(_Handle):
+    _destroy = "emb_bins_destroy"
+
+
+# --------------------------------------------------------------------------- #
+# the C ABI, one wrapper per call
+# --------------------------------------------------------------------------- #
+def emb_status_get(stream=None) -> int:
+    out = ctypes.c_int32(0)
+    _check(load().emb_status_get(_stream(stream), ctypes.byref(out)), "emb_status_get")
+    return out.value
+
+
+def emb_launch_count() -> int:
+    out = ctypes.c_int64(0)
+    _check(load().emb_launch_count(ctypes.byref(out)), "emb_launch_count")
+    return out.value
+
+
+def emb_directions() -> list:
+    buf = (ctypes.c_int32 * 81)()
+    _check(load().emb_directions(buf), "emb_directions")
+    return [tuple(buf[3 * i:3 * i + 3]) for i in range(27)]
+
+
+def emb_mesh_create(verts: torch.Tensor, tris: torch.Tensor, R: int, check_watertight: bool = True,
+                    stream=None) -> Mesh:
+    verts = verts.to(device="cuda", dtype=torch.float32).contiguous()
+    tris = tris.to(device="cuda", dtype=torch.int32).contiguous()
+    h = ctypes.c_void_p()
+    rc = load().emb_mesh_create(_ptr(verts), _ptr(tris), verts.shape[0], tris.shape[0], int(R),
+                                int(bool(check_watertight)), _stream(stream), ctypes.byref(h))
+    _check(rc, "emb_mesh_create")
+    m = Mesh(h)
+    m.V, m.T, m.R = verts.shape[0], tris.shape[0], int(R)
+    return m
+
+
+def emb_forest_root(R: int, max_level: int, stream=None) -> Forest:
+    h = ctypes.c_void_p()
+    _check(load().emb_forest_root(int(R), int(max_level), _stream(stream), ctypes.byref(h)), "emb_forest_root")
+    f = Forest(h)
+    f.R, f.max_level = int(R), int(max_level)
+    return f
+
+
+def emb_forest_refine(forest: Forest, level: int, flags: torch.Tensor, stream=None):
+    _check(load().emb_forest_refine(forest.h, int(level), _ptr(flags), _stream(stream)), "emb_forest_refine")
+
+
+def emb_forest_num_blocks(forest: Forest, level: int) -> int:
+    out = ctypes.c_int64(0)
+    _check(load().emb_forest_num_blocks(forest.h, int(level), ctypes.byref(out)), "emb_forest_num_blocks")
+    return out.value
+
+
+def emb_forest_blocks(forest: Forest, level: int, stream=None) -> torch.Tensor:
+    n = emb_forest_num_blocks(forest, level)
+    out = torch.empty((n, 3), dtype=torch.int32, device="cuda")
+    _check(load().emb_forest_blocks(forest.h, int(level), _ptr(out), _stream(stream)), "emb_forest_blocks")
+    return out
+
+
+def emb_forest_neighbors(forest: Forest, level: int, stream=None) -> torch.Tensor:
+    n = emb_forest_num_blocks(forest, level)
+    out = torch.empty((n, 26), dtype=torch.int32, device="cuda")
+    _check(load().emb_forest_neighbors(forest.h, int(level), _ptr(out), _stream(stream)), "emb_forest_neighbors")
+    return out
+
+
+def emb_forest_masks(forest: Forest, level: int, stream=None) -> torch.Tensor:
+    n = emb_forest_num_blocks(forest, level)
+    out = torch.empty(n, dtype=torch.int64, device="cuda")
+    _check(load().emb_forest_masks(forest.h, int(level), _ptr(out), _stream(stream)), "emb_forest_masks")
+    return out
+
+
+def emb_bin(mesh: Mesh, forest: Forest, level: int, lattice: int = 19, stream=None) -> Bins:
+    h = ctypes.c_void_p()
+    _check(load().emb_bin(mesh.h, forest.h, int(level), int(lattice), _stream(stream), ctypes.byref(h)), "emb_bin")
+    b = Bins(h, keep=(mesh, forest))
+    b.level = int(level)
+    return b
+
+
+def emb_bins_stats(bins: Bins):
+    a, b = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(load().emb_bins_stats(bins.h, ctypes.byref(a), ctypes.byref(b)), "emb_bins_stats")
+    return a.value, b.value
+
+
+def emb_bins_copy(bins: Bins, forest: Forest | None = None, stream=None) -> dict:
+    """Filtered triangle ids and, at the finest level, the CSR bins (int32 tensors)."""
+    nf, npairs = emb_bins_stats(bins)
+    out = dict(filtered=torch.empty(max(nf, 1), dtype=torch.int32, device="cuda"))
+    want_csr = forest is not None
+    if want_csr:
+        n = emb_forest_num_blocks(forest, bins.level)
+        out["off"] = torch.empty(n + 1, dtype=torch.int32, device="cuda")
+        out["ent"] = torch.empty(max(npairs, 1), dtype=torch.int32, device="cuda")
+    _check(load().emb_bins_copy(bins.h, _ptr(out["filtered"]), _ptr(out.get("off")), _ptr(out.get("ent")),
+                                _stream(stream)), "emb_bins_copy")
+    out["filtered"] = out["filtered"][:nf]
+    if want_csr:
+        out["ent"] = out["ent"][:npairs]
+    return out
+
+
+def emb_voxelize(forest: Forest, bins: Bins, level: int, out: torch.Tensor | None = None, stream=None):
+    """Solid mask words of `level` (int64 tensor holding the uint64 bit patterns)."""
+    if out is None:
+        out = torch.empty(emb_forest_num_blocks(forest, level), dtype=torch.int64, device="cuda")
+    _check(load().emb_voxelize(forest.h, bins.h, int(level), _ptr(out), _stream(stream)), "emb_voxelize")
+    return out
+
+
+def emb_refine_flags(forest: Forest, bins: Bins, level: int, band: int, out: torch.Tensor | None = None,
+                     stream=None):
+    if out is None:
+        out = torch.empty(emb_forest_num_blocks(forest, level), dtype=torch.uint8, device="cuda")
+    _check(load().emb_refine_flags(forest.h, bins.h, int(level), int(band), _ptr(out), _stream(stream)),
+           "emb_refine_flags")
+    return out
+
+
+def emb_cutlinks_count(forest: Forest, lattice: int, stream=None) -> int:
+    out = ctypes.c_int64(0)
+    _check(load().emb_cutlinks_count(forest.h, int(lattice), ctypes.byref(out), _stream(stream)), "emb_cutlinks_count")
+    return out.value
+
+
+def emb_cutlinks(forest: Forest, bins: Bins, lattice: int, capacity: int | None = None, out: dict | None = None,
+                 stream=None) -> dict:
+    """Cut-link table {cell int32, dir uint8, q float32, tri int32, count int64 (device)}."""
+    if capacity is None:
+        capacity = emb_cutlinks_count(forest, lattice, stream)
+    if out is None:
+        out = dict(cell=torch.empty(max(capacity, 1), dtype=torch.int32, device="cuda"),
+                   dir=torch.empty(max(capacity, 1), dtype=torch.uint8, device="cuda"),
+                   q=torch.empty(max(capacity, 1), dtype=torch.float32, device="cuda"),
+                   tri=torch.empty(max(capacity, 1), dtype=torch.int32, device="cuda"),
+                   count=torch.zeros(1, dtype=torch.int64, device="cuda"))
+    rc = load().emb_cutlinks(forest.h, bins.h, int(lattice), _ptr(out["cell"]), _ptr(out["dir"]), _ptr(out["q"]),
+                             _ptr(out["tri"]), int(capacity), _ptr(out["count"]), _stream(stream))
+    _check(rc, "emb_cutlinks")
+    n = capacity
+    return {k: (v[:n] if k != "count" else v) for k, v in out.items()}
+
+
+def emb_mex_force(forest: Forest, lattice: int, cell, dir, q, pop: torch.Tensor, out: torch.Tensor | None = None,
+                  stream=None) -> torch.Tensor:
+    if out is None:
+        out = torch.empty(3, dtype=torch.float32, device="cuda")
+    _check(load().emb_mex_force(forest.h, int(lattice), _ptr(cell), _ptr(dir), _ptr(q), q.numel(), _ptr(pop),
+                                pop.shape[1], _ptr(out), _stream(stream)), "emb_mex_force")
+    return out
+
+
+def emb_mex_force_backward(forest: Forest, lattice: int, cell, dir, q, pop: torch.Tensor, gF: torch.Tensor,
+                           out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    if out is None:
+        out = torch.empty_like(q)
+    gF = gF.to(device="cuda", dtype=torch.float32).contiguous()
+    _check(load().emb_mex_force_backward(forest.h, int(lattice), _ptr(cell), _ptr(dir), _ptr(q), q.numel(),
+                                         _ptr(pop), pop.shape[1], _ptr(gF), _ptr(out), _stream(stream)),
+           "emb_mex_force_backward")
+    return out
+
+
+def emb_cutlinks_backward(mesh: Mesh, forest: Forest, cell, dir, q, tri, gq: torch.Tensor,
+                          out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    if out is None:
+        out = torch.empty((mesh.V, 3), dtype=torch.float32, device="cuda")
+    gq = gq.to(device="cuda", dtype=torch.float32).contiguous()
+    _check(load().emb_cutlinks_backward(mesh.h, forest.h, _ptr(cell), _ptr(dir), _ptr(q), _ptr(tri), q.numel(),
+                                        _ptr(gq), _ptr(out), _stream(stream)), "emb_cutlinks_backward")
+    return out
+
+
+# --------------------------------------------------------------------------- #
+# the whole path
+# --------------------------------------------------------------------------- #
+@dataclass
+class Embedding:
+    mesh: Mesh
+    forest: Forest
+    levels: int
+    lattice: int
+    blocks: list = field(default_factory=list)   # per level (n, 3) int32, filled by fetch_blocks
+    masks: list = field(default_factory=list)    # per level int64 mask words
+    flags: list = field(default_factory=list)    # per level < finest, uint8
+    links: dict | None = None
+    bins: list = field(default_factory=list)
+    stats: dict = field(default_factory=dict)
+
+    def fetch_blocks(self):
+        self.blocks = [emb_forest_blocks(self.forest, L) for L in range(self.levels + 1)]
+        return self.blocks
+
+    def units(self) -> int:
+        """Cells over all levels plus cut links (the throughput unit)."""
+        cells = sum(64 * emb_forest_num_blocks(self.forest, L) for L in range(self.levels + 1))
+        return cells + (0 if self.links is None else int(self.links["q"].numel()))
+
+
+def embed(verts: torch.Tensor, tris: torch.Tensor, R: int, levels: int, band: int = 2, lattice: int = 19,
+          check_watertight: bool = True, mesh: Mesh | None = None, keep_bins: bool = False,
+          check_status: bool = True, stream=None) -> Embedding:
+    """Embed a closed mesh into a forest with root R^3 blocks and levels 0..levels.
+
+    Per level: emb_bin, emb_voxelize, then (below the finest level)
+    emb_refine_flags and emb_forest_refine; at the finest level the cut-link
+    table of `lattice` (19 or 27).
+    """
+    if mesh is None:
+        mesh = emb_mesh_create(verts, tris, R, check_watertight, stream)
+    forest = emb_forest_root(R, levels, stream)
+    E = Embedding(mesh=mesh, forest=forest, levels=levels, lattice=lattice)
+    for L in range(levels + 1):
+        bins = emb_bin(mesh, forest, L, lattice, stream)
+        E.masks.append(emb_voxelize(forest, bins, L, stream=stream))
+        if L < levels:
+            fl = emb_refine_flags(forest, bins, L, band, stream=stream)
+            E.flags.append(fl)
+            emb_forest_refine(forest, L, fl, stream)
+        else:
+            E.links = emb_cutlinks(forest, bins, lattice, stream=stream)
+        if keep_bins:
+            E.bins.append(bins)
+        else:
+            bins.close()
+    if check_status:
+        st = emb_status_get(stream)
+        if st != EMB_OK:
+            raise EmbError(st, "embed (device status)")
+    return E

@@ -1,0 +1,128 @@
+"""Force, dF/dq and dq/dV on the GPU against the FP64 oracle and finite differences."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from synth import link_weights, populations, workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _setup(name, orc):
+    import torch
+
+    import paper_2512_01251_gb300 as P
+    w = workload(name)
+    v, t = w.build_mesh()
+    E = P.embed(torch.from_numpy(v), torch.from_numpy(t), w.R, w.levels, w.band, 19)
+    blocks_f = P.emb_forest_blocks(E.forest, w.levels).cpu().numpy().astype(np.int64)
+    mask_f = E.masks[-1].cpu().numpy().view(np.uint64)
+    L = E.links
+    lk = dict(cell=L["cell"].cpu().numpy().astype(np.int64), dir=L["dir"].cpu().numpy().astype(np.int64),
+              q=L["q"].cpu().numpy().astype(np.float64), tri=L["tri"].cpu().numpy().astype(np.int64))
+    return w, v, t, E, blocks_f, mask_f, lk
+
+
+@pytest.mark.parametrize("name", ["icosphere_320", "star_1k", "diff_112k"])
+def test_force_and_adjoints_match_oracle(orc, name):
+    import torch
+
+    import paper_2512_01251_gb300 as P
+    w, v, t, E, blocks_f, mask_f, lk = _setup(name, orc)
+    L = E.links
+    ncell = len(blocks_f) * 64
+    pop_np = populations(ncell, seed=w.extra.get("pop_seed", 20251206))
+    pop = torch.from_numpy(pop_np).cuda()
+    partner = orc.partner_cells(w.R, w.levels, blocks_f, mask_f, lk["cell"], lk["dir"])
+
+    F = P.emb_mex_force(E.forest, 19, L["cell"], L["dir"], L["q"], pop).cpu().numpy().astype(np.float64)
+    F_ref = orc.mex_force(lk, pop_np, partner)
+    scale = np.abs(orc.mex_force_dq(lk, pop_np, partner)).sum() + len(lk["q"])  # size of the summed terms
+    assert np.all(np.abs(F - F_ref) <= 1e-6 * np.abs(F_ref) + 1e-9 * scale), (F, F_ref)
+
+    gF = np.array([0.3, -1.2, 0.7])
+    gq = P.emb_mex_force_backward(E.forest, 19, L["cell"], L["dir"], L["q"], pop,
+                                  torch.tensor(gF, dtype=torch.float32)).cpu().numpy()
+    gq_ref = orc.mex_force_dq(lk, pop_np, partner) @ gF.astype(np.float32).astype(np.float64)
+    np.testing.assert_allclose(gq, gq_ref, rtol=1e-5, atol=1e-7 * np.abs(gq_ref).max())
+
+    wk = link_weights(len(lk["q"]), seed=w.extra.get("w_seed", 20251207))
+    gv = P.emb_cutlinks_backward(E.mesh, E.forest, L["cell"], L["dir"], L["q"], L["tri"],
+                                 torch.from_numpy(wk).cuda()).cpu().numpy().astype(np.float64)
+    gv_ref = orc.grad_verts_from_gq(lk, wk.astype(np.float64), orc.int_coords(v, w.R), t, w.R, w.levels,
+                                    blocks_f, len(v))
+    rel = np.linalg.norm(gv - gv_ref) / np.linalg.norm(gv_ref)
+    assert rel <= 1e-4, rel
+    assert np.abs(gv - gv_ref).max() <= 1e-4 * np.abs(gv_ref).max()
+
+
+def test_autograd_chain_matches_composed_oracle(orc):
+    import torch
+
+    from paper_2512_01251_gb300.autograd import embed_q, mex_force
+    w = workload("star_1k")
+    v, t = w.build_mesh()
+    verts = torch.from_numpy(v).cuda().requires_grad_(True)
+    E, q = embed_q(verts, torch.from_numpy(t), w.R, w.levels, w.band, 19)
+    blocks_f = E.fetch_blocks()[-1].cpu().numpy().astype(np.int64)
+    pop_np = populations(len(blocks_f) * 64, seed=5)
+    F = mex_force(q, E, torch.from_numpy(pop_np).cuda())
+    F[0].backward()
+    g = verts.grad.cpu().numpy().astype(np.float64)
+    lk = dict(cell=E.links["cell"].cpu().numpy().astype(np.int64), dir=E.links["dir"].cpu().numpy().astype(np.int64),
+              q=E.links["q"].cpu().numpy().astype(np.float64), tri=E.links["tri"].cpu().numpy().astype(np.int64))
+    mask_f = E.masks[-1].cpu().numpy().view(np.uint64)
+    partner = orc.partner_cells(w.R, w.levels, blocks_f, mask_f, lk["cell"], lk["dir"])
+    gq = orc.mex_force_dq(lk, pop_np, partner)[:, 0]
+    ref = orc.grad_verts_from_gq(lk, gq, orc.int_coords(v, w.R), t, w.R, w.levels, blocks_f, len(v))
+    assert np.linalg.norm(g - ref) <= 1e-4 * np.linalg.norm(ref)
+
+
+def test_gradient_central_differences_on_gpu():
+    """Move one vertex by +-8 grid units (the inputs stay snapped) and re-embed on the GPU;
+    where the link set and each link's triangle stay fixed, dL = sum_k w_k dq_k must match
+    the analytic gradient of L = sum_k w_k q_k."""
+    import torch
+
+    import paper_2512_01251_gb300 as P
+    w = workload("star_1k")
+    v, t = w.build_mesh()
+    E = P.embed(torch.from_numpy(v), torch.from_numpy(t), w.R, w.levels, w.band, 19)
+    n = E.links["q"].numel()
+    wk = link_weights(n, seed=11)
+    g = P.emb_cutlinks_backward(E.mesh, E.forest, E.links["cell"], E.links["dir"], E.links["q"], E.links["tri"],
+                                torch.from_numpy(wk).cuda()).cpu().numpy().astype(np.float64)
+    key0 = (E.links["cell"].cpu().numpy().astype(np.int64) * 32 + E.links["dir"].cpu().numpy()) * (1 << 24) + \
+        E.links["tri"].cpu().numpy()
+    rng = np.random.default_rng(4)
+    used = np.unique(t[E.links["tri"].cpu().numpy()])
+    checked = 0
+    delta = 8.0 / (1 << 20)
+    for vid in rng.choice(used, 24, replace=False):
+        for d in range(3):
+            qs = []
+            same = True
+            for sgn in (1, -1):
+                vp = v.copy()
+                vp[vid, d] = np.float32(v[vid, d] + sgn * delta)
+                Ep = P.embed(torch.from_numpy(vp), torch.from_numpy(t), w.R, w.levels, w.band, 19)
+                key = (Ep.links["cell"].cpu().numpy().astype(np.int64) * 32 + Ep.links["dir"].cpu().numpy()) * \
+                    (1 << 24) + Ep.links["tri"].cpu().numpy()
+                if len(key) != len(key0) or np.any(key != key0):
+                    same = False
+                    break
+                qs.append(Ep.links["q"].cpu().numpy().astype(np.float64))
+            if not same:
+                continue
+            fd = float(wk.astype(np.float64) @ (qs[0] - qs[1])) / (2 * delta)
+            assert abs(fd - g[vid, d]) <= 2e-3 * max(1.0, abs(g[vid, d])), (vid, d, fd, g[vid, d])
+            checked += 1
+    assert checked >= 20
