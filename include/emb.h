@@ -202,6 +202,29 @@ emb_status emb_mex_force_backward(emb_forest f, int32_t lattice, const int32_t *
                                   const float *d_q, int64_t n, const float *d_pop, int64_t pop_stride,
                                   const float *d_gF, float *d_gq, void *stream);
 
+/* Allocation-free variant of emb_mex_force, for callers that cannot call
+ * cudaMalloc: a solver time loop that reserved all device memory up front through
+ * its own pool, or code that must not pay a driver allocation (latency, implicit
+ * device synchronisation) inside a time step.  The paper has no counterpart; this
+ * is a deployment convenience.  Same arguments and result as emb_mex_force, within
+ * float rounding: the per-CTA partial sums (one per 256 links) go to a fixed
+ * 192 KB array inside the library instead of a stream-ordered allocation, so the
+ * partial sums are grouped differently.  The call allocates nothing, and nothing in
+ * the array needs to start at zero (each call writes every partial it reads).
+ * Limits and rules:
+ *   - n <= 2,097,152 links, else EMB_ERR_CAPACITY before any work is enqueued;
+ *   - the finest level's neighbour table must already exist, built by
+ *     emb_cutlinks_count, emb_cutlinks, emb_mex_force or emb_forest_neighbors on
+ *     this forest; else EMB_ERR_STATE;
+ *   - the first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture;
+ *   - all calls share the one array, so calls that overlap on the GPU (other
+ *     streams, other threads) race: serialise them. */
+emb_status emb_mex_force_noalloc(emb_forest f, int32_t lattice, const int32_t *d_cell, const uint8_t *d_dir,
+                                 const float *d_q, int64_t n, const float *d_pop, int64_t pop_stride, float *d_F,
+                                 void *stream);
+
 /* Adjoint of the link table with respect to the vertex positions (world
  * units): d_gverts (V x 3 float32, overwritten) = sum_k d_gq[k] dq_k/dV with
  * dq/dV_j = lambda_j n / (h n.c) for the three vertices of link k's triangle

@@ -32,6 +32,7 @@ from .emb import (  # noqa: F401
     emb_mesh_create,
     emb_mex_force,
     emb_mex_force_backward,
+    emb_mex_force_noalloc,
     emb_refine_flags,
     emb_status_get,
     emb_voxelize,

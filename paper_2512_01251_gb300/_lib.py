@@ -42,6 +42,7 @@ SIGNATURES = {
     "emb_cutlinks": (I32, [P, P, I32, P, P, P, P, I64, P, P]),
     "emb_mex_force": (I32, [P, I32, P, P, P, I64, P, I64, P, P]),
     "emb_mex_force_backward": (I32, [P, I32, P, P, P, I64, P, I64, P, P, P]),
+    "emb_mex_force_noalloc": (I32, [P, I32, P, P, P, I64, P, I64, P, P]),
     "emb_cutlinks_backward": (I32, [P, P, P, P, P, P, I64, P, P, P]),
 }
 

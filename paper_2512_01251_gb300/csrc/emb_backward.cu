@@ -5,6 +5,8 @@
 // All reductions have a fixed order: per-CTA trees in FP64 followed by one CTA
 // summing the partials in index order, and per-vertex sums taken in ascending
 // (link, corner) order.  No floating-point atomics are used.
+#include <mutex>
+
 #include "emb_internal.cuh"
 
 #define MEX_BLOCK 256
@@ -172,6 +174,68 @@ extern "C" emb_status emb_mex_force_backward(emb_forest f, int32_t lattice, cons
     if (!d_cell || !d_dir || !d_q || !d_pop || !d_gF || !d_gq) return EMB_ERR_BAD_INPUT;
     const EmbLevel &lv = f->lv[f->max_level];
     EMB_LAUNCH((k_mex_bwd), emb_grid(n, 256), 256, 0, s)(d_cell, d_dir, d_q, n, d_pop, pop_stride, lv.nbr, lv.mask, d_gF, d_gq);
+    EMB_CUDA_TRY(cudaGetLastError());
+    return EMB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of emb_mex_force
+// ---------------------------------------------------------------------------
+// Some callers cannot call cudaMalloc: a solver time loop that reserved all
+// device memory up front through its own pool, or code that must not pay a
+// driver allocation (latency, implicit device synchronisation) inside a time
+// step.  For them the per-CTA partial sums of the force live in this
+// file-scope array instead of a stream-ordered allocation.  Every GPU that loads
+// the library holds it (3 x EMB_NOALLOC_MEX_PARTS doubles = 192 KB) until exit.
+#define EMB_NOALLOC_MEX_PARTS 8192
+static __device__ __align__(256) double g_mex_noalloc_part[3 * EMB_NOALLOC_MEX_PARTS];
+
+static std::mutex g_mex_noalloc_mu;
+static double *g_mex_noalloc_ptr[64] = {nullptr};  // device address of the array, per device
+
+// The array's device address for the current device, looked up once per device.
+// In host code the array's name is only a host-side stand-in, so the address must
+// come from cudaGetSymbolAddress with the device current.
+static emb_status mex_noalloc_scratch(double **out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return EMB_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_mex_noalloc_mu);
+    if (!g_mex_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_mex_noalloc_part);
+        if (e != cudaSuccess || !p) {
+            emb_note_cuda_error(e, "cudaGetSymbolAddress(g_mex_noalloc_part)", __FILE__, __LINE__);
+            return EMB_ERR_CUDA;
+        }
+        g_mex_noalloc_ptr[dev] = (double *)p;
+    }
+    *out = g_mex_noalloc_ptr[dev];
+    return EMB_OK;
+}
+
+extern "C" emb_status emb_mex_force_noalloc(emb_forest f, int32_t lattice, const int32_t *d_cell, const uint8_t *d_dir,
+                                            const float *d_q, int64_t n, const float *d_pop, int64_t pop_stride,
+                                            float *d_F, void *stream)
+{
+    if (!f || (lattice != 19 && lattice != 27) || n < 0 || !d_F) return EMB_ERR_BAD_INPUT;
+    if (n > 0 && (!d_cell || !d_dir || !d_q || !d_pop)) return EMB_ERR_BAD_INPUT;
+    const int L = f->max_level;
+    if (f->top != L || !f->lv[L].mask_valid) return EMB_ERR_STATE;
+    const EmbLevel &lv = f->lv[L];
+    if (pop_stride < lv.n * 64) return EMB_ERR_BAD_INPUT;
+    // the neighbour table must already exist (emb_cutlinks or emb_mex_force built it): building it would allocate
+    if (lv.n > 0 && !lv.nbr) return EMB_ERR_STATE;
+    // one partial sum per CTA of MEX_BLOCK links
+    const int64_t nparts64 = n > 0 ? (n + MEX_BLOCK - 1) / MEX_BLOCK : 1;
+    if (nparts64 > EMB_NOALLOC_MEX_PARTS) return EMB_ERR_CAPACITY;  // more than 2,097,152 links
+    double *part = nullptr;
+    emb_status rc = mex_noalloc_scratch(&part);
+    if (rc != EMB_OK) return rc;
+    cudaStream_t s = emb_stream(stream);
+    const int nparts = (int)nparts64;
+    EMB_LAUNCH((k_mex_partial), nparts, MEX_BLOCK, 0, s)(d_cell, d_dir, d_q, n, d_pop, pop_stride, lv.nbr, lv.mask, part);
+    EMB_LAUNCH((k_mex_final), 1, MEX_BLOCK, 0, s)(part, nparts, d_F);
     EMB_CUDA_TRY(cudaGetLastError());
     return EMB_OK;
 }

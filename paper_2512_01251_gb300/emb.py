@@ -237,6 +237,15 @@ def emb_mex_force(forest: Forest, lattice: int, cell, dir, q, pop: torch.Tensor,
     return out
 
 
+def emb_mex_force_noalloc(forest: Forest, lattice: int, cell, dir, q, pop: torch.Tensor, out: torch.Tensor,
+                          stream=None) -> torch.Tensor:
+    """emb_mex_force without any device allocation (for callers that cannot allocate
+    mid-run); `out` (3 float32 on the device) must be provided by the caller."""
+    _check(load().emb_mex_force_noalloc(forest.h, int(lattice), _ptr(cell), _ptr(dir), _ptr(q), q.numel(), _ptr(pop),
+                                        pop.shape[1], _ptr(out), _stream(stream)), "emb_mex_force_noalloc")
+    return out
+
+
 def emb_mex_force_backward(forest: Forest, lattice: int, cell, dir, q, pop: torch.Tensor, gF: torch.Tensor,
                            out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     if out is None:
