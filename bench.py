@@ -368,6 +368,8 @@ def run_ours(args):
 
     if rank == 0 and not args.no_extras:
         line["e2e"] = e2e_leg(P, v, t, w, lattice, args, stream)
+        line["fwd_bwd"] = fwd_bwd_leg(P)
+        line["batched"] = batch_leg(P)
         units_s, secs = oracle_sample(v, t, w, lattice, 6, seed=7)
         line["cpu_baseline"] = dict(value=units_s / secs, unit=UNIT, cores=omp_threads(), kind="oracle",
                                     sample=("6 surface blocks of the finest level: 64 cell states each, the states "
@@ -379,6 +381,118 @@ def run_ours(args):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def fwd_bwd_leg(P, reps=10):
+    """Differentiation workload: the ~112K-triangle mesh, root 16^3, levels 0..3, D3Q19, populations
+    = equilibrium(rho=1, u=(0.05,0,0)) * (1 + 0.01 N(0,1)).  Forward = cut-link table + force;
+    backward = dF/dq + dq/dV reduced per vertex.  Median CUDA-event times over `reps`."""
+    import torch
+
+    from synth import link_weights, populations
+    w = workload("diff_112k")
+    v, t = w.build_mesh()
+    verts = torch.from_numpy(v).cuda()
+    tris = torch.from_numpy(t).cuda()
+    E = P.embed(verts, tris, w.R, w.levels, w.band, 19, keep_bins=True)
+    fin = E.bins[-1]
+    n = E.links["q"].numel()
+    nblk = P.emb_forest_num_blocks(E.forest, w.levels)
+    pop = torch.from_numpy(populations(nblk * 64, seed=w.extra["pop_seed"])).cuda()
+    gq_w = torch.from_numpy(link_weights(n, seed=w.extra["w_seed"])).cuda()
+    gF = torch.tensor([1.0, 0.0, 0.0], device="cuda")
+    L = dict(cell=torch.empty(n, dtype=torch.int32, device="cuda"), dir=torch.empty(n, dtype=torch.uint8, device="cuda"),
+             q=torch.empty(n, dtype=torch.float32, device="cuda"), tri=torch.empty(n, dtype=torch.int32, device="cuda"),
+             count=torch.zeros(1, dtype=torch.int64, device="cuda"))
+    F = torch.empty(3, dtype=torch.float32, device="cuda")
+    gq = torch.empty(n, dtype=torch.float32, device="cuda")
+    gv = torch.empty((len(v), 3), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    fw, bw, em = [], [], []
+    for i in range(reps + 2):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        torch.cuda.synchronize()
+        e0.record(stream)
+        P.emb_cutlinks(E.forest, fin, 19, capacity=n, out=L)
+        P.emb_mex_force(E.forest, 19, L["cell"], L["dir"], L["q"], pop, out=F)
+        e1.record(stream)
+        P.emb_mex_force_backward(E.forest, 19, L["cell"], L["dir"], L["q"], pop, gF, out=gq)
+        gq.add_(gq_w)  # d/dq of F_x + sum_k w_k q_k
+        P.emb_cutlinks_backward(E.mesh, E.forest, L["cell"], L["dir"], L["q"], L["tri"], gq, out=gv)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        if i >= 2:
+            fw.append(e0.elapsed_time(e1))
+            bw.append(e1.elapsed_time(e2))
+    for i in range(reps + 1):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        P.embed(verts, tris, w.R, w.levels, w.band, 19, check_watertight=False, check_status=False)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if i >= 1:
+            em.append(a.elapsed_time(b))
+    fmed, bmed, emed = statistics.median(fw), statistics.median(bw), statistics.median(em)
+    return dict(workload=f"diff_112k: {len(t)} triangles, root {w.R}^3, levels 0..{w.levels}, D3Q19, {n} cut links",
+                forward_ms=round(fmed, 4), backward_ms=round(bmed, 4), backward_over_forward=round(bmed / fmed, 3),
+                embed_ms=round(emed, 4), backward_over_embed=round(bmed / emed, 3),
+                forward="emb_cutlinks + emb_mex_force", backward="emb_mex_force_backward + emb_cutlinks_backward")
+
+
+def batch_leg(P, reps=5):
+    """The batched workload: 48 seeded radial meshes (triangle counts log-uniform in
+    1e3..5e5, random rotations, radii 0.15..0.4), each in its own forest (root 8^3..24^3,
+    2..4 levels, band 2, D3Q19).  Plain = the per-call path mesh after mesh on one stream;
+    batched = the captured graph of the planned replay (autotuned launch shape).  Both
+    start from triangle records already on the device."""
+    import torch
+
+    from synth import batch_meshes
+    cases = batch_meshes(48)
+    meshes = [P.emb_mesh_create(torch.from_numpy(c["verts"]), torch.from_numpy(c["tris"]), c["R"]) for c in cases]
+    verts = [torch.from_numpy(c["verts"]).cuda() for c in cases]
+    tris = [torch.from_numpy(c["tris"]).cuda() for c in cases]
+
+    def plain_once():
+        units = 0
+        for c, m, v_, t_ in zip(cases, meshes, verts, tris):
+            E = P.embed(v_, t_, c["R"], c["levels"], c["band"], c["lattice"], mesh=m, check_status=False)
+            units += E.units()
+        return units
+
+    plain_once()
+    torch.cuda.synchronize()
+    pt = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        units = plain_once()
+        torch.cuda.synchronize()
+        pt.append(1e3 * (time.perf_counter() - t0))
+    B = P.emb_batch_create(meshes, [c["levels"] for c in cases], [c["band"] for c in cases],
+                           [c["lattice"] for c in cases])
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        choice = P.emb_batch_autotune(B, s)
+        P.emb_batch_capture(B, s)
+        P.emb_batch_launch(B, s)
+        s.synchronize()
+        bt = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            P.emb_batch_launch(B, s)
+            s.synchronize()
+            bt.append(1e3 * (time.perf_counter() - t0))
+        st_ = P.emb_status_get(s)
+    bunits = sum(64 * sum(P.emb_batch_info(B, j)[0]) + P.emb_batch_info(B, j)[1] for j in range(len(cases)))
+    pm, bm = statistics.median(pt), statistics.median(bt)
+    return dict(workload=f"batch_48: 48 radial meshes, {sum(len(c['tris']) for c in cases)} triangles in total, "
+                         f"roots 8^3..24^3, 2..4 levels, D3Q19",
+                plain_ms=round(pm, 3), batched_ms=round(bm, 3), speedup=round(pm / bm, 2),
+                plain_units_per_s=units / (pm / 1e3), batched_units_per_s=bunits / (bm / 1e3),
+                same_units=bool(units == bunits), status=st_,
+                autotuned=dict(streams=choice[0], tri_block=choice[1], link_ctas_per_sm=choice[2]),
+                timing="host wall clock around a synchronised run (the plain path synchronises inside)")
 
 
 def e2e_leg(P, v, t, w, lattice, args, stream):

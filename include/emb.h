@@ -234,6 +234,47 @@ emb_status emb_cutlinks_backward(emb_mesh m, emb_forest f, const int32_t *d_cell
                                  const float *d_q, const int32_t *d_tri, int64_t n, const float *d_gq,
                                  float *d_gverts, void *stream);
 
+/* --------------------------------------------------------------- batch ---- */
+/* Batched embedding of up to 64 meshes (no counterpart in the paper, which embeds
+ * one geometry at a time; this serves workloads with many bodies).
+ *
+ * emb_batch_create plans: it embeds every mesh once through the per-call path
+ * above (synchronising), records every count, and allocates every buffer a replay
+ * needs.  meshes[j] is used by reference (keep it alive); levels[j] is the finest
+ * level, bands[j] the near-wall band, lattices[j] 19 or 27.
+ *
+ * emb_batch_run replays the whole batch with no allocation and no host
+ * synchronisation: per-mesh pipelines on several internal streams, every count
+ * recomputed on the device checked against the plan (device status
+ * EMB_ERR_STATE on a difference, e.g. moved geometry), and the cut links of all
+ * meshes from one persistent kernel launch over a shared (mesh, block) work
+ * queue.  Results are identical to the per-call path.  `stream` must not be the
+ * legacy default stream for emb_batch_capture.
+ *
+ * emb_batch_capture records emb_batch_run into a CUDA graph; emb_batch_launch
+ * replays that graph on `stream`.
+ *
+ * emb_batch_autotune times a small set of launch shapes on this batch and keeps
+ * the fastest; h_choice (3 int32, may be NULL) receives the chosen stream count,
+ * thread-block size of the triangle-parallel kernels, and resident link CTAs per
+ * SM (0 = as many as fit).  It synchronises and drops a captured graph.
+ *
+ * emb_batch_info: planned blocks per level (levels[j] + 1 int64) and link count of
+ * mesh j (host).  emb_batch_results copies mesh j's results of the last replay into
+ * caller buffers (any pointer may be NULL): the solid mask words and block
+ * coordinates (bx, by, bz int32) of `level`, and the cut-link table. */
+typedef struct emb_batch_s *emb_batch;
+emb_status emb_batch_create(const emb_mesh *meshes, const int32_t *levels, const int32_t *bands,
+                            const int32_t *lattices, int32_t n, void *stream, emb_batch *out);
+emb_status emb_batch_run(emb_batch b, void *stream);
+emb_status emb_batch_capture(emb_batch b, void *stream);
+emb_status emb_batch_launch(emb_batch b, void *stream);
+emb_status emb_batch_autotune(emb_batch b, void *stream, int32_t *h_choice);
+emb_status emb_batch_info(emb_batch b, int32_t j, int64_t *h_blocks, int64_t *h_links);
+emb_status emb_batch_results(emb_batch b, int32_t j, int32_t level, uint64_t *d_mask, int32_t *d_blocks,
+                             int32_t *d_cell, uint8_t *d_dir, float *d_q, int32_t *d_tri, void *stream);
+void emb_batch_destroy(emb_batch b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -44,6 +44,14 @@ SIGNATURES = {
     "emb_mex_force_backward": (I32, [P, I32, P, P, P, I64, P, I64, P, P, P]),
     "emb_mex_force_noalloc": (I32, [P, I32, P, P, P, I64, P, I64, P, P]),
     "emb_cutlinks_backward": (I32, [P, P, P, P, P, P, I64, P, P, P]),
+    "emb_batch_create": (I32, [P, P, P, P, I32, P, ctypes.POINTER(P)]),
+    "emb_batch_run": (I32, [P, P]),
+    "emb_batch_capture": (I32, [P, P]),
+    "emb_batch_launch": (I32, [P, P]),
+    "emb_batch_autotune": (I32, [P, P, P]),
+    "emb_batch_info": (I32, [P, I32, P, PI64]),
+    "emb_batch_results": (I32, [P, I32, I32, P, P, P, P, P, P, P]),
+    "emb_batch_destroy": (None, [P]),
 }
 
 _lib = None

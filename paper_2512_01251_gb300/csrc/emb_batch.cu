@@ -1,0 +1,457 @@
+// Batched embedding of many meshes (a deployment path; the paper embeds one
+// geometry at a time, Sec. 3).
+//
+// emb_batch_create plans: it embeds every mesh once through the per-call path
+// (which synchronises to size its buffers) and records every count (blocks per
+// level, filtered triangles per level, flagged blocks, bin entries, blocks with
+// links, links).  It then allocates, once, every buffer a replay needs.
+//
+// emb_batch_run replays the whole batch from those plans with no allocation
+// and no host synchronisation: the per-mesh pipelines are enqueued round-robin
+// on several streams, every count the device recomputes is checked against the
+// plan by a one-thread kernel (EMB_ERR_STATE on any difference, e.g. when the
+// geometry moved), and all meshes' cut links are produced by one persistent
+// launch of the link kernel over a shared work queue of (mesh, block) items.
+// Because it neither allocates nor synchronises, the replay can be captured in a
+// CUDA graph (emb_batch_capture) and relaunched (emb_batch_launch).
+// emb_batch_autotune times a small set of launch shapes (stream count, thread
+// block size of the triangle-parallel kernels, resident link CTAs per SM) on
+// this batch and keeps the fastest.
+#include <stdlib.h>
+
+#include <vector>
+
+#include "emb_internal.cuh"
+
+#define BATCH_MAX_STREAMS 16
+
+struct BLevel {
+    EmbLevel lv;                     // key, hash, bitmap, mask (+ nbr at the finest level)
+    uint8_t *flags = nullptr;        // refine flags (levels below the finest)
+    uint32_t *flist = nullptr;       // filtered triangles
+    int64_t nf = 0, F = 0;           // planned counts
+};
+
+struct BMesh {
+    emb_mesh m = nullptr;
+    int R = 0, Lf = 0, band = 0, lattice = 0;
+    emb_forest_s geo;                // frame and level geometry (no buffers)
+    BLevel L[EMB_MAX_LEVELS];
+    // scratch sized for the largest level / the triangle count
+    uint32_t *flag = nullptr, *pos = nullptr;       // T + 1
+    unsigned long long *s_acc = nullptr;            // max blocks
+    unsigned int *p_acc = nullptr;
+    uint32_t *cnt = nullptr, *rank = nullptr;       // max blocks + 1
+    uint32_t *pc = nullptr;                         // max bitmap words + 1
+    uint64_t *tmp = nullptr;                        // scan scratch
+    // finest level
+    uint32_t *bin_off = nullptr, *bin_ent = nullptr;
+    uint64_t *cand = nullptr;
+    uint32_t *work_n = nullptr, *work = nullptr, *blk_off = nullptr;
+    int32_t *o_cell = nullptr, *o_tri = nullptr;
+    uint8_t *o_dir = nullptr;
+    float *o_q = nullptr;
+    int64_t pairs = 0, nwork = 0, links = 0;
+    std::vector<void *> owned;
+};
+
+struct emb_batch_s {
+    std::vector<BMesh> m;
+    cudaStream_t st[BATCH_MAX_STREAMS] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[BATCH_MAX_STREAMS] = {};
+    unsigned int *next = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    // launch shape (autotuned)
+    int nstreams = 8, tri_block = 256, link_ctas = 0;
+    int device = 0;
+};
+
+template <class T>
+static emb_status balloc(BMesh &B, T **p, size_t count)
+{
+    void *q = nullptr;
+    EMB_CUDA_TRY(cudaMalloc(&q, (count ? count : 1) * sizeof(T)));
+    B.owned.push_back(q);
+    *p = (T *)q;
+    return EMB_OK;
+}
+
+#define BTRY(x)                          \
+    do {                                 \
+        emb_status _r = (x);             \
+        if (_r != EMB_OK) return _r;     \
+    } while (0)
+
+// Embeds mesh B once through the per-call path, recording every count.
+static emb_status plan_mesh(BMesh &B, cudaStream_t s)
+{
+    emb_forest f = nullptr;
+    BTRY(emb_forest_root(B.R, B.Lf, s, &f));
+    emb_status rc = EMB_OK;
+    uint8_t *fl = nullptr;
+    for (int L = 0; L <= B.Lf && rc == EMB_OK; ++L) {
+        emb_bins b = nullptr;
+        rc = emb_bin(B.m, f, L, B.lattice, s, &b);
+        if (rc != EMB_OK) break;
+        B.L[L].nf = b->nf;
+        rc = emb_voxelize(f, b, L, nullptr, s);
+        if (rc == EMB_OK && L < B.Lf) {
+            const int64_t n = f->lv[L].n;
+            if (cudaMallocAsync(&fl, n + 1, s) != cudaSuccess) rc = EMB_ERR_CUDA;
+            if (rc == EMB_OK) rc = emb_refine_flags(f, b, L, B.band, fl, s);
+            if (rc == EMB_OK) rc = emb_forest_refine(f, L, fl, s);
+            if (rc == EMB_OK) B.L[L].F = f->lv[L + 1].n / 8;
+            cudaFreeAsync(fl, s);
+        } else if (rc == EMB_OK) {
+            B.pairs = b->npairs;
+            int64_t nl = 0;
+            rc = emb_cutlinks_count(f, B.lattice, &nl, s);
+            B.links = nl;
+            if (rc == EMB_OK) {
+                uint32_t nw = 0;
+                if (cudaMemcpyAsync(&nw, f->work_n + f->lv[L].n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) !=
+                        cudaSuccess ||
+                    cudaStreamSynchronize(s) != cudaSuccess)
+                    rc = EMB_ERR_CUDA;
+                B.nwork = nw;
+            }
+        }
+        emb_bins_destroy(b);
+    }
+    if (rc == EMB_OK) {
+        B.geo.R = f->R;
+        B.geo.r_o = f->r_o;
+        B.geo.k = f->k;
+        B.geo.max_level = f->max_level;
+        B.geo.top = f->top;
+        for (int L = 0; L <= B.Lf; ++L) {
+            B.L[L].lv.n = f->lv[L].n;
+            B.L[L].lv.nb_axis = f->lv[L].nb_axis;
+        }
+    }
+    emb_forest_destroy(f);
+    return rc;
+}
+
+// Allocates every buffer of a replay of mesh B.
+static emb_status alloc_mesh(BMesh &B)
+{
+    const int64_t T = B.m->T;
+    int64_t nmax = 1, wmax = 1;
+    for (int L = 0; L <= B.Lf; ++L) {
+        EmbLevel &lv = B.L[L].lv;
+        nmax = lv.n > nmax ? lv.n : nmax;
+        const int64_t nw = emb_bitmap_words(lv.nb_axis);
+        wmax = nw > wmax ? nw : wmax;
+        BTRY(balloc(B, &lv.key, lv.n + 1));
+        lv.hcap = emb_hash_capacity(lv.n);
+        BTRY(balloc(B, &lv.hkey, lv.hcap));
+        BTRY(balloc(B, &lv.hval, lv.hcap));
+        if (nw > 0) {
+            BTRY(balloc(B, &lv.bits, nw));
+            BTRY(balloc(B, &lv.wpre, nw + 1));
+        }
+        BTRY(balloc(B, &lv.mask, lv.n + 1));
+        BTRY(balloc(B, &B.L[L].flist, T + 1));
+        if (L < B.Lf) BTRY(balloc(B, &B.L[L].flags, lv.n + 1));
+    }
+    EmbLevel &fin = B.L[B.Lf].lv;
+    BTRY(balloc(B, &fin.nbr, fin.n * 26 + 1));
+    BTRY(balloc(B, &B.flag, T + 1));
+    BTRY(balloc(B, &B.pos, T + 1));
+    BTRY(balloc(B, &B.s_acc, nmax));
+    BTRY(balloc(B, &B.p_acc, nmax));
+    BTRY(balloc(B, &B.cnt, nmax + 1));
+    BTRY(balloc(B, &B.rank, nmax + 1));
+    BTRY(balloc(B, &B.pc, wmax + 1));
+    const int64_t sw = emb_scan_tmp_words(T > nmax ? (T > wmax ? T : wmax) : (nmax > wmax ? nmax : wmax));
+    BTRY(balloc(B, &B.tmp, sw));
+    BTRY(balloc(B, &B.bin_off, fin.n + 1));
+    BTRY(balloc(B, &B.bin_ent, B.pairs + 1));
+    BTRY(balloc(B, &B.cand, fin.n * 26 + 1));
+    BTRY(balloc(B, &B.work_n, fin.n + 1));
+    BTRY(balloc(B, &B.work, fin.n + 1));
+    BTRY(balloc(B, &B.blk_off, fin.n + 1));
+    BTRY(balloc(B, &B.o_cell, B.links + 1));
+    BTRY(balloc(B, &B.o_dir, B.links + 1));
+    BTRY(balloc(B, &B.o_q, B.links + 1));
+    BTRY(balloc(B, &B.o_tri, B.links + 1));
+    return EMB_OK;
+}
+
+// Enqueues the pipeline of mesh B up to (not including) the link kernel, on stream s.
+static emb_status enqueue_mesh(BMesh &B, int tri_block, cudaStream_t s)
+{
+    const int4 *rec = B.m->rec;
+    const int64_t T = B.m->T;
+    BTRY(emb_enq_root_keys(B.R, B.L[0].lv.key, s));
+    BTRY(emb_enq_level_index(B.L[0].lv, B.pc, B.tmp, s));
+    for (int L = 0; L <= B.Lf; ++L) {
+        BLevel &BL = B.L[L];
+        EmbLevel &lv = BL.lv;
+        const LevelGeom g = level_geom(&B.geo, L);
+        BTRY(emb_enq_filter(rec, T, g, B.flag, B.pos, BL.flist, B.tmp, tri_block, s));
+        BTRY(emb_expect_u32(B.pos + T, (uint64_t)BL.nf, s));
+        BTRY(emb_enq_voxelize(rec, BL.flist, BL.nf, g, lv, B.s_acc, B.p_acc, tri_block, s));
+        if (L < B.Lf) {
+            const long long dil = emb_refine_dilation(&B.geo, L, B.band);
+            if (dil < 0) return EMB_ERR_RANGE;
+            BTRY(emb_enq_refine(rec, T, g, dil, lv, BL.flags, s));
+            BTRY(emb_enq_flag_ranks(lv, BL.flags, B.cnt, B.rank, B.tmp, s));
+            BTRY(emb_expect_u32(B.rank + lv.n, (uint64_t)BL.F, s));
+            EmbLevel &C = B.L[L + 1].lv;
+            BTRY(emb_enq_children(lv, BL.flags, B.rank, C.key, C.n, s));
+            BTRY(emb_enq_level_index(C, B.pc, B.tmp, s));
+        } else {
+            BTRY(emb_enq_bin_count(rec, T, g, lv, B.cnt, B.bin_off, B.tmp, s));
+            BTRY(emb_expect_u32(B.bin_off + lv.n, (uint64_t)B.pairs, s));
+            BTRY(emb_enq_bin_fill(rec, T, g, lv, B.cnt, B.bin_off, B.bin_ent, s));
+            BTRY(emb_enq_neighbors(lv, s));
+            BTRY(emb_enq_link_prep(lv, B.lattice, B.cand, B.cnt, B.rank, B.work_n, B.work, B.blk_off, B.tmp, s));
+            BTRY(emb_expect_u32(B.work_n + lv.n, (uint64_t)B.nwork, s));
+            BTRY(emb_expect_u32(B.blk_off + lv.n, (uint64_t)B.links, s));
+        }
+    }
+    return EMB_OK;
+}
+
+static void free_mesh(BMesh &B)
+{
+    for (void *p : B.owned) cudaFree(p);
+    B.owned.clear();
+}
+
+extern "C" void emb_batch_destroy(emb_batch b)
+{
+    if (!b) return;
+    cudaDeviceSynchronize();
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (int i = 0; i < BATCH_MAX_STREAMS; ++i) {
+        if (b->st[i]) cudaStreamDestroy(b->st[i]);
+        if (b->ev_join[i]) cudaEventDestroy(b->ev_join[i]);
+    }
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->next) cudaFree(b->next);
+    for (BMesh &B : b->m) free_mesh(B);
+    delete b;
+}
+
+extern "C" emb_status emb_batch_create(const emb_mesh *meshes, const int32_t *levels, const int32_t *bands,
+                                       const int32_t *lattices, int32_t n, void *stream, emb_batch *out)
+{
+    if (!out || !meshes || !levels || !bands || !lattices || n < 1 || n > EMB_MAX_BATCH) return EMB_ERR_BAD_INPUT;
+    *out = nullptr;
+    cudaStream_t s = emb_stream(stream);
+    emb_batch b = new emb_batch_s();
+    cudaGetDevice(&b->device);
+    b->m.resize(n);
+    emb_status rc = EMB_OK;
+    for (int j = 0; j < n && rc == EMB_OK; ++j) {
+        BMesh &B = b->m[j];
+        if (!meshes[j] || levels[j] < 0 || levels[j] >= EMB_MAX_LEVELS || bands[j] < 1 ||
+            (lattices[j] != 19 && lattices[j] != 27)) {
+            rc = EMB_ERR_BAD_INPUT;
+            break;
+        }
+        B.m = meshes[j];
+        B.R = meshes[j]->R;
+        B.Lf = levels[j];
+        B.band = bands[j];
+        B.lattice = lattices[j];
+        rc = plan_mesh(B, s);
+        if (rc == EMB_OK) rc = alloc_mesh(B);
+    }
+    if (rc == EMB_OK && cudaMalloc(&b->next, sizeof(unsigned int)) != cudaSuccess) rc = EMB_ERR_CUDA;
+    if (rc == EMB_OK) rc = emb_link_emit_init();  // kernel attributes are set outside of any capture
+    if (rc == EMB_OK && !emb_status_word()) rc = EMB_ERR_CUDA;
+    for (int i = 0; i < BATCH_MAX_STREAMS && rc == EMB_OK; ++i) {
+        if (cudaStreamCreateWithFlags(&b->st[i], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->ev_join[i], cudaEventDisableTiming) != cudaSuccess)
+            rc = EMB_ERR_CUDA;
+    }
+    if (rc == EMB_OK && cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess) rc = EMB_ERR_CUDA;
+    if (rc == EMB_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = EMB_ERR_CUDA;
+    if (rc != EMB_OK) {
+        emb_batch_destroy(b);
+        return rc;
+    }
+    *out = b;
+    return EMB_OK;
+}
+
+// The replay: fork to the worker streams, one pipeline per mesh, join, one link launch.
+static emb_status batch_enqueue(emb_batch b, cudaStream_t s)
+{
+    const int K = b->nstreams < 1 ? 1 : (b->nstreams > BATCH_MAX_STREAMS ? BATCH_MAX_STREAMS : b->nstreams);
+    EMB_CUDA_TRY(cudaEventRecord(b->ev_fork, s));
+    for (int i = 0; i < K; ++i) EMB_CUDA_TRY(cudaStreamWaitEvent(b->st[i], b->ev_fork, 0));
+    // largest meshes first, spread over the streams
+    std::vector<int> order(b->m.size());
+    for (size_t j = 0; j < order.size(); ++j) order[j] = (int)j;
+    for (size_t a = 1; a < order.size(); ++a)
+        for (size_t c = a; c > 0 && b->m[order[c]].m->T > b->m[order[c - 1]].m->T; --c) {
+            int t = order[c];
+            order[c] = order[c - 1];
+            order[c - 1] = t;
+        }
+    for (size_t q = 0; q < order.size(); ++q) BTRY(enqueue_mesh(b->m[order[q]], b->tri_block, b->st[q % K]));
+    for (int i = 0; i < K; ++i) {
+        EMB_CUDA_TRY(cudaEventRecord(b->ev_join[i], b->st[i]));
+        EMB_CUDA_TRY(cudaStreamWaitEvent(s, b->ev_join[i], 0));
+    }
+    LinkTable tab;
+    tab.n = (int)b->m.size();
+    for (int j = 0; j < tab.n; ++j) {
+        BMesh &B = b->m[j];
+        const EmbLevel &fin = B.L[B.Lf].lv;
+        LinkMesh &M = tab.m[j];
+        M.key = fin.key;
+        M.cand = B.cand;
+        M.blk_off = B.blk_off;
+        M.bin_off = B.bin_off;
+        M.bin_ent = B.bin_ent;
+        M.rec = B.m->rec;
+        M.work = B.work;
+        M.work_n = B.work_n + fin.n;
+        M.o_cell = B.o_cell;
+        M.o_dir = B.o_dir;
+        M.o_q = B.o_q;
+        M.o_tri = B.o_tri;
+        M.g = level_geom(&B.geo, B.Lf);
+        M.cap = (uint32_t)B.links;
+    }
+    return emb_enq_link_emit(tab, b->next, b->link_ctas, s);
+}
+
+extern "C" emb_status emb_batch_run(emb_batch b, void *stream)
+{
+    if (!b) return EMB_ERR_BAD_INPUT;
+    return batch_enqueue(b, emb_stream(stream));
+}
+
+extern "C" emb_status emb_batch_capture(emb_batch b, void *stream)
+{
+    if (!b) return EMB_ERR_BAD_INPUT;
+    cudaStream_t s = emb_stream(stream);
+    if (!s) return EMB_ERR_BAD_INPUT;  // the legacy default stream cannot be captured
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    if (b->graph) {
+        cudaGraphDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    EMB_CUDA_TRY(cudaStreamSynchronize(s));
+    EMB_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    emb_status rc = batch_enqueue(b, s);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (rc != EMB_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return EMB_ERR_CUDA;
+    b->graph = g;
+    EMB_CUDA_TRY(cudaGraphInstantiate(&b->exec, g, 0));
+    return EMB_OK;
+}
+
+extern "C" emb_status emb_batch_launch(emb_batch b, void *stream)
+{
+    if (!b) return EMB_ERR_BAD_INPUT;
+    if (!b->exec) return EMB_ERR_STATE;
+    EMB_CUDA_TRY(cudaGraphLaunch(b->exec, emb_stream(stream)));
+    return EMB_OK;
+}
+
+extern "C" emb_status emb_batch_autotune(emb_batch b, void *stream, int32_t *h_choice)
+{
+    if (!b) return EMB_ERR_BAD_INPUT;
+    cudaStream_t s = emb_stream(stream);
+    struct Cand {
+        int nstreams, tri_block, link_ctas;
+    };
+    const Cand cands[] = {{1, 256, 0}, {4, 256, 0}, {8, 256, 0}, {16, 256, 0}, {8, 128, 0},
+                          {8, 512, 0}, {8, 256, 2}, {16, 128, 0}, {16, 512, 0}};
+    const int nc = (int)(sizeof(cands) / sizeof(cands[0]));
+    cudaEvent_t e0, e1;
+    EMB_CUDA_TRY(cudaEventCreate(&e0));
+    EMB_CUDA_TRY(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_i = 0;
+    for (int i = 0; i < nc; ++i) {
+        b->nstreams = cands[i].nstreams;
+        b->tri_block = cands[i].tri_block;
+        b->link_ctas = cands[i].link_ctas;
+        BTRY(batch_enqueue(b, s));  // warm-up
+        float tot = 0;
+        for (int r = 0; r < 3; ++r) {
+            EMB_CUDA_TRY(cudaEventRecord(e0, s));
+            BTRY(batch_enqueue(b, s));
+            EMB_CUDA_TRY(cudaEventRecord(e1, s));
+            EMB_CUDA_TRY(cudaEventSynchronize(e1));
+            float ms = 0;
+            EMB_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+            tot += ms;
+        }
+        if (tot < best) {
+            best = tot;
+            best_i = i;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->nstreams = cands[best_i].nstreams;
+    b->tri_block = cands[best_i].tri_block;
+    b->link_ctas = cands[best_i].link_ctas;
+    if (b->exec) {  // a captured graph no longer matches the chosen shape
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    if (h_choice) {
+        h_choice[0] = b->nstreams;
+        h_choice[1] = b->tri_block;
+        h_choice[2] = b->link_ctas;
+    }
+    return EMB_OK;
+}
+
+extern "C" emb_status emb_batch_info(emb_batch b, int32_t j, int64_t *h_blocks, int64_t *h_links)
+{
+    if (!b || j < 0 || j >= (int32_t)b->m.size()) return EMB_ERR_BAD_INPUT;
+    const BMesh &B = b->m[j];
+    if (h_blocks)
+        for (int L = 0; L <= B.Lf; ++L) h_blocks[L] = B.L[L].lv.n;
+    if (h_links) *h_links = B.links;
+    return EMB_OK;
+}
+
+extern "C" emb_status emb_batch_results(emb_batch b, int32_t j, int32_t level, uint64_t *d_mask, int32_t *d_blocks,
+                                        int32_t *d_cell, uint8_t *d_dir, float *d_q, int32_t *d_tri, void *stream)
+{
+    if (!b || j < 0 || j >= (int32_t)b->m.size()) return EMB_ERR_BAD_INPUT;
+    const BMesh &B = b->m[j];
+    if (level < 0 || level > B.Lf) return EMB_ERR_BAD_INPUT;
+    cudaStream_t s = emb_stream(stream);
+    const EmbLevel &lv = B.L[level].lv;
+    if (d_mask && lv.n)
+        EMB_CUDA_TRY(cudaMemcpyAsync(d_mask, lv.mask, lv.n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+    if (d_blocks && lv.n) {
+        emb_forest_s tmp;
+        tmp.R = B.R;
+        tmp.top = level;
+        tmp.lv[level] = lv;
+        emb_status rc = emb_forest_blocks(&tmp, level, d_blocks, stream);
+        tmp.lv[level] = EmbLevel();  // not owned
+        BTRY(rc);
+    }
+    const size_t n = (size_t)B.links;
+    if (d_cell && n) EMB_CUDA_TRY(cudaMemcpyAsync(d_cell, B.o_cell, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    if (d_dir && n) EMB_CUDA_TRY(cudaMemcpyAsync(d_dir, B.o_dir, n, cudaMemcpyDeviceToDevice, s));
+    if (d_q && n) EMB_CUDA_TRY(cudaMemcpyAsync(d_q, B.o_q, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    if (d_tri && n) EMB_CUDA_TRY(cudaMemcpyAsync(d_tri, B.o_tri, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    return EMB_OK;
+}

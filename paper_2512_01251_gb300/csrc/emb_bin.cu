@@ -150,6 +150,43 @@ __global__ void __launch_bounds__(EMB_WU_WARPS * 32) k_bin_pairs(const int4 *__r
             }
 }
 
+// Step 1 (enqueue only): flag, pos, flist hold T + 1 uint32; the kept count ends at
+// pos[T]; tmp is scan scratch for T entries.
+emb_status emb_enq_filter(const int4 *rec, int64_t T, LevelGeom g, uint32_t *flag, uint32_t *pos, uint32_t *flist,
+                          uint64_t *tmp, int block, cudaStream_t s)
+{
+    EMB_LAUNCH((k_xfilter), emb_grid(T, block), block, 0, s)(rec, T, g, flag);
+    emb_status rc = emb_scan_into(flag, pos, T, tmp, s);
+    if (rc != EMB_OK) return rc;
+    EMB_LAUNCH((k_compact), emb_grid(T, 256), 256, 0, s)(flag, pos, T, flist);
+    EMB_CUDA_TRY(cudaGetLastError());
+    return EMB_OK;
+}
+
+// Steps 2-9 at the finest level, counting half (enqueue only): cnt holds n + 1
+// uint32, off receives n + 1 offsets (pairs total at off[n]); tmp: scan scratch for n.
+emb_status emb_enq_bin_count(const int4 *rec, int64_t T, LevelGeom g, const EmbLevel &lv, uint32_t *cnt, uint32_t *off,
+                             uint64_t *tmp, cudaStream_t s)
+{
+    EMB_CUDA_TRY(cudaMemsetAsync(cnt, 0, (lv.n + 1) * sizeof(uint32_t), s));
+    EMB_LAUNCH((k_bin_pairs<0>), emb_grid(T, 32 * EMB_WU_WARPS), 32 * EMB_WU_WARPS, 0, s)(rec, T, g, g.half,
+                                                                                          emb_lookup_of(lv), cnt,
+                                                                                          nullptr, nullptr);
+    return emb_scan_into(cnt, off, lv.n, tmp, s);
+}
+
+// Filling half: ent holds off[n] entries; cnt is reused as the per-block cursor.
+emb_status emb_enq_bin_fill(const int4 *rec, int64_t T, LevelGeom g, const EmbLevel &lv, uint32_t *cnt,
+                            const uint32_t *off, uint32_t *ent, cudaStream_t s)
+{
+    EMB_CUDA_TRY(cudaMemsetAsync(cnt, 0, (lv.n + 1) * sizeof(uint32_t), s));
+    EMB_LAUNCH((k_bin_pairs<1>), emb_grid(T, 32 * EMB_WU_WARPS), 32 * EMB_WU_WARPS, 0, s)(rec, T, g, g.half,
+                                                                                          emb_lookup_of(lv), cnt, off,
+                                                                                          ent);
+    EMB_CUDA_TRY(cudaGetLastError());
+    return EMB_OK;
+}
+
 extern "C" emb_status emb_bin(emb_mesh m, emb_forest f, int32_t level, int32_t lattice, void *stream, emb_bins *out)
 {
     if (!m || !f || !out) return EMB_ERR_BAD_INPUT;
@@ -166,48 +203,42 @@ extern "C" emb_status emb_bin(emb_mesh m, emb_forest f, int32_t level, int32_t l
     LevelGeom g = level_geom(f, level);
     const EmbLevel &lv = f->lv[level];
     emb_status rc = EMB_OK;
-    uint32_t *flag = nullptr, *pos = nullptr;
-    uint64_t nf = 0;
+    uint32_t *flag = nullptr, *pos = nullptr, *cnt = nullptr;
+    uint64_t *tmp = nullptr;
+    uint32_t nf = 0, np = 0;
+    const int64_t tw = emb_scan_tmp_words(m->T > lv.n ? m->T : lv.n);
     // step 1: exact x-line filter, compacted in ascending order
     if (cudaMallocAsync(&flag, (m->T + 1) * sizeof(uint32_t), s) != cudaSuccess ||
-        cudaMallocAsync(&pos, (m->T + 1) * sizeof(uint32_t), s) != cudaSuccess) {
+        cudaMallocAsync(&pos, (m->T + 1) * sizeof(uint32_t), s) != cudaSuccess ||
+        cudaMallocAsync(&tmp, tw * sizeof(uint64_t), s) != cudaSuccess ||
+        cudaMalloc(&b->flist, (m->T + 1) * sizeof(uint32_t)) != cudaSuccess) {
         emb_bins_destroy(b);
         return EMB_ERR_CUDA;
     }
-    EMB_LAUNCH((k_xfilter), emb_grid(m->T, 256), 256, 0, s)(m->rec, m->T, g, flag);
-    rc = emb_scan_u32(flag, pos, m->T, &nf, s);
-    if (rc == EMB_OK) {
-        b->nf = (int64_t)nf;
-        if (cudaMalloc(&b->flist, (nf + 1) * sizeof(uint32_t)) != cudaSuccess) rc = EMB_ERR_CUDA;
-    }
-    if (rc == EMB_OK && nf > 0) EMB_LAUNCH((k_compact), emb_grid(m->T, 256), 256, 0, s)(flag, pos, m->T, b->flist);
-    cudaFreeAsync(flag, s);
-    cudaFreeAsync(pos, s);
+    rc = emb_enq_filter(m->rec, m->T, g, flag, pos, b->flist, tmp, 256, s);
+    if (rc == EMB_OK && cudaMemcpyAsync(&nf, pos + m->T, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        rc = EMB_ERR_CUDA;
     // steps 2-9 at the finest level: CSR bins of link-relevant triangles per block
-    if (rc == EMB_OK && level == f->max_level && lv.n > 0) {
-        uint32_t *cnt = nullptr;
-        uint64_t np = 0;
-        long long dil = g.half;
+    const bool finest = level == f->max_level && lv.n > 0;
+    if (rc == EMB_OK && finest) {
         if (cudaMallocAsync(&cnt, (lv.n + 1) * sizeof(uint32_t), s) != cudaSuccess ||
-            cudaMalloc(&b->off, (lv.n + 1) * sizeof(uint32_t)) != cudaSuccess) {
-            emb_bins_destroy(b);
-            return EMB_ERR_CUDA;
-        }
-        cudaMemsetAsync(cnt, 0, (lv.n + 1) * sizeof(uint32_t), s);
-        EMB_LAUNCH((k_bin_pairs<0>), emb_grid(m->T, 32 * EMB_WU_WARPS), 32 * EMB_WU_WARPS, 0, s)(m->rec, m->T, g, dil, emb_lookup_of(lv), cnt, nullptr,
-                                                           nullptr);
-        rc = emb_scan_u32(cnt, b->off, lv.n, &np, s);
-        if (rc == EMB_OK) {
-            b->npairs = (int64_t)np;
-            if (cudaMalloc(&b->ent, (np + 1) * sizeof(uint32_t)) != cudaSuccess) rc = EMB_ERR_CUDA;
-        }
-        if (rc == EMB_OK) {
-            cudaMemsetAsync(cnt, 0, (lv.n + 1) * sizeof(uint32_t), s);
-            EMB_LAUNCH((k_bin_pairs<1>), emb_grid(m->T, 32 * EMB_WU_WARPS), 32 * EMB_WU_WARPS, 0, s)(m->rec, m->T, g, dil, emb_lookup_of(lv), cnt,
-                                                               b->off, b->ent);
-        }
-        cudaFreeAsync(cnt, s);
+            cudaMalloc(&b->off, (lv.n + 1) * sizeof(uint32_t)) != cudaSuccess)
+            rc = EMB_ERR_CUDA;
+        if (rc == EMB_OK) rc = emb_enq_bin_count(m->rec, m->T, g, lv, cnt, b->off, tmp, s);
+        if (rc == EMB_OK && cudaMemcpyAsync(&np, b->off + lv.n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            rc = EMB_ERR_CUDA;
     }
+    if (rc == EMB_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = EMB_ERR_CUDA;
+    b->nf = nf;
+    if (rc == EMB_OK && finest) {
+        b->npairs = np;
+        if (cudaMalloc(&b->ent, ((size_t)np + 1) * sizeof(uint32_t)) != cudaSuccess) rc = EMB_ERR_CUDA;
+        if (rc == EMB_OK) rc = emb_enq_bin_fill(m->rec, m->T, g, lv, cnt, b->off, b->ent, s);
+    }
+    if (flag) cudaFreeAsync(flag, s);
+    if (pos) cudaFreeAsync(pos, s);
+    if (cnt) cudaFreeAsync(cnt, s);
+    if (tmp) cudaFreeAsync(tmp, s);
     if (rc == EMB_OK && cudaGetLastError() != cudaSuccess) rc = EMB_ERR_CUDA;
     if (rc != EMB_OK) {
         emb_bins_destroy(b);

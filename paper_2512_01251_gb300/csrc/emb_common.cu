@@ -182,23 +182,49 @@ __global__ void k_scan_apply(const uint32_t *__restrict__ in, uint32_t *__restri
     }
 }
 
+int64_t emb_scan_tmp_words(int64_t n) { return (n + 1 + SCAN_TILE - 1) / SCAN_TILE + 1; }
+
 // d_out gets n + 1 entries: exclusive prefix sums and, at index n, the total.
-emb_status emb_scan_u32(const uint32_t *d_in, uint32_t *d_out, int64_t n, uint64_t *h_total, cudaStream_t s)
+// tmp: emb_scan_tmp_words(n) uint64 words of scratch.  Enqueues only.
+emb_status emb_scan_into(const uint32_t *d_in, uint32_t *d_out, int64_t n, uint64_t *tmp, cudaStream_t s)
 {
     int *st = emb_status_word();
     if (!st) return EMB_ERR_CUDA;
     int64_t ntiles = (n + 1 + SCAN_TILE - 1) / SCAN_TILE;
-    uint64_t *tmp = nullptr;
-    EMB_CUDA_TRY(cudaMallocAsync(&tmp, (ntiles + 1) * sizeof(uint64_t), s));
     EMB_LAUNCH((k_scan_tile_sums), (int)ntiles, SCAN_BLOCK, 0, s)(d_in, n, tmp);
     EMB_LAUNCH((k_scan_sums), 1, SCAN_BLOCK, 0, s)(tmp, ntiles, tmp + ntiles);
     EMB_LAUNCH((k_scan_apply), (int)ntiles, SCAN_BLOCK, 0, s)(d_in, d_out, n, tmp, st);
     EMB_CUDA_TRY(cudaGetLastError());
+    return EMB_OK;
+}
+
+emb_status emb_scan_u32(const uint32_t *d_in, uint32_t *d_out, int64_t n, uint64_t *h_total, cudaStream_t s)
+{
+    uint64_t *tmp = nullptr;
+    int64_t ntiles = (n + 1 + SCAN_TILE - 1) / SCAN_TILE;
+    EMB_CUDA_TRY(cudaMallocAsync(&tmp, emb_scan_tmp_words(n) * sizeof(uint64_t), s));
+    emb_status rc = emb_scan_into(d_in, d_out, n, tmp, s);
+    if (rc != EMB_OK) return rc;
     if (h_total) {
         EMB_CUDA_TRY(cudaMemcpyAsync(h_total, tmp + ntiles, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
         EMB_CUDA_TRY(cudaStreamSynchronize(s));
     }
     EMB_CUDA_TRY(cudaFreeAsync(tmp, s));
+    return EMB_OK;
+}
+
+// Raises EMB_ERR_STATE when a count recomputed on the device differs from the planned one.
+__global__ void k_expect_u32(const uint32_t *__restrict__ got, uint64_t expect, int *st)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0 && (uint64_t)*got != expect) emb_set_status(st, EMB_ERR_STATE);
+}
+
+emb_status emb_expect_u32(const uint32_t *d_got, uint64_t expect, cudaStream_t s)
+{
+    int *st = emb_status_word();
+    if (!st) return EMB_ERR_CUDA;
+    EMB_LAUNCH((k_expect_u32), 1, 32, 0, s)(d_got, expect, st);
+    EMB_CUDA_TRY(cudaGetLastError());
     return EMB_OK;
 }
 
@@ -241,41 +267,64 @@ __global__ void k_word_popc(const uint64_t *__restrict__ bits, int64_t nw, uint3
     if (i < nw) out[i] = (uint32_t)__popcll(bits[i]);
 }
 
-emb_status emb_build_hash(EmbLevel &lv, cudaStream_t s)
+int64_t emb_hash_capacity(int64_t n)
+{
+    int64_t cap = 1024;
+    while (cap < 2 * n) cap <<= 1;
+    return cap;
+}
+
+int64_t emb_bitmap_words(int64_t nb)
+{
+    int64_t cells = nb * nb * nb;
+    return cells <= EMB_BITMAP_MAX_BITS ? (cells + 63) / 64 : 0;
+}
+
+// Hash and rank bitmap of a level whose keys are in place; buffers sized by
+// emb_hash_capacity / emb_bitmap_words; pc: words + 1 uint32, tmp: scan scratch.
+emb_status emb_enq_level_index(EmbLevel &lv, uint32_t *pc, uint64_t *tmp, cudaStream_t s)
 {
     int *st = emb_status_word();
     if (!st) return EMB_ERR_CUDA;
-    int64_t cap = 1024;
-    while (cap < 2 * lv.n) cap <<= 1;
-    if (lv.hkey) EMB_CUDA_TRY(cudaFreeAsync(lv.hkey, s));
-    if (lv.hval) EMB_CUDA_TRY(cudaFreeAsync(lv.hval, s));
-    EMB_CUDA_TRY(cudaMallocAsync(&lv.hkey, cap * sizeof(uint64_t), s));
-    EMB_CUDA_TRY(cudaMallocAsync(&lv.hval, cap * sizeof(int32_t), s));
-    EMB_CUDA_TRY(cudaMemsetAsync(lv.hkey, 0xFF, cap * sizeof(uint64_t), s));
-    lv.hcap = cap;
-    if (lv.n > 0) EMB_LAUNCH((k_hash_insert), emb_grid(lv.n, 256), 256, 0, s)(lv.key, lv.n, lv.hkey, lv.hval, cap, st);
-    if (lv.bits) EMB_CUDA_TRY(cudaFreeAsync(lv.bits, s));
-    if (lv.wpre) EMB_CUDA_TRY(cudaFreeAsync(lv.wpre, s));
-    lv.bits = nullptr;
-    lv.wpre = nullptr;
-    int64_t cells = lv.nb_axis * lv.nb_axis * lv.nb_axis;
-    if (cells <= EMB_BITMAP_MAX_BITS) {
-        int64_t nw = (cells + 63) / 64;
-        uint32_t *pc = nullptr;
-        EMB_CUDA_TRY(cudaMallocAsync(&lv.bits, nw * sizeof(uint64_t), s));
-        EMB_CUDA_TRY(cudaMallocAsync(&lv.wpre, (nw + 1) * sizeof(uint32_t), s));
-        EMB_CUDA_TRY(cudaMallocAsync(&pc, (nw + 1) * sizeof(uint32_t), s));
+    EMB_CUDA_TRY(cudaMemsetAsync(lv.hkey, 0xFF, lv.hcap * sizeof(uint64_t), s));
+    if (lv.n > 0) EMB_LAUNCH((k_hash_insert), emb_grid(lv.n, 256), 256, 0, s)(lv.key, lv.n, lv.hkey, lv.hval, lv.hcap, st);
+    int64_t nw = emb_bitmap_words(lv.nb_axis);
+    if (lv.bits && nw > 0) {
         EMB_CUDA_TRY(cudaMemsetAsync(lv.bits, 0, nw * sizeof(uint64_t), s));
         if (lv.n > 0)
-            EMB_LAUNCH((k_bits_set), emb_grid(lv.n, 256), 256, 0, s)(lv.key, lv.n, lv.nb_axis,
-                                                                    (unsigned long long *)lv.bits);
+            EMB_LAUNCH((k_bits_set), emb_grid(lv.n, 256), 256, 0, s)(lv.key, lv.n, lv.nb_axis, (unsigned long long *)lv.bits);
         EMB_LAUNCH((k_word_popc), emb_grid(nw, 256), 256, 0, s)(lv.bits, nw, pc);
-        emb_status rc = emb_scan_u32(pc, lv.wpre, nw, nullptr, s);
-        EMB_CUDA_TRY(cudaFreeAsync(pc, s));
+        emb_status rc = emb_scan_into(pc, lv.wpre, nw, tmp, s);
         if (rc != EMB_OK) return rc;
     }
     EMB_CUDA_TRY(cudaGetLastError());
     return EMB_OK;
+}
+
+emb_status emb_build_hash(EmbLevel &lv, cudaStream_t s)
+{
+    if (lv.hkey) EMB_CUDA_TRY(cudaFreeAsync(lv.hkey, s));
+    if (lv.hval) EMB_CUDA_TRY(cudaFreeAsync(lv.hval, s));
+    if (lv.bits) EMB_CUDA_TRY(cudaFreeAsync(lv.bits, s));
+    if (lv.wpre) EMB_CUDA_TRY(cudaFreeAsync(lv.wpre, s));
+    lv.bits = nullptr;
+    lv.wpre = nullptr;
+    lv.hcap = emb_hash_capacity(lv.n);
+    EMB_CUDA_TRY(cudaMallocAsync(&lv.hkey, lv.hcap * sizeof(uint64_t), s));
+    EMB_CUDA_TRY(cudaMallocAsync(&lv.hval, lv.hcap * sizeof(int32_t), s));
+    int64_t nw = emb_bitmap_words(lv.nb_axis);
+    uint32_t *pc = nullptr;
+    uint64_t *tmp = nullptr;
+    if (nw > 0) {
+        EMB_CUDA_TRY(cudaMallocAsync(&lv.bits, nw * sizeof(uint64_t), s));
+        EMB_CUDA_TRY(cudaMallocAsync(&lv.wpre, (nw + 1) * sizeof(uint32_t), s));
+        EMB_CUDA_TRY(cudaMallocAsync(&pc, (nw + 1) * sizeof(uint32_t), s));
+        EMB_CUDA_TRY(cudaMallocAsync(&tmp, emb_scan_tmp_words(nw) * sizeof(uint64_t), s));
+    }
+    emb_status rc = emb_enq_level_index(lv, pc, tmp, s);
+    if (pc) EMB_CUDA_TRY(cudaFreeAsync(pc, s));
+    if (tmp) EMB_CUDA_TRY(cudaFreeAsync(tmp, s));
+    return rc;
 }
 
 __global__ void k_neighbors(const uint64_t *__restrict__ key, int64_t n, int64_t nb, EmbLookup lk, int32_t *__restrict__ nbr)
@@ -295,12 +344,17 @@ __global__ void k_neighbors(const uint64_t *__restrict__ key, int64_t n, int64_t
     nbr[i] = r;
 }
 
-emb_status emb_build_neighbors(EmbLevel &lv, cudaStream_t s)
+emb_status emb_enq_neighbors(EmbLevel &lv, cudaStream_t s)
 {
-    if (lv.nbr) return EMB_OK;
-    EMB_CUDA_TRY(cudaMallocAsync(&lv.nbr, (lv.n * 26 + 1) * sizeof(int32_t), s));
     if (lv.n > 0)
         EMB_LAUNCH((k_neighbors), emb_grid(lv.n * 26, 256), 256, 0, s)(lv.key, lv.n, lv.nb_axis, emb_lookup_of(lv), lv.nbr);
     EMB_CUDA_TRY(cudaGetLastError());
     return EMB_OK;
+}
+
+emb_status emb_build_neighbors(EmbLevel &lv, cudaStream_t s)
+{
+    if (lv.nbr) return EMB_OK;
+    EMB_CUDA_TRY(cudaMallocAsync(&lv.nbr, (lv.n * 26 + 1) * sizeof(int32_t), s));
+    return emb_enq_neighbors(lv, s);
 }

@@ -264,27 +264,39 @@ __device__ __noinline__ void scan_cell_slow(const uint32_t *__restrict__ bin_ent
     }
 }
 
-__global__ void __launch_bounds__(LE_WARPS * 32, 4) k_link_emit(const uint64_t *__restrict__ key, const uint32_t *__restrict__ work,
-                                                                const uint32_t *__restrict__ work_n, unsigned int *__restrict__ next, LevelGeom g,
-                                                                const uint64_t *__restrict__ cand,
-                                                                const uint32_t *__restrict__ blk_off,
-                                                                const uint32_t *__restrict__ bin_off,
-                                                                const uint32_t *__restrict__ bin_ent,
-                                                                const int4 *__restrict__ rec, int32_t *__restrict__ o_cell,
-                                                                uint8_t *__restrict__ o_dir, float *__restrict__ o_q,
-                                                                int32_t *__restrict__ o_tri, int *st)
+__global__ void __launch_bounds__(LE_WARPS * 32, 4) k_link_emit(const __grid_constant__ LinkTable tab,
+                                                                unsigned int *__restrict__ next, int *st)
 {
     extern __shared__ __align__(16) unsigned char le_smem[];
+    __shared__ uint32_t s_pre[EMB_MAX_BATCH + 1];  // work items of meshes before j
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     LeWarp &S = reinterpret_cast<LeWarp *>(le_smem)[w];
-    // persistent warps: take the next block with links from the work list
+    if (threadIdx.x == 0) {
+        uint32_t acc = 0;
+        for (int j = 0; j < tab.n; ++j) {
+            s_pre[j] = acc;
+            acc += *tab.m[j].work_n;
+        }
+        s_pre[tab.n] = acc;
+    }
+    __syncthreads();
+    // persistent warps: take the next (mesh, block with links) item of the shared work queue
     for (;;) {
     unsigned int widx = 0;
     if (lane == 0) widx = atomicAdd(next, 1u);
     widx = __shfl_sync(0xffffffffu, widx, 0);
-    if (widx >= *work_n) return;
-    const int64_t b = work[widx];
-    const uint32_t base = blk_off[b];
+    if (widx >= s_pre[tab.n]) return;
+    int mj = 0;
+    while (mj + 1 < tab.n && s_pre[mj + 1] <= widx) ++mj;
+    const LinkMesh &M = tab.m[mj];
+    const uint64_t *__restrict__ key = M.key;
+    const uint64_t *__restrict__ cand = M.cand;
+    const uint32_t *__restrict__ bin_off = M.bin_off;
+    const uint32_t *__restrict__ bin_ent = M.bin_ent;
+    const int4 *__restrict__ rec = M.rec;
+    const LevelGeom g = M.g;
+    const int64_t b = M.work[widx - s_pre[mj]];
+    const uint32_t base = M.blk_off[b];
     // candidate directions of cells lane and 32 + lane from the block's direction words
     const uint64_t wd = lane < 26 ? cand[b * 26 + lane] : 0ull;
     uint32_t c0 = 0, c1 = 0;
@@ -532,14 +544,18 @@ __global__ void __launch_bounds__(LE_WARPS * 32, 4) k_link_emit(const uint64_t *
                 if (bT >= 0) tri_NM(rec, bT, px, py, pz, cx, cy, cz, bN, bM);
                 const uint32_t o = base + off + r;
                 ++r;
-                o_cell[o] = (int32_t)(b * 64 + t);
-                o_dir[o] = (uint8_t)d;
+                if (o >= M.cap) {
+                    emb_set_status(st, EMB_ERR_CAPACITY);
+                    continue;
+                }
+                M.o_cell[o] = (int32_t)(b * 64 + t);
+                M.o_dir[o] = (uint8_t)d;
                 if (bT >= 0) {
-                    o_q[o] = __fdiv_rn(i128_to_float(bN), (float)bM * (float)h);
-                    o_tri[o] = bT;
+                    M.o_q[o] = __fdiv_rn(i128_to_float(bN), (float)bM * (float)h);
+                    M.o_tri[o] = bT;
                 } else {
-                    o_q[o] = -1.0f;
-                    o_tri[o] = -1;
+                    M.o_q[o] = -1.0f;
+                    M.o_tri[o] = -1;
                     emb_set_status(st, EMB_ERR_STATE);  // a fluid-to-solid link must cross the surface
                 }
             }
@@ -580,6 +596,60 @@ static void free_candidates(emb_forest f, cudaStream_t s)
     }
 }
 
+// Link preparation for the finest level (enqueue only, neighbour table in place):
+// cand (26 n words), cnt and flag (n + 1 uint32, scratch), work_n (n + 1: the
+// work-list scan, count at work_n[n]), work (n), blk_off (n + 1: link offsets,
+// total at blk_off[n]), tmp (scan scratch for n).
+emb_status emb_enq_link_prep(const EmbLevel &lv, int lattice, uint64_t *cand, uint32_t *cnt, uint32_t *flag,
+                             uint32_t *work_n, uint32_t *work, uint32_t *blk_off, uint64_t *tmp, cudaStream_t s)
+{
+    EMB_CUDA_TRY(cudaMemsetAsync(cnt, 0, (lv.n + 1) * sizeof(uint32_t), s));
+    EMB_CUDA_TRY(cudaMemsetAsync(flag, 0, (lv.n + 1) * sizeof(uint32_t), s));
+    if (lv.n > 0) {
+        EMB_LAUNCH((k_link_cand), emb_grid(lv.n, 128), 128, 0, s)(lv.mask, lv.nbr, lv.n, lattice, cand, cnt);
+        EMB_LAUNCH((k_nonempty), emb_grid(lv.n, 256), 256, 0, s)(cnt, lv.n, flag);
+    }
+    emb_status rc = emb_scan_into(flag, work_n, lv.n, tmp, s);
+    if (rc != EMB_OK) return rc;
+    if (lv.n > 0) EMB_LAUNCH((k_compact_ids), emb_grid(lv.n, 256), 256, 0, s)(flag, work_n, lv.n, work);
+    EMB_CUDA_TRY(cudaGetLastError());
+    return emb_scan_into(cnt, blk_off, lv.n, tmp, s);
+}
+
+size_t emb_link_emit_smem() { return LE_WARPS * sizeof(LeWarp); }
+
+static int g_le_per_sm = 0, g_le_sms = 0;
+
+// Kernel attributes and occupancy of the link kernel (once per process; call
+// before any stream capture).
+emb_status emb_link_emit_init()
+{
+    if (g_le_per_sm) return EMB_OK;
+    const size_t smem = emb_link_emit_smem();
+    EMB_CUDA_TRY(cudaFuncSetAttribute(k_link_emit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int dev = 0, per_sm = 0;
+    EMB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_link_emit, LE_WARPS * 32, smem));
+    EMB_CUDA_TRY(cudaGetDevice(&dev));
+    EMB_CUDA_TRY(cudaDeviceGetAttribute(&g_le_sms, cudaDevAttrMultiProcessorCount, dev));
+    g_le_per_sm = per_sm < 1 ? 1 : per_sm;
+    return EMB_OK;
+}
+
+// One persistent launch over the meshes of `tab`; `next` is the queue cursor.
+emb_status emb_enq_link_emit(const LinkTable &tab, unsigned int *next, int ctas_per_sm, cudaStream_t s)
+{
+    int *st = emb_status_word();
+    if (!st) return EMB_ERR_CUDA;
+    emb_status rc = emb_link_emit_init();
+    if (rc != EMB_OK) return rc;
+    const size_t smem = emb_link_emit_smem();
+    const int use = ctas_per_sm > 0 && ctas_per_sm < g_le_per_sm ? ctas_per_sm : g_le_per_sm;
+    EMB_CUDA_TRY(cudaMemsetAsync(next, 0, sizeof(unsigned int), s));
+    EMB_LAUNCH((k_link_emit), use * g_le_sms, LE_WARPS * 32, smem, s)(tab, next, st);
+    EMB_CUDA_TRY(cudaGetLastError());
+    return EMB_OK;
+}
+
 static emb_status build_candidates(emb_forest f, int lattice, cudaStream_t s)
 {
     int L = f->max_level;
@@ -595,22 +665,18 @@ static emb_status build_candidates(emb_forest f, int lattice, cudaStream_t s)
     EMB_CUDA_TRY(cudaMallocAsync(&f->work, (lv.n + 1) * sizeof(uint32_t), s));
     if (!f->next) EMB_CUDA_TRY(cudaMalloc(&f->next, sizeof(unsigned int)));
     uint32_t *cnt = nullptr, *flag = nullptr;
+    uint64_t *tmp = nullptr;
     EMB_CUDA_TRY(cudaMallocAsync(&cnt, (lv.n + 1) * sizeof(uint32_t), s));
     EMB_CUDA_TRY(cudaMallocAsync(&flag, (lv.n + 1) * sizeof(uint32_t), s));
-    EMB_CUDA_TRY(cudaMemsetAsync(cnt, 0, (lv.n + 1) * sizeof(uint32_t), s));
-    if (lv.n > 0)
-        EMB_LAUNCH((k_link_cand), emb_grid(lv.n, 128), 128, 0, s)(lv.mask, lv.nbr, lv.n, lattice, f->cand, cnt);
-    // work list: blocks with links, ascending; the count ends up at pos[n]
-    if (lv.n > 0) EMB_LAUNCH((k_nonempty), emb_grid(lv.n, 256), 256, 0, s)(cnt, lv.n, flag);
-    rc = emb_scan_u32(flag, f->work_n, lv.n, nullptr, s);
+    EMB_CUDA_TRY(cudaMallocAsync(&tmp, emb_scan_tmp_words(lv.n) * sizeof(uint64_t), s));
+    rc = emb_enq_link_prep(lv, lattice, f->cand, cnt, flag, f->work_n, f->work, f->blk_off, tmp, s);
     if (rc != EMB_OK) return rc;
-    if (lv.n > 0) EMB_LAUNCH((k_compact_ids), emb_grid(lv.n, 256), 256, 0, s)(flag, f->work_n, lv.n, f->work);
-    EMB_CUDA_TRY(cudaGetLastError());
-    uint64_t total = 0;
-    rc = emb_scan_u32(cnt, f->blk_off, lv.n, &total, s);
+    uint32_t total = 0;
+    EMB_CUDA_TRY(cudaMemcpyAsync(&total, f->blk_off + lv.n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    EMB_CUDA_TRY(cudaStreamSynchronize(s));
     EMB_CUDA_TRY(cudaFreeAsync(cnt, s));
     EMB_CUDA_TRY(cudaFreeAsync(flag, s));
-    if (rc != EMB_OK) return rc;
+    EMB_CUDA_TRY(cudaFreeAsync(tmp, s));
     f->n_links = (int64_t)total;
     f->cand_lattice = lattice;
     return EMB_OK;
@@ -644,22 +710,25 @@ extern "C" emb_status emb_cutlinks(emb_forest f, emb_bins b, int32_t lattice, in
     }
     if (f->n_links == 0) return EMB_OK;
     if (!d_cell || !d_dir || !d_q || !d_tri) return EMB_ERR_BAD_INPUT;
-    LevelGeom g = level_geom(f, f->max_level);
-    static int grid = 0;
-    const size_t smem = LE_WARPS * sizeof(LeWarp);
-    if (!grid) {
-        EMB_CUDA_TRY(cudaFuncSetAttribute(k_link_emit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        int per_sm = 0, dev = 0, sms = 0;
-        EMB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_link_emit, LE_WARPS * 32, smem));
-        EMB_CUDA_TRY(cudaGetDevice(&dev));
-        EMB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        grid = (per_sm > 0 ? per_sm : 1) * sms;
-    }
-    // the work list sits in work_n[0 .. n) with its length at work_n[n]
-    EMB_CUDA_TRY(cudaMemsetAsync(f->next, 0, sizeof(unsigned int), s));
-    EMB_LAUNCH((k_link_emit), grid, LE_WARPS * 32, smem, s)(lv.key, f->work, f->work_n + lv.n, f->next, g,
-                                                           f->cand, f->blk_off,
-                                                           b->off, b->ent, b->m->rec, d_cell, d_dir, d_q, d_tri, st);
+    LinkTable tab;
+    tab.n = 1;
+    LinkMesh &M = tab.m[0];
+    M.key = lv.key;
+    M.cand = f->cand;
+    M.blk_off = f->blk_off;
+    M.bin_off = b->off;
+    M.bin_ent = b->ent;
+    M.rec = b->m->rec;
+    M.work = f->work;
+    M.work_n = f->work_n + lv.n;
+    M.o_cell = d_cell;
+    M.o_dir = d_dir;
+    M.o_q = d_q;
+    M.o_tri = d_tri;
+    M.g = level_geom(f, f->max_level);
+    M.cap = (uint32_t)(capacity < 0xFFFFFFFFll ? capacity : 0xFFFFFFFFll);
+    rc = emb_enq_link_emit(tab, f->next, 0, s);
+    if (rc != EMB_OK) return rc;
     EMB_CUDA_TRY(cudaGetLastError());
     return EMB_OK;
 }

@@ -105,8 +105,8 @@ extern "C" emb_status emb_forest_root(int32_t R, int32_t max_level, void *stream
         emb_forest_destroy(f);
         return EMB_ERR_CUDA;
     }
-    EMB_LAUNCH((k_root_keys), emb_grid(lv.n, 256), 256, 0, s)(R, lv.key);
-    emb_status rc = emb_build_hash(lv, s);
+    emb_status rc = emb_enq_root_keys(R, lv.key, s);
+    if (rc == EMB_OK) rc = emb_build_hash(lv, s);
     if (rc != EMB_OK) {
         emb_forest_destroy(f);
         return rc;
@@ -128,6 +128,32 @@ extern "C" void emb_forest_destroy(emb_forest f)
     delete f;
 }
 
+// Refinement in two enqueue-only halves (buffers supplied by the caller):
+//  (1) ranks of the flagged blocks of P: cnt, rank hold P.n + 1 uint32; the number
+//      of flagged blocks F ends at rank[P.n]; tmp is scan scratch for P.n entries;
+//  (2) the 8 F children keys, written in (z, y, x) order into ckey.
+emb_status emb_enq_flag_ranks(const EmbLevel &P, const uint8_t *d_flags, uint32_t *cnt, uint32_t *rank, uint64_t *tmp,
+                              cudaStream_t s)
+{
+    if (P.n > 0) EMB_LAUNCH((k_flags_u32), emb_grid(P.n, 256), 256, 0, s)(d_flags, P.n, cnt);
+    return emb_scan_into(cnt, rank, P.n, tmp, s);
+}
+
+emb_status emb_enq_children(const EmbLevel &P, const uint8_t *d_flags, const uint32_t *rank, uint64_t *ckey, int64_t Cn,
+                            cudaStream_t s)
+{
+    if (P.n > 0 && Cn > 0) EMB_LAUNCH((k_make_children), emb_grid(P.n, 256), 256, 0, s)(P.key, P.n, d_flags, rank, ckey);
+    EMB_CUDA_TRY(cudaGetLastError());
+    return EMB_OK;
+}
+
+emb_status emb_enq_root_keys(int64_t R, uint64_t *key, cudaStream_t s)
+{
+    EMB_LAUNCH((k_root_keys), emb_grid(R * R * R, 256), 256, 0, s)(R, key);
+    EMB_CUDA_TRY(cudaGetLastError());
+    return EMB_OK;
+}
+
 extern "C" emb_status emb_forest_refine(emb_forest f, int32_t level, const uint8_t *d_flags, void *stream)
 {
     if (!f) return EMB_ERR_BAD_INPUT;
@@ -138,19 +164,23 @@ extern "C" emb_status emb_forest_refine(emb_forest f, int32_t level, const uint8
     EmbLevel &C = f->lv[level + 1];
     free_level(C);
     uint32_t *cnt = nullptr, *rank = nullptr;
+    uint64_t *tmp = nullptr;
     EMB_CUDA_TRY(cudaMallocAsync(&cnt, (P.n + 1) * sizeof(uint32_t), s));
     EMB_CUDA_TRY(cudaMallocAsync(&rank, (P.n + 1) * sizeof(uint32_t), s));
-    if (P.n > 0) EMB_LAUNCH((k_flags_u32), emb_grid(P.n, 256), 256, 0, s)(d_flags, P.n, cnt);
-    uint64_t F = 0;
-    emb_status rc = emb_scan_u32(cnt, rank, P.n, &F, s);
+    EMB_CUDA_TRY(cudaMallocAsync(&tmp, emb_scan_tmp_words(P.n) * sizeof(uint64_t), s));
+    emb_status rc = emb_enq_flag_ranks(P, d_flags, cnt, rank, tmp, s);
     if (rc != EMB_OK) return rc;
+    uint32_t F = 0;
+    EMB_CUDA_TRY(cudaMemcpyAsync(&F, rank + P.n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    EMB_CUDA_TRY(cudaStreamSynchronize(s));
     C.n = 8 * (int64_t)F;
     C.nb_axis = P.nb_axis * 2;
     EMB_CUDA_TRY(cudaMalloc(&C.key, (C.n + 1) * sizeof(uint64_t)));
-    if (P.n > 0 && C.n > 0) EMB_LAUNCH((k_make_children), emb_grid(P.n, 256), 256, 0, s)(P.key, P.n, d_flags, rank, C.key);
-    EMB_CUDA_TRY(cudaGetLastError());
+    rc = emb_enq_children(P, d_flags, rank, C.key, C.n, s);
+    if (rc != EMB_OK) return rc;
     EMB_CUDA_TRY(cudaFreeAsync(cnt, s));
     EMB_CUDA_TRY(cudaFreeAsync(rank, s));
+    EMB_CUDA_TRY(cudaFreeAsync(tmp, s));
     rc = emb_build_hash(C, s);
     if (rc != EMB_OK) return rc;
     f->top = level + 1;

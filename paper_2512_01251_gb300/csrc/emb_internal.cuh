@@ -140,10 +140,70 @@ static inline LevelGeom level_geom(const emb_forest_s *f, int L)
 // ---------------------------------------------------------------------------
 // small host helpers (defined in emb_common.cu)
 // ---------------------------------------------------------------------------
+// Scans: d_out gets n + 1 entries (exclusive sums, total at n).  emb_scan_u32
+// allocates its scratch and can read the total back (synchronising); emb_scan_into
+// only enqueues, with emb_scan_tmp_words(n) words of caller scratch.
 emb_status emb_scan_u32(const uint32_t *d_in, uint32_t *d_out, int64_t n, uint64_t *h_total, cudaStream_t s);
+emb_status emb_scan_into(const uint32_t *d_in, uint32_t *d_out, int64_t n, uint64_t *tmp, cudaStream_t s);
+int64_t emb_scan_tmp_words(int64_t n);
+// Device check that a count recomputed during a planned replay equals the plan.
+emb_status emb_expect_u32(const uint32_t *d_got, uint64_t expect, cudaStream_t s);
+// Level index (hash + rank bitmap) and neighbour table.
+int64_t emb_hash_capacity(int64_t n);
+int64_t emb_bitmap_words(int64_t nb);
+emb_status emb_enq_level_index(EmbLevel &lv, uint32_t *pc, uint64_t *tmp, cudaStream_t s);
 emb_status emb_build_hash(EmbLevel &lv, cudaStream_t s);
+emb_status emb_enq_neighbors(EmbLevel &lv, cudaStream_t s);
 emb_status emb_build_neighbors(EmbLevel &lv, cudaStream_t s);
 int emb_grid(int64_t n, int block);
+// Forest steps (enqueue only; buffers supplied by the caller).
+emb_status emb_enq_root_keys(int64_t R, uint64_t *key, cudaStream_t s);
+emb_status emb_enq_flag_ranks(const EmbLevel &P, const uint8_t *d_flags, uint32_t *cnt, uint32_t *rank, uint64_t *tmp,
+                              cudaStream_t s);
+emb_status emb_enq_children(const EmbLevel &P, const uint8_t *d_flags, const uint32_t *rank, uint64_t *ckey, int64_t Cn,
+                            cudaStream_t s);
+// Binning, voxelization and refine flags (enqueue only).
+struct LevelGeom;
+emb_status emb_enq_filter(const int4 *rec, int64_t T, LevelGeom g, uint32_t *flag, uint32_t *pos, uint32_t *flist,
+                          uint64_t *tmp, int block, cudaStream_t s);
+emb_status emb_enq_bin_count(const int4 *rec, int64_t T, LevelGeom g, const EmbLevel &lv, uint32_t *cnt, uint32_t *off,
+                             uint64_t *tmp, cudaStream_t s);
+emb_status emb_enq_bin_fill(const int4 *rec, int64_t T, LevelGeom g, const EmbLevel &lv, uint32_t *cnt,
+                            const uint32_t *off, uint32_t *ent, cudaStream_t s);
+emb_status emb_enq_voxelize(const int4 *rec, const uint32_t *flist, int64_t nf, LevelGeom g, const EmbLevel &lv,
+                            unsigned long long *s_acc, unsigned int *p_acc, int block, cudaStream_t s);
+emb_status emb_enq_refine(const int4 *rec, int64_t T, LevelGeom g, long long dil, const EmbLevel &lv, uint8_t *flags,
+                          cudaStream_t s);
+long long emb_refine_dilation(const emb_forest_s *f, int L, int band);
+
+// Cut links: per-mesh arguments of the persistent link kernel, passed by value as
+// a table so one launch can serve a whole batch of meshes.
+#define EMB_MAX_BATCH 64
+struct LinkMesh {
+    const uint64_t *key;       // finest block keys
+    const uint64_t *cand;      // 26 direction words per block
+    const uint32_t *blk_off;   // link offsets per block
+    const uint32_t *bin_off;   // CSR bins
+    const uint32_t *bin_ent;
+    const int4 *rec;           // triangle records
+    const uint32_t *work;      // blocks with links
+    const uint32_t *work_n;    // their count (device)
+    int32_t *o_cell;
+    uint8_t *o_dir;
+    float *o_q;
+    int32_t *o_tri;
+    LevelGeom g;
+    uint32_t cap;              // capacity of the output table
+};
+struct LinkTable {
+    int n;
+    LinkMesh m[EMB_MAX_BATCH];
+};
+emb_status emb_enq_link_prep(const EmbLevel &lv, int lattice, uint64_t *cand, uint32_t *cnt, uint32_t *flag,
+                             uint32_t *work_n, uint32_t *work, uint32_t *blk_off, uint64_t *tmp, cudaStream_t s);
+emb_status emb_enq_link_emit(const LinkTable &tab, unsigned int *next, int ctas_per_sm, cudaStream_t s);
+emb_status emb_link_emit_init();
+size_t emb_link_emit_smem();
 
 // ---------------------------------------------------------------------------
 // device helpers

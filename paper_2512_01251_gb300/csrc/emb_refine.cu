@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(EMB_WU_WARPS * 32) k_refine(const int4 *__rest
 }
 
 // (rho_L - 1/2) h_L in frame units, or -1 if it is not an integer.
-static long long refine_dilation(const emb_forest_s *f, int L, int band)
+long long emb_refine_dilation(const emb_forest_s *f, int L, int band)
 {
     const int sh = 16;  // rho is kept as an integer multiple of 2^-16
     long long rho = (long long)band << sh;
@@ -104,6 +104,17 @@ static long long refine_dilation(const emb_forest_s *f, int L, int band)
     return num >> sh;
 }
 
+// Enqueue only: flags (lv.n bytes) are cleared and set.
+emb_status emb_enq_refine(const int4 *rec, int64_t T, LevelGeom g, long long dil, const EmbLevel &lv, uint8_t *flags,
+                          cudaStream_t s)
+{
+    if (lv.n == 0) return EMB_OK;
+    EMB_CUDA_TRY(cudaMemsetAsync(flags, 0, lv.n, s));
+    EMB_LAUNCH((k_refine), emb_grid(T, 32 * EMB_WU_WARPS), 32 * EMB_WU_WARPS, 0, s)(rec, T, g, dil, emb_lookup_of(lv), flags);
+    EMB_CUDA_TRY(cudaGetLastError());
+    return EMB_OK;
+}
+
 extern "C" emb_status emb_refine_flags(emb_forest f, emb_bins b, int32_t level, int32_t band, uint8_t *d_flags,
                                        void *stream)
 {
@@ -112,12 +123,7 @@ extern "C" emb_status emb_refine_flags(emb_forest f, emb_bins b, int32_t level, 
     const EmbLevel &lv = f->lv[level];
     if (lv.n == 0) return EMB_OK;
     if (!d_flags) return EMB_ERR_BAD_INPUT;
-    long long dil = refine_dilation(f, level, band);
+    long long dil = emb_refine_dilation(f, level, band);
     if (dil < 0) return EMB_ERR_RANGE;
-    cudaStream_t s = emb_stream(stream);
-    LevelGeom g = level_geom(f, level);
-    EMB_CUDA_TRY(cudaMemsetAsync(d_flags, 0, lv.n, s));
-    EMB_LAUNCH((k_refine), emb_grid(b->m->T, 32 * EMB_WU_WARPS), 32 * EMB_WU_WARPS, 0, s)(b->m->rec, b->m->T, g, dil, emb_lookup_of(lv), d_flags);
-    EMB_CUDA_TRY(cudaGetLastError());
-    return EMB_OK;
+    return emb_enq_refine(b->m->rec, b->m->T, level_geom(f, level), dil, lv, d_flags, emb_stream(stream));
 }

@@ -101,13 +101,27 @@ __global__ void k_xscan(const uint64_t *__restrict__ key, int64_t n, const unsig
     }
 }
 
+// Enqueue only: s_acc (n uint64) and p_acc (n uint32) are scratch; writes lv.mask.
+emb_status emb_enq_voxelize(const int4 *rec, const uint32_t *flist, int64_t nf, LevelGeom g, const EmbLevel &lv,
+                            unsigned long long *s_acc, unsigned int *p_acc, int block, cudaStream_t s)
+{
+    int *st = emb_status_word();
+    if (!st) return EMB_ERR_CUDA;
+    if (lv.n == 0) return EMB_OK;
+    EMB_CUDA_TRY(cudaMemsetAsync(s_acc, 0, lv.n * sizeof(unsigned long long), s));
+    EMB_CUDA_TRY(cudaMemsetAsync(p_acc, 0, lv.n * sizeof(unsigned int), s));
+    if (nf > 0)
+        EMB_LAUNCH((k_vox), emb_grid(nf, block), block, 0, s)(rec, flist, nf, g, emb_lookup_of(lv), s_acc, p_acc, st);
+    EMB_LAUNCH((k_xscan), emb_grid(lv.n, 256), 256, 0, s)(lv.key, lv.n, s_acc, p_acc, lv.mask);
+    EMB_CUDA_TRY(cudaGetLastError());
+    return EMB_OK;
+}
+
 extern "C" emb_status emb_voxelize(emb_forest f, emb_bins b, int32_t level, uint64_t *d_solid_mask, void *stream)
 {
     if (!f || !b) return EMB_ERR_BAD_INPUT;
     if (b->f != f || b->level != level || level < 0 || level > f->top) return EMB_ERR_STATE;
     cudaStream_t s = emb_stream(stream);
-    int *st = emb_status_word();
-    if (!st) return EMB_ERR_CUDA;
     EmbLevel &lv = f->lv[level];
     LevelGeom g = level_geom(f, level);
     if (lv.n == 0) {
@@ -119,13 +133,8 @@ extern "C" emb_status emb_voxelize(emb_forest f, emb_bins b, int32_t level, uint
     unsigned int *p_acc = nullptr;
     EMB_CUDA_TRY(cudaMallocAsync(&s_acc, lv.n * sizeof(unsigned long long), s));
     EMB_CUDA_TRY(cudaMallocAsync(&p_acc, lv.n * sizeof(unsigned int), s));
-    EMB_CUDA_TRY(cudaMemsetAsync(s_acc, 0, lv.n * sizeof(unsigned long long), s));
-    EMB_CUDA_TRY(cudaMemsetAsync(p_acc, 0, lv.n * sizeof(unsigned int), s));
-    if (b->nf > 0)
-        EMB_LAUNCH((k_vox), emb_grid(b->nf, 128), 128, 0, s)(b->m->rec, b->flist, b->nf, g, emb_lookup_of(lv), s_acc, p_acc,
-                                                    st);
-    EMB_LAUNCH((k_xscan), emb_grid(lv.n, 256), 256, 0, s)(lv.key, lv.n, s_acc, p_acc, lv.mask);
-    EMB_CUDA_TRY(cudaGetLastError());
+    emb_status rc = emb_enq_voxelize(b->m->rec, b->flist, b->nf, g, lv, s_acc, p_acc, 128, s);
+    if (rc != EMB_OK) return rc;
     if (d_solid_mask)
         EMB_CUDA_TRY(cudaMemcpyAsync(d_solid_mask, lv.mask, lv.n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
     EMB_CUDA_TRY(cudaFreeAsync(s_acc, s));

@@ -83,6 +83,10 @@ class Bins(_Handle):
     _destroy = "emb_bins_destroy"
 
 
+class Batch(_Handle):
+    _destroy = "emb_batch_destroy"
+
+
 # --------------------------------------------------------------------------- #
 # the C ABI, one wrapper per call
 # --------------------------------------------------------------------------- #
@@ -324,3 +328,66 @@ def embed(verts: torch.Tensor, tris: torch.Tensor, R: int, levels: int, band: in
         if st != EMB_OK:
             raise EmbError(st, "embed (device status)")
     return E
+
+
+# --------------------------------------------------------------------------- #
+# batches of meshes
+# --------------------------------------------------------------------------- #
+def emb_batch_create(meshes: list, levels: list, bands: list, lattices: list, stream=None) -> Batch:
+    n = len(meshes)
+    arr = (ctypes.c_void_p * n)(*[m.h for m in meshes])
+    lv = (ctypes.c_int32 * n)(*levels)
+    bd = (ctypes.c_int32 * n)(*bands)
+    lt = (ctypes.c_int32 * n)(*lattices)
+    h = ctypes.c_void_p()
+    _check(load().emb_batch_create(arr, lv, bd, lt, n, _stream(stream), ctypes.byref(h)), "emb_batch_create")
+    b = Batch(h, keep=tuple(meshes))
+    b.levels, b.lattices, b.n = list(levels), list(lattices), n
+    return b
+
+
+def emb_batch_run(batch: Batch, stream=None):
+    _check(load().emb_batch_run(batch.h, _stream(stream)), "emb_batch_run")
+
+
+def emb_batch_capture(batch: Batch, stream=None):
+    _check(load().emb_batch_capture(batch.h, _stream(stream)), "emb_batch_capture")
+
+
+def emb_batch_launch(batch: Batch, stream=None):
+    _check(load().emb_batch_launch(batch.h, _stream(stream)), "emb_batch_launch")
+
+
+def emb_batch_autotune(batch: Batch, stream=None) -> tuple:
+    c = (ctypes.c_int32 * 3)()
+    _check(load().emb_batch_autotune(batch.h, _stream(stream), c), "emb_batch_autotune")
+    return tuple(c)
+
+
+def emb_batch_info(batch: Batch, j: int):
+    blocks = (ctypes.c_int64 * (batch.levels[j] + 1))()
+    links = ctypes.c_int64(0)
+    _check(load().emb_batch_info(batch.h, int(j), blocks, ctypes.byref(links)), "emb_batch_info")
+    return list(blocks), links.value
+
+
+def emb_batch_results(batch: Batch, j: int, stream=None) -> dict:
+    """Mesh j of the last replay: per level (blocks, masks), and its cut-link table."""
+    blocks, n = emb_batch_info(batch, j)
+    out = dict(blocks=[], masks=[])
+    for L, nb in enumerate(blocks):
+        m = torch.empty(max(nb, 1), dtype=torch.int64, device="cuda")
+        bc = torch.empty((max(nb, 1), 3), dtype=torch.int32, device="cuda")
+        _check(load().emb_batch_results(batch.h, int(j), L, _ptr(m), _ptr(bc), None, None, None, None, _stream(stream)),
+               "emb_batch_results")
+        out["masks"].append(m[:nb])
+        out["blocks"].append(bc[:nb])
+    links = dict(cell=torch.empty(max(n, 1), dtype=torch.int32, device="cuda"),
+                 dir=torch.empty(max(n, 1), dtype=torch.uint8, device="cuda"),
+                 q=torch.empty(max(n, 1), dtype=torch.float32, device="cuda"),
+                 tri=torch.empty(max(n, 1), dtype=torch.int32, device="cuda"))
+    _check(load().emb_batch_results(batch.h, int(j), 0, None, None, _ptr(links["cell"]), _ptr(links["dir"]),
+                                    _ptr(links["q"]), _ptr(links["tri"]), _stream(stream)), "emb_batch_results")
+    out["links"] = {k: v[:n] for k, v in links.items()}
+    return out
+
