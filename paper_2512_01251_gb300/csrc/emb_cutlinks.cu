@@ -92,13 +92,17 @@ __global__ void k_link_cand(const uint64_t *__restrict__ mask, const int32_t *__
 // cube [P - h, P + h]; because the cells form a 4x4x4 lattice, the set of cells
 // passing that test is a sub-box, built as a 64-bit mask with a few bit
 // operations.  The surviving (triangle, cell) pairs of a tile are spread over the
-// 32 lanes with a prefix sum, so the exact tests run with full lanes.  Each pair
-// gets its three edge moments (U - P) x (V - P) once; every candidate direction
-// c of the cell then costs the dot products c . m (entries of c in {-1,0,1}).
-// Crossings are appended to a per-cell bucket; afterwards the owner lane of each
-// cell resolves the nearest crossing per direction with exact rational
-// comparisons and writes the links.  A bucket that overflows sends its cell
-// through an exact per-cell scan of the whole bin instead.
+// 32 lanes with a prefix sum.  Per pair, the directions whose segment box misses
+// the triangle box are dropped, the plane offset D = n . (A - P) is formed once,
+// and each remaining direction c first needs the two segment ends on opposite
+// sides of the plane (D against D - h n.c) before the three Pluecker signs are
+// evaluated.  When every vertex lies within 2^14 of P the Pluecker products fit
+// 32-bit integers and D fits 64 bits; otherwise a 128-bit path is taken.
+// Crossings, with q already rounded, are appended to a per-cell bucket;
+// afterwards the owner lane of each cell keeps, per direction, the nearest one
+// (exact rational comparison when a link crosses more than one face) and writes
+// the links.  A bucket that overflows sends its cell through an exact per-cell
+// scan of the whole bin instead.
 #define LE_WARPS 4
 #define LE_TILE 32
 #define LE_BCAP 28
@@ -111,8 +115,8 @@ struct TriT {
 
 struct LeWarp {
     TriT tile[LE_TILE];
-    uint2 hit[32][LE_BCAP];  // (triangle id, direction)
-    int best[27][32];        // nearest crossed triangle per (direction, slot) during resolution
+    uint2 hit[LE_BCAP][32];  // per slot: (bin-local index | direction << 24, q bits)
+    int best[27][32];        // per (direction, slot): index of the nearest hit during resolution
     int hcnt[32];
     uint32_t cm[32];         // candidate directions of each slot's cell
 };
@@ -264,7 +268,76 @@ __device__ __noinline__ void scan_cell_slow(const uint32_t *__restrict__ bin_ent
     }
 }
 
-__global__ void __launch_bounds__(LE_WARPS * 32, 4) k_link_emit(const __grid_constant__ LinkTable tab,
+// A cell whose bucket overflowed: exact per-cell scan of the whole bin, links written directly.
+__device__ __noinline__ void emit_cell_slow(const LinkMesh &M, uint32_t e0, uint32_t e1, long long px, long long py,
+                                           long long pz, long long h, uint32_t cm, uint32_t o0, int64_t cell, int *st)
+{
+    int bestT[27];
+    scan_cell_slow(M.bin_ent, e0, e1, M.rec, px, py, pz, h, cm, bestT);
+    uint32_t mm = cm, o = o0;
+    while (mm) {
+        const int d = __ffs(mm) - 1;
+        mm &= mm - 1;
+        if (o >= M.cap) {
+            emb_set_status(st, EMB_ERR_CAPACITY);
+            ++o;
+            continue;
+        }
+        const int tr = bestT[d];
+        float q = -1.0f;
+        if (tr >= 0) {
+            int cx, cy, cz;
+            emb_dir(d, cx, cy, cz);
+            i128 N;
+            long long Mq;
+            tri_NM(M.rec, tr, px, py, pz, cx, cy, cz, N, Mq);
+            q = __fdiv_rn(i128_to_float(N), (float)Mq * (float)h);
+        } else {
+            emb_set_status(st, EMB_ERR_STATE);
+        }
+        M.o_cell[o] = (int32_t)cell;
+        M.o_dir[o] = (uint8_t)d;
+        M.o_q[o] = q;
+        M.o_tri[o] = tr;
+        ++o;
+    }
+}
+
+__device__ __forceinline__ int side_sign64(long long X, long long nx, long long ny, long long nz)
+{
+    if (X != 0) return X > 0 ? 1 : -1;
+    if (nx) return nx > 0 ? -1 : 1;
+    if (ny) return ny > 0 ? -1 : 1;
+    return nz > 0 ? -1 : 1;
+}
+
+// Exact segment test for a pair whose vertices are not all within 2^14 of P
+// (128-bit plane offsets, 64-bit Pluecker products); returns t = N / (h M).
+__device__ __noinline__ bool pair_cross_wide(const TriT &T, long long px, long long py, long long pz, int cx, int cy,
+                                             int cz, long long h, float *q)
+{
+    const long long ax = T.ax - px, ay = T.ay - py, az = T.az - pz;
+    const long long bx = T.bx - px, by = T.by - py, bz = T.bz - pz;
+    const long long qx = T.cx - px, qy = T.cy - py, qz = T.cz - pz;
+    const long long m1x = ay * bz - az * by, m1y = az * bx - ax * bz, m1z = ax * by - ay * bx;
+    const long long m2x = by * qz - bz * qy, m2y = bz * qx - bx * qz, m2z = bx * qy - by * qx;
+    const long long m3x = qy * az - qz * ay, m3y = qz * ax - qx * az, m3z = qx * ay - qy * ax;
+    i128 D = 0;
+    bool haveD = false;
+    if (!seg_cross(cx, cy, cz, h, ax, ay, az, bx, by, bz, qx, qy, qz, T.nx, T.ny, T.nz, m1x, m1y, m1z, m2x, m2y, m2z, m3x,
+                   m3y, m3z, D, haveD))
+        return false;
+    const long long nc = cdot(cx, cy, cz, T.nx, T.ny, T.nz);
+    const i128 N = nc > 0 ? D : -D;
+    const long long M = nc > 0 ? nc : -nc;
+    *q = __fdiv_rn(i128_to_float(N), (float)M * (float)h);
+    return true;
+}
+
+#ifndef LE_MINB
+#define LE_MINB 4
+#endif
+__global__ void __launch_bounds__(LE_WARPS * 32, LE_MINB) k_link_emit(const __grid_constant__ LinkTable tab,
                                                                 unsigned int *__restrict__ next, int *st)
 {
     extern __shared__ __align__(16) unsigned char le_smem[];
@@ -282,286 +355,271 @@ __global__ void __launch_bounds__(LE_WARPS * 32, 4) k_link_emit(const __grid_con
     __syncthreads();
     // persistent warps: take the next (mesh, block with links) item of the shared work queue
     for (;;) {
-    unsigned int widx = 0;
-    if (lane == 0) widx = atomicAdd(next, 1u);
-    widx = __shfl_sync(0xffffffffu, widx, 0);
-    if (widx >= s_pre[tab.n]) return;
-    int mj = 0;
-    while (mj + 1 < tab.n && s_pre[mj + 1] <= widx) ++mj;
-    const LinkMesh &M = tab.m[mj];
-    const uint64_t *__restrict__ key = M.key;
-    const uint64_t *__restrict__ cand = M.cand;
-    const uint32_t *__restrict__ bin_off = M.bin_off;
-    const uint32_t *__restrict__ bin_ent = M.bin_ent;
-    const int4 *__restrict__ rec = M.rec;
-    const LevelGeom g = M.g;
-    const int64_t b = M.work[widx - s_pre[mj]];
-    const uint32_t base = M.blk_off[b];
-    // candidate directions of cells lane and 32 + lane from the block's direction words
-    const uint64_t wd = lane < 26 ? cand[b * 26 + lane] : 0ull;
-    uint32_t c0 = 0, c1 = 0;
-    unsigned long long bmask = 0;
+        unsigned int widx = 0;
+        if (lane == 0) widx = atomicAdd(next, 1u);
+        widx = __shfl_sync(0xffffffffu, widx, 0);
+        if (widx >= s_pre[tab.n]) return;
+        int mj = 0;
+        while (mj + 1 < tab.n && s_pre[mj + 1] <= widx) ++mj;
+        const LinkMesh &M = tab.m[mj];
+        const uint32_t *__restrict__ bin_ent = M.bin_ent;
+        const int4 *__restrict__ rec = M.rec;
+        const int64_t b = M.work[widx - s_pre[mj]];
+        const uint32_t base = M.blk_off[b];
+        // candidate directions of cells lane and 32 + lane from the block's direction words
+        const uint64_t wd = lane < 26 ? M.cand[b * 26 + lane] : 0ull;
+        uint32_t c0 = 0, c1 = 0;
+        unsigned long long bmask = 0;
 #pragma unroll
-    for (int d = 0; d < 26; ++d) {
-        const uint64_t wdd = ((unsigned long long)__shfl_sync(0xffffffffu, (unsigned)(wd >> 32), d) << 32) |
-                             (unsigned long long)__shfl_sync(0xffffffffu, (unsigned)wd, d);
-        bmask |= wdd;
-        c0 |= (uint32_t)((wdd >> lane) & 1ull) << (d + 1);
-        c1 |= (uint32_t)((wdd >> (32 + lane)) & 1ull) << (d + 1);
-    }
-    const int nbc = __popcll(bmask);
-    // exclusive link offsets of cells lane and 32 + lane, in cell order
-    uint32_t k0 = __popc(c0), k1 = __popc(c1), i0 = k0, i1 = k1;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t t0 = __shfl_up_sync(0xffffffffu, i0, o), t1 = __shfl_up_sync(0xffffffffu, i1, o);
-        if (lane >= o) {
-            i0 += t0;
-            i1 += t1;
+        for (int d = 0; d < 26; ++d) {
+            const uint64_t wdd = ((unsigned long long)__shfl_sync(0xffffffffu, (unsigned)(wd >> 32), d) << 32) |
+                                 (unsigned long long)__shfl_sync(0xffffffffu, (unsigned)wd, d);
+            bmask |= wdd;
+            c0 |= (uint32_t)((wdd >> lane) & 1ull) << (d + 1);
+            c1 |= (uint32_t)((wdd >> (32 + lane)) & 1ull) << (d + 1);
         }
-    }
-    const uint32_t tot0 = __shfl_sync(0xffffffffu, i0, 31);
-    const uint32_t ex0 = i0 - k0, ex1 = tot0 + i1 - k1;
-    const uint64_t bk = key[b];
-    const long long X0 = 4 * (long long)(bk & EMB_KEY_MASK) * g.h, Y0 = 4 * (long long)((bk >> EMB_KEY_BITS) & EMB_KEY_MASK) * g.h,
-                    Z0 = 4 * (long long)(bk >> (2 * EMB_KEY_BITS)) * g.h;
-    const uint32_t e0 = bin_off[b], e1 = bin_off[b + 1];
-    const long long h = g.h, half = g.half;
-    const int lh = __ffsll(h) - 1;  // h is a power of two
-    for (int chunk = 0; chunk * 32 < nbc; ++chunk) {
-        // the chunk's cells: set bits 32*chunk .. 32*chunk+31 of bmask
-        const int lo_bit = select64(bmask, chunk * 32);
-        const int ncc = min(32, nbc - chunk * 32);
-        const int hi_bit = select64(bmask, chunk * 32 + ncc - 1);
-        const unsigned long long cmask = bmask & bit_range(lo_bit, hi_bit);
-        // slot lane: its cell, candidates and link offset
-        const bool active = lane < ncc;
-        const int t = active ? select64(cmask, lane) : 0;
-        const uint32_t cm_lo = __shfl_sync(0xffffffffu, c0, t & 31), cm_hi = __shfl_sync(0xffffffffu, c1, t & 31);
-        const uint32_t ex_lo = __shfl_sync(0xffffffffu, ex0, t & 31), ex_hi = __shfl_sync(0xffffffffu, ex1, t & 31);
-        const uint32_t cm = active ? (t < 32 ? cm_lo : cm_hi) : 0u;
-        const uint32_t off = t < 32 ? ex_lo : ex_hi;
-        S.cm[lane] = cm;
-        S.hcnt[lane] = 0;
-        __syncwarp();
-        for (uint32_t e = e0; e < e1; e += LE_TILE) {
-            // stage triangle `lane` of this tile and the chunk cells its reach box touches
-            unsigned long long pm = 0;
-            if (e + lane < e1) {
-                const uint32_t id = bin_ent[e + lane];
-                const int4 A = rec[3 * (int64_t)id], B = rec[3 * (int64_t)id + 1], C = rec[3 * (int64_t)id + 2];
-                TriT s;
-                s.ax = A.x; s.ay = A.y; s.az = A.z;
-                s.bx = B.x; s.by = B.y; s.bz = B.z;
-                s.cx = C.x; s.cy = C.y; s.cz = C.z;
-                s.id = (int)id;
-                s.lox = min(A.x, min(B.x, C.x)); s.hix = max(A.x, max(B.x, C.x));
-                s.loy = min(A.y, min(B.y, C.y)); s.hiy = max(A.y, max(B.y, C.y));
-                s.loz = min(A.z, min(B.z, C.z)); s.hiz = max(A.z, max(B.z, C.z));
-                const long long ux = (long long)B.x - A.x, uy = (long long)B.y - A.y, uz = (long long)B.z - A.z;
-                const long long vx = (long long)C.x - A.x, vy = (long long)C.y - A.y, vz = (long long)C.z - A.z;
-                s.nx = uy * vz - uz * vy;
-                s.ny = uz * vx - ux * vz;
-                s.nz = ux * vy - uy * vx;
-                S.tile[lane] = s;
-                // cell i (centre X0 + (2i+1) half) reaches the box iff lo - h <= centre <= hi + h
-                int r0[3], r1[3];
-                const long long lo3[3] = {s.lox - X0, s.loy - Y0, s.loz - Z0};
-                const long long hi3[3] = {s.hix - X0, s.hiy - Y0, s.hiz - Z0};
+        const int nbc = __popcll(bmask);
+        // exclusive link offsets of cells lane and 32 + lane, in cell order
+        uint32_t k0 = __popc(c0), k1 = __popc(c1), i0 = k0, i1 = k1;
 #pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    long long a = lo3[d] - h - half;  // ceil(a / h)
-                    long long c = hi3[d] + h - half;  // floor(c / h)
-                    long long i0_ = -((-a) >> lh), i1_ = c >> lh;
-                    r0[d] = (int)(i0_ < 0 ? 0 : (i0_ > 4 ? 4 : i0_));
-                    r1[d] = (int)(i1_ > 3 ? 3 : (i1_ < -1 ? -1 : i1_));
-                }
-                if (r0[0] <= r1[0] && r0[1] <= r1[1] && r0[2] <= r1[2]) {
-                    const unsigned long long X = (unsigned long long)(((1u << (r1[0] + 1)) - 1u) & ~((1u << r0[0]) - 1u)) *
-                                                 0x1111111111111111ull;
-                    const unsigned long long Y = (((1ull << (4 * r1[1] + 4)) - 1ull) & ~((1ull << (4 * r0[1])) - 1ull)) *
-                                                 0x0001000100010001ull;
-                    const unsigned long long Z = bit_range(16 * r0[2], 16 * r1[2] + 15);
-                    pm = X & Y & Z & cmask;
-                }
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t t0 = __shfl_up_sync(0xffffffffu, i0, o), t1 = __shfl_up_sync(0xffffffffu, i1, o);
+            if (lane >= o) {
+                i0 += t0;
+                i1 += t1;
             }
+        }
+        const uint32_t tot0 = __shfl_sync(0xffffffffu, i0, 31);
+        const uint32_t ex0 = i0 - k0, ex1 = tot0 + i1 - k1;
+        const uint64_t bk = M.key[b];
+        const long long h = M.g.h, half = M.g.half;
+        const long long X0 = 4 * (long long)(bk & EMB_KEY_MASK) * h, Y0 = 4 * (long long)((bk >> EMB_KEY_BITS) & EMB_KEY_MASK) * h,
+                        Z0 = 4 * (long long)(bk >> (2 * EMB_KEY_BITS)) * h;
+        const uint32_t e0 = M.bin_off[b], e1 = M.bin_off[b + 1];
+        const int lh = __ffsll(h) - 1;  // h is a power of two
+        const long long LIM = 1ll << 14;
+        for (int chunk = 0; chunk * 32 < nbc; ++chunk) {
+            // the chunk's cells: set bits 32*chunk .. 32*chunk+31 of bmask
+            const int lo_bit = select64(bmask, chunk * 32);
+            const int ncc = min(32, nbc - chunk * 32);
+            const int hi_bit = select64(bmask, chunk * 32 + ncc - 1);
+            const unsigned long long cmask = bmask & bit_range(lo_bit, hi_bit);
+            // slot lane: its cell, candidates and link offset
+            const bool active = lane < ncc;
+            const int t = active ? select64(cmask, lane) : 0;
+            const uint32_t cm_lo = __shfl_sync(0xffffffffu, c0, t & 31), cm_hi = __shfl_sync(0xffffffffu, c1, t & 31);
+            const uint32_t ex_lo = __shfl_sync(0xffffffffu, ex0, t & 31), ex_hi = __shfl_sync(0xffffffffu, ex1, t & 31);
+            const uint32_t cm = active ? (t < 32 ? cm_lo : cm_hi) : 0u;
+            const uint32_t off = t < 32 ? ex_lo : ex_hi;
+            S.cm[lane] = cm;
+            S.hcnt[lane] = 0;
             __syncwarp();
-            // spread the tile's (triangle, cell) pairs over the lanes
-            const int np = __popcll(pm);
-            int incl = np;
+            for (uint32_t e = e0; e < e1; e += LE_TILE) {
+                // stage triangle `lane` of this tile and the chunk cells its reach box touches
+                unsigned long long pm = 0;
+                if (e + lane < e1) {
+                    const uint32_t id = bin_ent[e + lane];
+                    const int4 A = rec[3 * (int64_t)id], B = rec[3 * (int64_t)id + 1], C = rec[3 * (int64_t)id + 2];
+                    TriT s;
+                    s.ax = A.x; s.ay = A.y; s.az = A.z;
+                    s.bx = B.x; s.by = B.y; s.bz = B.z;
+                    s.cx = C.x; s.cy = C.y; s.cz = C.z;
+                    s.id = (int)id;
+                    s.lox = min(A.x, min(B.x, C.x)); s.hix = max(A.x, max(B.x, C.x));
+                    s.loy = min(A.y, min(B.y, C.y)); s.hiy = max(A.y, max(B.y, C.y));
+                    s.loz = min(A.z, min(B.z, C.z)); s.hiz = max(A.z, max(B.z, C.z));
+                    const long long ux = (long long)B.x - A.x, uy = (long long)B.y - A.y, uz = (long long)B.z - A.z;
+                    const long long vx = (long long)C.x - A.x, vy = (long long)C.y - A.y, vz = (long long)C.z - A.z;
+                    s.nx = uy * vz - uz * vy;
+                    s.ny = uz * vx - ux * vz;
+                    s.nz = ux * vy - uy * vx;
+                    S.tile[lane] = s;
+                    // cell i (centre X0 + (2i+1) half) reaches the box iff lo - h <= centre <= hi + h
+                    int r0[3], r1[3];
+                    const long long lo3[3] = {s.lox - X0, s.loy - Y0, s.loz - Z0};
+                    const long long hi3[3] = {s.hix - X0, s.hiy - Y0, s.hiz - Z0};
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                int tt = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += tt;
-            }
-            const int total = __shfl_sync(0xffffffffu, incl, 31);
-            for (int s0 = 0; s0 < total; s0 += 32) {
-                // ---- level 1: lane -> one (triangle, cell) pair of this tile
-                const int gidx = s0 + lane;
-                int lo = 0;
-#pragma unroll
-                for (int step = 16; step >= 1; step >>= 1) {
-                    int v = __shfl_sync(0xffffffffu, incl, lo + step - 1);
-                    if (v <= gidx) lo += step;
+                    for (int d = 0; d < 3; ++d) {
+                        long long a_ = lo3[d] - h - half;  // ceil(a / h)
+                        long long c_ = hi3[d] + h - half;  // floor(c / h)
+                        long long i0_ = -((-a_) >> lh), i1_ = c_ >> lh;
+                        r0[d] = (int)(i0_ < 0 ? 0 : (i0_ > 4 ? 4 : i0_));
+                        r1[d] = (int)(i1_ > 3 ? 3 : (i1_ < -1 ? -1 : i1_));
+                    }
+                    if (r0[0] <= r1[0] && r0[1] <= r1[1] && r0[2] <= r1[2]) {
+                        const unsigned long long X = (unsigned long long)(((1u << (r1[0] + 1)) - 1u) & ~((1u << r0[0]) - 1u)) *
+                                                     0x1111111111111111ull;
+                        const unsigned long long Y = (((1ull << (4 * r1[1] + 4)) - 1ull) & ~((1ull << (4 * r0[1])) - 1ull)) *
+                                                     0x0001000100010001ull;
+                        const unsigned long long Z = bit_range(16 * r0[2], 16 * r1[2] + 15);
+                        pm = X & Y & Z & cmask;
+                    }
                 }
-                const int ti = lo > 31 ? 31 : lo;
-                const int excl_i = __shfl_sync(0xffffffffu, incl - np, ti);
-                const unsigned long long pmi = ((unsigned long long)__shfl_sync(0xffffffffu, (unsigned)(pm >> 32), ti) << 32) |
-                                               (unsigned long long)__shfl_sync(0xffffffffu, (unsigned)pm, ti);
-                uint32_t ok = 0;
-                int cell = 0;
-                if (gidx < total) {
-                    cell = select64(pmi, gidx - excl_i);
+                __syncwarp();
+                // spread the tile's (triangle, cell) pairs over the lanes
+                const int np = __popcll(pm);
+                int incl = np;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    int tt = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += tt;
+                }
+                const int total = __shfl_sync(0xffffffffu, incl, 31);
+                for (int s0 = 0; s0 < total; s0 += 32) {
+                    const int gidx = s0 + lane;
+                    int lo = 0;
+#pragma unroll
+                    for (int step = 16; step >= 1; step >>= 1) {
+                        int v = __shfl_sync(0xffffffffu, incl, lo + step - 1);
+                        if (v <= gidx) lo += step;
+                    }
+                    const int ti = lo > 31 ? 31 : lo;
+                    const int excl_i = __shfl_sync(0xffffffffu, incl - np, ti);
+                    const unsigned long long pmi = ((unsigned long long)__shfl_sync(0xffffffffu, (unsigned)(pm >> 32), ti) << 32) |
+                                                   (unsigned long long)__shfl_sync(0xffffffffu, (unsigned)pm, ti);
+                    if (gidx >= total) continue;
+                    const int cell = select64(pmi, gidx - excl_i);
                     const int slot = __popcll(cmask & ((1ull << cell) - 1ull));
                     const TriT &T = S.tile[ti];
                     const long long px = X0 + (2 * (cell & 3) + 1) * half, py = Y0 + (2 * ((cell >> 2) & 3) + 1) * half,
                                     pz = Z0 + (2 * (cell >> 4) + 1) * half;
-                    // directions whose segment box meets the triangle box: along each axis the
-                    // segment covers [-h, 0], {0} or [0, h] relative to P
+                    const uint32_t ccm = S.cm[slot];
+                    const uint32_t local = e - e0 + (uint32_t)ti;
                     const long long l0 = T.lox - px, h0 = T.hix - px, l1 = T.loy - py, h1 = T.hiy - py,
                                     l2 = T.loz - pz, h2 = T.hiz - pz;
-                    ok = S.cm[slot];
-                    ok &= dirs_allowed(0, l0 <= 0 && h0 >= -h, l0 <= 0 && h0 >= 0, l0 <= h && h0 >= 0);
-                    ok &= dirs_allowed(1, l1 <= 0 && h1 >= -h, l1 <= 0 && h1 >= 0, l1 <= h && h1 >= 0);
-                    ok &= dirs_allowed(2, l2 <= 0 && h2 >= -h, l2 <= 0 && h2 >= 0, l2 <= h && h2 >= 0);
-                }
-                // ---- level 2: lane -> one (pair, direction) item of this batch
-                const int nk = __popc(ok);
-                int kincl = nk;
+                    const bool narrow = l0 > -LIM && h0 < LIM && l1 > -LIM && h1 < LIM && l2 > -LIM && h2 < LIM;
+                    if (narrow) {
+                        // all vertex offsets below 2^14 in magnitude: moments < 2^29, their signed sums
+                        // over the components of c below 2^31, n = m1 + m2 + m3, D below 2^47
+                        const int ax = (int)(T.ax - px), ay = (int)(T.ay - py), az = (int)(T.az - pz);
+                        const int bx = (int)(T.bx - px), by = (int)(T.by - py), bz = (int)(T.bz - pz);
+                        const int qx = (int)(T.cx - px), qy = (int)(T.cy - py), qz = (int)(T.cz - pz);
+                        const int m1x = ay * bz - az * by, m1y = az * bx - ax * bz, m1z = ax * by - ay * bx;
+                        const int m2x = by * qz - bz * qy, m2y = bz * qx - bx * qz, m2z = bx * qy - by * qx;
+                        const int m3x = qy * az - qz * ay, m3y = qz * ax - qx * az, m3z = qx * ay - qy * ax;
+                        const int nx = m1x + m2x + m3x, ny = m1y + m2y + m3y, nz = m1z + m2z + m3z;
+                        const long long D = (long long)nx * ax + (long long)ny * ay + (long long)nz * az;
+                        // line tests for the 13 direction pairs (odd index d and its opposite d + 1)
+                        uint32_t line = 0, degen = 0;
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    int tt = __shfl_up_sync(0xffffffffu, kincl, o);
-                    if (lane >= o) kincl += tt;
-                }
-                const int ktotal = __shfl_sync(0xffffffffu, kincl, 31);
-                for (int k0 = 0; k0 < ktotal; k0 += 32) {
-                    const int gk = k0 + lane;
-                    int pl = 0;
-#pragma unroll
-                    for (int step = 16; step >= 1; step >>= 1) {
-                        int v = __shfl_sync(0xffffffffu, kincl, pl + step - 1);
-                        if (v <= gk) pl += step;
-                    }
-                    const int src = pl > 31 ? 31 : pl;
-                    const int kex = __shfl_sync(0xffffffffu, kincl - nk, src);
-                    const uint32_t okp = __shfl_sync(0xffffffffu, ok, src);
-                    const int tip = __shfl_sync(0xffffffffu, ti, src);
-                    const int cellp = __shfl_sync(0xffffffffu, cell, src);
-                    if (gk >= ktotal) continue;
-                    const int d = select64((unsigned long long)okp, gk - kex);
-                    const int slot = __popcll(cmask & ((1ull << cellp) - 1ull));
-                    const TriT &T = S.tile[tip];
-                    const long long px = X0 + (2 * (cellp & 3) + 1) * half, py = Y0 + (2 * ((cellp >> 2) & 3) + 1) * half,
-                                    pz = Z0 + (2 * (cellp >> 4) + 1) * half;
-                    int cx, cy, cz;
-                    emb_dir(d, cx, cy, cz);
-                    const long long nc = cdot(cx, cy, cz, T.nx, T.ny, T.nz);
-                    if (nc == 0) continue;
-                    const int sn = nc > 0 ? 1 : -1;
-                    const long long ax = T.ax - px, ay = T.ay - py, az = T.az - pz;
-                    const long long bxx = T.bx - px, byy = T.by - py, bzz = T.bz - pz;
-                    const long long qx = T.cx - px, qy = T.cy - py, qz = T.cz - pz;
-                    int s1, s2, s3;
-                    const long long lim = 1ll << 14;
-                    if (T.lox - px > -lim && T.hix - px < lim && T.loy - py > -lim && T.hiy - py < lim && T.loz - pz > -lim &&
-                        T.hiz - pz < lim) {
-                        // every coordinate below 2^14 in magnitude: products < 2^28, sums < 2^31
-                        const int ax32 = (int)ax, ay32 = (int)ay, az32 = (int)az, bx32 = (int)bxx, by32 = (int)byy,
-                                  bz32 = (int)bzz, qx32 = (int)qx, qy32 = (int)qy, qz32 = (int)qz;
-                        int v1 = 0, v2 = 0, v3 = 0;
-                        if (cx) {
-                            const int e1 = ay32 * bz32 - az32 * by32, e2 = by32 * qz32 - bz32 * qy32, e3 = qy32 * az32 - qz32 * ay32;
-                            v1 += cx * e1; v2 += cx * e2; v3 += cx * e3;
+                        for (int r = 0; r < 13; ++r) {
+                            const int d = 2 * r + 1;
+                            if (!(ccm & (3u << d))) continue;
+                            int cx, cy, cz;
+                            emb_dir(d, cx, cy, cz);
+                            const int NC = cx * nx + cy * ny + cz * nz;
+                            const int V1 = cx * m1x + cy * m1y + cz * m1z;
+                            const int V2 = cx * m2x + cy * m2y + cz * m2z;
+                            const int V3 = cx * m3x + cy * m3y + cz * m3z;
+                            if (NC == 0) continue;  // line parallel to the face: never crosses
+                            if (V1 == 0 || V2 == 0 || V3 == 0) {
+                                degen |= 1u << d;
+                                continue;
+                            }
+                            if (((V1 ^ NC) | (V2 ^ NC) | (V3 ^ NC)) >= 0) line |= 1u << d;
                         }
-                        if (cy) {
-                            const int e1 = az32 * bx32 - ax32 * bz32, e2 = bz32 * qx32 - bx32 * qz32, e3 = qz32 * ax32 - qx32 * az32;
-                            v1 += cy * e1; v2 += cy * e2; v3 += cy * e3;
+                        // members of line-hit pairs that are candidates: the segment ends must straddle the plane
+                        uint32_t mm = (line | (line << 1)) & ccm;
+                        while (mm) {
+                            const int d = __ffs(mm) - 1;
+                            mm &= mm - 1;
+                            int cx, cy, cz;
+                            emb_dir(d, cx, cy, cz);
+                            const long long nc = (long long)(cx * nx + cy * ny + cz * nz);
+                            const int sn = nc > 0 ? 1 : -1;
+                            if (side_sign64(D, nx, ny, nz) != sn) continue;           // t <= 0
+                            if (side_sign64(D - h * nc, nx, ny, nz) != -sn) continue;  // t >= 1
+                            const long long N = sn > 0 ? D : -D, Mq = nc > 0 ? nc : -nc;
+                            const float q = __fdiv_rn((float)N, (float)Mq * (float)h);
+                            const int kk = atomicAdd(&S.hcnt[slot], 1);
+                            if (kk < LE_BCAP) S.hit[kk][slot] = make_uint2(local | ((uint32_t)d << 24), __float_as_uint(q));
                         }
-                        if (cz) {
-                            const int e1 = ax32 * by32 - ay32 * bx32, e2 = bx32 * qy32 - by32 * qx32, e3 = qx32 * ay32 - qy32 * ax32;
-                            v1 += cz * e1; v2 += cz * e2; v3 += cz * e3;
+                        // a zero Pluecker value: resolve the pair's directions exactly
+                        mm = (degen | (degen << 1)) & ccm;
+                        while (mm) {
+                            const int d = __ffs(mm) - 1;
+                            mm &= mm - 1;
+                            int cx, cy, cz;
+                            emb_dir(d, cx, cy, cz);
+                            float q;
+                            if (!pair_cross_wide(T, px, py, pz, cx, cy, cz, h, &q)) continue;
+                            const int kk = atomicAdd(&S.hcnt[slot], 1);
+                            if (kk < LE_BCAP) S.hit[kk][slot] = make_uint2(local | ((uint32_t)d << 24), __float_as_uint(q));
                         }
-                        s1 = plk_resolve(v1, cx, cy, cz, bxx - ax, byy - ay, bzz - az);
-                        if (s1 != sn) continue;
-                        s2 = plk_resolve(v2, cx, cy, cz, qx - bxx, qy - byy, qz - bzz);
-                        if (s2 != sn) continue;
-                        s3 = plk_resolve(v3, cx, cy, cz, ax - qx, ay - qy, az - qz);
-                        if (s3 != sn) continue;
                     } else {
-                        const long long m1x = ay * bzz - az * byy, m1y = az * bxx - ax * bzz, m1z = ax * byy - ay * bxx;
-                        const long long m2x = byy * qz - bzz * qy, m2y = bzz * qx - bxx * qz, m2z = bxx * qy - byy * qx;
-                        const long long m3x = qy * az - qz * ay, m3y = qz * ax - qx * az, m3z = qx * ay - qy * ax;
-                        if (plk_resolve(cdot(cx, cy, cz, m1x, m1y, m1z), cx, cy, cz, bxx - ax, byy - ay, bzz - az) != sn) continue;
-                        if (plk_resolve(cdot(cx, cy, cz, m2x, m2y, m2z), cx, cy, cz, qx - bxx, qy - byy, qz - bzz) != sn) continue;
-                        if (plk_resolve(cdot(cx, cy, cz, m3x, m3y, m3z), cx, cy, cz, ax - qx, ay - qy, az - qz) != sn) continue;
+                        uint32_t mm = ccm;
+                        while (mm) {
+                            const int d = __ffs(mm) - 1;
+                            mm &= mm - 1;
+                            int cx, cy, cz;
+                            emb_dir(d, cx, cy, cz);
+                            float q;
+                            if (!pair_cross_wide(T, px, py, pz, cx, cy, cz, h, &q)) continue;
+                            const int kk = atomicAdd(&S.hcnt[slot], 1);
+                            if (kk < LE_BCAP) S.hit[kk][slot] = make_uint2(local | ((uint32_t)d << 24), __float_as_uint(q));
+                        }
                     }
-                    const i128 D = mul128(T.nx, ax) + mul128(T.ny, ay) + mul128(T.nz, az);
-                    if (side_sign(D, T.nx, T.ny, T.nz) != sn) continue;                   // t <= 0
-                    if (side_sign(D - mul128(h, nc), T.nx, T.ny, T.nz) != -sn) continue;  // t >= 1
-                    const int kk = atomicAdd(&S.hcnt[slot], 1);
-                    if (kk < LE_BCAP) S.hit[slot][kk] = make_uint2((unsigned)T.id, (unsigned)d);
+                }
+                __syncwarp();
+            }
+            // resolve: the owner lane of each cell keeps, per direction, the nearest crossing
+            if (active) {
+                const long long px = X0 + (2 * (t & 3) + 1) * half, py = Y0 + (2 * ((t >> 2) & 3) + 1) * half,
+                                pz = Z0 + (2 * (t >> 4) + 1) * half;
+                const int nh = S.hcnt[lane];
+                if (nh > LE_BCAP) {
+                    emit_cell_slow(M, e0, e1, px, py, pz, h, cm, base + off, b * 64 + t, st);
+                } else {
+                    for (int d = 0; d < 27; ++d) S.best[d][lane] = -1;
+                    for (int k = 0; k < nh; ++k) {
+                        const uint2 hv = S.hit[k][lane];
+                        const int d = (int)(hv.x >> 24), prev = S.best[d][lane];
+                        bool better = prev < 0;
+                        if (!better) {
+                            // several faces cross this link: compare t exactly
+                            int cx, cy, cz;
+                            emb_dir(d, cx, cy, cz);
+                            const int tn = (int)bin_ent[e0 + (hv.x & 0xFFFFFFu)];
+                            const int to = (int)bin_ent[e0 + (S.hit[prev][lane].x & 0xFFFFFFu)];
+                            i128 Nn, No;
+                            long long Mn, Mo;
+                            tri_NM(rec, tn, px, py, pz, cx, cy, cz, Nn, Mn);
+                            tri_NM(rec, to, px, py, pz, cx, cy, cz, No, Mo);
+                            const i128 l = Nn * (i128)Mo, rr = No * (i128)Mn;
+                            better = l < rr || (l == rr && tn < to);
+                        }
+                        if (better) S.best[d][lane] = k;
+                    }
+                    uint32_t mm = cm;
+                    uint32_t o = base + off;
+                    while (mm) {
+                        const int d = __ffs(mm) - 1;
+                        mm &= mm - 1;
+                        if (o >= M.cap) {
+                            emb_set_status(st, EMB_ERR_CAPACITY);
+                            ++o;
+                            continue;
+                        }
+                        int tr = -1;
+                        float q = -1.0f;
+                        const int k = S.best[d][lane];
+                        if (k >= 0) {
+                            const uint2 hv = S.hit[k][lane];
+                            tr = (int)bin_ent[e0 + (hv.x & 0xFFFFFFu)];
+                            q = __uint_as_float(hv.y);
+                        } else {
+                            emb_set_status(st, EMB_ERR_STATE);  // a fluid-to-solid link must cross the surface
+                        }
+                        M.o_cell[o] = (int32_t)(b * 64 + t);
+                        M.o_dir[o] = (uint8_t)d;
+                        M.o_q[o] = q;
+                        M.o_tri[o] = tr;
+                        ++o;
+                    }
                 }
             }
             __syncwarp();
         }
-        // resolve: the owner lane of each cell picks, per direction, the nearest crossing
-        if (active) {
-            const long long px = X0 + (2 * (t & 3) + 1) * half, py = Y0 + (2 * ((t >> 2) & 3) + 1) * half,
-                            pz = Z0 + (2 * (t >> 4) + 1) * half;
-            const int nh = S.hcnt[lane];
-            int slowT[27];
-            const bool slow = nh > LE_BCAP;
-            if (slow) scan_cell_slow(bin_ent, e0, e1, rec, px, py, pz, h, cm, slowT);
-            if (!slow) {
-                for (int d = 0; d < 27; ++d) S.best[d][lane] = -1;
-                for (int k = 0; k < nh; ++k) {
-                    const uint2 hv = S.hit[lane][k];
-                    const int d = (int)hv.y, tr = (int)hv.x, prev = S.best[d][lane];
-                    bool better = prev < 0;
-                    if (!better) {
-                        int cx, cy, cz;
-                        emb_dir(d, cx, cy, cz);
-                        i128 Nn, No;
-                        long long Mn, Mo;
-                        tri_NM(rec, tr, px, py, pz, cx, cy, cz, Nn, Mn);
-                        tri_NM(rec, prev, px, py, pz, cx, cy, cz, No, Mo);
-                        const i128 l = Nn * (i128)Mo, rr = No * (i128)Mn;
-                        better = l < rr || (l == rr && tr < prev);
-                    }
-                    if (better) S.best[d][lane] = tr;
-                }
-            }
-            uint32_t mm = cm;
-            int r = 0;
-            while (mm) {
-                const int d = __ffs(mm) - 1;
-                mm &= mm - 1;
-                int cx, cy, cz;
-                emb_dir(d, cx, cy, cz);
-                const int bT = slow ? slowT[d] : S.best[d][lane];
-                i128 bN = 0;
-                long long bM = 1;
-                if (bT >= 0) tri_NM(rec, bT, px, py, pz, cx, cy, cz, bN, bM);
-                const uint32_t o = base + off + r;
-                ++r;
-                if (o >= M.cap) {
-                    emb_set_status(st, EMB_ERR_CAPACITY);
-                    continue;
-                }
-                M.o_cell[o] = (int32_t)(b * 64 + t);
-                M.o_dir[o] = (uint8_t)d;
-                if (bT >= 0) {
-                    M.o_q[o] = __fdiv_rn(i128_to_float(bN), (float)bM * (float)h);
-                    M.o_tri[o] = bT;
-                } else {
-                    M.o_q[o] = -1.0f;
-                    M.o_tri[o] = -1;
-                    emb_set_status(st, EMB_ERR_STATE);  // a fluid-to-solid link must cross the surface
-                }
-            }
-        }
-        __syncwarp();
-    }
     }
 }
 
