@@ -25,8 +25,8 @@ __global__ void k_xfilter(const int4 *__restrict__ rec, int64_t T, LevelGeom g, 
     if (nx != 0) {
         int sx = nx > 0 ? 1 : -1;
         long long j0, j1, k0, k1;
-        line_range(min(A.y, min(B.y, C.y)), max(A.y, max(B.y, C.y)), g.h, g.half, g.ncell, j0, j1);
-        line_range(min(A.z, min(B.z, C.z)), max(A.z, max(B.z, C.z)), g.h, g.half, g.ncell, k0, k1);
+        line_range(min(A.y, min(B.y, C.y)), max(A.y, max(B.y, C.y)), g.lh, g.half, g.ncell, j0, j1);
+        line_range(min(A.z, min(B.z, C.z)), max(A.z, max(B.z, C.z)), g.lh, g.half, g.ncell, k0, k1);
         for (long long k = k0; k <= k1 && !hit; ++k) {
             int pz = (int)((2 * k + 1) * g.half);
             for (long long j = j0; j <= j1; ++j) {
@@ -76,9 +76,9 @@ __global__ void __launch_bounds__(EMB_WU_WARPS * 32) k_bin_pairs(const int4 *__r
         if (uy * vz - uz * vy == 0 && uz * vx - ux * vz == 0 && ux * vy - uy * vx == 0) valid = false;
     }
     if (valid) {
-        emb_block_range(min(A.x, min(B.x, C.x)), max(A.x, max(B.x, C.x)), g.W, dil, g.nb, b0[0], b1[0]);
-        emb_block_range(min(A.y, min(B.y, C.y)), max(A.y, max(B.y, C.y)), g.W, dil, g.nb, b0[1], b1[1]);
-        emb_block_range(min(A.z, min(B.z, C.z)), max(A.z, max(B.z, C.z)), g.W, dil, g.nb, b0[2], b1[2]);
+        emb_block_range(min(A.x, min(B.x, C.x)), max(A.x, max(B.x, C.x)), g.lW, dil, g.nb, b0[0], b1[0]);
+        emb_block_range(min(A.y, min(B.y, C.y)), max(A.y, max(B.y, C.y)), g.lW, dil, g.nb, b0[1], b1[1]);
+        emb_block_range(min(A.z, min(B.z, C.z)), max(A.z, max(B.z, C.z)), g.lW, dil, g.nb, b0[2], b1[2]);
     }
     S.A[lane] = A;
     S.B[lane] = B;
@@ -106,8 +106,11 @@ __global__ void __launch_bounds__(EMB_WU_WARPS * 32) k_bin_pairs(const int4 *__r
                                 : 0;
     const unsigned own_sum = __reduce_add_sync(0xffffffffu, (unsigned)min(own, 1ll << 20));
     if (total <= EMB_WU_MAX && 4 * total <= (long long)own_sum) {
-        for (long long c = lane; c < total; c += 32) {
-            const long long bx = u0[0] + c % nx, by = u0[1] + (c / nx) % ny, bz = u0[2] + c / (nx * ny);
+        // total <= EMB_WU_MAX: decode the union index in 32-bit arithmetic
+        const unsigned ux = (unsigned)nx, uxy = (unsigned)(nx * ny);
+        for (unsigned c = lane; c < (unsigned)total; c += 32) {
+            const unsigned cz = c / uxy, cr = c - cz * uxy, cy = cr / ux;
+            const long long bx = u0[0] + (long long)(cr - cy * ux), by = u0[1] + (long long)cy, bz = u0[2] + (long long)cz;
             const int32_t id = emb_lookup(lk, bx, by, bz);
             if (id < 0) continue;
             const long long lx = bx * g.W - dil, ly = by * g.W - dil, lz = bz * g.W - dil;

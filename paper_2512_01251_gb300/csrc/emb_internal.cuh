@@ -121,15 +121,18 @@ struct emb_bins_s {
 
 // Geometry of one level in frame units.
 struct LevelGeom {
-    long long h, half, W;  // cell size, half cell, block width
+    long long h, half, W;  // cell size, half cell, block width (powers of two)
     long long ncell;       // cells per axis
     long long nb;          // blocks per axis
+    int lh, lW;            // log2 h, log2 W
 };
 
 static inline LevelGeom level_geom(const emb_forest_s *f, int L)
 {
     LevelGeom g;
-    g.h = 1ll << (18 - f->k - L);
+    g.lh = 18 - f->k - L;
+    g.lW = g.lh + 2;
+    g.h = 1ll << g.lh;
     g.half = g.h >> 1;
     g.W = 4 * g.h;
     g.nb = (long long)f->R << L;
@@ -255,11 +258,10 @@ __device__ __forceinline__ int32_t emb_lookup(const EmbLookup &l, int64_t bx, in
     return emb_hash_find(l.hkey, l.hval, l.hcap, emb_key(bx, by, bz));
 }
 
-__device__ __forceinline__ int64_t emb_floordiv(int64_t a, int64_t b)  // b > 0
-{
-    int64_t q = a / b;
-    return (a % b != 0 && a < 0) ? q - 1 : q;
-}
+// floor(a / 2^s) and ceil(a / 2^s) for signed a (arithmetic shifts; the cell and
+// block widths of every level are powers of two).
+__device__ __forceinline__ int64_t emb_floor_shr(int64_t a, int s) { return a >> s; }
+__device__ __forceinline__ int64_t emb_ceil_shr(int64_t a, int s) { return -((-a) >> s); }
 
 __device__ __forceinline__ int sgn_ll(long long v) { return (v > 0) - (v < 0); }
 __device__ __forceinline__ int sgn_i128(i128 v) { return (v > 0) - (v < 0); }
@@ -372,22 +374,22 @@ __device__ __forceinline__ bool emb_point_in_box(const int4 &P, long long lx, lo
 }
 
 // Enumerate the block range [b0, b1] along one axis whose boxes dilated by dil
-// meet the interval [mn, mx] (block width W, nb blocks on the axis).
-__device__ __forceinline__ void emb_block_range(long long mn, long long mx, long long W, long long dil, long long nb,
+// meet the interval [mn, mx] (block width 2^lW, nb blocks on the axis).
+__device__ __forceinline__ void emb_block_range(long long mn, long long mx, int lW, long long dil, long long nb,
                                                 long long &b0, long long &b1)
 {
-    b0 = -emb_floordiv(-(mn - dil - W), W);  // ceil((mn - dil - W) / W)
-    b1 = emb_floordiv(mx + dil, W);
+    b0 = emb_ceil_shr(mn - dil - (1ll << lW), lW);
+    b1 = emb_floor_shr(mx + dil, lW);
     if (b0 < 0) b0 = 0;
     if (b1 > nb - 1) b1 = nb - 1;
 }
 
-// Range of line indices j with centre (2j+1) half inside [mn, mx], clamped.
-__device__ __forceinline__ void line_range(long long mn, long long mx, long long h, long long half, long long ncell,
+// Range of line indices j with centre (2j+1) half inside [mn, mx], clamped (cell size 2^lh).
+__device__ __forceinline__ void line_range(long long mn, long long mx, int lh, long long half, long long ncell,
                                            long long &j0, long long &j1)
 {
-    j0 = -emb_floordiv(-(mn - half), h);
-    j1 = emb_floordiv(mx - half, h);
+    j0 = emb_ceil_shr(mn - half, lh);
+    j1 = emb_floor_shr(mx - half, lh);
     if (j0 < 0) j0 = 0;
     if (j1 > ncell - 1) j1 = ncell - 1;
 }

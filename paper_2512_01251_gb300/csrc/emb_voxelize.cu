@@ -32,9 +32,9 @@ __global__ void k_vox(const int4 *__restrict__ rec, const uint32_t *__restrict__
     if (nx == 0) return;
     int sx = nx > 0 ? 1 : -1;
     long long j0, j1, k0, k1;
-    line_range(min(A.y, min(B.y, C.y)), max(A.y, max(B.y, C.y)), g.h, g.half, g.ncell, j0, j1);
-    line_range(min(A.z, min(B.z, C.z)), max(A.z, max(B.z, C.z)), g.h, g.half, g.ncell, k0, k1);
-    long long bx0 = emb_floordiv(min(A.x, min(B.x, C.x)), g.W), bx1 = emb_floordiv(max(A.x, max(B.x, C.x)), g.W);
+    line_range(min(A.y, min(B.y, C.y)), max(A.y, max(B.y, C.y)), g.lh, g.half, g.ncell, j0, j1);
+    line_range(min(A.z, min(B.z, C.z)), max(A.z, max(B.z, C.z)), g.lh, g.half, g.ncell, k0, k1);
+    long long bx0 = emb_floor_shr(min(A.x, min(B.x, C.x)), g.lW), bx1 = emb_floor_shr(max(A.x, max(B.x, C.x)), g.lW);
     if (bx0 < 0) bx0 = 0;
     if (bx1 > g.nb - 1) bx1 = g.nb - 1;
     for (long long k = k0; k <= k1; ++k) {
