@@ -304,30 +304,46 @@ __global__ void k_qbwd_fill(const int32_t *__restrict__ vid, int64_t m, const ui
     slot[voff[v] + p] = (uint32_t)e;
 }
 
-// Per vertex: sum its entries in ascending entry order (entries are unordered in the slot range).
+// One warp per vertex.  The fill left a vertex's entries unordered in slot[a, b);
+// each lane ranks its entries among all of them (entry ids are distinct) and
+// stores them at their rank in `sorted`, so sorted[a, b) ascends.  After a warp
+// barrier lane l sums the entries of ranks l, l + 32, l + 64, ... in that order
+// and the 32 lane sums meet in a fixed butterfly: the result does not depend on
+// the order the atomics of the fill happened to take.  Work per vertex is
+// c^2 / 32 comparisons per lane for c entries.
 __global__ void k_qbwd_reduce(const uint32_t *__restrict__ voff, const uint32_t *__restrict__ slot,
-                              const float *__restrict__ val, int64_t V, float *__restrict__ gv)
+                              uint32_t *__restrict__ sorted, const float *__restrict__ val, int64_t V,
+                              float *__restrict__ gv)
 {
-    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= V) return;
-    uint32_t a = voff[v], b = voff[v + 1];
-    double sx = 0, sy = 0, sz = 0;
-    long long last = -1;
-    for (uint32_t it = a; it < b; ++it) {
-        // next smallest entry id above `last`
-        uint32_t best = 0xFFFFFFFFu;
-        for (uint32_t j = a; j < b; ++j) {
-            uint32_t e = slot[j];
-            if ((long long)e > last && e < best) best = e;
-        }
-        last = best;
-        sx += val[3 * (int64_t)best];
-        sy += val[3 * (int64_t)best + 1];
-        sz += val[3 * (int64_t)best + 2];
+    const int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (v >= V) return;  // uniform per warp
+    const uint32_t a = voff[v], b = voff[v + 1];
+    for (uint32_t i = a + lane; i < b; i += 32) {
+        const uint32_t e = slot[i];
+        uint32_t r = 0;
+        for (uint32_t j = a; j < b; ++j) r += slot[j] < e;
+        sorted[a + r] = e;
     }
-    gv[3 * v] = (float)sx;
-    gv[3 * v + 1] = (float)sy;
-    gv[3 * v + 2] = (float)sz;
+    __syncwarp();
+    double sx = 0, sy = 0, sz = 0;
+    for (uint32_t i = a + lane; i < b; i += 32) {
+        const int64_t e = sorted[i];
+        sx += val[3 * e];
+        sy += val[3 * e + 1];
+        sz += val[3 * e + 2];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        sz += __shfl_xor_sync(0xffffffffu, sz, o);
+    }
+    if (lane == 0) {
+        gv[3 * v] = (float)sx;
+        gv[3 * v + 1] = (float)sy;
+        gv[3 * v + 2] = (float)sz;
+    }
 }
 
 extern "C" emb_status emb_cutlinks_backward(emb_mesh m, emb_forest f, const int32_t *d_cell, const uint8_t *d_dir,
@@ -344,28 +360,32 @@ extern "C" emb_status emb_cutlinks_backward(emb_mesh m, emb_forest f, const int3
     const EmbLevel &lv = f->lv[f->max_level];
     LevelGeom g = level_geom(f, f->max_level);
     double scale = (double)(1ll << 20) * (double)f->r_o;
-    float *val = nullptr;
-    int32_t *vid = nullptr;
-    uint32_t *vcnt = nullptr, *voff = nullptr, *slot = nullptr;
-    EMB_CUDA_TRY(cudaMallocAsync(&val, (9 * n + 1) * sizeof(float), s));
-    EMB_CUDA_TRY(cudaMallocAsync(&vid, (3 * n + 1) * sizeof(int32_t), s));
-    EMB_CUDA_TRY(cudaMallocAsync(&vcnt, (m->V + 1) * sizeof(uint32_t), s));
-    EMB_CUDA_TRY(cudaMallocAsync(&voff, (m->V + 1) * sizeof(uint32_t), s));
-    EMB_CUDA_TRY(cudaMallocAsync(&slot, (3 * n + 1) * sizeof(uint32_t), s));
+    // one scratch allocation: val (9n floats), vid (3n), slot (3n), vcnt and voff (V + 1 each), scan scratch
+    const size_t a_val = (size_t)(9 * n + 1) * sizeof(float), a_ent = (size_t)(3 * n + 1) * sizeof(uint32_t),
+                 a_v = (size_t)(m->V + 1) * sizeof(uint32_t), a_tmp = emb_scan_tmp_words(m->V) * sizeof(uint64_t);
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    char *scratch = nullptr;
+    EMB_CUDA_TRY(cudaMallocAsync((void **)&scratch, up(a_val) + 2 * up(a_ent) + 2 * up(a_v) + up(a_tmp), s));
+    float *val = (float *)scratch;
+    int32_t *vid = (int32_t *)(scratch + up(a_val));
+    uint32_t *slot = (uint32_t *)(scratch + up(a_val) + up(a_ent));
+    uint32_t *vcnt = (uint32_t *)(scratch + up(a_val) + 2 * up(a_ent));
+    uint32_t *voff = (uint32_t *)(scratch + up(a_val) + 2 * up(a_ent) + up(a_v));
+    uint64_t *tmp = (uint64_t *)(scratch + up(a_val) + 2 * up(a_ent) + 2 * up(a_v));
     EMB_CUDA_TRY(cudaMemsetAsync(vcnt, 0, (m->V + 1) * sizeof(uint32_t), s));
     if (n > 0)
         EMB_LAUNCH((k_qbwd_terms), emb_grid(n, 256), 256, 0, s)(lv.key, g, scale, d_cell, d_dir, d_q, d_tri, d_gq, n, m->rec, m->T,
                                                       val, vid, vcnt, st);
-    emb_status rc = emb_scan_u32(vcnt, voff, m->V, nullptr, s);
-    if (rc != EMB_OK) return rc;
+    emb_status rc = emb_scan_into(vcnt, voff, m->V, tmp, s);
+    if (rc != EMB_OK) {
+        cudaFreeAsync(scratch, s);
+        return rc;
+    }
     EMB_CUDA_TRY(cudaMemsetAsync(vcnt, 0, (m->V + 1) * sizeof(uint32_t), s));
     if (n > 0) EMB_LAUNCH((k_qbwd_fill), emb_grid(3 * n, 256), 256, 0, s)(vid, 3 * n, voff, vcnt, slot);
-    EMB_LAUNCH((k_qbwd_reduce), emb_grid(m->V, 256), 256, 0, s)(voff, slot, val, m->V, d_gverts);
+    // vid is spent after the fill and holds the sorted entries of each vertex
+    EMB_LAUNCH((k_qbwd_reduce), emb_grid(32 * m->V, 256), 256, 0, s)(voff, slot, (uint32_t *)vid, val, m->V, d_gverts);
     EMB_CUDA_TRY(cudaGetLastError());
-    EMB_CUDA_TRY(cudaFreeAsync(val, s));
-    EMB_CUDA_TRY(cudaFreeAsync(vid, s));
-    EMB_CUDA_TRY(cudaFreeAsync(vcnt, s));
-    EMB_CUDA_TRY(cudaFreeAsync(voff, s));
-    EMB_CUDA_TRY(cudaFreeAsync(slot, s));
+    EMB_CUDA_TRY(cudaFreeAsync(scratch, s));
     return EMB_OK;
 }
