@@ -491,7 +491,8 @@ def batch_leg(P, reps=5):
                 plain_ms=round(pm, 3), batched_ms=round(bm, 3), speedup=round(pm / bm, 2),
                 plain_units_per_s=units / (pm / 1e3), batched_units_per_s=bunits / (bm / 1e3),
                 same_units=bool(units == bunits), status=st_,
-                autotuned=dict(streams=choice[0], tri_block=choice[1], link_ctas_per_sm=choice[2]),
+                autotuned=dict(streams=choice[0], tri_block=choice[1], link_ctas_per_sm=choice[2],
+                               link_placement="per mesh" if choice[3] else "joint"),
                 timing="host wall clock around a synchronised run (the plain path synchronises inside)")
 
 

@@ -247,17 +247,23 @@ emb_status emb_cutlinks_backward(emb_mesh m, emb_forest f, const int32_t *d_cell
  * synchronisation: per-mesh pipelines on several internal streams, every count
  * recomputed on the device checked against the plan (device status
  * EMB_ERR_STATE on a difference, e.g. moved geometry), and the cut links of all
- * meshes from one persistent kernel launch over a shared (mesh, block) work
- * queue.  Results are identical to the per-call path.  `stream` must not be the
- * legacy default stream for emb_batch_capture.
+ * meshes either from one persistent kernel launch over a shared (mesh, block)
+ * work queue after all pipelines ("joint" placement) or from one launch per mesh
+ * on that mesh's stream right after its pipeline, its grid sized to the mesh's
+ * work ("per-mesh" placement, which overlaps link work with other meshes'
+ * pipelines).  Results are identical to the per-call path in either placement.
+ * `stream` must not be the legacy default stream for emb_batch_capture.
  *
  * emb_batch_capture records emb_batch_run into a CUDA graph; emb_batch_launch
  * replays that graph on `stream`.
  *
  * emb_batch_autotune times a small set of launch shapes on this batch and keeps
- * the fastest; h_choice (3 int32, may be NULL) receives the chosen stream count,
- * thread-block size of the triangle-parallel kernels, and resident link CTAs per
- * SM (0 = as many as fit).  It synchronises and drops a captured graph.
+ * the fastest; h_choice (4 int32, may be NULL) receives the chosen stream count
+ * (1..16), thread-block size of the triangle-parallel kernels (128, 256 or 512),
+ * resident link CTAs per SM (0 = as many as fit) and link placement (0 joint,
+ * 1 per mesh).  It synchronises and drops a captured graph.  emb_batch_configure
+ * sets such a 4-value shape directly (host array; EMB_ERR_BAD_INPUT outside the
+ * ranges above) and drops a captured graph; it enqueues nothing.
  *
  * emb_batch_info: planned blocks per level (levels[j] + 1 int64) and link count of
  * mesh j (host).  emb_batch_results copies mesh j's results of the last replay into
@@ -270,6 +276,7 @@ emb_status emb_batch_run(emb_batch b, void *stream);
 emb_status emb_batch_capture(emb_batch b, void *stream);
 emb_status emb_batch_launch(emb_batch b, void *stream);
 emb_status emb_batch_autotune(emb_batch b, void *stream, int32_t *h_choice);
+emb_status emb_batch_configure(emb_batch b, const int32_t *h_choice);
 emb_status emb_batch_info(emb_batch b, int32_t j, int64_t *h_blocks, int64_t *h_links);
 emb_status emb_batch_results(emb_batch b, int32_t j, int32_t level, uint64_t *d_mask, int32_t *d_blocks,
                              int32_t *d_cell, uint8_t *d_dir, float *d_q, int32_t *d_tri, void *stream);

@@ -11,12 +11,16 @@
 // on several streams, every count the device recomputes is checked against the
 // plan by a one-thread kernel (EMB_ERR_STATE on any difference, e.g. when the
 // geometry moved), and all meshes' cut links are produced by one persistent
-// launch of the link kernel over a shared work queue of (mesh, block) items.
+// launch of the link kernel over a shared work queue of (mesh, block) items
+// once every pipeline is done ("joint" placement), or each mesh's links by a
+// launch on its own stream right after its pipeline, with a grid sized to its
+// work, so that the link work of early meshes overlaps the pipelines of later
+// ones ("per-mesh" placement).
 // Because it neither allocates nor synchronises, the replay can be captured in a
 // CUDA graph (emb_batch_capture) and relaunched (emb_batch_launch).
 // emb_batch_autotune times a small set of launch shapes (stream count, thread
 // block size of the triangle-parallel kernels, resident link CTAs per SM) on
-// this batch and keeps the fastest.
+// this batch and keeps the fastest; emb_batch_configure sets one directly.
 #include <stdlib.h>
 
 #include <vector>
@@ -48,6 +52,7 @@ struct BMesh {
     uint32_t *bin_off = nullptr, *bin_ent = nullptr;
     uint64_t *cand = nullptr;
     uint32_t *work_n = nullptr, *work = nullptr, *blk_off = nullptr;
+    unsigned int *next = nullptr;                   // queue cursor of a per-mesh link launch
     int32_t *o_cell = nullptr, *o_tri = nullptr;
     uint8_t *o_dir = nullptr;
     float *o_q = nullptr;
@@ -62,8 +67,9 @@ struct emb_batch_s {
     unsigned int *next = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    // launch shape (autotuned)
-    int nstreams = 8, tri_block = 256, link_ctas = 0;
+    // launch shape (autotuned): streams, block size of the triangle-parallel
+    // kernels, link CTAs per SM (0 = as many as fit), link placement (0 joint, 1 per mesh)
+    int nstreams = 8, tri_block = 256, link_ctas = 0, per_mesh_links = 1;
     int device = 0;
 };
 
@@ -173,6 +179,7 @@ static emb_status alloc_mesh(BMesh &B)
     BTRY(balloc(B, &B.work_n, fin.n + 1));
     BTRY(balloc(B, &B.work, fin.n + 1));
     BTRY(balloc(B, &B.blk_off, fin.n + 1));
+    BTRY(balloc(B, &B.next, 1));
     BTRY(balloc(B, &B.o_cell, B.links + 1));
     BTRY(balloc(B, &B.o_dir, B.links + 1));
     BTRY(balloc(B, &B.o_q, B.links + 1));
@@ -282,6 +289,28 @@ extern "C" emb_status emb_batch_create(const emb_mesh *meshes, const int32_t *le
 }
 
 // The replay: fork to the worker streams, one pipeline per mesh, join, one link launch.
+// The link-kernel view of mesh B's finest level.
+static LinkMesh link_mesh(BMesh &B)
+{
+    const EmbLevel &fin = B.L[B.Lf].lv;
+    LinkMesh M;
+    M.key = fin.key;
+    M.cand = B.cand;
+    M.blk_off = B.blk_off;
+    M.bin_off = B.bin_off;
+    M.bin_ent = B.bin_ent;
+    M.rec = B.m->rec;
+    M.work = B.work;
+    M.work_n = B.work_n + fin.n;
+    M.o_cell = B.o_cell;
+    M.o_dir = B.o_dir;
+    M.o_q = B.o_q;
+    M.o_tri = B.o_tri;
+    M.g = level_geom(&B.geo, B.Lf);
+    M.cap = (uint32_t)B.links;
+    return M;
+}
+
 static emb_status batch_enqueue(emb_batch b, cudaStream_t s)
 {
     const int K = b->nstreams < 1 ? 1 : (b->nstreams > BATCH_MAX_STREAMS ? BATCH_MAX_STREAMS : b->nstreams);
@@ -296,33 +325,25 @@ static emb_status batch_enqueue(emb_batch b, cudaStream_t s)
             order[c] = order[c - 1];
             order[c - 1] = t;
         }
-    for (size_t q = 0; q < order.size(); ++q) BTRY(enqueue_mesh(b->m[order[q]], b->tri_block, b->st[q % K]));
+    for (size_t q = 0; q < order.size(); ++q) {
+        BMesh &B = b->m[order[q]];
+        BTRY(enqueue_mesh(B, b->tri_block, b->st[q % K]));
+        if (b->per_mesh_links) {
+            LinkTable one;
+            one.n = 1;
+            one.m[0] = link_mesh(B);
+            BTRY(emb_enq_link_emit(one, B.next, b->link_ctas, b->st[q % K], B.nwork > 0 ? B.nwork : 1));
+        }
+    }
     for (int i = 0; i < K; ++i) {
         EMB_CUDA_TRY(cudaEventRecord(b->ev_join[i], b->st[i]));
         EMB_CUDA_TRY(cudaStreamWaitEvent(s, b->ev_join[i], 0));
     }
+    if (b->per_mesh_links) return EMB_OK;
     LinkTable tab;
     tab.n = (int)b->m.size();
-    for (int j = 0; j < tab.n; ++j) {
-        BMesh &B = b->m[j];
-        const EmbLevel &fin = B.L[B.Lf].lv;
-        LinkMesh &M = tab.m[j];
-        M.key = fin.key;
-        M.cand = B.cand;
-        M.blk_off = B.blk_off;
-        M.bin_off = B.bin_off;
-        M.bin_ent = B.bin_ent;
-        M.rec = B.m->rec;
-        M.work = B.work;
-        M.work_n = B.work_n + fin.n;
-        M.o_cell = B.o_cell;
-        M.o_dir = B.o_dir;
-        M.o_q = B.o_q;
-        M.o_tri = B.o_tri;
-        M.g = level_geom(&B.geo, B.Lf);
-        M.cap = (uint32_t)B.links;
-    }
-    return emb_enq_link_emit(tab, b->next, b->link_ctas, s);
+    for (int j = 0; j < tab.n; ++j) tab.m[j] = link_mesh(b->m[j]);
+    return emb_enq_link_emit(tab, b->next, b->link_ctas, s, 0);
 }
 
 extern "C" emb_status emb_batch_run(emb_batch b, void *stream)
@@ -372,10 +393,11 @@ extern "C" emb_status emb_batch_autotune(emb_batch b, void *stream, int32_t *h_c
     if (!b) return EMB_ERR_BAD_INPUT;
     cudaStream_t s = emb_stream(stream);
     struct Cand {
-        int nstreams, tri_block, link_ctas;
+        int nstreams, tri_block, link_ctas, per_mesh;
     };
-    const Cand cands[] = {{1, 256, 0}, {4, 256, 0}, {8, 256, 0}, {16, 256, 0}, {8, 128, 0},
-                          {8, 512, 0}, {8, 256, 2}, {16, 128, 0}, {16, 512, 0}};
+    const Cand cands[] = {{1, 256, 0, 0},  {8, 256, 0, 0},  {16, 256, 0, 0}, {8, 256, 2, 0},  {16, 128, 0, 0},
+                          {4, 256, 0, 1},  {8, 256, 0, 1},  {16, 256, 0, 1}, {16, 128, 0, 1}, {16, 512, 0, 1},
+                          {16, 256, 2, 1}, {8, 128, 2, 1}};
     const int nc = (int)(sizeof(cands) / sizeof(cands[0]));
     cudaEvent_t e0, e1;
     EMB_CUDA_TRY(cudaEventCreate(&e0));
@@ -386,6 +408,7 @@ extern "C" emb_status emb_batch_autotune(emb_batch b, void *stream, int32_t *h_c
         b->nstreams = cands[i].nstreams;
         b->tri_block = cands[i].tri_block;
         b->link_ctas = cands[i].link_ctas;
+        b->per_mesh_links = cands[i].per_mesh;
         BTRY(batch_enqueue(b, s));  // warm-up
         float tot = 0;
         for (int r = 0; r < 3; ++r) {
@@ -407,6 +430,7 @@ extern "C" emb_status emb_batch_autotune(emb_batch b, void *stream, int32_t *h_c
     b->nstreams = cands[best_i].nstreams;
     b->tri_block = cands[best_i].tri_block;
     b->link_ctas = cands[best_i].link_ctas;
+    b->per_mesh_links = cands[best_i].per_mesh;
     if (b->exec) {  // a captured graph no longer matches the chosen shape
         cudaGraphExecDestroy(b->exec);
         b->exec = nullptr;
@@ -415,6 +439,25 @@ extern "C" emb_status emb_batch_autotune(emb_batch b, void *stream, int32_t *h_c
         h_choice[0] = b->nstreams;
         h_choice[1] = b->tri_block;
         h_choice[2] = b->link_ctas;
+        h_choice[3] = b->per_mesh_links;
+    }
+    return EMB_OK;
+}
+
+extern "C" emb_status emb_batch_configure(emb_batch b, const int32_t *h_choice)
+{
+    if (!b || !h_choice) return EMB_ERR_BAD_INPUT;
+    const int ns = h_choice[0], tb = h_choice[1], lc = h_choice[2], pm = h_choice[3];
+    if (ns < 1 || ns > BATCH_MAX_STREAMS || (tb != 128 && tb != 256 && tb != 512) || lc < 0 || lc > 64 ||
+        (pm != 0 && pm != 1))
+        return EMB_ERR_BAD_INPUT;
+    b->nstreams = ns;
+    b->tri_block = tb;
+    b->link_ctas = lc;
+    b->per_mesh_links = pm;
+    if (b->exec) {  // a captured graph no longer matches the shape
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
     }
     return EMB_OK;
 }

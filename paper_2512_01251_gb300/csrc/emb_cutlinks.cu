@@ -694,7 +694,11 @@ emb_status emb_link_emit_init()
 }
 
 // One persistent launch over the meshes of `tab`; `next` is the queue cursor.
-emb_status emb_enq_link_emit(const LinkTable &tab, unsigned int *next, int ctas_per_sm, cudaStream_t s)
+// The grid fills every SM (ctas_per_sm resident CTAs each, 0 = as many as fit)
+// unless the work is smaller: with `items` > 0 (the blocks with links, known to
+// the caller) it stops at about items_per_warp items per warp, so that a small
+// mesh leaves SMs to the kernels of other streams.
+emb_status emb_enq_link_emit(const LinkTable &tab, unsigned int *next, int ctas_per_sm, cudaStream_t s, int64_t items)
 {
     int *st = emb_status_word();
     if (!st) return EMB_ERR_CUDA;
@@ -702,8 +706,14 @@ emb_status emb_enq_link_emit(const LinkTable &tab, unsigned int *next, int ctas_
     if (rc != EMB_OK) return rc;
     const size_t smem = emb_link_emit_smem();
     const int use = ctas_per_sm > 0 && ctas_per_sm < g_le_per_sm ? ctas_per_sm : g_le_per_sm;
+    int64_t grid = (int64_t)use * g_le_sms;
+    if (items > 0) {
+        const int64_t items_per_warp = 4;
+        const int64_t need = (items + LE_WARPS * items_per_warp - 1) / (LE_WARPS * items_per_warp);
+        if (need < grid) grid = need;
+    }
     EMB_CUDA_TRY(cudaMemsetAsync(next, 0, sizeof(unsigned int), s));
-    EMB_LAUNCH((k_link_emit), use * g_le_sms, LE_WARPS * 32, smem, s)(tab, next, st);
+    EMB_LAUNCH((k_link_emit), (int)grid, LE_WARPS * 32, smem, s)(tab, next, st);
     EMB_CUDA_TRY(cudaGetLastError());
     return EMB_OK;
 }
@@ -785,7 +795,7 @@ extern "C" emb_status emb_cutlinks(emb_forest f, emb_bins b, int32_t lattice, in
     M.o_tri = d_tri;
     M.g = level_geom(f, f->max_level);
     M.cap = (uint32_t)(capacity < 0xFFFFFFFFll ? capacity : 0xFFFFFFFFll);
-    rc = emb_enq_link_emit(tab, f->next, 0, s);
+    rc = emb_enq_link_emit(tab, f->next, 0, s, 0);
     if (rc != EMB_OK) return rc;
     EMB_CUDA_TRY(cudaGetLastError());
     return EMB_OK;

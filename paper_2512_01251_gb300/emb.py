@@ -359,9 +359,15 @@ def emb_batch_launch(batch: Batch, stream=None):
 
 
 def emb_batch_autotune(batch: Batch, stream=None) -> tuple:
-    c = (ctypes.c_int32 * 3)()
+    """(streams, tri_block, link CTAs per SM, per-mesh link placement) of the fastest shape."""
+    c = (ctypes.c_int32 * 4)()
     _check(load().emb_batch_autotune(batch.h, _stream(stream), c), "emb_batch_autotune")
     return tuple(c)
+
+
+def emb_batch_configure(batch: Batch, streams: int, tri_block: int, link_ctas: int = 0, per_mesh_links: int = 1):
+    c = (ctypes.c_int32 * 4)(streams, tri_block, link_ctas, per_mesh_links)
+    _check(load().emb_batch_configure(batch.h, c), "emb_batch_configure")
 
 
 def emb_batch_info(batch: Batch, j: int):
