@@ -53,6 +53,7 @@ struct BMesh {
     uint64_t *cand = nullptr;
     uint32_t *work_n = nullptr, *work = nullptr, *blk_off = nullptr;
     unsigned int *next = nullptr;                   // queue cursor of a per-mesh link launch
+    EmbBigQ bq = {nullptr, nullptr, 0};             // chunk queue of large triangles
     int32_t *o_cell = nullptr, *o_tri = nullptr;
     uint8_t *o_dir = nullptr;
     float *o_q = nullptr;
@@ -180,6 +181,9 @@ static emb_status alloc_mesh(BMesh &B)
     BTRY(balloc(B, &B.work, fin.n + 1));
     BTRY(balloc(B, &B.blk_off, fin.n + 1));
     BTRY(balloc(B, &B.next, 1));
+    BTRY(balloc(B, &B.bq.n, 1));
+    BTRY(balloc(B, &B.bq.q, (size_t)emb_bigq_capacity(T)));
+    B.bq.cap = (uint32_t)emb_bigq_capacity(T);
     BTRY(balloc(B, &B.o_cell, B.links + 1));
     BTRY(balloc(B, &B.o_dir, B.links + 1));
     BTRY(balloc(B, &B.o_q, B.links + 1));
@@ -200,20 +204,20 @@ static emb_status enqueue_mesh(BMesh &B, int tri_block, cudaStream_t s)
         const LevelGeom g = level_geom(&B.geo, L);
         BTRY(emb_enq_filter(rec, T, g, B.flag, B.pos, BL.flist, B.tmp, tri_block, s));
         BTRY(emb_expect_u32(B.pos + T, (uint64_t)BL.nf, s));
-        BTRY(emb_enq_voxelize(rec, BL.flist, BL.nf, g, lv, B.s_acc, B.p_acc, tri_block, s));
+        BTRY(emb_enq_voxelize(rec, BL.flist, BL.nf, g, lv, B.s_acc, B.p_acc, B.bq, tri_block, s));
         if (L < B.Lf) {
             const long long dil = emb_refine_dilation(&B.geo, L, B.band);
             if (dil < 0) return EMB_ERR_RANGE;
-            BTRY(emb_enq_refine(rec, T, g, dil, lv, BL.flags, s));
+            BTRY(emb_enq_refine(rec, T, g, dil, lv, BL.flags, B.bq, s));
             BTRY(emb_enq_flag_ranks(lv, BL.flags, B.cnt, B.rank, B.tmp, s));
             BTRY(emb_expect_u32(B.rank + lv.n, (uint64_t)BL.F, s));
             EmbLevel &C = B.L[L + 1].lv;
             BTRY(emb_enq_children(lv, BL.flags, B.rank, C.key, C.n, s));
             BTRY(emb_enq_level_index(C, B.pc, B.tmp, s));
         } else {
-            BTRY(emb_enq_bin_count(rec, T, g, lv, B.cnt, B.bin_off, B.tmp, s));
+            BTRY(emb_enq_bin_count(rec, T, g, lv, B.cnt, B.bin_off, B.tmp, B.bq, s));
             BTRY(emb_expect_u32(B.bin_off + lv.n, (uint64_t)B.pairs, s));
-            BTRY(emb_enq_bin_fill(rec, T, g, lv, B.cnt, B.bin_off, B.bin_ent, s));
+            BTRY(emb_enq_bin_fill(rec, T, g, lv, B.cnt, B.bin_off, B.bin_ent, B.bq, s));
             BTRY(emb_enq_neighbors(lv, s));
             BTRY(emb_enq_link_prep(lv, B.lattice, B.cand, B.cnt, B.rank, B.work_n, B.work, B.blk_off, B.tmp, s));
             BTRY(emb_expect_u32(B.work_n + lv.n, (uint64_t)B.nwork, s));

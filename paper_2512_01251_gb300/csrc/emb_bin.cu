@@ -27,6 +27,17 @@ __global__ void k_xfilter(const int4 *__restrict__ rec, int64_t T, LevelGeom g, 
         long long j0, j1, k0, k1;
         line_range(min(A.y, min(B.y, C.y)), max(A.y, max(B.y, C.y)), g.lh, g.half, g.ncell, j0, j1);
         line_range(min(A.z, min(B.z, C.z)), max(A.z, max(B.z, C.z)), g.lh, g.half, g.ncell, k0, k1);
+        if (j1 >= j0 && k1 >= k0) {
+            // the line nearest the centroid first: it settles a large triangle in one test
+            long long jc = emb_floor_shr((long long)A.y + B.y + C.y, g.lh) / 3;
+            long long kc = emb_floor_shr((long long)A.z + B.z + C.z, g.lh) / 3;
+            jc = jc < j0 ? j0 : (jc > j1 ? j1 : jc);
+            kc = kc < k0 ? k0 : (kc > k1 ? k1 : kc);
+            const int py = (int)((2 * jc + 1) * g.half), pz = (int)((2 * kc + 1) * g.half);
+            if (emb_orient_yz(A.y, A.z, B.y, B.z, py, pz) == sx && emb_orient_yz(B.y, B.z, C.y, C.z, py, pz) == sx &&
+                emb_orient_yz(C.y, C.z, A.y, A.z, py, pz) == sx)
+                hit = 1;
+        }
         for (long long k = k0; k <= k1 && !hit; ++k) {
             int pz = (int)((2 * k + 1) * g.half);
             for (long long j = j0; j <= j1; ++j) {
@@ -49,37 +60,72 @@ __global__ void k_compact(const uint32_t *__restrict__ flag, const uint32_t *__r
     if (i < n && flag[i]) out[pos[i]] = (uint32_t)i;
 }
 
+// Triangle t as the binning pass sees it: false for a degenerate triangle (zero
+// normal, never crossed by a link), else its vertices and candidate block ranges.
+__device__ __forceinline__ bool bin_setup(const int4 *__restrict__ rec, int64_t t, const LevelGeom &g, long long dil,
+                                          int4 &A, int4 &B, int4 &C, long long b0[3], long long b1[3])
+{
+    A = rec[3 * t];
+    B = rec[3 * t + 1];
+    C = rec[3 * t + 2];
+    long long ux = (long long)B.x - A.x, uy = (long long)B.y - A.y, uz = (long long)B.z - A.z;
+    long long vx = (long long)C.x - A.x, vy = (long long)C.y - A.y, vz = (long long)C.z - A.z;
+    if (uy * vz - uz * vy == 0 && uz * vx - ux * vz == 0 && ux * vy - uy * vx == 0) return false;
+    emb_block_range(min(A.x, min(B.x, C.x)), max(A.x, max(B.x, C.x)), g.lW, dil, g.nb, b0[0], b1[0]);
+    emb_block_range(min(A.y, min(B.y, C.y)), max(A.y, max(B.y, C.y)), g.lW, dil, g.nb, b0[1], b1[1]);
+    emb_block_range(min(A.z, min(B.z, C.z)), max(A.z, max(B.z, C.z)), g.lW, dil, g.nb, b0[2], b1[2]);
+    return true;
+}
+
+__device__ __forceinline__ unsigned long long box_items(const long long b0[3], const long long b1[3])
+{
+    if (b1[0] < b0[0] || b1[1] < b0[1] || b1[2] < b0[2]) return 0;
+    return (unsigned long long)(b1[0] - b0[0] + 1) * (unsigned long long)(b1[1] - b0[1] + 1) *
+           (unsigned long long)(b1[2] - b0[2] + 1);
+}
+
+// Pair (t, block (bx, by, bz)) if the block exists and t overlaps its dilated box.
+template <int MODE>
+__device__ __forceinline__ void bin_block(const int4 &A, const int4 &B, const int4 &C, uint32_t t, long long bx,
+                                          long long by, long long bz, const LevelGeom &g, long long dil,
+                                          const EmbLookup &lk, uint32_t *__restrict__ cnt,
+                                          const uint32_t *__restrict__ off, uint32_t *__restrict__ ent)
+{
+    const int32_t id = emb_lookup(lk, bx, by, bz);
+    if (id < 0) return;
+    const long long lx = bx * g.W - dil, ly = by * g.W - dil, lz = bz * g.W - dil;
+    const long long hx = lx + g.W + 2 * dil, hy = ly + g.W + 2 * dil, hz = lz + g.W + 2 * dil;
+    if (!(emb_point_in_box(A, lx, ly, lz, hx, hy, hz) || emb_point_in_box(B, lx, ly, lz, hx, hy, hz) ||
+          emb_point_in_box(C, lx, ly, lz, hx, hy, hz) || emb_tri_box(A, B, C, lx, ly, lz, hx, hy, hz)))
+        return;
+    if (MODE == 0) {
+        atomicAdd(cnt + id, 1u);
+    } else {
+        const uint32_t p = atomicAdd(cnt + id, 1u);
+        ent[off[id] + p] = t;
+    }
+}
+
 // The (triangle, block) pairs of 32 consecutive triangles, visited warp-cooperatively
-// over the union of their candidate blocks (see emb_internal.cuh).
-// MODE 0: count pairs per block; MODE 1: fill the CSR bins.  Degenerate
-// triangles (zero normal) are never crossed by a link and are left out.
+// over the union of their candidate blocks (see emb_internal.cuh); a lane whose
+// triangle is left out of the union walks its own candidates, or queues them in
+// chunks when there are many.  MODE 0: count pairs per block; MODE 1: fill the CSR
+// bins.  Degenerate triangles (zero normal) are never crossed by a link and are
+// left out.
 template <int MODE>
 __global__ void __launch_bounds__(EMB_WU_WARPS * 32) k_bin_pairs(const int4 *__restrict__ rec, int64_t T, LevelGeom g,
                                                                  long long dil, EmbLookup lk, uint32_t *__restrict__ cnt,
                                                                  const uint32_t *__restrict__ off,
-                                                                 uint32_t *__restrict__ ent)
+                                                                 uint32_t *__restrict__ ent, EmbBigQ Q)
 {
     __shared__ WuTri tiles[EMB_WU_WARPS];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WuTri &S = tiles[w];
     const int64_t t0 = ((int64_t)blockIdx.x * EMB_WU_WARPS + w) * 32;
     const int64_t t = t0 + lane;
-    bool valid = t < T;
     long long b0[3] = {1ll << 40, 1ll << 40, 1ll << 40}, b1[3] = {-1, -1, -1};
     int4 A = make_int4(0, 0, 0, 0), B = A, C = A;
-    if (valid) {
-        A = rec[3 * t];
-        B = rec[3 * t + 1];
-        C = rec[3 * t + 2];
-        long long ux = (long long)B.x - A.x, uy = (long long)B.y - A.y, uz = (long long)B.z - A.z;
-        long long vx = (long long)C.x - A.x, vy = (long long)C.y - A.y, vz = (long long)C.z - A.z;
-        if (uy * vz - uz * vy == 0 && uz * vx - ux * vz == 0 && ux * vy - uy * vx == 0) valid = false;
-    }
-    if (valid) {
-        emb_block_range(min(A.x, min(B.x, C.x)), max(A.x, max(B.x, C.x)), g.lW, dil, g.nb, b0[0], b1[0]);
-        emb_block_range(min(A.y, min(B.y, C.y)), max(A.y, max(B.y, C.y)), g.lW, dil, g.nb, b0[1], b1[1]);
-        emb_block_range(min(A.z, min(B.z, C.z)), max(A.z, max(B.z, C.z)), g.lW, dil, g.nb, b0[2], b1[2]);
-    }
+    const bool valid = t < T && bin_setup(rec, t, g, dil, A, B, C, b0, b1);
     S.A[lane] = A;
     S.B[lane] = B;
     S.C[lane] = C;
@@ -100,11 +146,8 @@ __global__ void __launch_bounds__(EMB_WU_WARPS * 32) k_bin_pairs(const int4 *__r
     if (nx <= 0 || ny <= 0 || nz <= 0) return;
     const long long total = nx * ny * nz;
     // per-triangle candidates summed over the warp: the union pays off only when it is much smaller
-    const long long own = valid ? (b1[0] >= b0[0] && b1[1] >= b0[1] && b1[2] >= b0[2]
-                                       ? (b1[0] - b0[0] + 1) * (b1[1] - b0[1] + 1) * (b1[2] - b0[2] + 1)
-                                       : 0)
-                                : 0;
-    const unsigned own_sum = __reduce_add_sync(0xffffffffu, (unsigned)min(own, 1ll << 20));
+    const unsigned long long own = valid ? box_items(b0, b1) : 0;
+    const unsigned own_sum = __reduce_add_sync(0xffffffffu, (unsigned)min(own, 1ull << 20));
     if (total <= EMB_WU_MAX && 4 * total <= (long long)own_sum) {
         // total <= EMB_WU_MAX: decode the union index in 32-bit arithmetic
         const unsigned ux = (unsigned)nx, uxy = (unsigned)(nx * ny);
@@ -132,25 +175,70 @@ __global__ void __launch_bounds__(EMB_WU_WARPS * 32) k_bin_pairs(const int4 *__r
         }
         return;
     }
-    // large or loose union: each lane enumerates the blocks of its own triangle
+    // large or loose union: each lane takes its own triangle
     if (!valid) return;
+    if (own > EMB_BIG_ITEMS && emb_bigq_push(Q, (uint32_t)t, own)) return;
     for (long long bz = b0[2]; bz <= b1[2]; ++bz)
         for (long long by = b0[1]; by <= b1[1]; ++by)
-            for (long long bx = b0[0]; bx <= b1[0]; ++bx) {
-                int32_t id = emb_lookup(lk, bx, by, bz);
-                if (id < 0) continue;
-                long long lx = bx * g.W - dil, ly = by * g.W - dil, lz = bz * g.W - dil;
-                long long hx = lx + g.W + 2 * dil, hy = ly + g.W + 2 * dil, hz = lz + g.W + 2 * dil;
-                bool ov = emb_point_in_box(A, lx, ly, lz, hx, hy, hz) || emb_point_in_box(B, lx, ly, lz, hx, hy, hz) ||
-                          emb_point_in_box(C, lx, ly, lz, hx, hy, hz) || emb_tri_box(A, B, C, lx, ly, lz, hx, hy, hz);
-                if (!ov) continue;
-                if (MODE == 0) {
-                    atomicAdd(cnt + id, 1u);
-                } else {
-                    uint32_t p = atomicAdd(cnt + id, 1u);
-                    ent[off[id] + p] = (uint32_t)t;
-                }
-            }
+            for (long long bx = b0[0]; bx <= b1[0]; ++bx)
+                bin_block<MODE>(A, B, C, (uint32_t)t, bx, by, bz, g, dil, lk, cnt, off, ent);
+}
+
+// Decomposition of candidate index i of the box [b0, b1] (x fastest) and its step by 32.
+struct BoxWalk {
+    long long nx, ny, x, y, z, dx, dy, dz;
+    __device__ __forceinline__ void start(const long long b0[3], const long long b1[3], unsigned long long i)
+    {
+        nx = b1[0] - b0[0] + 1;
+        ny = b1[1] - b0[1] + 1;
+        x = (long long)(i % (unsigned long long)nx);
+        const unsigned long long r = i / (unsigned long long)nx;
+        y = (long long)(r % (unsigned long long)ny);
+        z = (long long)(r / (unsigned long long)ny);
+        dx = 32 % nx;
+        dy = (32 / nx) % ny;
+        dz = (32 / nx) / ny;
+    }
+    __device__ __forceinline__ void step()
+    {
+        x += dx;
+        y += dy;
+        z += dz;
+        if (x >= nx) {
+            x -= nx;
+            ++y;
+        }
+        if (y >= ny) {
+            y -= ny;
+            ++z;
+        }
+    }
+};
+
+// The queued chunks of large triangles, one warp per chunk.
+template <int MODE>
+__global__ void __launch_bounds__(EMB_BIG_BLOCK) k_bin_pairs_big(const int4 *__restrict__ rec, LevelGeom g, long long dil,
+                                                                 EmbLookup lk, uint32_t *__restrict__ cnt,
+                                                                 const uint32_t *__restrict__ off,
+                                                                 uint32_t *__restrict__ ent, EmbBigQ Q)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned long long nq = emb_bigq_count(Q);
+    const unsigned long long nw = (unsigned long long)gridDim.x * (EMB_BIG_BLOCK / 32);
+    for (unsigned long long e = (unsigned long long)blockIdx.x * (EMB_BIG_BLOCK / 32) + (threadIdx.x >> 5); e < nq;
+         e += nw) {
+        const uint2 E = Q.q[e];
+        if (E.x == EMB_BIG_NONE) continue;
+        int4 A, B, C;
+        long long b0[3], b1[3];
+        if (!bin_setup(rec, E.x, g, dil, A, B, C, b0, b1)) continue;
+        unsigned long long i0, i1;
+        emb_bigq_range(E.y, box_items(b0, b1), i0, i1);
+        BoxWalk bw;
+        bw.start(b0, b1, i0 + lane);
+        for (unsigned long long it = i0 + lane; it < i1; it += 32, bw.step())
+            bin_block<MODE>(A, B, C, E.x, b0[0] + bw.x, b0[1] + bw.y, b0[2] + bw.z, g, dil, lk, cnt, off, ent);
+    }
 }
 
 // Step 1 (enqueue only): flag, pos, flist hold T + 1 uint32; the kept count ends at
@@ -169,23 +257,28 @@ emb_status emb_enq_filter(const int4 *rec, int64_t T, LevelGeom g, uint32_t *fla
 // Steps 2-9 at the finest level, counting half (enqueue only): cnt holds n + 1
 // uint32, off receives n + 1 offsets (pairs total at off[n]); tmp: scan scratch for n.
 emb_status emb_enq_bin_count(const int4 *rec, int64_t T, LevelGeom g, const EmbLevel &lv, uint32_t *cnt, uint32_t *off,
-                             uint64_t *tmp, cudaStream_t s)
+                             uint64_t *tmp, const EmbBigQ &Q, cudaStream_t s)
 {
     EMB_CUDA_TRY(cudaMemsetAsync(cnt, 0, (lv.n + 1) * sizeof(uint32_t), s));
-    EMB_LAUNCH((k_bin_pairs<0>), emb_grid(T, 32 * EMB_WU_WARPS), 32 * EMB_WU_WARPS, 0, s)(rec, T, g, g.half,
-                                                                                          emb_lookup_of(lv), cnt,
-                                                                                          nullptr, nullptr);
+    const EmbLookup lk = emb_lookup_of(lv);
+    if (Q.cap) EMB_CUDA_TRY(cudaMemsetAsync(Q.n, 0, sizeof(unsigned long long), s));
+    EMB_LAUNCH((k_bin_pairs<0>), emb_grid(T, 32 * EMB_WU_WARPS), 32 * EMB_WU_WARPS, 0, s)(rec, T, g, g.half, lk, cnt,
+                                                                                          nullptr, nullptr, Q);
+    if (Q.cap)
+        EMB_LAUNCH((k_bin_pairs_big<0>), EMB_BIG_GRID, EMB_BIG_BLOCK, 0, s)(rec, g, g.half, lk, cnt, nullptr, nullptr, Q);
     return emb_scan_into(cnt, off, lv.n, tmp, s);
 }
 
 // Filling half: ent holds off[n] entries; cnt is reused as the per-block cursor.
 emb_status emb_enq_bin_fill(const int4 *rec, int64_t T, LevelGeom g, const EmbLevel &lv, uint32_t *cnt,
-                            const uint32_t *off, uint32_t *ent, cudaStream_t s)
+                            const uint32_t *off, uint32_t *ent, const EmbBigQ &Q, cudaStream_t s)
 {
     EMB_CUDA_TRY(cudaMemsetAsync(cnt, 0, (lv.n + 1) * sizeof(uint32_t), s));
-    EMB_LAUNCH((k_bin_pairs<1>), emb_grid(T, 32 * EMB_WU_WARPS), 32 * EMB_WU_WARPS, 0, s)(rec, T, g, g.half,
-                                                                                          emb_lookup_of(lv), cnt, off,
-                                                                                          ent);
+    const EmbLookup lk = emb_lookup_of(lv);
+    if (Q.cap) EMB_CUDA_TRY(cudaMemsetAsync(Q.n, 0, sizeof(unsigned long long), s));
+    EMB_LAUNCH((k_bin_pairs<1>), emb_grid(T, 32 * EMB_WU_WARPS), 32 * EMB_WU_WARPS, 0, s)(rec, T, g, g.half, lk, cnt,
+                                                                                          off, ent, Q);
+    if (Q.cap) EMB_LAUNCH((k_bin_pairs_big<1>), EMB_BIG_GRID, EMB_BIG_BLOCK, 0, s)(rec, g, g.half, lk, cnt, off, ent, Q);
     EMB_CUDA_TRY(cudaGetLastError());
     return EMB_OK;
 }
@@ -209,6 +302,7 @@ extern "C" emb_status emb_bin(emb_mesh m, emb_forest f, int32_t level, int32_t l
     uint32_t *flag = nullptr, *pos = nullptr, *cnt = nullptr;
     uint64_t *tmp = nullptr;
     uint32_t nf = 0, np = 0;
+    EmbBigQ Q = {nullptr, nullptr, 0};
     const int64_t tw = emb_scan_tmp_words(m->T > lv.n ? m->T : lv.n);
     // step 1: exact x-line filter, compacted in ascending order
     if (cudaMallocAsync(&flag, (m->T + 1) * sizeof(uint32_t), s) != cudaSuccess ||
@@ -227,7 +321,8 @@ extern "C" emb_status emb_bin(emb_mesh m, emb_forest f, int32_t level, int32_t l
         if (cudaMallocAsync(&cnt, (lv.n + 1) * sizeof(uint32_t), s) != cudaSuccess ||
             cudaMalloc(&b->off, (lv.n + 1) * sizeof(uint32_t)) != cudaSuccess)
             rc = EMB_ERR_CUDA;
-        if (rc == EMB_OK) rc = emb_enq_bin_count(m->rec, m->T, g, lv, cnt, b->off, tmp, s);
+        if (rc == EMB_OK) rc = emb_bigq_alloc(Q, m->T, s);
+        if (rc == EMB_OK) rc = emb_enq_bin_count(m->rec, m->T, g, lv, cnt, b->off, tmp, Q, s);
         if (rc == EMB_OK && cudaMemcpyAsync(&np, b->off + lv.n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
             rc = EMB_ERR_CUDA;
     }
@@ -236,8 +331,9 @@ extern "C" emb_status emb_bin(emb_mesh m, emb_forest f, int32_t level, int32_t l
     if (rc == EMB_OK && finest) {
         b->npairs = np;
         if (cudaMalloc(&b->ent, ((size_t)np + 1) * sizeof(uint32_t)) != cudaSuccess) rc = EMB_ERR_CUDA;
-        if (rc == EMB_OK) rc = emb_enq_bin_fill(m->rec, m->T, g, lv, cnt, b->off, b->ent, s);
+        if (rc == EMB_OK) rc = emb_enq_bin_fill(m->rec, m->T, g, lv, cnt, b->off, b->ent, Q, s);
     }
+    emb_bigq_free(Q, s);
     if (flag) cudaFreeAsync(flag, s);
     if (pos) cudaFreeAsync(pos, s);
     if (cnt) cudaFreeAsync(cnt, s);

@@ -358,3 +358,32 @@ emb_status emb_build_neighbors(EmbLevel &lv, cudaStream_t s)
     EMB_CUDA_TRY(cudaMallocAsync(&lv.nbr, (lv.n * 26 + 1) * sizeof(int32_t), s));
     return emb_enq_neighbors(lv, s);
 }
+
+// ---------------------------------------------------------------------------
+// chunk queue of large triangles
+// ---------------------------------------------------------------------------
+int64_t emb_bigq_capacity(int64_t T)
+{
+    const int64_t c = 16 * T + 1024;
+    return c < (1 << 20) ? c : (1 << 20);
+}
+
+emb_status emb_bigq_alloc(EmbBigQ &Q, int64_t T, cudaStream_t s)
+{
+    Q.q = nullptr;
+    Q.n = nullptr;
+    Q.cap = (uint32_t)emb_bigq_capacity(T);
+    char *p = nullptr;
+    EMB_CUDA_TRY(cudaMallocAsync((void **)&p, 256 + (size_t)Q.cap * sizeof(uint2), s));
+    Q.n = (unsigned long long *)p;
+    Q.q = (uint2 *)(p + 256);
+    return EMB_OK;
+}
+
+void emb_bigq_free(EmbBigQ &Q, cudaStream_t s)
+{
+    if (Q.n) cudaFreeAsync(Q.n, s);
+    Q.q = nullptr;
+    Q.n = nullptr;
+    Q.cap = 0;
+}

@@ -169,14 +169,16 @@ emb_status emb_enq_children(const EmbLevel &P, const uint8_t *d_flags, const uin
 struct LevelGeom;
 emb_status emb_enq_filter(const int4 *rec, int64_t T, LevelGeom g, uint32_t *flag, uint32_t *pos, uint32_t *flist,
                           uint64_t *tmp, int block, cudaStream_t s);
+struct EmbBigQ;
 emb_status emb_enq_bin_count(const int4 *rec, int64_t T, LevelGeom g, const EmbLevel &lv, uint32_t *cnt, uint32_t *off,
-                             uint64_t *tmp, cudaStream_t s);
+                             uint64_t *tmp, const EmbBigQ &Q, cudaStream_t s);
 emb_status emb_enq_bin_fill(const int4 *rec, int64_t T, LevelGeom g, const EmbLevel &lv, uint32_t *cnt,
-                            const uint32_t *off, uint32_t *ent, cudaStream_t s);
+                            const uint32_t *off, uint32_t *ent, const EmbBigQ &Q, cudaStream_t s);
 emb_status emb_enq_voxelize(const int4 *rec, const uint32_t *flist, int64_t nf, LevelGeom g, const EmbLevel &lv,
-                            unsigned long long *s_acc, unsigned int *p_acc, int block, cudaStream_t s);
+                            unsigned long long *s_acc, unsigned int *p_acc, const EmbBigQ &Q, int block,
+                            cudaStream_t s);
 emb_status emb_enq_refine(const int4 *rec, int64_t T, LevelGeom g, long long dil, const EmbLevel &lv, uint8_t *flags,
-                          cudaStream_t s);
+                          const EmbBigQ &Q, cudaStream_t s);
 long long emb_refine_dilation(const emb_forest_s *f, int L, int band);
 
 // Cut links: per-mesh arguments of the persistent link kernel, passed by value as
@@ -424,3 +426,60 @@ __device__ __forceinline__ bool wu_overlap(const WuTri &S, int j, long long lx, 
            emb_point_in_box(C, lx, ly, lz, ux, uy, uz) || emb_tri_box(A, B, C, lx, ly, lz, ux, uy, uz);
 }
 
+// ---------------------------------------------------------------------------
+// work split of large triangles
+// ---------------------------------------------------------------------------
+// The triangle-parallel kernels give each triangle to one thread.  A triangle
+// with more than EMB_BIG_ITEMS items (x-lines, or candidate blocks) would keep
+// its thread busy long after the rest of the grid is done (a coarse mesh on a
+// fine level), so the thread instead appends ceil(items / EMB_BIG_CHUNK) chunk
+// entries to a queue, and a second kernel walks every chunk with one warp.  A
+// thread that finds the queue full walks its items itself: the queue's size
+// affects the speed only, never the result.
+#define EMB_BIG_ITEMS 64
+#define EMB_BIG_CHUNK 512
+#define EMB_BIG_NONE 0xFFFFFFFFu
+struct EmbBigQ {
+    uint2 *q;               // entries (triangle, chunk | chunk count << 16); EMB_BIG_NONE = unused
+    unsigned long long *n;  // entries requested (may exceed cap)
+    uint32_t cap;           // 0: no queue, every thread walks its own items
+};
+
+// Reserves the chunks of triangle t; false when they do not fit.
+__device__ __forceinline__ bool emb_bigq_push(const EmbBigQ &Q, uint32_t t, unsigned long long items)
+{
+    if (Q.cap == 0) return false;
+    unsigned long long nch = (items + EMB_BIG_CHUNK - 1) / EMB_BIG_CHUNK;
+    if (nch > 0xFFFFull) nch = 0xFFFFull;
+    const unsigned long long base = atomicAdd(Q.n, nch);
+    if (base + nch > Q.cap) {
+        for (unsigned long long e = base; e < Q.cap; ++e) Q.q[e] = make_uint2(EMB_BIG_NONE, 0u);
+        return false;
+    }
+    for (uint32_t c = 0; c < (uint32_t)nch; ++c) Q.q[base + c] = make_uint2(t, c | ((uint32_t)nch << 16));
+    return true;
+}
+
+// Items [i0, i1) of the chunk described by an entry's second word.
+__device__ __forceinline__ void emb_bigq_range(uint32_t y, unsigned long long items, unsigned long long &i0,
+                                               unsigned long long &i1)
+{
+    const unsigned long long c = y & 0xFFFFu, nch = y >> 16;
+    const unsigned long long span = (items + nch - 1) / nch;
+    i0 = c * span;
+    i1 = i0 + span < items ? i0 + span : items;
+}
+
+// Entries to walk (entries beyond the capacity were never written).
+__device__ __forceinline__ unsigned long long emb_bigq_count(const EmbBigQ &Q)
+{
+    const unsigned long long n = *Q.n;
+    return n < Q.cap ? n : Q.cap;
+}
+
+// Host side (emb_common.cu): capacity for T triangles, allocation, per-launch reset.
+int64_t emb_bigq_capacity(int64_t T);
+emb_status emb_bigq_alloc(EmbBigQ &Q, int64_t T, cudaStream_t s);  // stream-ordered
+void emb_bigq_free(EmbBigQ &Q, cudaStream_t s);
+#define EMB_BIG_GRID 1216   // CTAs of the chunk kernels (8 per SM on 152 SMs)
+#define EMB_BIG_BLOCK 128

@@ -11,11 +11,47 @@
 //
 // Warp-cooperative over 32 consecutive triangles (see emb_internal.cuh): each
 // candidate block of the warp's union range is looked up once and tested
-// against the 32 triangles; flags are idempotent byte stores.
+// against the 32 triangles; triangles left out of the union are walked by their
+// own lane, or in queued chunks by whole warps when they have many candidate
+// blocks.  Flags are idempotent byte stores.
 #include "emb_internal.cuh"
 
+__device__ __forceinline__ void refine_setup(const int4 *__restrict__ rec, int64_t t, const LevelGeom &g, long long dil,
+                                             int4 &A, int4 &B, int4 &C, long long b0[3], long long b1[3])
+{
+    A = rec[3 * t];
+    B = rec[3 * t + 1];
+    C = rec[3 * t + 2];
+    emb_block_range(min(A.x, min(B.x, C.x)), max(A.x, max(B.x, C.x)), g.lW, dil, g.nb, b0[0], b1[0]);
+    emb_block_range(min(A.y, min(B.y, C.y)), max(A.y, max(B.y, C.y)), g.lW, dil, g.nb, b0[1], b1[1]);
+    emb_block_range(min(A.z, min(B.z, C.z)), max(A.z, max(B.z, C.z)), g.lW, dil, g.nb, b0[2], b1[2]);
+}
+
+__device__ __forceinline__ unsigned long long refine_items(const long long b0[3], const long long b1[3])
+{
+    if (b1[0] < b0[0] || b1[1] < b0[1] || b1[2] < b0[2]) return 0;
+    return (unsigned long long)(b1[0] - b0[0] + 1) * (unsigned long long)(b1[1] - b0[1] + 1) *
+           (unsigned long long)(b1[2] - b0[2] + 1);
+}
+
+// Flag block (bx, by, bz) if it exists, is not flagged yet and the triangle meets its dilated box.
+__device__ __forceinline__ void refine_block(const int4 &A, const int4 &B, const int4 &C, long long bx, long long by,
+                                             long long bz, const LevelGeom &g, long long dil, const EmbLookup &lk,
+                                             uint8_t *__restrict__ flags)
+{
+    const int32_t id = emb_lookup(lk, bx, by, bz);
+    if (id < 0) return;
+    if (*((volatile uint8_t *)flags + id)) return;
+    const long long lx = bx * g.W - dil, ly = by * g.W - dil, lz = bz * g.W - dil;
+    const long long hx = lx + g.W + 2 * dil, hy = ly + g.W + 2 * dil, hz = lz + g.W + 2 * dil;
+    if (emb_point_in_box(A, lx, ly, lz, hx, hy, hz) || emb_point_in_box(B, lx, ly, lz, hx, hy, hz) ||
+        emb_point_in_box(C, lx, ly, lz, hx, hy, hz) || emb_tri_box(A, B, C, lx, ly, lz, hx, hy, hz))
+        flags[id] = 1;
+}
+
 __global__ void __launch_bounds__(EMB_WU_WARPS * 32) k_refine(const int4 *__restrict__ rec, int64_t T, LevelGeom g,
-                                                              long long dil, EmbLookup lk, uint8_t *__restrict__ flags)
+                                                              long long dil, EmbLookup lk, uint8_t *__restrict__ flags,
+                                                              EmbBigQ Q)
 {
     __shared__ WuTri tiles[EMB_WU_WARPS];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -24,14 +60,7 @@ __global__ void __launch_bounds__(EMB_WU_WARPS * 32) k_refine(const int4 *__rest
     const bool valid = t < T;
     long long b0[3] = {1ll << 40, 1ll << 40, 1ll << 40}, b1[3] = {-1, -1, -1};
     int4 A = make_int4(0, 0, 0, 0), B = A, C = A;
-    if (valid) {
-        A = rec[3 * t];
-        B = rec[3 * t + 1];
-        C = rec[3 * t + 2];
-        emb_block_range(min(A.x, min(B.x, C.x)), max(A.x, max(B.x, C.x)), g.lW, dil, g.nb, b0[0], b1[0]);
-        emb_block_range(min(A.y, min(B.y, C.y)), max(A.y, max(B.y, C.y)), g.lW, dil, g.nb, b0[1], b1[1]);
-        emb_block_range(min(A.z, min(B.z, C.z)), max(A.z, max(B.z, C.z)), g.lW, dil, g.nb, b0[2], b1[2]);
-    }
+    if (valid) refine_setup(rec, t, g, dil, A, B, C, b0, b1);
     S.A[lane] = A;
     S.B[lane] = B;
     S.C[lane] = C;
@@ -52,11 +81,8 @@ __global__ void __launch_bounds__(EMB_WU_WARPS * 32) k_refine(const int4 *__rest
     if (nx <= 0 || ny <= 0 || nz <= 0) return;
     const long long total = nx * ny * nz;
     // per-triangle candidates summed over the warp: the union pays off only when it is much smaller
-    const long long own = valid ? (b1[0] >= b0[0] && b1[1] >= b0[1] && b1[2] >= b0[2]
-                                       ? (b1[0] - b0[0] + 1) * (b1[1] - b0[1] + 1) * (b1[2] - b0[2] + 1)
-                                       : 0)
-                                : 0;
-    const unsigned own_sum = __reduce_add_sync(0xffffffffu, (unsigned)min(own, 1ll << 20));
+    const unsigned long long own = valid ? refine_items(b0, b1) : 0;
+    const unsigned own_sum = __reduce_add_sync(0xffffffffu, (unsigned)min(own, 1ull << 20));
     if (total <= EMB_WU_MAX && 4 * total <= (long long)own_sum) {
         // total <= EMB_WU_MAX: decode the union index in 32-bit arithmetic
         const unsigned ux = (unsigned)nx, uxy = (unsigned)(nx * ny);
@@ -76,20 +102,51 @@ __global__ void __launch_bounds__(EMB_WU_WARPS * 32) k_refine(const int4 *__rest
         }
         return;
     }
-    // large or loose union: each lane enumerates the blocks of its own triangle
+    // large or loose union: each lane takes its own triangle, queued in chunks when it has many candidates
     if (!valid) return;
+    if (own > EMB_BIG_ITEMS && emb_bigq_push(Q, (uint32_t)t, own)) return;
     for (long long bz = b0[2]; bz <= b1[2]; ++bz)
         for (long long by = b0[1]; by <= b1[1]; ++by)
-            for (long long bx = b0[0]; bx <= b1[0]; ++bx) {
-                int32_t id = emb_lookup(lk, bx, by, bz);
-                if (id < 0) continue;
-                if (*((volatile uint8_t *)flags + id)) continue;
-                long long lx = bx * g.W - dil, ly = by * g.W - dil, lz = bz * g.W - dil;
-                long long hx = lx + g.W + 2 * dil, hy = ly + g.W + 2 * dil, hz = lz + g.W + 2 * dil;
-                if (emb_point_in_box(A, lx, ly, lz, hx, hy, hz) || emb_point_in_box(B, lx, ly, lz, hx, hy, hz) ||
-                    emb_point_in_box(C, lx, ly, lz, hx, hy, hz) || emb_tri_box(A, B, C, lx, ly, lz, hx, hy, hz))
-                    flags[id] = 1;
+            for (long long bx = b0[0]; bx <= b1[0]; ++bx) refine_block(A, B, C, bx, by, bz, g, dil, lk, flags);
+}
+
+// The queued chunks of large triangles, one warp per chunk (candidates x fastest).
+__global__ void __launch_bounds__(EMB_BIG_BLOCK) k_refine_big(const int4 *__restrict__ rec, LevelGeom g, long long dil,
+                                                              EmbLookup lk, uint8_t *__restrict__ flags, EmbBigQ Q)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned long long nq = emb_bigq_count(Q);
+    const unsigned long long nw = (unsigned long long)gridDim.x * (EMB_BIG_BLOCK / 32);
+    for (unsigned long long e = (unsigned long long)blockIdx.x * (EMB_BIG_BLOCK / 32) + (threadIdx.x >> 5); e < nq;
+         e += nw) {
+        const uint2 E = Q.q[e];
+        if (E.x == EMB_BIG_NONE) continue;
+        int4 A, B, C;
+        long long b0[3], b1[3];
+        refine_setup(rec, E.x, g, dil, A, B, C, b0, b1);
+        unsigned long long i0, i1;
+        emb_bigq_range(E.y, refine_items(b0, b1), i0, i1);
+        const long long nx = b1[0] - b0[0] + 1, ny = b1[1] - b0[1] + 1;
+        const unsigned long long first = i0 + lane;
+        long long x = (long long)(first % (unsigned long long)nx);
+        long long y = (long long)((first / (unsigned long long)nx) % (unsigned long long)ny);
+        long long z = (long long)((first / (unsigned long long)nx) / (unsigned long long)ny);
+        const long long dx = 32 % nx, dy = (32 / nx) % ny, dz = (32 / nx) / ny;
+        for (unsigned long long it = first; it < i1; it += 32) {
+            refine_block(A, B, C, b0[0] + x, b0[1] + y, b0[2] + z, g, dil, lk, flags);
+            x += dx;
+            y += dy;
+            z += dz;
+            if (x >= nx) {
+                x -= nx;
+                ++y;
             }
+            if (y >= ny) {
+                y -= ny;
+                ++z;
+            }
+        }
+    }
 }
 
 // (rho_L - 1/2) h_L in frame units, or -1 if it is not an integer.
@@ -109,11 +166,14 @@ long long emb_refine_dilation(const emb_forest_s *f, int L, int band)
 
 // Enqueue only: flags (lv.n bytes) are cleared and set.
 emb_status emb_enq_refine(const int4 *rec, int64_t T, LevelGeom g, long long dil, const EmbLevel &lv, uint8_t *flags,
-                          cudaStream_t s)
+                          const EmbBigQ &Q, cudaStream_t s)
 {
     if (lv.n == 0) return EMB_OK;
     EMB_CUDA_TRY(cudaMemsetAsync(flags, 0, lv.n, s));
-    EMB_LAUNCH((k_refine), emb_grid(T, 32 * EMB_WU_WARPS), 32 * EMB_WU_WARPS, 0, s)(rec, T, g, dil, emb_lookup_of(lv), flags);
+    const EmbLookup lk = emb_lookup_of(lv);
+    if (Q.cap) EMB_CUDA_TRY(cudaMemsetAsync(Q.n, 0, sizeof(unsigned long long), s));
+    EMB_LAUNCH((k_refine), emb_grid(T, 32 * EMB_WU_WARPS), 32 * EMB_WU_WARPS, 0, s)(rec, T, g, dil, lk, flags, Q);
+    if (Q.cap) EMB_LAUNCH((k_refine_big), EMB_BIG_GRID, EMB_BIG_BLOCK, 0, s)(rec, g, dil, lk, flags, Q);
     EMB_CUDA_TRY(cudaGetLastError());
     return EMB_OK;
 }
@@ -128,5 +188,11 @@ extern "C" emb_status emb_refine_flags(emb_forest f, emb_bins b, int32_t level, 
     if (!d_flags) return EMB_ERR_BAD_INPUT;
     long long dil = emb_refine_dilation(f, level, band);
     if (dil < 0) return EMB_ERR_RANGE;
-    return emb_enq_refine(b->m->rec, b->m->T, level_geom(f, level), dil, lv, d_flags, emb_stream(stream));
+    cudaStream_t s = emb_stream(stream);
+    EmbBigQ Q;
+    emb_status rc = emb_bigq_alloc(Q, b->m->T, s);
+    if (rc != EMB_OK) return rc;
+    rc = emb_enq_refine(b->m->rec, b->m->T, level_geom(f, level), dil, lv, d_flags, Q, s);
+    emb_bigq_free(Q, s);
+    return rc;
 }

@@ -18,60 +18,128 @@
 // neighbour-to-neighbour walk along +x.
 #include "emb_internal.cuh"
 
-__global__ void k_vox(const int4 *__restrict__ rec, const uint32_t *__restrict__ flist, int64_t nf, LevelGeom g,
-                      EmbLookup lk,
-                      unsigned long long *__restrict__ s_acc, unsigned int *__restrict__ p_acc, int *st)
+// One triangle as the voxelizer sees it: its x-lines (j, k) in [j0, j1] x [k0, k1]
+// and the x-range [bx0, bx1] of blocks its crossings can fall in.
+struct VoxTri {
+    int4 A, B, C;
+    long long nx, ny, nz;
+    int sx;
+    long long j0, j1, k0, k1, bx0, bx1;
+};
+
+// false for a triangle parallel to x (no line crosses it)
+__device__ __forceinline__ bool vox_setup(const int4 *__restrict__ rec, int64_t t, const LevelGeom &g, VoxTri &V)
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nf) return;
-    int64_t t = flist[i];
-    int4 A = rec[3 * t], B = rec[3 * t + 1], C = rec[3 * t + 2];
+    V.A = rec[3 * t];
+    V.B = rec[3 * t + 1];
+    V.C = rec[3 * t + 2];
+    const int4 A = V.A, B = V.B, C = V.C;
     long long ux = (long long)B.x - A.x, uy = (long long)B.y - A.y, uz = (long long)B.z - A.z;
     long long vx = (long long)C.x - A.x, vy = (long long)C.y - A.y, vz = (long long)C.z - A.z;
-    long long nx = uy * vz - uz * vy, ny = uz * vx - ux * vz, nz = ux * vy - uy * vx;
-    if (nx == 0) return;
-    int sx = nx > 0 ? 1 : -1;
-    long long j0, j1, k0, k1;
-    line_range(min(A.y, min(B.y, C.y)), max(A.y, max(B.y, C.y)), g.lh, g.half, g.ncell, j0, j1);
-    line_range(min(A.z, min(B.z, C.z)), max(A.z, max(B.z, C.z)), g.lh, g.half, g.ncell, k0, k1);
-    long long bx0 = emb_floor_shr(min(A.x, min(B.x, C.x)), g.lW), bx1 = emb_floor_shr(max(A.x, max(B.x, C.x)), g.lW);
-    if (bx0 < 0) bx0 = 0;
-    if (bx1 > g.nb - 1) bx1 = g.nb - 1;
-    for (long long k = k0; k <= k1; ++k) {
-        int pz = (int)((2 * k + 1) * g.half);
-        for (long long j = j0; j <= j1; ++j) {
-            int py = (int)((2 * j + 1) * g.half);
-            if (emb_orient_yz(A.y, A.z, B.y, B.z, py, pz) != sx || emb_orient_yz(B.y, B.z, C.y, C.z, py, pz) != sx ||
-                emb_orient_yz(C.y, C.z, A.y, A.z, py, pz) != sx)
-                continue;
-            // n . (A - (x, py, pz)) = D_yz + n_x (A_x - x); the crossing is at x_hit with
-            // x_hit - x = D(x) / n_x.
-            i128 Dyz = mul128(ny, (long long)A.y - py) + mul128(nz, (long long)A.z - pz);
-            bool owned = false;
-            for (long long bx = bx0; bx <= bx1 && !owned; ++bx) {
-                long long lo = bx * g.W;
-                i128 Dlo = Dyz + mul128(nx, (long long)A.x - lo);
-                if (sgn_i128(Dlo) * sx < 0) continue;                   // x_hit < lo
-                if (sgn_i128(Dlo - mul128(nx, g.W)) * sx >= 0) continue;  // x_hit >= lo + W
-                owned = true;
-                int32_t id = emb_lookup(lk, bx, j >> 2, k >> 2);
-                if (id < 0) {
-                    emb_set_status(st, EMB_ERR_STATE);  // a crossing outside every block
-                    break;
-                }
-                // cell q of this line (centre lo + (2q+1) half) lies before the crossing iff
-                // the perturbed centre sees the plane ahead: sign(D) == sign(n_x), D == 0 -> no
-                unsigned long long bits = 0;
+    V.nx = uy * vz - uz * vy;
+    V.ny = uz * vx - ux * vz;
+    V.nz = ux * vy - uy * vx;
+    if (V.nx == 0) return false;
+    V.sx = V.nx > 0 ? 1 : -1;
+    line_range(min(A.y, min(B.y, C.y)), max(A.y, max(B.y, C.y)), g.lh, g.half, g.ncell, V.j0, V.j1);
+    line_range(min(A.z, min(B.z, C.z)), max(A.z, max(B.z, C.z)), g.lh, g.half, g.ncell, V.k0, V.k1);
+    V.bx0 = emb_floor_shr(min(A.x, min(B.x, C.x)), g.lW);
+    V.bx1 = emb_floor_shr(max(A.x, max(B.x, C.x)), g.lW);
+    if (V.bx0 < 0) V.bx0 = 0;
+    if (V.bx1 > g.nb - 1) V.bx1 = g.nb - 1;
+    return true;
+}
+
+__device__ __forceinline__ unsigned long long vox_items(const VoxTri &V)
+{
+    if (V.j1 < V.j0 || V.k1 < V.k0) return 0;
+    return (unsigned long long)(V.j1 - V.j0 + 1) * (unsigned long long)(V.k1 - V.k0 + 1);
+}
+
+// The crossing of line (j, k) with the triangle, if any, recorded in its owner block.
+__device__ __forceinline__ void vox_line(const VoxTri &V, const LevelGeom &g, const EmbLookup &lk, long long j,
+                                         long long k, unsigned long long *__restrict__ s_acc,
+                                         unsigned int *__restrict__ p_acc, int *st)
+{
+    const int4 A = V.A, B = V.B, C = V.C;
+    const int sx = V.sx;
+    const int pz = (int)((2 * k + 1) * g.half), py = (int)((2 * j + 1) * g.half);
+    if (emb_orient_yz(A.y, A.z, B.y, B.z, py, pz) != sx || emb_orient_yz(B.y, B.z, C.y, C.z, py, pz) != sx ||
+        emb_orient_yz(C.y, C.z, A.y, A.z, py, pz) != sx)
+        return;
+    // n . (A - (x, py, pz)) = D_yz + n_x (A_x - x); the crossing is at x_hit with
+    // x_hit - x = D(x) / n_x.
+    const i128 Dyz = mul128(V.ny, (long long)A.y - py) + mul128(V.nz, (long long)A.z - pz);
+    for (long long bx = V.bx0; bx <= V.bx1; ++bx) {
+        const long long lo = bx * g.W;
+        const i128 Dlo = Dyz + mul128(V.nx, (long long)A.x - lo);
+        if (sgn_i128(Dlo) * sx < 0) continue;                     // x_hit < lo
+        if (sgn_i128(Dlo - mul128(V.nx, g.W)) * sx >= 0) continue;  // x_hit >= lo + W
+        const int32_t id = emb_lookup(lk, bx, j >> 2, k >> 2);
+        if (id < 0) {
+            emb_set_status(st, EMB_ERR_STATE);  // a crossing outside every block
+            return;
+        }
+        // cell q of this line (centre lo + (2q+1) half) lies before the crossing iff
+        // the perturbed centre sees the plane ahead: sign(D) == sign(n_x), D == 0 -> no
+        unsigned long long bits = 0;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    i128 Dq = Dlo - mul128(nx, (2 * q + 1) * g.half);
-                    if (sgn_i128(Dq) == sx) bits |= 1ull << q;
-                }
-                int line = (int)((j & 3) + 4 * (k & 3));
-                if (bits) atomicXor(s_acc + id, bits << (4 * line));
-                atomicXor(p_acc + id, 1u << line);
+        for (int q = 0; q < 4; ++q) {
+            const i128 Dq = Dlo - mul128(V.nx, (2 * q + 1) * g.half);
+            if (sgn_i128(Dq) == sx) bits |= 1ull << q;
+        }
+        const int line = (int)((j & 3) + 4 * (k & 3));
+        if (bits) atomicXor(s_acc + id, bits << (4 * line));
+        atomicXor(p_acc + id, 1u << line);
+        return;
+    }
+    emb_set_status(st, EMB_ERR_STATE);  // no block owns the crossing
+}
+
+__global__ void k_vox(const int4 *__restrict__ rec, const uint32_t *__restrict__ flist, int64_t nf, LevelGeom g,
+                      EmbLookup lk, unsigned long long *__restrict__ s_acc, unsigned int *__restrict__ p_acc,
+                      EmbBigQ Q, int *st)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nf) return;
+    const uint32_t t = flist[i];
+    VoxTri V;
+    if (!vox_setup(rec, t, g, V)) return;
+    const unsigned long long items = vox_items(V);
+    if (items > EMB_BIG_ITEMS && emb_bigq_push(Q, t, items)) return;
+    for (long long k = V.k0; k <= V.k1; ++k)
+        for (long long j = V.j0; j <= V.j1; ++j) vox_line(V, g, lk, j, k, s_acc, p_acc, st);
+}
+
+// The queued chunks of large triangles, one warp per chunk (lines in j-major order).
+__global__ void __launch_bounds__(EMB_BIG_BLOCK) k_vox_big(const int4 *__restrict__ rec, LevelGeom g, EmbLookup lk,
+                                                           unsigned long long *__restrict__ s_acc,
+                                                           unsigned int *__restrict__ p_acc, EmbBigQ Q, int *st)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned long long nq = emb_bigq_count(Q);
+    const unsigned long long nw = (unsigned long long)gridDim.x * (EMB_BIG_BLOCK / 32);
+    for (unsigned long long e = (unsigned long long)blockIdx.x * (EMB_BIG_BLOCK / 32) + (threadIdx.x >> 5); e < nq;
+         e += nw) {
+        const uint2 E = Q.q[e];
+        if (E.x == EMB_BIG_NONE) continue;
+        VoxTri V;
+        if (!vox_setup(rec, E.x, g, V)) continue;
+        const unsigned long long items = vox_items(V);
+        unsigned long long i0, i1;
+        emb_bigq_range(E.y, items, i0, i1);
+        const unsigned long long nj = (unsigned long long)(V.j1 - V.j0 + 1);
+        const unsigned long long first = i0 + lane;
+        long long jj = (long long)(first % nj), kk = (long long)(first / nj);
+        const long long dj = (long long)(32 % nj), dk = (long long)(32 / nj);
+        for (unsigned long long it = first; it < i1; it += 32) {
+            vox_line(V, g, lk, V.j0 + jj, V.k0 + kk, s_acc, p_acc, st);
+            jj += dj;
+            kk += dk;
+            if (jj >= (long long)nj) {
+                jj -= (long long)nj;
+                ++kk;
             }
-            if (!owned) emb_set_status(st, EMB_ERR_STATE);
         }
     }
 }
@@ -103,15 +171,19 @@ __global__ void k_xscan(const uint64_t *__restrict__ key, int64_t n, const unsig
 
 // Enqueue only: s_acc (n uint64) and p_acc (n uint32) are scratch; writes lv.mask.
 emb_status emb_enq_voxelize(const int4 *rec, const uint32_t *flist, int64_t nf, LevelGeom g, const EmbLevel &lv,
-                            unsigned long long *s_acc, unsigned int *p_acc, int block, cudaStream_t s)
+                            unsigned long long *s_acc, unsigned int *p_acc, const EmbBigQ &Q, int block, cudaStream_t s)
 {
     int *st = emb_status_word();
     if (!st) return EMB_ERR_CUDA;
     if (lv.n == 0) return EMB_OK;
     EMB_CUDA_TRY(cudaMemsetAsync(s_acc, 0, lv.n * sizeof(unsigned long long), s));
     EMB_CUDA_TRY(cudaMemsetAsync(p_acc, 0, lv.n * sizeof(unsigned int), s));
-    if (nf > 0)
-        EMB_LAUNCH((k_vox), emb_grid(nf, block), block, 0, s)(rec, flist, nf, g, emb_lookup_of(lv), s_acc, p_acc, st);
+    if (nf > 0) {
+        const EmbLookup lk = emb_lookup_of(lv);
+        if (Q.cap) EMB_CUDA_TRY(cudaMemsetAsync(Q.n, 0, sizeof(unsigned long long), s));
+        EMB_LAUNCH((k_vox), emb_grid(nf, block), block, 0, s)(rec, flist, nf, g, lk, s_acc, p_acc, Q, st);
+        if (Q.cap) EMB_LAUNCH((k_vox_big), EMB_BIG_GRID, EMB_BIG_BLOCK, 0, s)(rec, g, lk, s_acc, p_acc, Q, st);
+    }
     EMB_LAUNCH((k_xscan), emb_grid(lv.n, 256), 256, 0, s)(lv.key, lv.n, s_acc, p_acc, lv.mask);
     EMB_CUDA_TRY(cudaGetLastError());
     return EMB_OK;
@@ -133,7 +205,11 @@ extern "C" emb_status emb_voxelize(emb_forest f, emb_bins b, int32_t level, uint
     unsigned int *p_acc = nullptr;
     EMB_CUDA_TRY(cudaMallocAsync(&s_acc, lv.n * sizeof(unsigned long long), s));
     EMB_CUDA_TRY(cudaMallocAsync(&p_acc, lv.n * sizeof(unsigned int), s));
-    emb_status rc = emb_enq_voxelize(b->m->rec, b->flist, b->nf, g, lv, s_acc, p_acc, 128, s);
+    EmbBigQ Q;
+    emb_status rc = emb_bigq_alloc(Q, b->nf, s);
+    if (rc != EMB_OK) return rc;
+    rc = emb_enq_voxelize(b->m->rec, b->flist, b->nf, g, lv, s_acc, p_acc, Q, 128, s);
+    emb_bigq_free(Q, s);
     if (rc != EMB_OK) return rc;
     if (d_solid_mask)
         EMB_CUDA_TRY(cudaMemcpyAsync(d_solid_mask, lv.mask, lv.n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
