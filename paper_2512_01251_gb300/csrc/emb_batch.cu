@@ -53,6 +53,9 @@ struct BMesh {
     uint64_t *cand = nullptr;
     uint32_t *work_n = nullptr, *work = nullptr, *blk_off = nullptr;
     unsigned int *next = nullptr;                   // queue cursor of a per-mesh link launch
+    uint2 *witem = nullptr;                         // link work items
+    uint2 *extra = nullptr;                         // extra parts of split blocks
+    unsigned long long *extra_n = nullptr;
     EmbBigQ bq = {nullptr, nullptr, 0};             // chunk queue of large triangles
     int32_t *o_cell = nullptr, *o_tri = nullptr;
     uint8_t *o_dir = nullptr;
@@ -181,6 +184,9 @@ static emb_status alloc_mesh(BMesh &B)
     BTRY(balloc(B, &B.work, fin.n + 1));
     BTRY(balloc(B, &B.blk_off, fin.n + 1));
     BTRY(balloc(B, &B.next, 1));
+    BTRY(balloc(B, &B.witem, fin.n + 1));
+    BTRY(balloc(B, &B.extra, (size_t)emb_link_extra_capacity(fin.n)));
+    BTRY(balloc(B, &B.extra_n, 1));
     BTRY(balloc(B, &B.bq.n, 1));
     BTRY(balloc(B, &B.bq.q, (size_t)emb_bigq_capacity(T)));
     B.bq.cap = (uint32_t)emb_bigq_capacity(T);
@@ -222,6 +228,8 @@ static emb_status enqueue_mesh(BMesh &B, int tri_block, cudaStream_t s)
             BTRY(emb_enq_link_prep(lv, B.lattice, B.cand, B.cnt, B.rank, B.work_n, B.work, B.blk_off, B.tmp, s));
             BTRY(emb_expect_u32(B.work_n + lv.n, (uint64_t)B.nwork, s));
             BTRY(emb_expect_u32(B.blk_off + lv.n, (uint64_t)B.links, s));
+            BTRY(emb_enq_link_split(lv, B.work, B.work_n + lv.n, B.cand, B.blk_off, B.bin_off, B.witem, B.extra,
+                                    B.extra_n, (uint32_t)emb_link_extra_capacity(lv.n), s));
         }
     }
     return EMB_OK;
@@ -304,8 +312,11 @@ static LinkMesh link_mesh(BMesh &B)
     M.bin_off = B.bin_off;
     M.bin_ent = B.bin_ent;
     M.rec = B.m->rec;
-    M.work = B.work;
     M.work_n = B.work_n + fin.n;
+    M.witem = B.witem;
+    M.extra = B.extra;
+    M.extra_n = B.extra_n;
+    M.extra_cap = (uint32_t)emb_link_extra_capacity(fin.n);
     M.o_cell = B.o_cell;
     M.o_dir = B.o_dir;
     M.o_q = B.o_q;

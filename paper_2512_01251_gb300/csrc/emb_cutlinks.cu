@@ -7,7 +7,9 @@
 //   block and its 26 neighbours by 3-D bit shifts.
 // Counts per block -> exclusive scan -> link offsets (block-granular, in block
 //   order, so the table is sorted by (cell, direction)).
-// k_link_emit: one warp per block with links (details at the kernel).  Exact
+// k_link_split: a block whose links times bin triangles is large becomes several
+//   work items, each a contiguous range of its boundary cells.
+// k_link_emit: one warp per work item (details at the kernel).  Exact
 //   Pluecker sides for the line, exact plane sides for the two segment ends
 //   (query points pushed by (e, e^2, e^3)), and an exact rational comparison of
 //   t = N / (h M) between crossings (lowest triangle id on equality).  q = t is
@@ -85,27 +87,34 @@ __global__ void k_link_cand(const uint64_t *__restrict__ mask, const int32_t *__
     blk_cnt[b] = count;
 }
 
-// One warp per finest block.  The block's cells that have cut links are taken in
-// chunks of up to 32 (slot j = the j-th such cell of the chunk).  The block's bin
-// is staged 32 triangles at a time into the warp's shared-memory tile.  A
-// triangle can only cross a link from cell centre P if its bounding box meets the
-// cube [P - h, P + h]; because the cells form a 4x4x4 lattice, the set of cells
-// passing that test is a sub-box, built as a 64-bit mask with a few bit
-// operations.  The surviving (triangle, cell) pairs of a tile are spread over the
-// 32 lanes with a prefix sum.  Per pair, the directions whose segment box misses
-// the triangle box are dropped, the plane offset D = n . (A - P) is formed once,
-// and each remaining direction c first needs the two segment ends on opposite
-// sides of the plane (D against D - h n.c) before the three Pluecker signs are
-// evaluated.  When every vertex lies within 2^14 of P the Pluecker products fit
-// 32-bit integers and D fits 64 bits; otherwise a 128-bit path is taken.
-// Crossings, with q already rounded, are appended to a per-cell bucket;
-// afterwards the owner lane of each cell keeps, per direction, the nearest one
-// (exact rational comparison when a link crosses more than one face) and writes
-// the links.  A bucket that overflows sends its cell through an exact per-cell
-// scan of the whole bin instead.
+// One warp per work item: a finest block with links, or one part of a heavy block
+// (a contiguous range of its cells with links, see k_link_split).  The item's
+// cells that have cut links are taken in chunks of up to 32 (slot j = the j-th
+// such cell of the chunk).  The block's bin is staged 32 triangles at a time into
+// the warp's shared-memory tile.  A triangle can only cross a link from cell
+// centre P if its bounding box meets the cube [P - h, P + h]; because the cells
+// form a 4x4x4 lattice, the set of cells passing that test is a sub-box, built as
+// a 64-bit mask with a few bit operations.  The surviving (triangle, cell) pairs
+// of a tile are spread over the 32 lanes with a prefix sum.  Per pair, with the
+// vertices relative to P, the moments m_i of the three edges and D = n . (A - P)
+// are formed once; the three Pluecker signs c . m_i against c . n then test the
+// lines of all 13 direction pairs (c and -c share the line) at once, and only a
+// hit line checks the ends of its candidate segments against the plane (D
+// against D - h n.c).  When every vertex lies within 2^14 of P the moments fit
+// 32-bit integers and D fits 64 bits; otherwise, and for a zero Pluecker value,
+// a 128-bit path decides.  Crossings, with q already rounded, are appended to a
+// per-cell bucket; afterwards the owner lane of each cell keeps, per direction,
+// the nearest one (exact rational comparison when a link crosses more than one
+// face) and writes the links at the cell's offset in the table, which the
+// direction words fix whichever warp handles the cell.  A bucket that overflows
+// sends its cell through an exact per-cell scan of the whole bin instead.
 #define LE_WARPS 4
 #define LE_TILE 32
 #define LE_BCAP 28
+// A block is split into about (links x bin triangles) / LE_SPLIT_COST parts, at
+// most one per three links and LE_SPLIT_MAX in all.
+#define LE_SPLIT_COST 16384
+#define LE_SPLIT_MAX 64
 
 struct TriT {
     int ax, ay, az, bx, by, bz, cx, cy, cz, id;
@@ -342,18 +351,22 @@ __global__ void __launch_bounds__(LE_WARPS * 32, LE_MINB) k_link_emit(const __gr
 {
     extern __shared__ __align__(16) unsigned char le_smem[];
     __shared__ uint32_t s_pre[EMB_MAX_BATCH + 1];  // work items of meshes before j
+    __shared__ uint32_t s_ext[EMB_MAX_BATCH];      // extra parts of mesh j (they come first in its range)
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     LeWarp &S = reinterpret_cast<LeWarp *>(le_smem)[w];
     if (threadIdx.x == 0) {
         uint32_t acc = 0;
         for (int j = 0; j < tab.n; ++j) {
+            const LinkMesh &M = tab.m[j];
+            const unsigned long long ne = M.extra_n ? *M.extra_n : 0ull;
+            s_ext[j] = (uint32_t)(ne < M.extra_cap ? ne : M.extra_cap);
             s_pre[j] = acc;
-            acc += *tab.m[j].work_n;
+            acc += *M.work_n + s_ext[j];
         }
         s_pre[tab.n] = acc;
     }
     __syncthreads();
-    // persistent warps: take the next (mesh, block with links) item of the shared work queue
+    // persistent warps: take the next (mesh, part of a block with links) item of the shared work queue
     for (;;) {
         unsigned int widx = 0;
         if (lane == 0) widx = atomicAdd(next, 1u);
@@ -364,7 +377,10 @@ __global__ void __launch_bounds__(LE_WARPS * 32, LE_MINB) k_link_emit(const __gr
         const LinkMesh &M = tab.m[mj];
         const uint32_t *__restrict__ bin_ent = M.bin_ent;
         const int4 *__restrict__ rec = M.rec;
-        const int64_t b = M.work[widx - s_pre[mj]];
+        const uint32_t local = widx - s_pre[mj];
+        const uint2 E = local < s_ext[mj] ? M.extra[local] : M.witem[local - s_ext[mj]];
+        if (E.x == EMB_BIG_NONE) continue;
+        const int64_t b = E.x;
         const uint32_t base = M.blk_off[b];
         // candidate directions of cells lane and 32 + lane from the block's direction words
         const uint64_t wd = lane < 26 ? M.cand[b * 26 + lane] : 0ull;
@@ -398,11 +414,13 @@ __global__ void __launch_bounds__(LE_WARPS * 32, LE_MINB) k_link_emit(const __gr
         const uint32_t e0 = M.bin_off[b], e1 = M.bin_off[b + 1];
         const int lh = __ffsll(h) - 1;  // h is a power of two
         const long long LIM = 1ll << 14;
-        for (int chunk = 0; chunk * 32 < nbc; ++chunk) {
-            // the chunk's cells: set bits 32*chunk .. 32*chunk+31 of bmask
-            const int lo_bit = select64(bmask, chunk * 32);
-            const int ncc = min(32, nbc - chunk * 32);
-            const int hi_bit = select64(bmask, chunk * 32 + ncc - 1);
+        // this item's cells with links: ranks [kb0, kb1) among the set bits of bmask
+        const int kb0 = (int)(E.y & 0xFFu), kb1 = min(nbc, (int)((E.y >> 8) & 0xFFu));
+        for (int cb = kb0; cb < kb1; cb += 32) {
+            // the chunk's cells: set bits cb .. cb + 31 of bmask
+            const int lo_bit = select64(bmask, cb);
+            const int ncc = min(32, kb1 - cb);
+            const int hi_bit = select64(bmask, cb + ncc - 1);
             const unsigned long long cmask = bmask & bit_range(lo_bit, hi_bit);
             // slot lane: its cell, candidates and link offset
             const bool active = lane < ncc;
@@ -674,6 +692,64 @@ emb_status emb_enq_link_prep(const EmbLevel &lv, int lattice, uint64_t *cand, ui
     return emb_scan_into(cnt, blk_off, lv.n, tmp, s);
 }
 
+// Work items (thread per block with links): block b with l links, a bin of nt
+// triangles and nbc cells with links costs about l * nt exact tests and is cut
+// into P = min(ceil(l nt / LE_SPLIT_COST), nbc, LE_SPLIT_MAX) parts of
+// ceil(nbc / P) consecutive cells.  The first part is the block's own item; the
+// others are appended to `extra`, and when that is full the block stays whole,
+// which changes the speed only.
+__global__ void k_link_split(const uint32_t *__restrict__ work, const uint32_t *__restrict__ work_n,
+                             const uint64_t *__restrict__ cand, const uint32_t *__restrict__ blk_off,
+                             const uint32_t *__restrict__ bin_off, int64_t n, uint2 *__restrict__ witem,
+                             uint2 *__restrict__ extra, unsigned long long *__restrict__ extra_n, uint32_t cap)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || i >= (int64_t)*work_n) return;
+    const uint32_t b = work[i];
+    uint64_t bm = 0;
+    for (int d = 0; d < 26; ++d) bm |= cand[(int64_t)b * 26 + d];
+    const uint32_t nbc = (uint32_t)__popcll(bm);
+    const unsigned long long l = blk_off[b + 1] - blk_off[b], nt = bin_off[b + 1] - bin_off[b];
+    unsigned long long P = (l * nt + LE_SPLIT_COST - 1) / LE_SPLIT_COST;
+    P = P < nbc ? P : nbc;
+    P = P < LE_SPLIT_MAX ? P : LE_SPLIT_MAX;
+    uint32_t span = nbc;
+    if (P > 1) {
+        span = (uint32_t)((nbc + P - 1) / P);
+        P = (nbc + span - 1) / span;  // no empty part
+        const unsigned long long base = atomicAdd(extra_n, P - 1);
+        if (base + P - 1 > cap) {
+            for (unsigned long long e = base; e < cap; ++e) extra[e] = make_uint2(EMB_BIG_NONE, 0u);
+            span = nbc;
+        } else {
+            for (uint32_t p = 1; p < (uint32_t)P; ++p) {
+                const uint32_t k0 = p * span, k1 = k0 + span < nbc ? k0 + span : nbc;
+                extra[base + p - 1] = make_uint2(b, k0 | (k1 << 8));
+            }
+        }
+    }
+    witem[i] = make_uint2(b, 0u | (span << 8));
+}
+
+int64_t emb_link_extra_capacity(int64_t n)
+{
+    const int64_t c = 2 * n + 4096;
+    return c < (1 << 20) ? c : (1 << 20);
+}
+
+// Enqueue only: after emb_enq_link_prep and the finest bins; witem holds n entries.
+emb_status emb_enq_link_split(const EmbLevel &lv, const uint32_t *work, const uint32_t *work_n, const uint64_t *cand,
+                              const uint32_t *blk_off, const uint32_t *bin_off, uint2 *witem, uint2 *extra,
+                              unsigned long long *extra_n, uint32_t extra_cap, cudaStream_t s)
+{
+    EMB_CUDA_TRY(cudaMemsetAsync(extra_n, 0, sizeof(unsigned long long), s));
+    if (lv.n > 0)
+        EMB_LAUNCH((k_link_split), emb_grid(lv.n, 256), 256, 0, s)(work, work_n, cand, blk_off, bin_off, lv.n, witem,
+                                                                   extra, extra_n, extra_cap);
+    EMB_CUDA_TRY(cudaGetLastError());
+    return EMB_OK;
+}
+
 size_t emb_link_emit_smem() { return LE_WARPS * sizeof(LeWarp); }
 
 static int g_le_per_sm = 0, g_le_sms = 0;
@@ -787,7 +863,6 @@ extern "C" emb_status emb_cutlinks(emb_forest f, emb_bins b, int32_t lattice, in
     M.bin_off = b->off;
     M.bin_ent = b->ent;
     M.rec = b->m->rec;
-    M.work = f->work;
     M.work_n = f->work_n + lv.n;
     M.o_cell = d_cell;
     M.o_dir = d_dir;
@@ -795,7 +870,24 @@ extern "C" emb_status emb_cutlinks(emb_forest f, emb_bins b, int32_t lattice, in
     M.o_tri = d_tri;
     M.g = level_geom(f, f->max_level);
     M.cap = (uint32_t)(capacity < 0xFFFFFFFFll ? capacity : 0xFFFFFFFFll);
-    rc = emb_enq_link_emit(tab, f->next, 0, s, 0);
+    // parts of heavy blocks
+    const int64_t xcap = emb_link_extra_capacity(lv.n);
+    char *sp = nullptr;
+    const size_t a_w = ((size_t)(lv.n + 1) * sizeof(uint2) + 255) & ~(size_t)255;
+    EMB_CUDA_TRY(cudaMallocAsync((void **)&sp, 256 + a_w + (size_t)xcap * sizeof(uint2), s));
+    unsigned long long *xn = (unsigned long long *)sp;
+    uint2 *witem = (uint2 *)(sp + 256);
+    uint2 *extra = (uint2 *)(sp + 256 + a_w);
+    rc = emb_enq_link_split(lv, f->work, f->work_n + lv.n, f->cand, f->blk_off, b->off, witem, extra, xn, (uint32_t)xcap,
+                            s);
+    if (rc == EMB_OK) {
+        M.witem = witem;
+        M.extra = extra;
+        M.extra_n = xn;
+        M.extra_cap = (uint32_t)xcap;
+        rc = emb_enq_link_emit(tab, f->next, 0, s, 0);
+    }
+    cudaFreeAsync(sp, s);
     if (rc != EMB_OK) return rc;
     EMB_CUDA_TRY(cudaGetLastError());
     return EMB_OK;

@@ -191,8 +191,14 @@ struct LinkMesh {
     const uint32_t *bin_off;   // CSR bins
     const uint32_t *bin_ent;
     const int4 *rec;           // triangle records
-    const uint32_t *work;      // blocks with links
-    const uint32_t *work_n;    // their count (device)
+    // work items (block, first | end << 8): the cells with links of rank [first, end)
+    // among the block's; one per block with links (its count at *work_n), plus the
+    // further parts of heavy blocks in `extra` (EMB_BIG_NONE = unused entry)
+    const uint2 *witem;
+    const uint32_t *work_n;
+    const uint2 *extra;
+    const unsigned long long *extra_n;  // extra entries requested (valid: min(extra_n, extra_cap))
+    uint32_t extra_cap;
     int32_t *o_cell;
     uint8_t *o_dir;
     float *o_q;
@@ -206,6 +212,10 @@ struct LinkTable {
 };
 emb_status emb_enq_link_prep(const EmbLevel &lv, int lattice, uint64_t *cand, uint32_t *cnt, uint32_t *flag,
                              uint32_t *work_n, uint32_t *work, uint32_t *blk_off, uint64_t *tmp, cudaStream_t s);
+emb_status emb_enq_link_split(const EmbLevel &lv, const uint32_t *work, const uint32_t *work_n, const uint64_t *cand,
+                              const uint32_t *blk_off, const uint32_t *bin_off, uint2 *witem, uint2 *extra,
+                              unsigned long long *extra_n, uint32_t extra_cap, cudaStream_t s);
+int64_t emb_link_extra_capacity(int64_t n);
 emb_status emb_enq_link_emit(const LinkTable &tab, unsigned int *next, int ctas_per_sm, cudaStream_t s,
                              int64_t items);
 emb_status emb_link_emit_init();
