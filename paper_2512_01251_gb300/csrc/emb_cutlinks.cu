@@ -189,6 +189,22 @@ __device__ __forceinline__ int select64(unsigned long long m, int r)
     return pos;
 }
 
+// 32 x 32 bit-matrix transpose across a warp: lane r holds row r (bit c = entry
+// (r, c)); lane c receives column c (bit r = entry (r, c)).  Five stages, each
+// swapping the off-diagonal sub-blocks of the current size between lane pairs.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane)
+{
+    const uint32_t mk[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const int j = 16 >> k;
+        const uint32_t m = mk[k];
+        const uint32_t y = __shfl_xor_sync(0xffffffffu, x, j);
+        x = (lane & j) ? ((x & ~m) | ((y & ~m) >> j)) : ((x & m) | ((y & m) << j));
+    }
+    return x;
+}
+
 // Bits [lo, hi] of a 64-bit word (0 <= lo <= hi <= 63).
 __device__ __forceinline__ unsigned long long bit_range(int lo, int hi)
 {
@@ -382,18 +398,14 @@ __global__ void __launch_bounds__(LE_WARPS * 32, LE_MINB) k_link_emit(const __gr
         if (E.x == EMB_BIG_NONE) continue;
         const int64_t b = E.x;
         const uint32_t base = M.blk_off[b];
-        // candidate directions of cells lane and 32 + lane from the block's direction words
+        // candidate directions of cells lane and 32 + lane: lane d < 26 holds direction
+        // word d + 1; a 32 x 32 bit transpose of the low and of the high halves gives
+        // each lane the column of its two cells
         const uint64_t wd = lane < 26 ? M.cand[b * 26 + lane] : 0ull;
-        uint32_t c0 = 0, c1 = 0;
-        unsigned long long bmask = 0;
-#pragma unroll
-        for (int d = 0; d < 26; ++d) {
-            const uint64_t wdd = ((unsigned long long)__shfl_sync(0xffffffffu, (unsigned)(wd >> 32), d) << 32) |
-                                 (unsigned long long)__shfl_sync(0xffffffffu, (unsigned)wd, d);
-            bmask |= wdd;
-            c0 |= (uint32_t)((wdd >> lane) & 1ull) << (d + 1);
-            c1 |= (uint32_t)((wdd >> (32 + lane)) & 1ull) << (d + 1);
-        }
+        const uint32_t c0 = warp_transpose32((uint32_t)wd, lane) << 1;
+        const uint32_t c1 = warp_transpose32((uint32_t)(wd >> 32), lane) << 1;
+        const unsigned long long bmask =
+            ((unsigned long long)__ballot_sync(0xffffffffu, c1 != 0) << 32) | __ballot_sync(0xffffffffu, c0 != 0);
         const int nbc = __popcll(bmask);
         // exclusive link offsets of cells lane and 32 + lane, in cell order
         uint32_t k0 = __popc(c0), k1 = __popc(c1), i0 = k0, i1 = k1;
