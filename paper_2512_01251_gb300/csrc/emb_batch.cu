@@ -301,6 +301,15 @@ extern "C" emb_status emb_batch_create(const emb_mesh *meshes, const int32_t *le
 }
 
 // The replay: fork to the worker streams, one pipeline per mesh, join, one link launch.
+// Planned work of mesh B in rough units: triangle passes per level, bin entries,
+// blocks and links (used only to order and place the meshes).
+static double plan_cost(const BMesh &B)
+{
+    double c = (double)B.m->T * (B.Lf + 1) + 4.0 * (double)B.pairs + 4.0 * (double)B.links;
+    for (int L = 0; L <= B.Lf; ++L) c += 8.0 * (double)B.L[L].lv.n;
+    return c;
+}
+
 // The link-kernel view of mesh B's finest level.
 static LinkMesh link_mesh(BMesh &B)
 {
@@ -331,23 +340,28 @@ static emb_status batch_enqueue(emb_batch b, cudaStream_t s)
     const int K = b->nstreams < 1 ? 1 : (b->nstreams > BATCH_MAX_STREAMS ? BATCH_MAX_STREAMS : b->nstreams);
     EMB_CUDA_TRY(cudaEventRecord(b->ev_fork, s));
     for (int i = 0; i < K; ++i) EMB_CUDA_TRY(cudaStreamWaitEvent(b->st[i], b->ev_fork, 0));
-    // largest meshes first, spread over the streams
+    // meshes by decreasing planned work, each to the stream with the least work so far
     std::vector<int> order(b->m.size());
     for (size_t j = 0; j < order.size(); ++j) order[j] = (int)j;
     for (size_t a = 1; a < order.size(); ++a)
-        for (size_t c = a; c > 0 && b->m[order[c]].m->T > b->m[order[c - 1]].m->T; --c) {
+        for (size_t c = a; c > 0 && plan_cost(b->m[order[c]]) > plan_cost(b->m[order[c - 1]]); --c) {
             int t = order[c];
             order[c] = order[c - 1];
             order[c - 1] = t;
         }
+    double load[BATCH_MAX_STREAMS] = {0};
     for (size_t q = 0; q < order.size(); ++q) {
         BMesh &B = b->m[order[q]];
-        BTRY(enqueue_mesh(B, b->tri_block, b->st[q % K]));
+        int k = 0;
+        for (int i = 1; i < K; ++i)
+            if (load[i] < load[k]) k = i;
+        load[k] += plan_cost(B);
+        BTRY(enqueue_mesh(B, b->tri_block, b->st[k]));
         if (b->per_mesh_links) {
             LinkTable one;
             one.n = 1;
             one.m[0] = link_mesh(B);
-            BTRY(emb_enq_link_emit(one, B.next, b->link_ctas, b->st[q % K], B.nwork > 0 ? B.nwork : 1));
+            BTRY(emb_enq_link_emit(one, B.next, b->link_ctas, b->st[k], B.nwork > 0 ? B.nwork : 1));
         }
     }
     for (int i = 0; i < K; ++i) {

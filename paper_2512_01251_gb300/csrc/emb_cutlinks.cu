@@ -101,8 +101,10 @@ __global__ void k_link_cand(const uint64_t *__restrict__ mask, const int32_t *__
 // lines of all 13 direction pairs (c and -c share the line) at once, and only a
 // hit line checks the ends of its candidate segments against the plane (D
 // against D - h n.c).  When every vertex lies within 2^14 of P the moments fit
-// 32-bit integers and D fits 64 bits; otherwise, and for a zero Pluecker value,
-// a 128-bit path decides.  Crossings, with q already rounded, are appended to a
+// 32-bit integers and D fits 64 bits; otherwise the moments are formed in 64 bits
+// by widening products and D in 128 bits (coarse frames, where h itself is 2^14 or
+// more, take this path).  A zero Pluecker value sends its direction through the
+// exact per-direction test with the full tie-break.  Crossings, with q already rounded, are appended to a
 // per-cell bucket; afterwards the owner lane of each cell keeps, per direction,
 // the nearest one (exact rational comparison when a link crosses more than one
 // face) and writes the links at the cell's offset in the table, which the
@@ -577,7 +579,59 @@ __global__ void __launch_bounds__(LE_WARPS * 32, LE_MINB) k_link_emit(const __gr
                             if (kk < LE_BCAP) S.hit[kk][slot] = make_uint2(local | ((uint32_t)d << 24), __float_as_uint(q));
                         }
                     } else {
-                        uint32_t mm = ccm;
+                        // coordinates are below 2^25, so offsets fit 32 bits: moments (below 2^51)
+                        // and their signed sums in 64 bits from widening products, D in 128 bits
+                        const int ax = (int)(T.ax - px), ay = (int)(T.ay - py), az = (int)(T.az - pz);
+                        const int bx = (int)(T.bx - px), by = (int)(T.by - py), bz = (int)(T.bz - pz);
+                        const int qx = (int)(T.cx - px), qy = (int)(T.cy - py), qz = (int)(T.cz - pz);
+                        const long long m1x = (long long)ay * bz - (long long)az * by,
+                                        m1y = (long long)az * bx - (long long)ax * bz,
+                                        m1z = (long long)ax * by - (long long)ay * bx;
+                        const long long m2x = (long long)by * qz - (long long)bz * qy,
+                                        m2y = (long long)bz * qx - (long long)bx * qz,
+                                        m2z = (long long)bx * qy - (long long)by * qx;
+                        const long long m3x = (long long)qy * az - (long long)qz * ay,
+                                        m3y = (long long)qz * ax - (long long)qx * az,
+                                        m3z = (long long)qx * ay - (long long)qy * ax;
+                        const long long nx = m1x + m2x + m3x, ny = m1y + m2y + m3y, nz = m1z + m2z + m3z;
+                        uint32_t line = 0, degen = 0;
+#pragma unroll
+                        for (int r = 0; r < 13; ++r) {
+                            const int d = 2 * r + 1;
+                            if (!(ccm & (3u << d))) continue;
+                            int cx, cy, cz;
+                            emb_dir(d, cx, cy, cz);
+                            const long long NC = cx * nx + cy * ny + cz * nz;
+                            const long long V1 = cx * m1x + cy * m1y + cz * m1z;
+                            const long long V2 = cx * m2x + cy * m2y + cz * m2z;
+                            const long long V3 = cx * m3x + cy * m3y + cz * m3z;
+                            if (NC == 0) continue;
+                            if (V1 == 0 || V2 == 0 || V3 == 0) {
+                                degen |= 1u << d;
+                                continue;
+                            }
+                            if (((V1 ^ NC) | (V2 ^ NC) | (V3 ^ NC)) >= 0) line |= 1u << d;
+                        }
+                        uint32_t mm = (line | (line << 1)) & ccm;
+                        if (mm) {
+                            const i128 D = mul128(nx, ax) + mul128(ny, ay) + mul128(nz, az);
+                            while (mm) {
+                                const int d = __ffs(mm) - 1;
+                                mm &= mm - 1;
+                                int cx, cy, cz;
+                                emb_dir(d, cx, cy, cz);
+                                const long long nc = cx * nx + cy * ny + cz * nz;
+                                const int sn = nc > 0 ? 1 : -1;
+                                if (side_sign(D, nx, ny, nz) != sn) continue;                  // t <= 0
+                                if (side_sign(D - mul128(h, nc), nx, ny, nz) != -sn) continue;  // t >= 1
+                                const i128 N = sn > 0 ? D : -D;
+                                const long long Mq = nc > 0 ? nc : -nc;
+                                const float q = __fdiv_rn(i128_to_float(N), (float)Mq * (float)h);
+                                const int kk = atomicAdd(&S.hcnt[slot], 1);
+                                if (kk < LE_BCAP) S.hit[kk][slot] = make_uint2(local | ((uint32_t)d << 24), __float_as_uint(q));
+                            }
+                        }
+                        mm = (degen | (degen << 1)) & ccm;
                         while (mm) {
                             const int d = __ffs(mm) - 1;
                             mm &= mm - 1;
