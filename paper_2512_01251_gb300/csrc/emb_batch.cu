@@ -57,6 +57,7 @@ struct BMesh {
     uint2 *extra = nullptr;                         // extra parts of split blocks
     unsigned long long *extra_n = nullptr;
     EmbBigQ bq = {nullptr, nullptr, 0};             // chunk queue of large triangles
+    unsigned long long *fbits = nullptr;            // dense flagged bits (largest refined level)
     int32_t *o_cell = nullptr, *o_tri = nullptr;
     uint8_t *o_dir = nullptr;
     float *o_q = nullptr;
@@ -166,6 +167,12 @@ static emb_status alloc_mesh(BMesh &B)
         BTRY(balloc(B, &B.L[L].flist, T + 1));
         if (L < B.Lf) BTRY(balloc(B, &B.L[L].flags, lv.n + 1));
     }
+    int64_t fw = 1;
+    for (int L = 0; L < B.Lf; ++L) {
+        const int64_t nw = emb_bitmap_words(B.L[L].lv.nb_axis);
+        fw = nw > fw ? nw : fw;
+    }
+    BTRY(balloc(B, &B.fbits, fw));
     EmbLevel &fin = B.L[B.Lf].lv;
     BTRY(balloc(B, &fin.nbr, fin.n * 26 + 1));
     BTRY(balloc(B, &B.flag, T + 1));
@@ -214,7 +221,7 @@ static emb_status enqueue_mesh(BMesh &B, int tri_block, cudaStream_t s)
         if (L < B.Lf) {
             const long long dil = emb_refine_dilation(&B.geo, L, B.band);
             if (dil < 0) return EMB_ERR_RANGE;
-            BTRY(emb_enq_refine(rec, T, g, dil, lv, BL.flags, B.bq, s));
+            BTRY(emb_enq_refine(rec, T, g, dil, lv, BL.flags, B.fbits, B.bq, s));
             BTRY(emb_enq_flag_ranks(lv, BL.flags, B.cnt, B.rank, B.tmp, s));
             BTRY(emb_expect_u32(B.rank + lv.n, (uint64_t)BL.F, s));
             EmbLevel &C = B.L[L + 1].lv;

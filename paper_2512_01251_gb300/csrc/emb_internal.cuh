@@ -178,7 +178,7 @@ emb_status emb_enq_voxelize(const int4 *rec, const uint32_t *flist, int64_t nf, 
                             unsigned long long *s_acc, unsigned int *p_acc, const EmbBigQ &Q, int block,
                             cudaStream_t s);
 emb_status emb_enq_refine(const int4 *rec, int64_t T, LevelGeom g, long long dil, const EmbLevel &lv, uint8_t *flags,
-                          const EmbBigQ &Q, cudaStream_t s);
+                          unsigned long long *fbits, const EmbBigQ &Q, cudaStream_t s);
 long long emb_refine_dilation(const emb_forest_s *f, int L, int band);
 
 // Cut links: per-mesh arguments of the persistent link kernel, passed by value as

@@ -34,24 +34,42 @@ __device__ __forceinline__ unsigned long long refine_items(const long long b0[3]
            (unsigned long long)(b1[2] - b0[2] + 1);
 }
 
+// Flagged blocks of the level as one bit per dense position (bx + nb (by + nb bz)),
+// when the level is small enough to have one: the common "already flagged" case
+// then costs one cached load instead of a block lookup and a flag load.
+struct FlagBits {
+    unsigned long long *w;  // null: no dense bits, test the flag bytes
+    long long nb;
+    __device__ __forceinline__ bool test(long long bx, long long by, long long bz, unsigned long long &pos) const
+    {
+        pos = (unsigned long long)((bz * nb + by) * nb + bx);
+        return (((volatile unsigned long long *)w)[pos >> 6] >> (pos & 63)) & 1ull;
+    }
+    __device__ __forceinline__ void set(unsigned long long pos) const { atomicOr(w + (pos >> 6), 1ull << (pos & 63)); }
+};
+
 // Flag block (bx, by, bz) if it exists, is not flagged yet and the triangle meets its dilated box.
 __device__ __forceinline__ void refine_block(const int4 &A, const int4 &B, const int4 &C, long long bx, long long by,
                                              long long bz, const LevelGeom &g, long long dil, const EmbLookup &lk,
-                                             uint8_t *__restrict__ flags)
+                                             uint8_t *__restrict__ flags, const FlagBits &fb)
 {
+    unsigned long long pos = 0;
+    if (fb.w && fb.test(bx, by, bz, pos)) return;
     const int32_t id = emb_lookup(lk, bx, by, bz);
     if (id < 0) return;
     if (*((volatile uint8_t *)flags + id)) return;
     const long long lx = bx * g.W - dil, ly = by * g.W - dil, lz = bz * g.W - dil;
     const long long hx = lx + g.W + 2 * dil, hy = ly + g.W + 2 * dil, hz = lz + g.W + 2 * dil;
     if (emb_point_in_box(A, lx, ly, lz, hx, hy, hz) || emb_point_in_box(B, lx, ly, lz, hx, hy, hz) ||
-        emb_point_in_box(C, lx, ly, lz, hx, hy, hz) || emb_tri_box(A, B, C, lx, ly, lz, hx, hy, hz))
+        emb_point_in_box(C, lx, ly, lz, hx, hy, hz) || emb_tri_box(A, B, C, lx, ly, lz, hx, hy, hz)) {
         flags[id] = 1;
+        if (fb.w) fb.set(pos);
+    }
 }
 
-__global__ void __launch_bounds__(EMB_WU_WARPS * 32) k_refine(const int4 *__restrict__ rec, int64_t T, LevelGeom g,
+__global__ void __launch_bounds__(EMB_WU_WARPS * 32, 4) k_refine(const int4 *__restrict__ rec, int64_t T, LevelGeom g,
                                                               long long dil, EmbLookup lk, uint8_t *__restrict__ flags,
-                                                              EmbBigQ Q)
+                                                              FlagBits fb, EmbBigQ Q)
 {
     __shared__ WuTri tiles[EMB_WU_WARPS];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -89,6 +107,8 @@ __global__ void __launch_bounds__(EMB_WU_WARPS * 32) k_refine(const int4 *__rest
         for (unsigned c = lane; c < (unsigned)total; c += 32) {
             const unsigned cz = c / uxy, cr = c - cz * uxy, cy = cr / ux;
             const long long bx = u0[0] + (long long)(cr - cy * ux), by = u0[1] + (long long)cy, bz = u0[2] + (long long)cz;
+            unsigned long long pos = 0;
+            if (fb.w && fb.test(bx, by, bz, pos)) continue;
             const int32_t id = emb_lookup(lk, bx, by, bz);
             if (id < 0 || flags[id]) continue;
             const long long lx = bx * g.W - dil, ly = by * g.W - dil, lz = bz * g.W - dil;
@@ -96,6 +116,7 @@ __global__ void __launch_bounds__(EMB_WU_WARPS * 32) k_refine(const int4 *__rest
             for (int j = 0; j < 32; ++j) {
                 if (wu_overlap(S, j, lx, ly, lz, hx, hy, hz)) {
                     flags[id] = 1;
+                    if (fb.w) fb.set(pos);
                     break;
                 }
             }
@@ -107,12 +128,13 @@ __global__ void __launch_bounds__(EMB_WU_WARPS * 32) k_refine(const int4 *__rest
     if (own > EMB_BIG_ITEMS && emb_bigq_push(Q, (uint32_t)t, own)) return;
     for (long long bz = b0[2]; bz <= b1[2]; ++bz)
         for (long long by = b0[1]; by <= b1[1]; ++by)
-            for (long long bx = b0[0]; bx <= b1[0]; ++bx) refine_block(A, B, C, bx, by, bz, g, dil, lk, flags);
+            for (long long bx = b0[0]; bx <= b1[0]; ++bx) refine_block(A, B, C, bx, by, bz, g, dil, lk, flags, fb);
 }
 
 // The queued chunks of large triangles, one warp per chunk (candidates x fastest).
 __global__ void __launch_bounds__(EMB_BIG_BLOCK) k_refine_big(const int4 *__restrict__ rec, LevelGeom g, long long dil,
-                                                              EmbLookup lk, uint8_t *__restrict__ flags, EmbBigQ Q)
+                                                              EmbLookup lk, uint8_t *__restrict__ flags, FlagBits fb,
+                                                              EmbBigQ Q)
 {
     const int lane = threadIdx.x & 31;
     const unsigned long long nq = emb_bigq_count(Q);
@@ -133,7 +155,7 @@ __global__ void __launch_bounds__(EMB_BIG_BLOCK) k_refine_big(const int4 *__rest
         long long z = (long long)((first / (unsigned long long)nx) / (unsigned long long)ny);
         const long long dx = 32 % nx, dy = (32 / nx) % ny, dz = (32 / nx) / ny;
         for (unsigned long long it = first; it < i1; it += 32) {
-            refine_block(A, B, C, b0[0] + x, b0[1] + y, b0[2] + z, g, dil, lk, flags);
+            refine_block(A, B, C, b0[0] + x, b0[1] + y, b0[2] + z, g, dil, lk, flags, fb);
             x += dx;
             y += dy;
             z += dz;
@@ -166,14 +188,20 @@ long long emb_refine_dilation(const emb_forest_s *f, int L, int band)
 
 // Enqueue only: flags (lv.n bytes) are cleared and set.
 emb_status emb_enq_refine(const int4 *rec, int64_t T, LevelGeom g, long long dil, const EmbLevel &lv, uint8_t *flags,
-                          const EmbBigQ &Q, cudaStream_t s)
+                          unsigned long long *fbits, const EmbBigQ &Q, cudaStream_t s)
 {
     if (lv.n == 0) return EMB_OK;
     EMB_CUDA_TRY(cudaMemsetAsync(flags, 0, lv.n, s));
     const EmbLookup lk = emb_lookup_of(lv);
+    FlagBits fb = {nullptr, g.nb};
+    const int64_t nw = emb_bitmap_words(lv.nb_axis);
+    if (fbits && nw > 0) {
+        EMB_CUDA_TRY(cudaMemsetAsync(fbits, 0, nw * sizeof(unsigned long long), s));
+        fb.w = fbits;
+    }
     if (Q.cap) EMB_CUDA_TRY(cudaMemsetAsync(Q.n, 0, sizeof(unsigned long long), s));
-    EMB_LAUNCH((k_refine), emb_grid(T, 32 * EMB_WU_WARPS), 32 * EMB_WU_WARPS, 0, s)(rec, T, g, dil, lk, flags, Q);
-    if (Q.cap) EMB_LAUNCH((k_refine_big), EMB_BIG_GRID, EMB_BIG_BLOCK, 0, s)(rec, g, dil, lk, flags, Q);
+    EMB_LAUNCH((k_refine), emb_grid(T, 32 * EMB_WU_WARPS), 32 * EMB_WU_WARPS, 0, s)(rec, T, g, dil, lk, flags, fb, Q);
+    if (Q.cap) EMB_LAUNCH((k_refine_big), EMB_BIG_GRID, EMB_BIG_BLOCK, 0, s)(rec, g, dil, lk, flags, fb, Q);
     EMB_CUDA_TRY(cudaGetLastError());
     return EMB_OK;
 }
@@ -192,7 +220,11 @@ extern "C" emb_status emb_refine_flags(emb_forest f, emb_bins b, int32_t level, 
     EmbBigQ Q;
     emb_status rc = emb_bigq_alloc(Q, b->m->T, s);
     if (rc != EMB_OK) return rc;
-    rc = emb_enq_refine(b->m->rec, b->m->T, level_geom(f, level), dil, lv, d_flags, Q, s);
+    unsigned long long *fbits = nullptr;
+    const int64_t nw = emb_bitmap_words(lv.nb_axis);
+    if (nw > 0 && cudaMallocAsync(&fbits, nw * sizeof(unsigned long long), s) != cudaSuccess) fbits = nullptr;
+    rc = emb_enq_refine(b->m->rec, b->m->T, level_geom(f, level), dil, lv, d_flags, fbits, Q, s);
+    if (fbits) cudaFreeAsync(fbits, s);
     emb_bigq_free(Q, s);
     return rc;
 }
