@@ -50,6 +50,9 @@ struct BMesh {
     uint64_t *tmp = nullptr;                        // scan scratch
     // finest level
     uint32_t *bin_off = nullptr, *bin_ent = nullptr;
+    uint2 *list_bs = nullptr;                       // pair list of the binning pass (planned pairs)
+    uint32_t *list_tri = nullptr;
+    unsigned long long *list_n = nullptr;
     uint64_t *cand = nullptr;
     uint32_t *work_n = nullptr, *work = nullptr, *blk_off = nullptr;
     unsigned int *next = nullptr;                   // queue cursor of a per-mesh link launch
@@ -186,6 +189,9 @@ static emb_status alloc_mesh(BMesh &B)
     BTRY(balloc(B, &B.tmp, sw));
     BTRY(balloc(B, &B.bin_off, fin.n + 1));
     BTRY(balloc(B, &B.bin_ent, B.pairs + 1));
+    BTRY(balloc(B, &B.list_bs, B.pairs + 1));
+    BTRY(balloc(B, &B.list_tri, B.pairs + 1));
+    BTRY(balloc(B, &B.list_n, 1));
     BTRY(balloc(B, &B.cand, fin.n * 26 + 1));
     BTRY(balloc(B, &B.work_n, fin.n + 1));
     BTRY(balloc(B, &B.work, fin.n + 1));
@@ -217,7 +223,7 @@ static emb_status enqueue_mesh(BMesh &B, int tri_block, cudaStream_t s)
         const LevelGeom g = level_geom(&B.geo, L);
         BTRY(emb_enq_filter(rec, T, g, B.flag, B.pos, BL.flist, B.tmp, tri_block, s));
         BTRY(emb_expect_u32(B.pos + T, (uint64_t)BL.nf, s));
-        BTRY(emb_enq_voxelize(rec, BL.flist, BL.nf, g, lv, B.s_acc, B.p_acc, B.bq, tri_block, s));
+        BTRY(emb_enq_voxelize(rec, T, BL.flist, BL.nf, B.pos + T, g, lv, B.s_acc, B.p_acc, B.bq, tri_block, s));
         if (L < B.Lf) {
             const long long dil = emb_refine_dilation(&B.geo, L, B.band);
             if (dil < 0) return EMB_ERR_RANGE;
@@ -225,12 +231,14 @@ static emb_status enqueue_mesh(BMesh &B, int tri_block, cudaStream_t s)
             BTRY(emb_enq_flag_ranks(lv, BL.flags, B.cnt, B.rank, B.tmp, s));
             BTRY(emb_expect_u32(B.rank + lv.n, (uint64_t)BL.F, s));
             EmbLevel &C = B.L[L + 1].lv;
-            BTRY(emb_enq_children(lv, BL.flags, B.rank, C.key, C.n, s));
+            BTRY(emb_enq_children(lv, BL.flags, B.rank, C.key, C.n, true, s));
             BTRY(emb_enq_level_index(C, B.pc, B.tmp, s));
         } else {
-            BTRY(emb_enq_bin_count(rec, T, g, lv, B.cnt, B.bin_off, B.tmp, B.bq, s));
+            BTRY(emb_enq_bin_pairs(rec, T, g, lv, B.cnt, B.bin_off, B.list_bs, B.list_tri, B.list_n, (uint64_t)B.pairs,
+                                   B.tmp, B.bq, s));
             BTRY(emb_expect_u32(B.bin_off + lv.n, (uint64_t)B.pairs, s));
-            BTRY(emb_enq_bin_fill(rec, T, g, lv, B.cnt, B.bin_off, B.bin_ent, B.bq, s));
+            BTRY(emb_enq_bin_scatter(B.list_bs, B.list_tri, B.list_n, (uint64_t)B.pairs, B.bin_off, B.bin_ent,
+                                     (uint64_t)B.pairs, s));
             BTRY(emb_enq_neighbors(lv, s));
             BTRY(emb_enq_link_prep(lv, B.lattice, B.cand, B.cnt, B.rank, B.work_n, B.work, B.blk_off, B.tmp, s));
             BTRY(emb_expect_u32(B.work_n + lv.n, (uint64_t)B.nwork, s));
@@ -327,7 +335,9 @@ static LinkMesh link_mesh(BMesh &B)
     M.blk_off = B.blk_off;
     M.bin_off = B.bin_off;
     M.bin_ent = B.bin_ent;
+    M.ent_cap = (uint64_t)B.pairs;
     M.rec = B.m->rec;
+    M.T = (uint32_t)B.m->T;
     M.work_n = B.work_n + fin.n;
     M.witem = B.witem;
     M.extra = B.extra;

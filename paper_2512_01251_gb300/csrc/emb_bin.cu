@@ -9,8 +9,10 @@
 // existing blocks whose box, dilated by half a cell, it overlaps (exact
 // separating-axis test).  A link P -> P + h c starts at a cell centre, at least
 // h/2 inside the block, and has L-infinity length h, so it stays inside the box
-// dilated by h/2.  Pairs are counted per block with integer atomics, offsets
-// come from an exclusive scan, and a second pass fills the CSR bins.
+// dilated by h/2.  One pass over the geometry counts the pairs per block with
+// integer atomics (the count is also the pair's slot in its block) and appends
+// (block, slot, triangle) to a pair list; offsets come from an exclusive scan and
+// a scatter of the list fills the CSR bins.
 #include <stdlib.h>
 
 #include "emb_internal.cuh"
@@ -84,12 +86,25 @@ __device__ __forceinline__ unsigned long long box_items(const long long b0[3], c
            (unsigned long long)(b1[2] - b0[2] + 1);
 }
 
+// Pair list of one binning pass: entry e is (block, slot in the block) and the triangle.
+struct PairList {
+    uint2 *bs;
+    uint32_t *tri;
+    unsigned long long *n;  // entries requested (may exceed cap)
+    uint64_t cap;
+    __device__ __forceinline__ void put(unsigned long long e, uint32_t id, uint32_t slot, uint32_t t) const
+    {
+        if (e < cap) {
+            bs[e] = make_uint2(id, slot);
+            tri[e] = t;
+        }
+    }
+};
+
 // Pair (t, block (bx, by, bz)) if the block exists and t overlaps its dilated box.
-template <int MODE>
 __device__ __forceinline__ void bin_block(const int4 &A, const int4 &B, const int4 &C, uint32_t t, long long bx,
                                           long long by, long long bz, const LevelGeom &g, long long dil,
-                                          const EmbLookup &lk, uint32_t *__restrict__ cnt,
-                                          const uint32_t *__restrict__ off, uint32_t *__restrict__ ent)
+                                          const EmbLookup &lk, uint32_t *__restrict__ cnt, const PairList &PL)
 {
     const int32_t id = emb_lookup(lk, bx, by, bz);
     if (id < 0) return;
@@ -98,25 +113,18 @@ __device__ __forceinline__ void bin_block(const int4 &A, const int4 &B, const in
     if (!(emb_point_in_box(A, lx, ly, lz, hx, hy, hz) || emb_point_in_box(B, lx, ly, lz, hx, hy, hz) ||
           emb_point_in_box(C, lx, ly, lz, hx, hy, hz) || emb_tri_box(A, B, C, lx, ly, lz, hx, hy, hz)))
         return;
-    if (MODE == 0) {
-        atomicAdd(cnt + id, 1u);
-    } else {
-        const uint32_t p = atomicAdd(cnt + id, 1u);
-        ent[off[id] + p] = t;
-    }
+    const uint32_t slot = atomicAdd(cnt + id, 1u);
+    PL.put(atomicAdd(PL.n, 1ull), (uint32_t)id, slot, t);
 }
 
 // The (triangle, block) pairs of 32 consecutive triangles, visited warp-cooperatively
 // over the union of their candidate blocks (see emb_internal.cuh); a lane whose
 // triangle is left out of the union walks its own candidates, or queues them in
-// chunks when there are many.  MODE 0: count pairs per block; MODE 1: fill the CSR
-// bins.  Degenerate triangles (zero normal) are never crossed by a link and are
-// left out.
-template <int MODE>
+// chunks when there are many.  Degenerate triangles (zero normal) are never
+// crossed by a link and are left out.
 __global__ void __launch_bounds__(EMB_WU_WARPS * 32) k_bin_pairs(const int4 *__restrict__ rec, int64_t T, LevelGeom g,
                                                                  long long dil, EmbLookup lk, uint32_t *__restrict__ cnt,
-                                                                 const uint32_t *__restrict__ off,
-                                                                 uint32_t *__restrict__ ent, EmbBigQ Q)
+                                                                 PairList PL, EmbBigQ Q)
 {
     __shared__ WuTri tiles[EMB_WU_WARPS];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -149,27 +157,43 @@ __global__ void __launch_bounds__(EMB_WU_WARPS * 32) k_bin_pairs(const int4 *__r
     const unsigned long long own = valid ? box_items(b0, b1) : 0;
     const unsigned own_sum = __reduce_add_sync(0xffffffffu, (unsigned)min(own, 1ull << 20));
     if (total <= EMB_WU_MAX && 4 * total <= (long long)own_sum) {
-        // total <= EMB_WU_MAX: decode the union index in 32-bit arithmetic
+        // total <= EMB_WU_MAX: decode the union index in 32-bit arithmetic; the loop
+        // bound is uniform so that the list appends can be aggregated over the warp
         const unsigned ux = (unsigned)nx, uxy = (unsigned)(nx * ny);
-        for (unsigned c = lane; c < (unsigned)total; c += 32) {
-            const unsigned cz = c / uxy, cr = c - cz * uxy, cy = cr / ux;
-            const long long bx = u0[0] + (long long)(cr - cy * ux), by = u0[1] + (long long)cy, bz = u0[2] + (long long)cz;
-            const int32_t id = emb_lookup(lk, bx, by, bz);
-            if (id < 0) continue;
-            const long long lx = bx * g.W - dil, ly = by * g.W - dil, lz = bz * g.W - dil;
-            const long long hx = lx + g.W + 2 * dil, hy = ly + g.W + 2 * dil, hz = lz + g.W + 2 * dil;
+        for (unsigned c0 = 0; c0 < (unsigned)total; c0 += 32) {
+            const unsigned c = c0 + lane;
             uint32_t hits = 0;
-            for (int j = 0; j < 32; ++j)
-                if (wu_overlap(S, j, lx, ly, lz, hx, hy, hz)) hits |= 1u << j;
-            if (!hits) continue;
-            if (MODE == 0) {
-                atomicAdd(cnt + id, (uint32_t)__popc(hits));
-            } else {
-                uint32_t p = off[id] + atomicAdd(cnt + id, (uint32_t)__popc(hits));
+            int32_t id = -1;
+            if (c < (unsigned)total) {
+                const unsigned cz = c / uxy, cr = c - cz * uxy, cy = cr / ux;
+                const long long bx = u0[0] + (long long)(cr - cy * ux), by = u0[1] + (long long)cy,
+                                bz = u0[2] + (long long)cz;
+                id = emb_lookup(lk, bx, by, bz);
+                if (id >= 0) {
+                    const long long lx = bx * g.W - dil, ly = by * g.W - dil, lz = bz * g.W - dil;
+                    const long long hx = lx + g.W + 2 * dil, hy = ly + g.W + 2 * dil, hz = lz + g.W + 2 * dil;
+                    for (int j = 0; j < 32; ++j)
+                        if (wu_overlap(S, j, lx, ly, lz, hx, hy, hz)) hits |= 1u << j;
+                }
+            }
+            const uint32_t k = (uint32_t)__popc(hits);
+            uint32_t incl = k;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const uint32_t wtot = __shfl_sync(0xffffffffu, incl, 31);
+            if (wtot == 0) continue;
+            unsigned long long base = 0;
+            if (lane == 31) base = atomicAdd(PL.n, (unsigned long long)wtot);
+            base = __shfl_sync(0xffffffffu, base, 31) + (incl - k);
+            if (k) {
+                uint32_t slot = atomicAdd(cnt + id, k);
                 while (hits) {
                     const int j = __ffs(hits) - 1;
                     hits &= hits - 1;
-                    ent[p++] = (uint32_t)(t0 + j);
+                    PL.put(base++, (uint32_t)id, slot++, (uint32_t)(t0 + j));
                 }
             }
         }
@@ -180,8 +204,7 @@ __global__ void __launch_bounds__(EMB_WU_WARPS * 32) k_bin_pairs(const int4 *__r
     if (own > EMB_BIG_ITEMS && emb_bigq_push(Q, (uint32_t)t, own)) return;
     for (long long bz = b0[2]; bz <= b1[2]; ++bz)
         for (long long by = b0[1]; by <= b1[1]; ++by)
-            for (long long bx = b0[0]; bx <= b1[0]; ++bx)
-                bin_block<MODE>(A, B, C, (uint32_t)t, bx, by, bz, g, dil, lk, cnt, off, ent);
+            for (long long bx = b0[0]; bx <= b1[0]; ++bx) bin_block(A, B, C, (uint32_t)t, bx, by, bz, g, dil, lk, cnt, PL);
 }
 
 // Decomposition of candidate index i of the box [b0, b1] (x fastest) and its step by 32.
@@ -216,11 +239,9 @@ struct BoxWalk {
 };
 
 // The queued chunks of large triangles, one warp per chunk.
-template <int MODE>
 __global__ void __launch_bounds__(EMB_BIG_BLOCK) k_bin_pairs_big(const int4 *__restrict__ rec, LevelGeom g, long long dil,
-                                                                 EmbLookup lk, uint32_t *__restrict__ cnt,
-                                                                 const uint32_t *__restrict__ off,
-                                                                 uint32_t *__restrict__ ent, EmbBigQ Q)
+                                                                 EmbLookup lk, uint32_t *__restrict__ cnt, PairList PL,
+                                                                 EmbBigQ Q)
 {
     const int lane = threadIdx.x & 31;
     const unsigned long long nq = emb_bigq_count(Q);
@@ -237,7 +258,7 @@ __global__ void __launch_bounds__(EMB_BIG_BLOCK) k_bin_pairs_big(const int4 *__r
         BoxWalk bw;
         bw.start(b0, b1, i0 + lane);
         for (unsigned long long it = i0 + lane; it < i1; it += 32, bw.step())
-            bin_block<MODE>(A, B, C, E.x, b0[0] + bw.x, b0[1] + bw.y, b0[2] + bw.z, g, dil, lk, cnt, off, ent);
+            bin_block(A, B, C, E.x, b0[0] + bw.x, b0[1] + bw.y, b0[2] + bw.z, g, dil, lk, cnt, PL);
     }
 }
 
@@ -254,31 +275,47 @@ emb_status emb_enq_filter(const int4 *rec, int64_t T, LevelGeom g, uint32_t *fla
     return EMB_OK;
 }
 
-// Steps 2-9 at the finest level, counting half (enqueue only): cnt holds n + 1
-// uint32, off receives n + 1 offsets (pairs total at off[n]); tmp: scan scratch for n.
-emb_status emb_enq_bin_count(const int4 *rec, int64_t T, LevelGeom g, const EmbLevel &lv, uint32_t *cnt, uint32_t *off,
+// The pair list into the CSR bins: entry e goes to off[block] + slot (below ent_cap).
+__global__ void k_bin_scatter(const uint2 *__restrict__ bs, const uint32_t *__restrict__ tri,
+                              const unsigned long long *__restrict__ n, uint64_t cap, const uint32_t *__restrict__ off,
+                              uint32_t *__restrict__ ent, uint64_t ent_cap)
+{
+    const unsigned long long m = *n < cap ? *n : cap;
+    for (unsigned long long e = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint2 v = bs[e];
+        const uint64_t p = (uint64_t)off[v.x] + v.y;
+        if (p < ent_cap) ent[p] = tri[e];
+    }
+}
+
+// Steps 2-9 at the finest level, geometry half (enqueue only): cnt holds n + 1 uint32
+// and receives the pairs per block, off their n + 1 offsets (total at off[n]); the
+// list holds list_cap entries (list_n counts the requests); tmp: scan scratch for n.
+emb_status emb_enq_bin_pairs(const int4 *rec, int64_t T, LevelGeom g, const EmbLevel &lv, uint32_t *cnt, uint32_t *off,
+                             uint2 *list_bs, uint32_t *list_tri, unsigned long long *list_n, uint64_t list_cap,
                              uint64_t *tmp, const EmbBigQ &Q, cudaStream_t s)
 {
     EMB_CUDA_TRY(cudaMemsetAsync(cnt, 0, (lv.n + 1) * sizeof(uint32_t), s));
+    EMB_CUDA_TRY(cudaMemsetAsync(list_n, 0, sizeof(unsigned long long), s));
     const EmbLookup lk = emb_lookup_of(lv);
+    const PairList PL = {list_bs, list_tri, list_n, list_cap};
     if (Q.cap) EMB_CUDA_TRY(cudaMemsetAsync(Q.n, 0, sizeof(unsigned long long), s));
-    EMB_LAUNCH((k_bin_pairs<0>), emb_grid(T, 32 * EMB_WU_WARPS), 32 * EMB_WU_WARPS, 0, s)(rec, T, g, g.half, lk, cnt,
-                                                                                          nullptr, nullptr, Q);
-    if (Q.cap)
-        EMB_LAUNCH((k_bin_pairs_big<0>), EMB_BIG_GRID, EMB_BIG_BLOCK, 0, s)(rec, g, g.half, lk, cnt, nullptr, nullptr, Q);
+    if (T > 0)
+        EMB_LAUNCH((k_bin_pairs), emb_grid(T, 32 * EMB_WU_WARPS), 32 * EMB_WU_WARPS, 0, s)(rec, T, g, g.half, lk, cnt, PL,
+                                                                                           Q);
+    if (Q.cap) EMB_LAUNCH((k_bin_pairs_big), EMB_BIG_GRID, EMB_BIG_BLOCK, 0, s)(rec, g, g.half, lk, cnt, PL, Q);
     return emb_scan_into(cnt, off, lv.n, tmp, s);
 }
 
-// Filling half: ent holds off[n] entries; cnt is reused as the per-block cursor.
-emb_status emb_enq_bin_fill(const int4 *rec, int64_t T, LevelGeom g, const EmbLevel &lv, uint32_t *cnt,
-                            const uint32_t *off, uint32_t *ent, const EmbBigQ &Q, cudaStream_t s)
+// Scatter half: ent holds ent_cap entries.
+emb_status emb_enq_bin_scatter(const uint2 *list_bs, const uint32_t *list_tri, const unsigned long long *list_n,
+                               uint64_t list_cap, const uint32_t *off, uint32_t *ent, uint64_t ent_cap, cudaStream_t s)
 {
-    EMB_CUDA_TRY(cudaMemsetAsync(cnt, 0, (lv.n + 1) * sizeof(uint32_t), s));
-    const EmbLookup lk = emb_lookup_of(lv);
-    if (Q.cap) EMB_CUDA_TRY(cudaMemsetAsync(Q.n, 0, sizeof(unsigned long long), s));
-    EMB_LAUNCH((k_bin_pairs<1>), emb_grid(T, 32 * EMB_WU_WARPS), 32 * EMB_WU_WARPS, 0, s)(rec, T, g, g.half, lk, cnt,
-                                                                                          off, ent, Q);
-    if (Q.cap) EMB_LAUNCH((k_bin_pairs_big<1>), EMB_BIG_GRID, EMB_BIG_BLOCK, 0, s)(rec, g, g.half, lk, cnt, off, ent, Q);
+    int64_t grid = (int64_t)((list_cap + 255) / 256);
+    if (grid > 152 * 16) grid = 152 * 16;
+    if (grid < 1) grid = 1;
+    EMB_LAUNCH((k_bin_scatter), (int)grid, 256, 0, s)(list_bs, list_tri, list_n, list_cap, off, ent, ent_cap);
     EMB_CUDA_TRY(cudaGetLastError());
     return EMB_OK;
 }
@@ -317,22 +354,46 @@ extern "C" emb_status emb_bin(emb_mesh m, emb_forest f, int32_t level, int32_t l
         rc = EMB_ERR_CUDA;
     // steps 2-9 at the finest level: CSR bins of link-relevant triangles per block
     const bool finest = level == f->max_level && lv.n > 0;
+    uint64_t lcap = 0;
+    unsigned long long lreq = 0;
+    char *list = nullptr;
+    auto list_alloc = [&](uint64_t cap) -> emb_status {
+        if (list) cudaFreeAsync(list, s);
+        list = nullptr;
+        lcap = cap;
+        const size_t a = ((size_t)cap * sizeof(uint2) + 255) & ~(size_t)255;
+        if (cudaMallocAsync((void **)&list, 256 + a + (size_t)cap * sizeof(uint32_t), s) != cudaSuccess) return EMB_ERR_CUDA;
+        return EMB_OK;
+    };
+    auto lp_n = [&]() { return (unsigned long long *)list; };
+    auto lp_bs = [&]() { return (uint2 *)(list + 256); };
+    auto lp_tri = [&]() { return (uint32_t *)(list + 256 + (((size_t)lcap * sizeof(uint2) + 255) & ~(size_t)255)); };
     if (rc == EMB_OK && finest) {
         if (cudaMallocAsync(&cnt, (lv.n + 1) * sizeof(uint32_t), s) != cudaSuccess ||
             cudaMalloc(&b->off, (lv.n + 1) * sizeof(uint32_t)) != cudaSuccess)
             rc = EMB_ERR_CUDA;
         if (rc == EMB_OK) rc = emb_bigq_alloc(Q, m->T, s);
-        if (rc == EMB_OK) rc = emb_enq_bin_count(m->rec, m->T, g, lv, cnt, b->off, tmp, Q, s);
-        if (rc == EMB_OK && cudaMemcpyAsync(&np, b->off + lv.n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        if (rc == EMB_OK) rc = list_alloc((uint64_t)4 * m->T + (1 << 20));
+        if (rc == EMB_OK)
+            rc = emb_enq_bin_pairs(m->rec, m->T, g, lv, cnt, b->off, lp_bs(), lp_tri(), lp_n(), lcap, tmp, Q, s);
+        if (rc == EMB_OK && (cudaMemcpyAsync(&np, b->off + lv.n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                             cudaMemcpyAsync(&lreq, lp_n(), sizeof(lreq), cudaMemcpyDeviceToHost, s) != cudaSuccess))
             rc = EMB_ERR_CUDA;
     }
     if (rc == EMB_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = EMB_ERR_CUDA;
+    if (rc == EMB_OK && finest && lreq > lcap) {
+        // the list was too small: once more with its exact size
+        rc = list_alloc(lreq);
+        if (rc == EMB_OK)
+            rc = emb_enq_bin_pairs(m->rec, m->T, g, lv, cnt, b->off, lp_bs(), lp_tri(), lp_n(), lcap, tmp, Q, s);
+    }
     b->nf = nf;
     if (rc == EMB_OK && finest) {
         b->npairs = np;
         if (cudaMalloc(&b->ent, ((size_t)np + 1) * sizeof(uint32_t)) != cudaSuccess) rc = EMB_ERR_CUDA;
-        if (rc == EMB_OK) rc = emb_enq_bin_fill(m->rec, m->T, g, lv, cnt, b->off, b->ent, Q, s);
+        if (rc == EMB_OK) rc = emb_enq_bin_scatter(lp_bs(), lp_tri(), lp_n(), lcap, b->off, b->ent, (uint64_t)np, s);
     }
+    if (list) cudaFreeAsync(list, s);
     emb_bigq_free(Q, s);
     if (flag) cudaFreeAsync(flag, s);
     if (pos) cudaFreeAsync(pos, s);

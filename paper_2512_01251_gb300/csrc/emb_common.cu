@@ -257,6 +257,7 @@ __global__ void k_bits_set(const uint64_t *__restrict__ key, int64_t n, int64_t 
     uint64_t k = key[i];
     int64_t bx = (int64_t)(k & EMB_KEY_MASK), by = (int64_t)((k >> EMB_KEY_BITS) & EMB_KEY_MASK),
             bz = (int64_t)(k >> (2 * EMB_KEY_BITS));
+    if (bx >= nb || by >= nb || bz >= nb) return;  // only a replay whose counts left its plan gets here
     int64_t lin = (bz * nb + by) * nb + bx;
     atomicOr(bits + (lin >> 6), 1ull << (lin & 63));
 }

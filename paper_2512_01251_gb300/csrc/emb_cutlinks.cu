@@ -255,12 +255,13 @@ __device__ __forceinline__ bool seg_cross(int cx, int cy, int cz, long long h, l
 // Nearest crossed triangle of every candidate direction in `cm` for cell centre P,
 // by a plain exact scan of the whole bin (used for cells whose bucket overflowed).
 __device__ __noinline__ void scan_cell_slow(const uint32_t *__restrict__ bin_ent, uint32_t e0, uint32_t e1,
-                                            const int4 *__restrict__ rec, long long px, long long py, long long pz,
-                                            long long h, uint32_t cm, int *bestT)
+                                            const int4 *__restrict__ rec, uint32_t T, long long px, long long py,
+                                            long long pz, long long h, uint32_t cm, int *bestT)
 {
     for (int d = 0; d < 27; ++d) bestT[d] = -1;
     for (uint32_t e = e0; e < e1; ++e) {
         const int id = (int)bin_ent[e];
+        if ((uint32_t)id >= T) continue;
         const int4 A = rec[3 * (int64_t)id], B = rec[3 * (int64_t)id + 1], C = rec[3 * (int64_t)id + 2];
         const long long ax = A.x - px, ay = A.y - py, az = A.z - pz;
         const long long bx = B.x - px, by = B.y - py, bz = B.z - pz;
@@ -300,7 +301,7 @@ __device__ __noinline__ void emit_cell_slow(const LinkMesh &M, uint32_t e0, uint
                                            long long pz, long long h, uint32_t cm, uint32_t o0, int64_t cell, int *st)
 {
     int bestT[27];
-    scan_cell_slow(M.bin_ent, e0, e1, M.rec, px, py, pz, h, cm, bestT);
+    scan_cell_slow(M.bin_ent, e0, e1, M.rec, M.T, px, py, pz, h, cm, bestT);
     uint32_t mm = cm, o = o0;
     while (mm) {
         const int d = __ffs(mm) - 1;
@@ -425,7 +426,10 @@ __global__ void __launch_bounds__(LE_WARPS * 32, LE_MINB) k_link_emit(const __gr
         const long long h = M.g.h, half = M.g.half;
         const long long X0 = 4 * (long long)(bk & EMB_KEY_MASK) * h, Y0 = 4 * (long long)((bk >> EMB_KEY_BITS) & EMB_KEY_MASK) * h,
                         Z0 = 4 * (long long)(bk >> (2 * EMB_KEY_BITS)) * h;
-        const uint32_t e0 = M.bin_off[b], e1 = M.bin_off[b + 1];
+        // the bin, clamped to the entries that exist (a replay whose counts left its plan
+        // reports that through its count checks; its passes must stay in bounds)
+        const uint32_t e1 = (uint64_t)M.bin_off[b + 1] < M.ent_cap ? M.bin_off[b + 1] : (uint32_t)M.ent_cap;
+        const uint32_t e0 = M.bin_off[b] < e1 ? M.bin_off[b] : e1;
         const int lh = __ffsll(h) - 1;  // h is a power of two
         const long long LIM = 1ll << 14;
         // this item's cells with links: ranks [kb0, kb1) among the set bits of bmask
@@ -449,8 +453,8 @@ __global__ void __launch_bounds__(LE_WARPS * 32, LE_MINB) k_link_emit(const __gr
             for (uint32_t e = e0; e < e1; e += LE_TILE) {
                 // stage triangle `lane` of this tile and the chunk cells its reach box touches
                 unsigned long long pm = 0;
-                if (e + lane < e1) {
-                    const uint32_t id = bin_ent[e + lane];
+                const uint32_t id = e + lane < e1 ? bin_ent[e + lane] : 0xFFFFFFFFu;
+                if (id < M.T) {
                     const int4 A = rec[3 * (int64_t)id], B = rec[3 * (int64_t)id + 1], C = rec[3 * (int64_t)id + 2];
                     TriT s;
                     s.ax = A.x; s.ay = A.y; s.az = A.z;
@@ -928,7 +932,9 @@ extern "C" emb_status emb_cutlinks(emb_forest f, emb_bins b, int32_t lattice, in
     M.blk_off = f->blk_off;
     M.bin_off = b->off;
     M.bin_ent = b->ent;
+    M.ent_cap = (uint64_t)b->npairs;
     M.rec = b->m->rec;
+    M.T = (uint32_t)b->m->T;
     M.work_n = f->work_n + lv.n;
     M.o_cell = d_cell;
     M.o_dir = d_dir;

@@ -35,7 +35,7 @@ __device__ __forceinline__ int64_t lower_bound_u64(const uint64_t *__restrict__ 
 }
 
 __global__ void k_make_children(const uint64_t *__restrict__ key, int64_t n, const uint8_t *__restrict__ flags,
-                                const uint32_t *__restrict__ rank, uint64_t *__restrict__ ckey)
+                                const uint32_t *__restrict__ rank, uint64_t *__restrict__ ckey, int64_t Cn)
 {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n || !flags[p]) return;
@@ -52,7 +52,7 @@ __global__ void k_make_children(const uint64_t *__restrict__ key, int64_t n, con
         for (int dy = 0; dy < 2; ++dy)
             for (int dx = 0; dx < 2; ++dx) {
                 int64_t pos = 8 * r_pl + dz * 4 * F_pl + 4 * (r_row - r_pl) + dy * 2 * F_row + 2 * (r_p - r_row) + dx;
-                ckey[pos] = emb_key(2 * bx + dx, 2 * by + dy, 2 * bz + dz);
+                if (pos >= 0 && pos < Cn) ckey[pos] = emb_key(2 * bx + dx, 2 * by + dy, 2 * bz + dz);
             }
 }
 
@@ -139,10 +139,20 @@ emb_status emb_enq_flag_ranks(const EmbLevel &P, const uint8_t *d_flags, uint32_
     return emb_scan_into(cnt, rank, P.n, tmp, s);
 }
 
-emb_status emb_enq_children(const EmbLevel &P, const uint8_t *d_flags, const uint32_t *rank, uint64_t *ckey, int64_t Cn,
-                            cudaStream_t s)
+// Keys [8 F, Cn) of a planned replay that flagged fewer blocks than its plan: the
+// in-range key 0, so that every later pass over the level stays in bounds (the
+// count check of the replay reports the difference).
+__global__ void k_key_tail(uint64_t *__restrict__ ckey, int64_t Cn, const uint32_t *__restrict__ nflags)
 {
-    if (P.n > 0 && Cn > 0) EMB_LAUNCH((k_make_children), emb_grid(P.n, 256), 256, 0, s)(P.key, P.n, d_flags, rank, ckey);
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < Cn && i >= 8 * (int64_t)*nflags) ckey[i] = 0;
+}
+
+emb_status emb_enq_children(const EmbLevel &P, const uint8_t *d_flags, const uint32_t *rank, uint64_t *ckey, int64_t Cn,
+                            bool planned, cudaStream_t s)
+{
+    if (P.n > 0 && Cn > 0) EMB_LAUNCH((k_make_children), emb_grid(P.n, 256), 256, 0, s)(P.key, P.n, d_flags, rank, ckey, Cn);
+    if (planned && Cn > 0) EMB_LAUNCH((k_key_tail), emb_grid(Cn, 256), 256, 0, s)(ckey, Cn, rank + P.n);
     EMB_CUDA_TRY(cudaGetLastError());
     return EMB_OK;
 }
@@ -176,7 +186,7 @@ extern "C" emb_status emb_forest_refine(emb_forest f, int32_t level, const uint8
     C.n = 8 * (int64_t)F;
     C.nb_axis = P.nb_axis * 2;
     EMB_CUDA_TRY(cudaMalloc(&C.key, (C.n + 1) * sizeof(uint64_t)));
-    rc = emb_enq_children(P, d_flags, rank, C.key, C.n, s);
+    rc = emb_enq_children(P, d_flags, rank, C.key, C.n, false, s);
     if (rc != EMB_OK) return rc;
     EMB_CUDA_TRY(cudaFreeAsync(cnt, s));
     EMB_CUDA_TRY(cudaFreeAsync(rank, s));

@@ -164,19 +164,20 @@ emb_status emb_enq_root_keys(int64_t R, uint64_t *key, cudaStream_t s);
 emb_status emb_enq_flag_ranks(const EmbLevel &P, const uint8_t *d_flags, uint32_t *cnt, uint32_t *rank, uint64_t *tmp,
                               cudaStream_t s);
 emb_status emb_enq_children(const EmbLevel &P, const uint8_t *d_flags, const uint32_t *rank, uint64_t *ckey, int64_t Cn,
-                            cudaStream_t s);
+                            bool planned, cudaStream_t s);
 // Binning, voxelization and refine flags (enqueue only).
 struct LevelGeom;
 emb_status emb_enq_filter(const int4 *rec, int64_t T, LevelGeom g, uint32_t *flag, uint32_t *pos, uint32_t *flist,
                           uint64_t *tmp, int block, cudaStream_t s);
 struct EmbBigQ;
-emb_status emb_enq_bin_count(const int4 *rec, int64_t T, LevelGeom g, const EmbLevel &lv, uint32_t *cnt, uint32_t *off,
+emb_status emb_enq_bin_pairs(const int4 *rec, int64_t T, LevelGeom g, const EmbLevel &lv, uint32_t *cnt, uint32_t *off,
+                             uint2 *list_bs, uint32_t *list_tri, unsigned long long *list_n, uint64_t list_cap,
                              uint64_t *tmp, const EmbBigQ &Q, cudaStream_t s);
-emb_status emb_enq_bin_fill(const int4 *rec, int64_t T, LevelGeom g, const EmbLevel &lv, uint32_t *cnt,
-                            const uint32_t *off, uint32_t *ent, const EmbBigQ &Q, cudaStream_t s);
-emb_status emb_enq_voxelize(const int4 *rec, const uint32_t *flist, int64_t nf, LevelGeom g, const EmbLevel &lv,
-                            unsigned long long *s_acc, unsigned int *p_acc, const EmbBigQ &Q, int block,
-                            cudaStream_t s);
+emb_status emb_enq_bin_scatter(const uint2 *list_bs, const uint32_t *list_tri, const unsigned long long *list_n,
+                               uint64_t list_cap, const uint32_t *off, uint32_t *ent, uint64_t ent_cap, cudaStream_t s);
+emb_status emb_enq_voxelize(const int4 *rec, int64_t T, const uint32_t *flist, int64_t nf, const uint32_t *d_nf,
+                            LevelGeom g, const EmbLevel &lv, unsigned long long *s_acc, unsigned int *p_acc,
+                            const EmbBigQ &Q, int block, cudaStream_t s);
 emb_status emb_enq_refine(const int4 *rec, int64_t T, LevelGeom g, long long dil, const EmbLevel &lv, uint8_t *flags,
                           unsigned long long *fbits, const EmbBigQ &Q, cudaStream_t s);
 long long emb_refine_dilation(const emb_forest_s *f, int L, int band);
@@ -190,7 +191,9 @@ struct LinkMesh {
     const uint32_t *blk_off;   // link offsets per block
     const uint32_t *bin_off;   // CSR bins
     const uint32_t *bin_ent;
+    uint64_t ent_cap;          // bin entries that exist
     const int4 *rec;           // triangle records
+    uint32_t T;                // their count
     // work items (block, first | end << 8): the cells with links of rank [first, end)
     // among the block's; one per block with links (its count at *work_n), plus the
     // further parts of heavy blocks in `extra` (EMB_BIG_NONE = unused entry)

@@ -96,13 +96,15 @@ __device__ __forceinline__ void vox_line(const VoxTri &V, const LevelGeom &g, co
     emb_set_status(st, EMB_ERR_STATE);  // no block owns the crossing
 }
 
-__global__ void k_vox(const int4 *__restrict__ rec, const uint32_t *__restrict__ flist, int64_t nf, LevelGeom g,
-                      EmbLookup lk, unsigned long long *__restrict__ s_acc, unsigned int *__restrict__ p_acc,
-                      EmbBigQ Q, int *st)
+__global__ void k_vox(const int4 *__restrict__ rec, int64_t T, const uint32_t *__restrict__ flist, int64_t nf,
+                      const uint32_t *__restrict__ d_nf, LevelGeom g, EmbLookup lk,
+                      unsigned long long *__restrict__ s_acc, unsigned int *__restrict__ p_acc, EmbBigQ Q, int *st)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nf) return;
+    // nf: the planned count of a replay or the exact one; d_nf: the count this replay found
+    if (i >= nf || (d_nf && i >= (int64_t)*d_nf)) return;
     const uint32_t t = flist[i];
+    if ((int64_t)t >= T) return;
     VoxTri V;
     if (!vox_setup(rec, t, g, V)) return;
     const unsigned long long items = vox_items(V);
@@ -170,8 +172,9 @@ __global__ void k_xscan(const uint64_t *__restrict__ key, int64_t n, const unsig
 }
 
 // Enqueue only: s_acc (n uint64) and p_acc (n uint32) are scratch; writes lv.mask.
-emb_status emb_enq_voxelize(const int4 *rec, const uint32_t *flist, int64_t nf, LevelGeom g, const EmbLevel &lv,
-                            unsigned long long *s_acc, unsigned int *p_acc, const EmbBigQ &Q, int block, cudaStream_t s)
+emb_status emb_enq_voxelize(const int4 *rec, int64_t T, const uint32_t *flist, int64_t nf, const uint32_t *d_nf,
+                            LevelGeom g, const EmbLevel &lv, unsigned long long *s_acc, unsigned int *p_acc,
+                            const EmbBigQ &Q, int block, cudaStream_t s)
 {
     int *st = emb_status_word();
     if (!st) return EMB_ERR_CUDA;
@@ -181,7 +184,7 @@ emb_status emb_enq_voxelize(const int4 *rec, const uint32_t *flist, int64_t nf, 
     if (nf > 0) {
         const EmbLookup lk = emb_lookup_of(lv);
         if (Q.cap) EMB_CUDA_TRY(cudaMemsetAsync(Q.n, 0, sizeof(unsigned long long), s));
-        EMB_LAUNCH((k_vox), emb_grid(nf, block), block, 0, s)(rec, flist, nf, g, lk, s_acc, p_acc, Q, st);
+        EMB_LAUNCH((k_vox), emb_grid(nf, block), block, 0, s)(rec, T, flist, nf, d_nf, g, lk, s_acc, p_acc, Q, st);
         if (Q.cap) EMB_LAUNCH((k_vox_big), EMB_BIG_GRID, EMB_BIG_BLOCK, 0, s)(rec, g, lk, s_acc, p_acc, Q, st);
     }
     EMB_LAUNCH((k_xscan), emb_grid(lv.n, 256), 256, 0, s)(lv.key, lv.n, s_acc, p_acc, lv.mask);
@@ -208,7 +211,7 @@ extern "C" emb_status emb_voxelize(emb_forest f, emb_bins b, int32_t level, uint
     EmbBigQ Q;
     emb_status rc = emb_bigq_alloc(Q, b->nf, s);
     if (rc != EMB_OK) return rc;
-    rc = emb_enq_voxelize(b->m->rec, b->flist, b->nf, g, lv, s_acc, p_acc, Q, 128, s);
+    rc = emb_enq_voxelize(b->m->rec, b->m->T, b->flist, b->nf, nullptr, g, lv, s_acc, p_acc, Q, 128, s);
     emb_bigq_free(Q, s);
     if (rc != EMB_OK) return rc;
     if (d_solid_mask)
