@@ -89,6 +89,20 @@ emb_status emb_mesh_create(const float *d_verts, const int32_t *d_tris, int64_t 
                            int32_t check_watertight, void *stream, emb_mesh *out);
 void emb_mesh_destroy(emb_mesh m);
 
+/* Moving geometry (the paper's future work, Sec. 5, re-embedding a moving body):
+ * new positions for the same V vertices, same triangles.  d_verts: V x 3
+ * float32 under the rules of emb_mesh_create.  Rewrites the mesh's records in
+ * place on `stream`; enqueues one kernel, allocates nothing and does not
+ * synchronise, so it can precede a batch replay (or be captured with one) every
+ * step.  A coordinate off the 2^-20 grid or outside (0,1) leaves its record
+ * unchanged and raises EMB_ERR_BAD_INPUT in the device status word.  Forests,
+ * bins and link tables built before the call describe the old positions; a
+ * batch replay recomputes everything and reports EMB_ERR_STATE on the device
+ * when a count no longer matches its plan (re-create the batch then).
+ * Errors (immediate): EMB_ERR_BAD_INPUT (null handle or pointer, V differs from
+ * the mesh's), EMB_ERR_CUDA. */
+emb_status emb_mesh_update(emb_mesh m, const float *d_verts, int64_t V, void *stream);
+
 /* -------------------------------------------------------------- forest ---- */
 /* Root grid of R^3 blocks (Sec. 3.2) with room for levels 0..max_level.
  * Errors: EMB_ERR_BAD_INPUT (R < 1, max_level < 0 or > 15), EMB_ERR_RANGE. */

@@ -25,6 +25,7 @@ SIGNATURES = {
     "emb_launch_count": (I32, [PI64]),
     "emb_mesh_create": (I32, [P, P, I64, I64, I32, I32, P, ctypes.POINTER(P)]),
     "emb_mesh_destroy": (None, [P]),
+    "emb_mesh_update": (I32, [P, P, I64, P]),
     "emb_forest_root": (I32, [I32, I32, P, ctypes.POINTER(P)]),
     "emb_forest_destroy": (None, [P]),
     "emb_forest_refine": (I32, [P, I32, P, P]),

@@ -36,6 +36,35 @@ __global__ void k_mesh_records(const float *__restrict__ verts, const int32_t *_
     if (bad) atomicOr(err, bad);
 }
 
+// New vertex positions for the same triangles: corner j of triangle t takes the
+// coordinates of its vertex id (kept in the record's fourth word).  A coordinate
+// that is not a multiple of 2^-20 inside (0,1) leaves the record unchanged and
+// raises EMB_ERR_BAD_INPUT in the device status word.
+__global__ void k_mesh_move(const float *__restrict__ verts, int64_t V, int64_t T, int32_t r_o, int4 *__restrict__ rec,
+                            int *st)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 3 * T) return;
+    const int4 r = rec[e];
+    if (r.w < 0 || (int64_t)r.w >= V) {
+        emb_set_status(st, EMB_ERR_BAD_INPUT);
+        return;
+    }
+    int c[3];
+    bool ok = true;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const float m = verts[3 * (int64_t)r.w + d] * 1048576.0f;  // exact: power-of-two scaling
+        if (!(m > 0.0f && m < 1048576.0f && m == truncf(m))) ok = false;
+        c[d] = ok ? (int)m * r_o : 0;
+    }
+    if (!ok) {
+        emb_set_status(st, EMB_ERR_BAD_INPUT);
+        return;
+    }
+    rec[e] = make_int4(c[0], c[1], c[2], r.w);
+}
+
 __global__ void k_edge_insert(const int32_t *__restrict__ tris, int64_t T, unsigned long long *hk, int64_t cap, int *err)
 {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -145,4 +174,15 @@ extern "C" void emb_mesh_destroy(emb_mesh m)
     if (!m) return;
     if (m->rec) cudaFree(m->rec);
     free(m);
+}
+
+extern "C" emb_status emb_mesh_update(emb_mesh m, const float *d_verts, int64_t V, void *stream)
+{
+    if (!m || !d_verts || V != m->V) return EMB_ERR_BAD_INPUT;
+    int *st = emb_status_word();
+    if (!st) return EMB_ERR_CUDA;
+    cudaStream_t s = emb_stream(stream);
+    EMB_LAUNCH((k_mesh_move), emb_grid(3 * m->T, 256), 256, 0, s)(d_verts, V, m->T, m->r_o, m->rec, st);
+    EMB_CUDA_TRY(cudaGetLastError());
+    return EMB_OK;
 }

@@ -121,6 +121,13 @@ def emb_mesh_create(verts: torch.Tensor, tris: torch.Tensor, R: int, check_water
     return m
 
 
+def emb_mesh_update(mesh: Mesh, verts: torch.Tensor, stream=None):
+    """New positions for the mesh's vertices (same triangles); asynchronous, no allocation."""
+    verts = verts.to(device="cuda", dtype=torch.float32).contiguous()
+    _check(load().emb_mesh_update(mesh.h, _ptr(verts), verts.shape[0], _stream(stream)), "emb_mesh_update")
+    mesh._moved_verts = verts  # kept alive until the next update (the kernel may still be queued)
+
+
 def emb_forest_root(R: int, max_level: int, stream=None) -> Forest:
     h = ctypes.c_void_p()
     _check(load().emb_forest_root(int(R), int(max_level), _stream(stream), ctypes.byref(h)), "emb_forest_root")
