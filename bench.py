@@ -263,7 +263,8 @@ def run_ours(args):
                 mark("cutlinks_emit")
                 if timed is not None and timed.get("want_bins"):
                     timed["bins"] = P.emb_bins_copy(bins, forest)
-            stats.append(P.emb_bins_stats(bins))
+            if timed is not None and timed.get("want_bins"):
+                stats.append(P.emb_bins_stats(bins))  # reads counts back: outside the timed steps only
             bins.close()
         if timed is not None:
             timed["events"] = ev
@@ -290,7 +291,7 @@ def run_ours(args):
     last = None
     for i in range(args.steps):
         flush.fill_(i & 0xFF)
-        info = dict(want_bins=(i == args.steps - 1))
+        info = dict()
         mesh, forest, masks, links, stats = step(info)
         torch.cuda.synchronize()
         ev = info["events"]
@@ -307,6 +308,11 @@ def run_ours(args):
     st = P.emb_status_get()
     if st != P.EMB_OK:
         raise RuntimeError(f"device status {st} in the timed region")
+    # one more step, untimed, that reads the bin statistics back for the roofline and HBM views
+    info = dict(want_bins=True)
+    mesh, forest, masks, links, stats = step(info)
+    torch.cuda.synchronize()
+    last = (mesh, forest, masks, links, stats, info.get("bins"))
     total_ms = sum(step_ms)
     if dist is not None:
         tt = torch.tensor([total_ms], dtype=torch.float64, device="cuda")

@@ -108,6 +108,11 @@ static emb_status plan_mesh(BMesh &B, cudaStream_t s)
         emb_bins b = nullptr;
         rc = emb_bin(B.m, f, L, B.lattice, s, &b);
         if (rc != EMB_OK) break;
+        rc = emb_bins_sync(b);
+        if (rc != EMB_OK) {
+            emb_bins_destroy(b);
+            break;
+        }
         B.L[L].nf = b->nf;
         rc = emb_voxelize(f, b, L, nullptr, s);
         if (rc == EMB_OK && L < B.Lf) {

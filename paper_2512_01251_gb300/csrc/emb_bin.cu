@@ -14,6 +14,7 @@
 // (block, slot, triangle) to a pair list; offsets come from an exclusive scan and
 // a scatter of the list fills the CSR bins.
 #include <stdlib.h>
+#include <string.h>
 
 #include "emb_internal.cuh"
 
@@ -320,6 +321,52 @@ emb_status emb_enq_bin_scatter(const uint2 *list_bs, const uint32_t *list_tri, c
     return EMB_OK;
 }
 
+// The finest level's bins with a pair list of list_cap entries into ent (ent_cap
+// entries), all enqueued on s; the device counts land in b->dcount.
+static emb_status bin_finest(emb_bins b, uint64_t list_cap, uint64_t ent_cap, cudaStream_t s)
+{
+    const emb_mesh m = b->m;
+    const EmbLevel &lv = b->f->lv[b->level];
+    const LevelGeom g = level_geom(b->f, b->level);
+    emb_status rc = EMB_OK;
+    uint32_t *cnt = nullptr;
+    uint64_t *tmp = nullptr;
+    char *list = nullptr;
+    EmbBigQ Q = {nullptr, nullptr, 0};
+    const size_t a_bs = ((size_t)list_cap * sizeof(uint2) + 255) & ~(size_t)255;
+    if (cudaMallocAsync(&cnt, (lv.n + 1) * sizeof(uint32_t), s) != cudaSuccess ||
+        cudaMallocAsync(&tmp, emb_scan_tmp_words(lv.n) * sizeof(uint64_t), s) != cudaSuccess ||
+        cudaMallocAsync((void **)&list, 256 + a_bs + (size_t)list_cap * sizeof(uint32_t), s) != cudaSuccess)
+        rc = EMB_ERR_CUDA;
+    if (rc == EMB_OK && !b->off && cudaMalloc(&b->off, (lv.n + 1) * sizeof(uint32_t)) != cudaSuccess) rc = EMB_ERR_CUDA;
+    if (rc == EMB_OK && b->ent_cap != ent_cap) {
+        if (b->ent) cudaFreeAsync(b->ent, s);
+        b->ent = nullptr;
+        b->ent_cap = ent_cap;
+        if (cudaMallocAsync(&b->ent, ((size_t)ent_cap + 1) * sizeof(uint32_t), s) != cudaSuccess) rc = EMB_ERR_CUDA;
+    }
+    if (rc == EMB_OK) rc = emb_bigq_alloc(Q, m->T, s);
+    unsigned long long *ln = (unsigned long long *)list;
+    uint2 *lbs = (uint2 *)(list + 256);
+    uint32_t *ltri = (uint32_t *)(list + 256 + a_bs);
+    if (rc == EMB_OK) rc = emb_enq_bin_pairs(m->rec, m->T, g, lv, cnt, b->off, lbs, ltri, ln, list_cap, tmp, Q, s);
+    if (rc == EMB_OK) rc = emb_enq_bin_scatter(lbs, ltri, ln, list_cap, b->off, b->ent, ent_cap, s);
+    if (rc == EMB_OK &&
+        (cudaMemcpyAsync(b->dcount + 4, b->off + lv.n, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+         cudaMemcpyAsync(b->dcount + 8, ln, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s) != cudaSuccess))
+        rc = EMB_ERR_CUDA;
+    b->list_cap = list_cap;
+    emb_bigq_free(Q, s);
+    if (list) cudaFreeAsync(list, s);
+    if (cnt) cudaFreeAsync(cnt, s);
+    if (tmp) cudaFreeAsync(tmp, s);
+    return rc;
+}
+
+// No host synchronisation: the filtered count and, at the finest level, the bin
+// sizes stay on the device until emb_bins_sync reads them.  The finest bins start
+// from a pair list of 4 T + 2^20 entries; if that proved too small, emb_bins_sync
+// (called by every consumer that needs complete bins) redoes them exactly.
 extern "C" emb_status emb_bin(emb_mesh m, emb_forest f, int32_t level, int32_t lattice, void *stream, emb_bins *out)
 {
     if (!m || !f || !out) return EMB_ERR_BAD_INPUT;
@@ -333,78 +380,64 @@ extern "C" emb_status emb_bin(emb_mesh m, emb_forest f, int32_t level, int32_t l
     b->f = f;
     b->level = level;
     b->lattice = lattice;
+    b->s = s;
     LevelGeom g = level_geom(f, level);
     const EmbLevel &lv = f->lv[level];
     emb_status rc = EMB_OK;
-    uint32_t *flag = nullptr, *pos = nullptr, *cnt = nullptr;
+    uint32_t *flag = nullptr, *pos = nullptr;
     uint64_t *tmp = nullptr;
-    uint32_t nf = 0, np = 0;
-    EmbBigQ Q = {nullptr, nullptr, 0};
-    const int64_t tw = emb_scan_tmp_words(m->T > lv.n ? m->T : lv.n);
     // step 1: exact x-line filter, compacted in ascending order
     if (cudaMallocAsync(&flag, (m->T + 1) * sizeof(uint32_t), s) != cudaSuccess ||
         cudaMallocAsync(&pos, (m->T + 1) * sizeof(uint32_t), s) != cudaSuccess ||
-        cudaMallocAsync(&tmp, tw * sizeof(uint64_t), s) != cudaSuccess ||
-        cudaMalloc(&b->flist, (m->T + 1) * sizeof(uint32_t)) != cudaSuccess) {
+        cudaMallocAsync(&tmp, emb_scan_tmp_words(m->T) * sizeof(uint64_t), s) != cudaSuccess ||
+        cudaMalloc(&b->flist, (m->T + 1) * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&b->dcount, 16) != cudaSuccess) {
         emb_bins_destroy(b);
         return EMB_ERR_CUDA;
     }
+    EMB_CUDA_TRY(cudaMemsetAsync(b->dcount, 0, 16, s));
     rc = emb_enq_filter(m->rec, m->T, g, flag, pos, b->flist, tmp, 256, s);
-    if (rc == EMB_OK && cudaMemcpyAsync(&nf, pos + m->T, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    if (rc == EMB_OK && cudaMemcpyAsync(b->dcount, pos + m->T, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         rc = EMB_ERR_CUDA;
     // steps 2-9 at the finest level: CSR bins of link-relevant triangles per block
-    const bool finest = level == f->max_level && lv.n > 0;
-    uint64_t lcap = 0;
-    unsigned long long lreq = 0;
-    char *list = nullptr;
-    auto list_alloc = [&](uint64_t cap) -> emb_status {
-        if (list) cudaFreeAsync(list, s);
-        list = nullptr;
-        lcap = cap;
-        const size_t a = ((size_t)cap * sizeof(uint2) + 255) & ~(size_t)255;
-        if (cudaMallocAsync((void **)&list, 256 + a + (size_t)cap * sizeof(uint32_t), s) != cudaSuccess) return EMB_ERR_CUDA;
-        return EMB_OK;
-    };
-    auto lp_n = [&]() { return (unsigned long long *)list; };
-    auto lp_bs = [&]() { return (uint2 *)(list + 256); };
-    auto lp_tri = [&]() { return (uint32_t *)(list + 256 + (((size_t)lcap * sizeof(uint2) + 255) & ~(size_t)255)); };
-    if (rc == EMB_OK && finest) {
-        if (cudaMallocAsync(&cnt, (lv.n + 1) * sizeof(uint32_t), s) != cudaSuccess ||
-            cudaMalloc(&b->off, (lv.n + 1) * sizeof(uint32_t)) != cudaSuccess)
-            rc = EMB_ERR_CUDA;
-        if (rc == EMB_OK) rc = emb_bigq_alloc(Q, m->T, s);
-        if (rc == EMB_OK) rc = list_alloc((uint64_t)4 * m->T + (1 << 20));
-        if (rc == EMB_OK)
-            rc = emb_enq_bin_pairs(m->rec, m->T, g, lv, cnt, b->off, lp_bs(), lp_tri(), lp_n(), lcap, tmp, Q, s);
-        if (rc == EMB_OK && (cudaMemcpyAsync(&np, b->off + lv.n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-                             cudaMemcpyAsync(&lreq, lp_n(), sizeof(lreq), cudaMemcpyDeviceToHost, s) != cudaSuccess))
-            rc = EMB_ERR_CUDA;
+    if (rc == EMB_OK && level == f->max_level && lv.n > 0) {
+        const uint64_t cap = (uint64_t)4 * m->T + (1 << 20);
+        rc = bin_finest(b, cap, cap, s);
     }
-    if (rc == EMB_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = EMB_ERR_CUDA;
-    if (rc == EMB_OK && finest && lreq > lcap) {
-        // the list was too small: once more with its exact size
-        rc = list_alloc(lreq);
-        if (rc == EMB_OK)
-            rc = emb_enq_bin_pairs(m->rec, m->T, g, lv, cnt, b->off, lp_bs(), lp_tri(), lp_n(), lcap, tmp, Q, s);
-    }
-    b->nf = nf;
-    if (rc == EMB_OK && finest) {
-        b->npairs = np;
-        if (cudaMalloc(&b->ent, ((size_t)np + 1) * sizeof(uint32_t)) != cudaSuccess) rc = EMB_ERR_CUDA;
-        if (rc == EMB_OK) rc = emb_enq_bin_scatter(lp_bs(), lp_tri(), lp_n(), lcap, b->off, b->ent, (uint64_t)np, s);
-    }
-    if (list) cudaFreeAsync(list, s);
-    emb_bigq_free(Q, s);
-    if (flag) cudaFreeAsync(flag, s);
-    if (pos) cudaFreeAsync(pos, s);
-    if (cnt) cudaFreeAsync(cnt, s);
-    if (tmp) cudaFreeAsync(tmp, s);
+    cudaFreeAsync(flag, s);
+    cudaFreeAsync(pos, s);
+    cudaFreeAsync(tmp, s);
     if (rc == EMB_OK && cudaGetLastError() != cudaSuccess) rc = EMB_ERR_CUDA;
     if (rc != EMB_OK) {
         emb_bins_destroy(b);
         return rc;
     }
     *out = b;
+    return EMB_OK;
+}
+
+emb_status emb_bins_sync(emb_bins b)
+{
+    if (b->known) return EMB_OK;
+    unsigned char h[16];
+    EMB_CUDA_TRY(cudaMemcpyAsync(h, b->dcount, 16, cudaMemcpyDeviceToHost, b->s));
+    EMB_CUDA_TRY(cudaStreamSynchronize(b->s));
+    uint32_t nf = 0, np = 0;
+    unsigned long long lreq = 0;
+    memcpy(&nf, h, 4);
+    memcpy(&np, h + 4, 4);
+    memcpy(&lreq, h + 8, 8);
+    if (b->off && lreq > b->list_cap) {
+        // the pair list was too small: the bins once more, with its exact size
+        emb_status rc = bin_finest(b, lreq, lreq, b->s);
+        if (rc != EMB_OK) return rc;
+        EMB_CUDA_TRY(cudaMemcpyAsync(h, b->dcount, 16, cudaMemcpyDeviceToHost, b->s));
+        EMB_CUDA_TRY(cudaStreamSynchronize(b->s));
+        memcpy(&np, h + 4, 4);
+    }
+    b->nf = nf;
+    b->npairs = np;
+    b->known = true;
     return EMB_OK;
 }
 
@@ -415,12 +448,15 @@ extern "C" void emb_bins_destroy(emb_bins b)
     if (b->flist) cudaFree(b->flist);
     if (b->off) cudaFree(b->off);
     if (b->ent) cudaFree(b->ent);
+    if (b->dcount) cudaFree(b->dcount);
     delete b;
 }
 
 extern "C" emb_status emb_bins_stats(emb_bins b, int64_t *h_filtered, int64_t *h_pairs)
 {
     if (!b) return EMB_ERR_BAD_INPUT;
+    emb_status rc = emb_bins_sync(b);
+    if (rc != EMB_OK) return rc;
     if (h_filtered) *h_filtered = b->nf;
     if (h_pairs) *h_pairs = b->npairs;
     return EMB_OK;
@@ -429,6 +465,8 @@ extern "C" emb_status emb_bins_stats(emb_bins b, int64_t *h_filtered, int64_t *h
 extern "C" emb_status emb_bins_copy(emb_bins b, uint32_t *d_filtered, uint32_t *d_off, uint32_t *d_ent, void *stream)
 {
     if (!b) return EMB_ERR_BAD_INPUT;
+    emb_status rc = emb_bins_sync(b);
+    if (rc != EMB_OK) return rc;
     cudaStream_t s = emb_stream(stream);
     if (d_filtered && b->nf > 0)
         EMB_CUDA_TRY(cudaMemcpyAsync(d_filtered, b->flist, b->nf * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));

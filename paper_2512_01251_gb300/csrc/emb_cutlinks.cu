@@ -911,6 +911,11 @@ extern "C" emb_status emb_cutlinks(emb_forest f, emb_bins b, int32_t lattice, in
     if (!f || !b || (lattice != 19 && lattice != 27) || capacity < 0) return EMB_ERR_BAD_INPUT;
     if (b->f != f || b->level != f->max_level || !b->off) return EMB_ERR_STATE;
     cudaStream_t s = emb_stream(stream);
+    {
+        // complete bins (a pair list that proved too small is redone here)
+        const emb_status rb = emb_bins_sync(b);
+        if (rb != EMB_OK) return rb;
+    }
     int *st = emb_status_word();
     if (!st) return EMB_ERR_CUDA;
     emb_status rc = build_candidates(f, lattice, s);
@@ -932,7 +937,7 @@ extern "C" emb_status emb_cutlinks(emb_forest f, emb_bins b, int32_t lattice, in
     M.blk_off = f->blk_off;
     M.bin_off = b->off;
     M.bin_ent = b->ent;
-    M.ent_cap = (uint64_t)b->npairs;
+    M.ent_cap = (uint64_t)b->npairs;  // complete after emb_bins_sync
     M.rec = b->m->rec;
     M.T = (uint32_t)b->m->T;
     M.work_n = f->work_n + lv.n;

@@ -112,12 +112,21 @@ struct emb_bins_s {
     emb_mesh m;
     emb_forest f;
     int32_t level, lattice;
-    uint32_t *flist = nullptr;  // filtered triangle ids (ascending)
-    int64_t nf = 0;
+    cudaStream_t s = nullptr;   // stream of emb_bin (for reading the counts back)
+    uint32_t *flist = nullptr;  // filtered triangle ids (ascending), T + 1 entries
     uint32_t *off = nullptr;    // finest level only: CSR offsets (n_blocks + 1)
-    uint32_t *ent = nullptr;    // triangle ids
-    int64_t npairs = 0;
+    uint32_t *ent = nullptr;    // triangle ids, ent_cap entries
+    uint64_t ent_cap = 0;
+    uint64_t list_cap = 0;      // capacity of the pair list used by emb_bin
+    // device counts: filtered triangles, bin entries (uint32 each), pair-list requests (uint64)
+    unsigned char *dcount = nullptr;
+    // host copies, valid once `known` (emb_bins_sync)
+    bool known = false;
+    int64_t nf = 0, npairs = 0;
 };
+// Reads the counts of b back (synchronising b's stream) and, at the finest level,
+// redoes the bins with an exact pair list if the first one was too small.
+emb_status emb_bins_sync(emb_bins b);
 
 // Geometry of one level in frame units.
 struct LevelGeom {

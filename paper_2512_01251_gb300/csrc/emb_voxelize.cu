@@ -209,9 +209,11 @@ extern "C" emb_status emb_voxelize(emb_forest f, emb_bins b, int32_t level, uint
     EMB_CUDA_TRY(cudaMallocAsync(&s_acc, lv.n * sizeof(unsigned long long), s));
     EMB_CUDA_TRY(cudaMallocAsync(&p_acc, lv.n * sizeof(unsigned int), s));
     EmbBigQ Q;
-    emb_status rc = emb_bigq_alloc(Q, b->nf, s);
+    emb_status rc = emb_bigq_alloc(Q, b->m->T, s);
     if (rc != EMB_OK) return rc;
-    rc = emb_enq_voxelize(b->m->rec, b->m->T, b->flist, b->nf, nullptr, g, lv, s_acc, p_acc, Q, 128, s);
+    // the filtered count stays on the device: the grid covers every triangle and stops at it
+    rc = emb_enq_voxelize(b->m->rec, b->m->T, b->flist, b->known ? b->nf : b->m->T, (const uint32_t *)b->dcount, g, lv,
+                          s_acc, p_acc, Q, 128, s);
     emb_bigq_free(Q, s);
     if (rc != EMB_OK) return rc;
     if (d_solid_mask)
