@@ -140,14 +140,20 @@ emb_status emb_forest_masks(emb_forest f, int32_t level, uint64_t *d_out, void *
  *      CSR form holding every non-degenerate triangle that overlaps the block box
  *      dilated by half a cell (Alg. 2 dilates bins by the cell size; a link from
  *      a cell centre, itself half a cell inside the block, reaches at most one
- *      cell further, so half a cell suffices), built by count, exclusive scan and
- *      fill; ids within a bin are unordered.
- * `lattice` (19 or 27) is recorded for emb_cutlinks.  Synchronises once.
+ *      cell further, so half a cell suffices), built by one counting pass that
+ *      also lists the pairs, an exclusive scan and a scatter; ids within a bin
+ *      are unordered.
+ * `lattice` (19 or 27) is recorded for emb_cutlinks.  Enqueues only: the counts
+ * stay on the device until emb_bins_stats, emb_bins_copy or emb_cutlinks reads
+ * them (synchronising `stream`).  The finest bins start from a pair list of
+ * 4 T + 2^20 entries; when that proves too small, the first of those readers
+ * rebuilds them with the exact size before using them.
  * Errors: EMB_ERR_BAD_INPUT, EMB_ERR_STATE (level missing, mesh/forest frame mismatch). */
 emb_status emb_bin(emb_mesh m, emb_forest f, int32_t level, int32_t lattice, void *stream, emb_bins *out);
 void emb_bins_destroy(emb_bins b);
 
-/* Host statistics: filtered triangles and (at the finest level) bin entries. */
+/* Host statistics: filtered triangles and (at the finest level) bin entries.
+ * Synchronises the stream of emb_bin on first use. */
 emb_status emb_bins_stats(emb_bins b, int64_t *h_filtered, int64_t *h_pairs);
 
 /* Copies the bins out (Sec. 3.3's bins_face_ids / _N arrays): d_filtered gets the
