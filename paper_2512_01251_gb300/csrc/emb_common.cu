@@ -388,3 +388,17 @@ void emb_bigq_free(EmbBigQ &Q, cudaStream_t s)
     Q.n = nullptr;
     Q.cap = 0;
 }
+
+// Multiprocessors of the current device (cached per device; persistent grids).
+int emb_sm_count()
+{
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    if (!cached[dev]) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 152;
+        cached[dev] = n;
+    }
+    return cached[dev];
+}

@@ -168,6 +168,7 @@ emb_status emb_build_hash(EmbLevel &lv, cudaStream_t s);
 emb_status emb_enq_neighbors(EmbLevel &lv, cudaStream_t s);
 emb_status emb_build_neighbors(EmbLevel &lv, cudaStream_t s);
 int emb_grid(int64_t n, int block);
+int emb_sm_count();
 // Forest steps (enqueue only; buffers supplied by the caller).
 emb_status emb_enq_root_keys(int64_t R, uint64_t *key, cudaStream_t s);
 emb_status emb_enq_flag_ranks(const EmbLevel &P, const uint8_t *d_flags, uint32_t *cnt, uint32_t *rank, uint64_t *tmp,

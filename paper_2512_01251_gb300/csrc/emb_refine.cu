@@ -16,6 +16,10 @@
 // blocks.  Flags are idempotent byte stores.
 #include "emb_internal.cuh"
 
+#ifndef REFINE_MINB
+#define REFINE_MINB 4
+#endif
+
 __device__ __forceinline__ void refine_setup(const int4 *__restrict__ rec, int64_t t, const LevelGeom &g, long long dil,
                                              int4 &A, int4 &B, int4 &C, long long b0[3], long long b1[3])
 {
@@ -40,10 +44,12 @@ __device__ __forceinline__ unsigned long long refine_items(const long long b0[3]
 struct FlagBits {
     unsigned long long *w;  // null: no dense bits, test the flag bytes
     long long nb;
+    // A plain (L1-cached) load: a word cached before another SM set a bit only sends
+    // the candidate through the full test, which decides exactly.
     __device__ __forceinline__ bool test(long long bx, long long by, long long bz, unsigned long long &pos) const
     {
         pos = (unsigned long long)((bz * nb + by) * nb + bx);
-        return (((volatile unsigned long long *)w)[pos >> 6] >> (pos & 63)) & 1ull;
+        return (w[pos >> 6] >> (pos & 63)) & 1ull;
     }
     __device__ __forceinline__ void set(unsigned long long pos) const { atomicOr(w + (pos >> 6), 1ull << (pos & 63)); }
 };
@@ -67,68 +73,116 @@ __device__ __forceinline__ void refine_block(const int4 &A, const int4 &B, const
     }
 }
 
-__global__ void __launch_bounds__(EMB_WU_WARPS * 32, 4) k_refine(const int4 *__restrict__ rec, int64_t T, LevelGeom g,
+// The less common paths, kept out of line so that the kernel's main path needs few
+// registers and more warps stay resident to cover the latency of the record loads:
+// a union block not yet flagged, tested against the warp's 32 triangles ...
+static __device__ __noinline__ void refine_union_block(const WuTri &S, long long bx, long long by, long long bz,
+                                                       unsigned long long pos, const LevelGeom &g, long long dil,
+                                                       const EmbLookup &lk, uint8_t *__restrict__ flags,
+                                                       const FlagBits &fb)
+{
+    const int32_t id = emb_lookup(lk, bx, by, bz);
+    if (id < 0 || flags[id]) return;
+    const long long lx = bx * g.W - dil, ly = by * g.W - dil, lz = bz * g.W - dil;
+    const long long hx = lx + g.W + 2 * dil, hy = ly + g.W + 2 * dil, hz = lz + g.W + 2 * dil;
+    for (int j = 0; j < 32; ++j) {
+        if (wu_overlap(S, j, lx, ly, lz, hx, hy, hz)) {
+            flags[id] = 1;
+            if (fb.w) fb.set(pos);
+            return;
+        }
+    }
+}
+
+// ... and a triangle walking its own candidate blocks.
+static __device__ __noinline__ void refine_own(const int4 A, const int4 B, const int4 C, const long long *b0,
+                                               const long long *b1, const LevelGeom &g, long long dil,
+                                               const EmbLookup &lk, uint8_t *__restrict__ flags, const FlagBits &fb)
+{
+    for (long long bz = b0[2]; bz <= b1[2]; ++bz)
+        for (long long by = b0[1]; by <= b1[1]; ++by)
+            for (long long bx = b0[0]; bx <= b1[0]; ++bx) refine_block(A, B, C, bx, by, bz, g, dil, lk, flags, fb);
+}
+
+// Persistent warps over tiles of 32 consecutive triangles; each warp loads the
+// records of its next tile before it works on the current one, so that the loads
+// are in flight during the work (a warp otherwise spends most of its life after its
+// loads, in dependent lookups, and the record stream runs far below HBM speed).
+__global__ void __launch_bounds__(EMB_WU_WARPS * 32, REFINE_MINB) k_refine(const int4 *__restrict__ rec, int64_t T, LevelGeom g,
                                                               long long dil, EmbLookup lk, uint8_t *__restrict__ flags,
                                                               FlagBits fb, EmbBigQ Q)
 {
     __shared__ WuTri tiles[EMB_WU_WARPS];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WuTri &S = tiles[w];
-    const int64_t t = ((int64_t)blockIdx.x * EMB_WU_WARPS + w) * 32 + lane;
-    const bool valid = t < T;
-    long long b0[3] = {1ll << 40, 1ll << 40, 1ll << 40}, b1[3] = {-1, -1, -1};
-    int4 A = make_int4(0, 0, 0, 0), B = A, C = A;
-    if (valid) refine_setup(rec, t, g, dil, A, B, C, b0, b1);
-    S.A[lane] = A;
-    S.B[lane] = B;
-    S.C[lane] = C;
-    S.lo[0][lane] = valid ? min(A.x, min(B.x, C.x)) : 0x7fffffff;
-    S.hi[0][lane] = valid ? max(A.x, max(B.x, C.x)) : -0x7fffffff;
-    S.lo[1][lane] = min(A.y, min(B.y, C.y));
-    S.hi[1][lane] = max(A.y, max(B.y, C.y));
-    S.lo[2][lane] = min(A.z, min(B.z, C.z));
-    S.hi[2][lane] = max(A.z, max(B.z, C.z));
-    __syncwarp();
-    int u0[3], u1[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        u0[d] = __reduce_min_sync(0xffffffffu, (int)min(b0[d], (long long)0x7fffffff));
-        u1[d] = __reduce_max_sync(0xffffffffu, (int)b1[d]);
+    const int64_t ntiles = (T + 31) / 32;
+    const int64_t stride = (int64_t)gridDim.x * EMB_WU_WARPS;
+    int64_t tile = (int64_t)blockIdx.x * EMB_WU_WARPS + w;
+    int4 nA = make_int4(0, 0, 0, 0), nB = nA, nC = nA;
+    if (tile < ntiles && tile * 32 + lane < T) {
+        const int64_t t = tile * 32 + lane;
+        nA = rec[3 * t];
+        nB = rec[3 * t + 1];
+        nC = rec[3 * t + 2];
     }
-    const long long nx = u1[0] - u0[0] + 1, ny = u1[1] - u0[1] + 1, nz = u1[2] - u0[2] + 1;
-    if (nx <= 0 || ny <= 0 || nz <= 0) return;
-    const long long total = nx * ny * nz;
-    // per-triangle candidates summed over the warp: the union pays off only when it is much smaller
-    const unsigned long long own = valid ? refine_items(b0, b1) : 0;
-    const unsigned own_sum = __reduce_add_sync(0xffffffffu, (unsigned)min(own, 1ull << 20));
-    if (total <= EMB_WU_MAX && 4 * total <= (long long)own_sum) {
-        // total <= EMB_WU_MAX: decode the union index in 32-bit arithmetic
-        const unsigned ux = (unsigned)nx, uxy = (unsigned)(nx * ny);
-        for (unsigned c = lane; c < (unsigned)total; c += 32) {
-            const unsigned cz = c / uxy, cr = c - cz * uxy, cy = cr / ux;
-            const long long bx = u0[0] + (long long)(cr - cy * ux), by = u0[1] + (long long)cy, bz = u0[2] + (long long)cz;
-            unsigned long long pos = 0;
-            if (fb.w && fb.test(bx, by, bz, pos)) continue;
-            const int32_t id = emb_lookup(lk, bx, by, bz);
-            if (id < 0 || flags[id]) continue;
-            const long long lx = bx * g.W - dil, ly = by * g.W - dil, lz = bz * g.W - dil;
-            const long long hx = lx + g.W + 2 * dil, hy = ly + g.W + 2 * dil, hz = lz + g.W + 2 * dil;
-            for (int j = 0; j < 32; ++j) {
-                if (wu_overlap(S, j, lx, ly, lz, hx, hy, hz)) {
-                    flags[id] = 1;
-                    if (fb.w) fb.set(pos);
-                    break;
-                }
+    for (; tile < ntiles; tile += stride) {
+        const int64_t t = tile * 32 + lane;
+        const bool valid = t < T;
+        const int4 A = nA, B = nB, C = nC;
+        {
+            const int64_t tn = (tile + stride) * 32 + lane;
+            if (tile + stride < ntiles && tn < T) {
+                nA = rec[3 * tn];
+                nB = rec[3 * tn + 1];
+                nC = rec[3 * tn + 2];
             }
         }
-        return;
+        long long b0[3] = {1ll << 40, 1ll << 40, 1ll << 40}, b1[3] = {-1, -1, -1};
+        if (valid) {
+            emb_block_range(min(A.x, min(B.x, C.x)), max(A.x, max(B.x, C.x)), g.lW, dil, g.nb, b0[0], b1[0]);
+            emb_block_range(min(A.y, min(B.y, C.y)), max(A.y, max(B.y, C.y)), g.lW, dil, g.nb, b0[1], b1[1]);
+            emb_block_range(min(A.z, min(B.z, C.z)), max(A.z, max(B.z, C.z)), g.lW, dil, g.nb, b0[2], b1[2]);
+        }
+        __syncwarp();  // the previous tile's lanes are done with S
+        S.A[lane] = A;
+        S.B[lane] = B;
+        S.C[lane] = C;
+        S.lo[0][lane] = valid ? min(A.x, min(B.x, C.x)) : 0x7fffffff;
+        S.hi[0][lane] = valid ? max(A.x, max(B.x, C.x)) : -0x7fffffff;
+        S.lo[1][lane] = min(A.y, min(B.y, C.y));
+        S.hi[1][lane] = max(A.y, max(B.y, C.y));
+        S.lo[2][lane] = min(A.z, min(B.z, C.z));
+        S.hi[2][lane] = max(A.z, max(B.z, C.z));
+        __syncwarp();
+        int u0[3], u1[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            u0[d] = __reduce_min_sync(0xffffffffu, (int)min(b0[d], (long long)0x7fffffff));
+            u1[d] = __reduce_max_sync(0xffffffffu, (int)b1[d]);
+        }
+        const long long nx = u1[0] - u0[0] + 1, ny = u1[1] - u0[1] + 1, nz = u1[2] - u0[2] + 1;
+        if (nx <= 0 || ny <= 0 || nz <= 0) continue;
+        const long long total = nx * ny * nz;
+        // per-triangle candidates summed over the warp: the union pays off only when it is much smaller
+        const unsigned long long own = valid ? refine_items(b0, b1) : 0;
+        const unsigned own_sum = __reduce_add_sync(0xffffffffu, (unsigned)min(own, 1ull << 20));
+        if (total <= EMB_WU_MAX && 4 * total <= (long long)own_sum) {
+            // total <= EMB_WU_MAX: decode the union index in 32-bit arithmetic
+            const unsigned ux = (unsigned)nx, uxy = (unsigned)(nx * ny);
+            for (unsigned c = lane; c < (unsigned)total; c += 32) {
+                const unsigned cz = c / uxy, cr = c - cz * uxy, cy = cr / ux;
+                const long long bx = u0[0] + (long long)(cr - cy * ux), by = u0[1] + (long long)cy,
+                                bz = u0[2] + (long long)cz;
+                unsigned long long pos = 0;
+                if (fb.w && fb.test(bx, by, bz, pos)) continue;  // the common case: one cached load
+                refine_union_block(S, bx, by, bz, pos, g, dil, lk, flags, fb);
+            }
+            continue;
+        }
+        // large or loose union: each lane takes its own triangle, queued in chunks when it has many candidates
+        if (valid && !(own > EMB_BIG_ITEMS && emb_bigq_push(Q, (uint32_t)t, own)))
+            refine_own(A, B, C, b0, b1, g, dil, lk, flags, fb);
     }
-    // large or loose union: each lane takes its own triangle, queued in chunks when it has many candidates
-    if (!valid) return;
-    if (own > EMB_BIG_ITEMS && emb_bigq_push(Q, (uint32_t)t, own)) return;
-    for (long long bz = b0[2]; bz <= b1[2]; ++bz)
-        for (long long by = b0[1]; by <= b1[1]; ++by)
-            for (long long bx = b0[0]; bx <= b1[0]; ++bx) refine_block(A, B, C, bx, by, bz, g, dil, lk, flags, fb);
 }
 
 // The queued chunks of large triangles, one warp per chunk (candidates x fastest).
@@ -200,7 +254,11 @@ emb_status emb_enq_refine(const int4 *rec, int64_t T, LevelGeom g, long long dil
         fb.w = fbits;
     }
     if (Q.cap) EMB_CUDA_TRY(cudaMemsetAsync(Q.n, 0, sizeof(unsigned long long), s));
-    EMB_LAUNCH((k_refine), emb_grid(T, 32 * EMB_WU_WARPS), 32 * EMB_WU_WARPS, 0, s)(rec, T, g, dil, lk, flags, fb, Q);
+    int64_t grid = (T + 32 * EMB_WU_WARPS - 1) / (32 * EMB_WU_WARPS);
+    const int64_t resident = (int64_t)emb_sm_count() * REFINE_MINB;
+    if (grid > resident) grid = resident;
+    if (grid < 1) grid = 1;
+    EMB_LAUNCH((k_refine), (int)grid, 32 * EMB_WU_WARPS, 0, s)(rec, T, g, dil, lk, flags, fb, Q);
     if (Q.cap) EMB_LAUNCH((k_refine_big), EMB_BIG_GRID, EMB_BIG_BLOCK, 0, s)(rec, g, dil, lk, flags, fb, Q);
     EMB_CUDA_TRY(cudaGetLastError());
     return EMB_OK;

@@ -53,6 +53,12 @@ WORKLOADS = {
         "star_7m", dict(n_theta=1897, n_phi=1898, lmax=32, sigma=_sig_sq(0.08, 1.5), seed=20251204,
                         scale=(1.0, 0.6, 0.4)),
         "radial_star", R=32, levels=4, lattices=(27,)),
+    # profiling case: the 7.2M form at 3.0M triangles (144 MB of records, more than the
+    # 129 MB L2), root 32^3, levels 0..4, D3Q27
+    "star_3m": Workload(
+        "star_3m", dict(n_theta=1225, n_phi=1224, lmax=32, sigma=_sig_sq(0.08, 1.5), seed=20251205,
+                        scale=(1.0, 0.6, 0.4)),
+        "radial_star", R=32, levels=4, lattices=(27,)),
     # differentiation case: the 112K mesh, root 16^3, levels 0..3, D3Q19
     "diff_112k": Workload(
         "diff_112k", dict(n_theta=237, n_phi=236, lmax=8, sigma=_sig_sq(0.05, 2), seed=20251203),
