@@ -200,12 +200,56 @@ __global__ void __launch_bounds__(EMB_WU_WARPS * 32) k_bin_pairs(const int4 *__r
         }
         return;
     }
-    // large or loose union: each lane takes its own triangle
-    if (!valid) return;
-    if (own > EMB_BIG_ITEMS && emb_bigq_push(Q, (uint32_t)t, own)) return;
-    for (long long bz = b0[2]; bz <= b1[2]; ++bz)
-        for (long long by = b0[1]; by <= b1[1]; ++by)
-            for (long long bx = b0[0]; bx <= b1[0]; ++bx) bin_block(A, B, C, (uint32_t)t, bx, by, bz, g, dil, lk, cnt, PL);
+    // large or loose union: the warp's (triangle, candidate block) pairs, spread evenly
+    // over the lanes by a prefix sum of the lanes' candidate counts (a triangle with
+    // very many candidates goes to the chunk queue instead), with one list append
+    // per warp and round
+    const bool mine = valid && own > 0 && !(own > EMB_BIG_ITEMS && emb_bigq_push(Q, (uint32_t)t, own));
+    const uint32_t k = mine ? (uint32_t)own : 0u;
+    uint32_t incl = k;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const uint32_t wtot = __shfl_sync(0xffffffffu, incl, 31);
+    const int ox = (int)b0[0], oy = (int)b0[1], oz = (int)b0[2];
+    const int onx = mine ? (int)(b1[0] - b0[0] + 1) : 1, ony = mine ? (int)(b1[1] - b0[1] + 1) : 1;
+    for (uint32_t s0 = 0; s0 < wtot; s0 += 32) {
+        const uint32_t gi = s0 + lane;
+        int lo = 0;
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+            const uint32_t v = __shfl_sync(0xffffffffu, incl, lo + step - 1);
+            if (v <= gi) lo += step;
+        }
+        const int ti = lo > 31 ? 31 : lo;
+        const uint32_t first = __shfl_sync(0xffffffffu, incl, ti) - __shfl_sync(0xffffffffu, k, ti);
+        const int bx0 = __shfl_sync(0xffffffffu, ox, ti), by0 = __shfl_sync(0xffffffffu, oy, ti),
+                  bz0 = __shfl_sync(0xffffffffu, oz, ti), nbx = __shfl_sync(0xffffffffu, onx, ti),
+                  nby = __shfl_sync(0xffffffffu, ony, ti);
+        bool hit = false;
+        int32_t id = -1;
+        if (gi < wtot) {
+            const uint32_t r = gi - first, cx = r % (uint32_t)nbx, rr = r / (uint32_t)nbx, cy = rr % (uint32_t)nby,
+                           cz = rr / (uint32_t)nby;
+            const long long bx = bx0 + (long long)cx, by = by0 + (long long)cy, bz = bz0 + (long long)cz;
+            id = emb_lookup(lk, bx, by, bz);
+            if (id >= 0) {
+                const int4 TA = S.A[ti], TB = S.B[ti], TC = S.C[ti];
+                const long long lx = bx * g.W - dil, ly = by * g.W - dil, lz = bz * g.W - dil;
+                const long long hx = lx + g.W + 2 * dil, hy = ly + g.W + 2 * dil, hz = lz + g.W + 2 * dil;
+                hit = emb_point_in_box(TA, lx, ly, lz, hx, hy, hz) || emb_point_in_box(TB, lx, ly, lz, hx, hy, hz) ||
+                      emb_point_in_box(TC, lx, ly, lz, hx, hy, hz) || emb_tri_box(TA, TB, TC, lx, ly, lz, hx, hy, hz);
+            }
+        }
+        const unsigned hm = __ballot_sync(0xffffffffu, hit);
+        if (!hm) continue;
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(PL.n, (unsigned long long)__popc(hm));
+        base = __shfl_sync(0xffffffffu, base, 0) + (unsigned long long)__popc(hm & ((1u << lane) - 1u));
+        if (hit) PL.put(base, (uint32_t)id, atomicAdd(cnt + id, 1u), (uint32_t)(t0 + ti));
+    }
 }
 
 // Decomposition of candidate index i of the box [b0, b1] (x fastest) and its step by 32.
