@@ -178,12 +178,11 @@ class ClockSampler:
 
 
 def source_hash(*names):
+    """Hash of the kernel's own source files (the ones that hold its body)."""
     h = hashlib.sha256()
     for n in names:
         with open(os.path.join(ROOT, "paper_2512_01251_gb300", "csrc", n), "rb") as f:
             h.update(f.read())
-    with open(os.path.join(ROOT, "paper_2512_01251_gb300", "csrc", "emb_internal.cuh"), "rb") as f:
-        h.update(f.read())
     return h.hexdigest()[:16]
 
 
@@ -376,6 +375,7 @@ def run_ours(args):
         line["e2e"] = e2e_leg(P, v, t, w, lattice, args, stream)
         line["fwd_bwd"] = fwd_bwd_leg(P)
         line["batched"] = batch_leg(P)
+        line["ablation"] = ablation_leg(P, verts, tris, w, lattice)
         units_s, secs = oracle_sample(v, t, w, lattice, 6, seed=7)
         line["cpu_baseline"] = dict(value=units_s / secs, unit=UNIT, cores=omp_threads(), kind="oracle",
                                     sample=("6 surface blocks of the finest level: 64 cell states each, the states "
@@ -444,6 +444,45 @@ def fwd_bwd_leg(P, reps=10):
                 forward_ms=round(fmed, 4), backward_ms=round(bmed, 4), backward_over_forward=round(bmed / fmed, 3),
                 embed_ms=round(emed, 4), backward_over_embed=round(bmed / emed, 3),
                 forward="emb_cutlinks + emb_mex_force", backward="emb_mex_force_backward + emb_cutlinks_backward")
+
+
+def ablation_leg(P, verts, tris, w, lattice, reps=3):
+    """The paper's binning variants (Sec. 4: 'n', 'r', 'rc') on the bench workload: 'rc'
+    = exact x-line filter and compacted id list (the default), 'r' = the filter's flags
+    tested by the voxelizer without compaction, 'n' = no filter.  Median CUDA-event time
+    of emb_bin + emb_voxelize per level, and the triangles the filter keeps per level."""
+    import torch
+    stream = torch.cuda.current_stream()
+    out, kept = {}, []
+    for name, mode in (("rc", P.EMB_BIN_FILTER_COMPACT), ("r", P.EMB_BIN_FILTER_ONLY), ("n", P.EMB_BIN_NO_FILTER)):
+        runs = []
+        for rep in range(reps + 1):
+            mesh = P.emb_mesh_create(verts, tris, w.R, check_watertight=False)
+            forest = P.emb_forest_root(w.R, w.levels)
+            ev, keep = [], []
+            for L in range(w.levels + 1):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                bins = P.emb_bin(mesh, forest, L, lattice, mode=mode)
+                P.emb_voxelize(forest, bins, L)
+                b.record(stream)
+                ev.append((a, b))
+                if L < w.levels:
+                    P.emb_forest_refine(forest, L, P.emb_refine_flags(forest, bins, L, w.band))
+                keep.append(bins)
+            torch.cuda.synchronize()
+            if rep > 0:
+                runs.append([a.elapsed_time(b) for a, b in ev])
+            if mode == P.EMB_BIN_FILTER_COMPACT and rep == reps:
+                kept = [P.emb_bins_stats(bb)[0] for bb in keep]
+            for bb in keep:
+                bb.close()
+        per_level = [statistics.median(r[L] for r in runs) for L in range(w.levels + 1)]
+        out[name] = dict(ms_per_level=[round(x, 4) for x in per_level], ms_total=round(sum(per_level), 4))
+    out["kept_per_level"] = kept
+    out["triangles"] = len(tris)
+    out["timing"] = "emb_bin + emb_voxelize per level, CUDA events, median of %d" % reps
+    return out
 
 
 def batch_leg(P, reps=5):

@@ -150,6 +150,20 @@ emb_status emb_forest_masks(emb_forest f, int32_t level, uint64_t *d_out, void *
  * rebuilds them with the exact size before using them.
  * Errors: EMB_ERR_BAD_INPUT, EMB_ERR_STATE (level missing, mesh/forest frame mismatch). */
 emb_status emb_bin(emb_mesh m, emb_forest f, int32_t level, int32_t lattice, void *stream, emb_bins *out);
+
+/* emb_bin with a choice of the filter step, for the ablation of Sec. 4 (the
+ * paper's binning variants 'n', 'r' and 'rc'):
+ *   EMB_BIN_FILTER_COMPACT  exact x-line filter, compacted id list (emb_bin);
+ *   EMB_BIN_FILTER_ONLY     the same filter, kept as per-triangle flags that the
+ *                           voxelizer tests, without compaction ('r');
+ *   EMB_BIN_NO_FILTER       every triangle goes to the voxelizer ('n').
+ * The filter is exact, so all three give the same masks; only the work differs.
+ * Errors: those of emb_bin, and EMB_ERR_BAD_INPUT for an unknown mode. */
+#define EMB_BIN_FILTER_COMPACT 0
+#define EMB_BIN_FILTER_ONLY 1
+#define EMB_BIN_NO_FILTER 2
+emb_status emb_bin_ex(emb_mesh m, emb_forest f, int32_t level, int32_t lattice, int32_t mode, void *stream,
+                      emb_bins *out);
 void emb_bins_destroy(emb_bins b);
 
 /* Host statistics: filtered triangles and (at the finest level) bin entries.

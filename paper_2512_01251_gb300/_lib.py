@@ -34,6 +34,7 @@ SIGNATURES = {
     "emb_forest_neighbors": (I32, [P, I32, P, P]),
     "emb_forest_masks": (I32, [P, I32, P, P]),
     "emb_bin": (I32, [P, P, I32, I32, P, ctypes.POINTER(P)]),
+    "emb_bin_ex": (I32, [P, P, I32, I32, I32, P, ctypes.POINTER(P)]),
     "emb_bins_destroy": (None, [P]),
     "emb_bins_stats": (I32, [P, PI64, PI64]),
     "emb_bins_copy": (I32, [P, P, P, P, P]),

@@ -228,7 +228,7 @@ static emb_status enqueue_mesh(BMesh &B, int tri_block, cudaStream_t s)
         const LevelGeom g = level_geom(&B.geo, L);
         BTRY(emb_enq_filter(rec, T, g, B.flag, B.pos, BL.flist, B.tmp, tri_block, s));
         BTRY(emb_expect_u32(B.pos + T, (uint64_t)BL.nf, s));
-        BTRY(emb_enq_voxelize(rec, T, BL.flist, BL.nf, B.pos + T, g, lv, B.s_acc, B.p_acc, B.bq, tri_block, s));
+        BTRY(emb_enq_voxelize(rec, T, BL.flist, BL.nf, B.pos + T, nullptr, g, lv, B.s_acc, B.p_acc, B.bq, tri_block, s));
         if (L < B.Lf) {
             const long long dil = emb_refine_dilation(&B.geo, L, B.band);
             if (dil < 0) return EMB_ERR_RANGE;

@@ -382,7 +382,8 @@ static emb_status bin_finest(emb_bins b, uint64_t list_cap, uint64_t ent_cap, cu
         cudaMallocAsync(&tmp, emb_scan_tmp_words(lv.n) * sizeof(uint64_t), s) != cudaSuccess ||
         cudaMallocAsync((void **)&list, 256 + a_bs + (size_t)list_cap * sizeof(uint32_t), s) != cudaSuccess)
         rc = EMB_ERR_CUDA;
-    if (rc == EMB_OK && !b->off && cudaMalloc(&b->off, (lv.n + 1) * sizeof(uint32_t)) != cudaSuccess) rc = EMB_ERR_CUDA;
+    if (rc == EMB_OK && !b->off && cudaMallocAsync(&b->off, (lv.n + 1) * sizeof(uint32_t), s) != cudaSuccess)
+        rc = EMB_ERR_CUDA;
     if (rc == EMB_OK && b->ent_cap != ent_cap) {
         if (b->ent) cudaFreeAsync(b->ent, s);
         b->ent = nullptr;
@@ -407,14 +408,29 @@ static emb_status bin_finest(emb_bins b, uint64_t list_cap, uint64_t ent_cap, cu
     return rc;
 }
 
+// Every triangle id (the list of the modes without compaction), and its count.
+__global__ void k_iota(uint32_t *__restrict__ out, int64_t n, uint32_t *__restrict__ count)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (uint32_t)i;
+    if (i == 0) *count = (uint32_t)n;
+}
+
+extern "C" emb_status emb_bin(emb_mesh m, emb_forest f, int32_t level, int32_t lattice, void *stream, emb_bins *out)
+{
+    return emb_bin_ex(m, f, level, lattice, EMB_BIN_FILTER_COMPACT, stream, out);
+}
+
 // No host synchronisation: the filtered count and, at the finest level, the bin
 // sizes stay on the device until emb_bins_sync reads them.  The finest bins start
 // from a pair list of 4 T + 2^20 entries; if that proved too small, emb_bins_sync
 // (called by every consumer that needs complete bins) redoes them exactly.
-extern "C" emb_status emb_bin(emb_mesh m, emb_forest f, int32_t level, int32_t lattice, void *stream, emb_bins *out)
+extern "C" emb_status emb_bin_ex(emb_mesh m, emb_forest f, int32_t level, int32_t lattice, int32_t mode, void *stream,
+                                 emb_bins *out)
 {
     if (!m || !f || !out) return EMB_ERR_BAD_INPUT;
     if (lattice != 19 && lattice != 27) return EMB_ERR_BAD_INPUT;
+    if (mode != EMB_BIN_FILTER_COMPACT && mode != EMB_BIN_FILTER_ONLY && mode != EMB_BIN_NO_FILTER) return EMB_ERR_BAD_INPUT;
     if (level < 0 || level > f->top) return EMB_ERR_STATE;
     if (m->R != f->R) return EMB_ERR_STATE;
     *out = nullptr;
@@ -431,24 +447,36 @@ extern "C" emb_status emb_bin(emb_mesh m, emb_forest f, int32_t level, int32_t l
     uint32_t *flag = nullptr, *pos = nullptr;
     uint64_t *tmp = nullptr;
     // step 1: exact x-line filter, compacted in ascending order
+    // every buffer is stream-ordered on s: the bins are freed the same way, without a
+    // device synchronisation (the flags of the mode without compaction live in the bins)
     if (cudaMallocAsync(&flag, (m->T + 1) * sizeof(uint32_t), s) != cudaSuccess ||
         cudaMallocAsync(&pos, (m->T + 1) * sizeof(uint32_t), s) != cudaSuccess ||
         cudaMallocAsync(&tmp, emb_scan_tmp_words(m->T) * sizeof(uint64_t), s) != cudaSuccess ||
-        cudaMalloc(&b->flist, (m->T + 1) * sizeof(uint32_t)) != cudaSuccess ||
-        cudaMalloc(&b->dcount, 16) != cudaSuccess) {
+        cudaMallocAsync(&b->flist, (m->T + 1) * sizeof(uint32_t), s) != cudaSuccess ||
+        cudaMallocAsync(&b->dcount, 16, s) != cudaSuccess) {
         emb_bins_destroy(b);
         return EMB_ERR_CUDA;
     }
     EMB_CUDA_TRY(cudaMemsetAsync(b->dcount, 0, 16, s));
-    rc = emb_enq_filter(m->rec, m->T, g, flag, pos, b->flist, tmp, 256, s);
-    if (rc == EMB_OK && cudaMemcpyAsync(b->dcount, pos + m->T, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-        rc = EMB_ERR_CUDA;
+    if (mode == EMB_BIN_FILTER_COMPACT) {
+        rc = emb_enq_filter(m->rec, m->T, g, flag, pos, b->flist, tmp, 256, s);
+        if (rc == EMB_OK && cudaMemcpyAsync(b->dcount, pos + m->T, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            rc = EMB_ERR_CUDA;
+    } else {
+        // ablations: the filter flags kept per triangle without compaction, or no filter
+        if (mode == EMB_BIN_FILTER_ONLY) {
+            rc = emb_enq_filter(m->rec, m->T, g, flag, pos, b->flist, tmp, 256, s);
+            b->keep = flag;
+            flag = nullptr;
+        }
+        if (rc == EMB_OK) EMB_LAUNCH((k_iota), emb_grid(m->T, 256), 256, 0, s)(b->flist, m->T, (uint32_t *)b->dcount);
+    }
     // steps 2-9 at the finest level: CSR bins of link-relevant triangles per block
     if (rc == EMB_OK && level == f->max_level && lv.n > 0) {
         const uint64_t cap = (uint64_t)4 * m->T + (1 << 20);
         rc = bin_finest(b, cap, cap, s);
     }
-    cudaFreeAsync(flag, s);
+    if (flag) cudaFreeAsync(flag, s);
     cudaFreeAsync(pos, s);
     cudaFreeAsync(tmp, s);
     if (rc == EMB_OK && cudaGetLastError() != cudaSuccess) rc = EMB_ERR_CUDA;
@@ -485,14 +513,14 @@ emb_status emb_bins_sync(emb_bins b)
     return EMB_OK;
 }
 
+// Stream-ordered frees on the stream of emb_bin: no device synchronisation, so a
+// pipeline that drops each level's bins keeps the GPU busy.
 extern "C" void emb_bins_destroy(emb_bins b)
 {
     if (!b) return;
-    cudaDeviceSynchronize();
-    if (b->flist) cudaFree(b->flist);
-    if (b->off) cudaFree(b->off);
-    if (b->ent) cudaFree(b->ent);
-    if (b->dcount) cudaFree(b->dcount);
+    void *bufs[] = {b->flist, b->off, b->ent, b->dcount, b->keep};
+    for (void *p : bufs)
+        if (p) cudaFreeAsync(p, b->s);
     delete b;
 }
 

@@ -114,6 +114,7 @@ struct emb_bins_s {
     int32_t level, lattice;
     cudaStream_t s = nullptr;   // stream of emb_bin (for reading the counts back)
     uint32_t *flist = nullptr;  // filtered triangle ids (ascending), T + 1 entries
+    uint32_t *keep = nullptr;   // filter mode without compaction: per-triangle filter flags
     uint32_t *off = nullptr;    // finest level only: CSR offsets (n_blocks + 1)
     uint32_t *ent = nullptr;    // triangle ids, ent_cap entries
     uint64_t ent_cap = 0;
@@ -186,8 +187,8 @@ emb_status emb_enq_bin_pairs(const int4 *rec, int64_t T, LevelGeom g, const EmbL
 emb_status emb_enq_bin_scatter(const uint2 *list_bs, const uint32_t *list_tri, const unsigned long long *list_n,
                                uint64_t list_cap, const uint32_t *off, uint32_t *ent, uint64_t ent_cap, cudaStream_t s);
 emb_status emb_enq_voxelize(const int4 *rec, int64_t T, const uint32_t *flist, int64_t nf, const uint32_t *d_nf,
-                            LevelGeom g, const EmbLevel &lv, unsigned long long *s_acc, unsigned int *p_acc,
-                            const EmbBigQ &Q, int block, cudaStream_t s);
+                            const uint32_t *keep, LevelGeom g, const EmbLevel &lv, unsigned long long *s_acc,
+                            unsigned int *p_acc, const EmbBigQ &Q, int block, cudaStream_t s);
 emb_status emb_enq_refine(const int4 *rec, int64_t T, LevelGeom g, long long dil, const EmbLevel &lv, uint8_t *flags,
                           unsigned long long *fbits, const EmbBigQ &Q, cudaStream_t s);
 long long emb_refine_dilation(const emb_forest_s *f, int L, int band);

@@ -97,7 +97,7 @@ __device__ __forceinline__ void vox_line(const VoxTri &V, const LevelGeom &g, co
 }
 
 __global__ void k_vox(const int4 *__restrict__ rec, int64_t T, const uint32_t *__restrict__ flist, int64_t nf,
-                      const uint32_t *__restrict__ d_nf, LevelGeom g, EmbLookup lk,
+                      const uint32_t *__restrict__ d_nf, const uint32_t *__restrict__ keep, LevelGeom g, EmbLookup lk,
                       unsigned long long *__restrict__ s_acc, unsigned int *__restrict__ p_acc, EmbBigQ Q, int *st)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -105,6 +105,7 @@ __global__ void k_vox(const int4 *__restrict__ rec, int64_t T, const uint32_t *_
     if (i >= nf || (d_nf && i >= (int64_t)*d_nf)) return;
     const uint32_t t = flist[i];
     if ((int64_t)t >= T) return;
+    if (keep && !keep[t]) return;  // filtered out, the list not compacted
     VoxTri V;
     if (!vox_setup(rec, t, g, V)) return;
     const unsigned long long items = vox_items(V);
@@ -173,8 +174,8 @@ __global__ void k_xscan(const uint64_t *__restrict__ key, int64_t n, const unsig
 
 // Enqueue only: s_acc (n uint64) and p_acc (n uint32) are scratch; writes lv.mask.
 emb_status emb_enq_voxelize(const int4 *rec, int64_t T, const uint32_t *flist, int64_t nf, const uint32_t *d_nf,
-                            LevelGeom g, const EmbLevel &lv, unsigned long long *s_acc, unsigned int *p_acc,
-                            const EmbBigQ &Q, int block, cudaStream_t s)
+                            const uint32_t *keep, LevelGeom g, const EmbLevel &lv, unsigned long long *s_acc,
+                            unsigned int *p_acc, const EmbBigQ &Q, int block, cudaStream_t s)
 {
     int *st = emb_status_word();
     if (!st) return EMB_ERR_CUDA;
@@ -184,7 +185,7 @@ emb_status emb_enq_voxelize(const int4 *rec, int64_t T, const uint32_t *flist, i
     if (nf > 0) {
         const EmbLookup lk = emb_lookup_of(lv);
         if (Q.cap) EMB_CUDA_TRY(cudaMemsetAsync(Q.n, 0, sizeof(unsigned long long), s));
-        EMB_LAUNCH((k_vox), emb_grid(nf, block), block, 0, s)(rec, T, flist, nf, d_nf, g, lk, s_acc, p_acc, Q, st);
+        EMB_LAUNCH((k_vox), emb_grid(nf, block), block, 0, s)(rec, T, flist, nf, d_nf, keep, g, lk, s_acc, p_acc, Q, st);
         if (Q.cap) EMB_LAUNCH((k_vox_big), EMB_BIG_GRID, EMB_BIG_BLOCK, 0, s)(rec, g, lk, s_acc, p_acc, Q, st);
     }
     EMB_LAUNCH((k_xscan), emb_grid(lv.n, 256), 256, 0, s)(lv.key, lv.n, s_acc, p_acc, lv.mask);
@@ -212,8 +213,8 @@ extern "C" emb_status emb_voxelize(emb_forest f, emb_bins b, int32_t level, uint
     emb_status rc = emb_bigq_alloc(Q, b->m->T, s);
     if (rc != EMB_OK) return rc;
     // the filtered count stays on the device: the grid covers every triangle and stops at it
-    rc = emb_enq_voxelize(b->m->rec, b->m->T, b->flist, b->known ? b->nf : b->m->T, (const uint32_t *)b->dcount, g, lv,
-                          s_acc, p_acc, Q, 128, s);
+    rc = emb_enq_voxelize(b->m->rec, b->m->T, b->flist, b->known ? b->nf : b->m->T, (const uint32_t *)b->dcount, b->keep,
+                          g, lv, s_acc, p_acc, Q, 128, s);
     emb_bigq_free(Q, s);
     if (rc != EMB_OK) return rc;
     if (d_solid_mask)

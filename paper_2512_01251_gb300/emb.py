@@ -167,9 +167,18 @@ def emb_forest_masks(forest: Forest, level: int, stream=None) -> torch.Tensor:
     return out
 
 
-def emb_bin(mesh: Mesh, forest: Forest, level: int, lattice: int = 19, stream=None) -> Bins:
+EMB_BIN_FILTER_COMPACT, EMB_BIN_FILTER_ONLY, EMB_BIN_NO_FILTER = 0, 1, 2
+
+
+def emb_bin(mesh: Mesh, forest: Forest, level: int, lattice: int = 19, stream=None,
+            mode: int = EMB_BIN_FILTER_COMPACT) -> Bins:
+    """mode: EMB_BIN_FILTER_COMPACT (default), or the ablations EMB_BIN_FILTER_ONLY / EMB_BIN_NO_FILTER."""
     h = ctypes.c_void_p()
-    _check(load().emb_bin(mesh.h, forest.h, int(level), int(lattice), _stream(stream), ctypes.byref(h)), "emb_bin")
+    if mode == EMB_BIN_FILTER_COMPACT:
+        _check(load().emb_bin(mesh.h, forest.h, int(level), int(lattice), _stream(stream), ctypes.byref(h)), "emb_bin")
+    else:
+        _check(load().emb_bin_ex(mesh.h, forest.h, int(level), int(lattice), int(mode), _stream(stream),
+                                 ctypes.byref(h)), "emb_bin_ex")
     b = Bins(h, keep=(mesh, forest))
     b.level = int(level)
     return b
@@ -306,7 +315,7 @@ class Embedding:
 
 def embed(verts: torch.Tensor, tris: torch.Tensor, R: int, levels: int, band: int = 2, lattice: int = 19,
           check_watertight: bool = True, mesh: Mesh | None = None, keep_bins: bool = False,
-          check_status: bool = True, stream=None) -> Embedding:
+          check_status: bool = True, stream=None, bin_mode: int = EMB_BIN_FILTER_COMPACT) -> Embedding:
     """Embed a closed mesh into a forest with root R^3 blocks and levels 0..levels.
 
     Per level: emb_bin, emb_voxelize, then (below the finest level)
@@ -318,7 +327,7 @@ def embed(verts: torch.Tensor, tris: torch.Tensor, R: int, levels: int, band: in
     forest = emb_forest_root(R, levels, stream)
     E = Embedding(mesh=mesh, forest=forest, levels=levels, lattice=lattice)
     for L in range(levels + 1):
-        bins = emb_bin(mesh, forest, L, lattice, stream)
+        bins = emb_bin(mesh, forest, L, lattice, stream, mode=bin_mode)
         E.masks.append(emb_voxelize(forest, bins, L, stream=stream))
         if L < levels:
             fl = emb_refine_flags(forest, bins, L, band, stream=stream)
