@@ -10,6 +10,9 @@ Parity status of each function (see also the module functions' docstrings):
   * ``build_forest``, ``masks``, ``refine_flags``, ``cut_links`` — pinned by
     closed forms, half-space representations, clipping and invariants
     (tests/test_oracle_pins.py).
+  * ``paper_flags``, ``build_forest_paper``, ``n_prop`` (the paper's block-layer
+    refinement rules) — pinned by the closed form of a block-aligned box and the
+    2:1 invariant (tests/test_oracle_paper_policy.py).
   * ``mex_force``/``mex_force_dq``/``dq_dverts`` — the derivative formulas are
     pinned by finite differences and a closed form; the Bouzidi branch rule for
     a missing interpolation partner and the momentum-exchange sign convention
@@ -241,6 +244,104 @@ def build_forest(tri9, R: int, levels: int, band: int):
     return blocks, flags
 
 
+# --------------------------------------------------------------------------- #
+# The paper's refinement policy (Sec. 3.4, "Refinement Flagging and Propagation")
+# --------------------------------------------------------------------------- #
+def n_prop(d_spec: float, R: int) -> int:
+    """Eq. N_prop: 1 + floor((1/2^L) d_spec / (sqrt(2) Dx_{b,L})) with Dx_{b,L} = 4 Dx_L the
+    block length.  With Dx_L = Dx_0 / 2^L the 2^L factors cancel, so the count is the
+    same on every level: 1 + floor(d_spec R / sqrt(2)) for d_spec in units of the unit
+    domain (Dx_{b,0} = 1 / R)."""
+    return 1 + int(np.floor((float(d_spec) * R) / np.sqrt(2.0)))
+
+
+def _nbr_offsets() -> np.ndarray:
+    return np.array([(dx, dy, dz) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)
+                     if (dx, dy, dz) != (0, 0, 0)], dtype=np.int64)
+
+
+def paper_flags(blocks: np.ndarray, mask_words: np.ndarray, nb: int, L: int, nprop: int) -> np.ndarray:
+    """Refinement flags of one level under the paper's block-layer rules, step by step:
+
+    - a block is solid if one of its cells is solid and fully fluid otherwise;
+    - solid-boundary: a solid block with a fully fluid neighbour (among the blocks of
+      the level, 26-neighbourhood); marked;
+    - every block next to a solid-boundary block is marked (the fluid ones are the
+      solid-adjacent blocks);
+    - nprop rounds of propagation, each reading the marks of the previous round
+      (ping-pong): an unmarked block next to a marked one is marked if it is fully
+      fluid, or solid and this is the first round;
+    - a block on the refinement interface (an in-domain neighbour position without a
+      block of this level, L > 0) is never marked: refining it would break 2:1.
+    Returns a uint8 flag per block (blocks sorted by z, y, x)."""
+    blocks = np.asarray(blocks, dtype=np.int64)
+    n = len(blocks)
+    idx = {tuple(b): i for i, b in enumerate(blocks.tolist())}
+    solid = np.asarray(mask_words, dtype=np.uint64) != 0
+    off = _nbr_offsets()
+    nbr = np.full((n, 26), -1, dtype=np.int64)
+    eligible = np.ones(n, dtype=bool)
+    for i, b in enumerate(blocks.tolist()):
+        for d, o in enumerate(off.tolist()):
+            q = (b[0] + o[0], b[1] + o[1], b[2] + o[2])
+            if all(0 <= c < nb for c in q):
+                j = idx.get(q, -1)
+                nbr[i, d] = j
+                if j < 0 and L > 0:
+                    eligible[i] = False
+
+    def any_nbr(sel: np.ndarray) -> np.ndarray:
+        out = np.zeros(n, dtype=bool)
+        for d in range(26):
+            j = nbr[:, d]
+            ok = j >= 0
+            out[ok] |= sel[j[ok]]
+        return out
+
+    fluid_b = ~solid
+    sb = solid & any_nbr(fluid_b)
+    marked = sb & eligible
+    marked = marked | (any_nbr(sb) & eligible)
+    for r in range(nprop):
+        scope = fluid_b | (solid if r == 0 else np.zeros(n, dtype=bool))
+        marked = marked | (any_nbr(marked) & scope & eligible)
+    return marked.astype(np.uint8)
+
+
+def build_forest_paper(tri9, R: int, levels: int, d_spec: float):
+    """Top-down forest under the paper's rules: per level the exact masks, then
+    paper_flags.  Returns blocks per level, flags per level (< finest), masks per level."""
+    blocks = [root_blocks(R)]
+    flags, m = [], []
+    np_ = n_prop(d_spec, R)
+    for L in range(levels + 1):
+        m.append(masks(tri9, R, L, blocks[L]))
+        if L == levels:
+            break
+        f = paper_flags(blocks[L], m[L], R << L, L, np_)
+        flags.append(f)
+        blocks.append(children(blocks[L], f))
+    return blocks, flags, m
+
+
+def balanced_2to1(blocks_by_level, R: int) -> bool:
+    """2:1 balance: the 26 neighbour positions of every block of level L+1 are covered by
+    blocks of level L+1 or by their parent positions at level L (inside the domain)."""
+    off = _nbr_offsets()
+    for L in range(1, len(blocks_by_level)):
+        fine = {tuple(b) for b in blocks_by_level[L].tolist()}
+        coarse = {tuple(b) for b in blocks_by_level[L - 1].tolist()}
+        nb = R << L
+        for b in blocks_by_level[L].tolist():
+            for o in off.tolist():
+                q = (b[0] + o[0], b[1] + o[1], b[2] + o[2])
+                if not all(0 <= c < nb for c in q):
+                    continue
+                if q not in fine and (q[0] // 2, q[1] // 2, q[2] // 2) not in coarse:
+                    return False
+    return True
+
+
 def cell_centres(R: int, L: int, blocks: np.ndarray) -> np.ndarray:
     """(n*64, 3) integer centres; cell t = x + 4 y + 16 z inside each block."""
     _, k = frame(R)
@@ -266,13 +367,16 @@ def masks(tri9, R, L, blocks, dir: int = 1) -> np.ndarray:
     return pack_masks(solid(tri9, cell_centres(R, L, blocks), dir))
 
 
-def cut_links(tri9, R, levels, blocks_f, mask_f, lattice: int):
+def cut_links(tri9, R, levels, blocks_f, mask_f, lattice: int, existing_only: bool = False):
     """Flat cut-link table at the finest level, sorted by (cell, dir).
 
     For every fluid cell P and every lattice direction i != 0 whose neighbour
     P + h c_i is solid (decided by the same point predicate; a neighbour outside
     the domain is fluid): q = min over crossed triangles of the crossing
-    parameter t in [0, 1].  Returns dict(cell, dir, q, tri, ncross).
+    parameter t in [0, 1].  With existing_only, a neighbour cell whose block is
+    not in the finest level counts as fluid (the paper identifies boundary cells
+    from the masks of neighbouring blocks of the level).  Returns dict(cell, dir,
+    q, tri, ncross).
     """
     h = h_units(R, levels)
     dom = domain_units(R)
@@ -285,6 +389,10 @@ def cut_links(tri9, R, levels, blocks_f, mask_f, lattice: int):
     cand_dir = np.tile(dirs, len(cells))
     Q = P[cand_cell] + h * C[cand_dir]
     inside = np.all((Q > 0) & (Q < dom), axis=1)
+    if existing_only:
+        present = {tuple(b) for b in np.asarray(blocks_f, dtype=np.int64).tolist()}
+        qb = (Q // (4 * h)).astype(np.int64)
+        inside &= np.array([tuple(x) in present for x in qb.tolist()], dtype=bool)
     s = np.zeros(len(Q), dtype=np.uint8)
     if np.any(inside):
         uq, inv = np.unique(Q[inside], axis=0, return_inverse=True)
@@ -296,13 +404,19 @@ def cut_links(tri9, R, levels, blocks_f, mask_f, lattice: int):
     return dict(cell=cell.astype(np.int64), dir=d.astype(np.int64), q=q, tri=arg, ncross=ncross)
 
 
-def embed(verts, tris, R: int, levels: int, band: int = 2, lattice: int = 19):
-    """Whole path: forest, masks per level, refine flags, cut links."""
+def embed(verts, tris, R: int, levels: int, band: int = 2, lattice: int = 19, d_spec: float | None = None):
+    """Whole path: forest, masks per level, refine flags, cut links.  With d_spec (a
+    near-wall distance in units of the unit domain) the forest follows the paper's
+    block-layer refinement rules instead of the exact distance rule of `band`."""
     X = int_coords(verts, R)
     tri9 = tri_coords(X, tris)
-    blocks, flags = build_forest(tri9, R, levels, band)
-    m = [masks(tri9, R, L, blocks[L]) for L in range(levels + 1)]
-    lk = cut_links(tri9, R, levels, blocks[levels], m[levels], lattice)
+    if d_spec is None:
+        blocks, flags = build_forest(tri9, R, levels, band)
+        m = [masks(tri9, R, L, blocks[L]) for L in range(levels + 1)]
+        lk = cut_links(tri9, R, levels, blocks[levels], m[levels], lattice)
+    else:
+        blocks, flags, m = build_forest_paper(tri9, R, levels, d_spec)
+        lk = cut_links(tri9, R, levels, blocks[levels], m[levels], lattice, existing_only=True)
     return dict(X=X, tri9=tri9, blocks=blocks, flags=flags, masks=m, links=lk)
 
 

@@ -101,7 +101,7 @@ extern "C" emb_status emb_forest_root(int32_t R, int32_t max_level, void *stream
     EmbLevel &lv = f->lv[0];
     lv.n = (int64_t)R * R * R;
     lv.nb_axis = R;
-    if (cudaMalloc(&lv.key, lv.n * sizeof(uint64_t)) != cudaSuccess) {
+    if (cudaMallocAsync(&lv.key, lv.n * sizeof(uint64_t), s) != cudaSuccess) {
         emb_forest_destroy(f);
         return EMB_ERR_CUDA;
     }
@@ -115,6 +115,8 @@ extern "C" emb_status emb_forest_root(int32_t R, int32_t max_level, void *stream
     return EMB_OK;
 }
 
+// Level arrays come from the stream-ordered pool of the calls that built them; the
+// teardown synchronises the device once and returns them all.
 extern "C" void emb_forest_destroy(emb_forest f)
 {
     if (!f) return;
@@ -185,7 +187,7 @@ extern "C" emb_status emb_forest_refine(emb_forest f, int32_t level, const uint8
     EMB_CUDA_TRY(cudaStreamSynchronize(s));
     C.n = 8 * (int64_t)F;
     C.nb_axis = P.nb_axis * 2;
-    EMB_CUDA_TRY(cudaMalloc(&C.key, (C.n + 1) * sizeof(uint64_t)));
+    EMB_CUDA_TRY(cudaMallocAsync(&C.key, (C.n + 1) * sizeof(uint64_t), s));
     rc = emb_enq_children(P, d_flags, rank, C.key, C.n, false, s);
     if (rc != EMB_OK) return rc;
     EMB_CUDA_TRY(cudaFreeAsync(cnt, s));

@@ -204,7 +204,7 @@ extern "C" emb_status emb_voxelize(emb_forest f, emb_bins b, int32_t level, uint
         lv.mask_valid = 1;
         return EMB_OK;
     }
-    if (!lv.mask) EMB_CUDA_TRY(cudaMalloc(&lv.mask, lv.n * sizeof(uint64_t)));
+    if (!lv.mask) EMB_CUDA_TRY(cudaMallocAsync(&lv.mask, lv.n * sizeof(uint64_t), s));
     unsigned long long *s_acc = nullptr;
     unsigned int *p_acc = nullptr;
     EMB_CUDA_TRY(cudaMallocAsync(&s_acc, lv.n * sizeof(unsigned long long), s));
