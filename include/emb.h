@@ -185,8 +185,9 @@ emb_status emb_bins_copy(emb_bins b, uint32_t *d_filtered, uint32_t *d_off, uint
  * then completes every line (the role of the external propagation of Alg. 4).
  * Writes one uint64 per level block (bit t = cell t solid) into d_solid_mask
  * (may be NULL) and keeps a copy in the forest.
- * Errors: EMB_ERR_STATE (bins of another level, missing level);
- * device status EMB_ERR_STATE if a crossing falls outside every block. */
+ * Exact for any forest: a crossing inside a block position the level does not have
+ * (a region left coarser) is carried along its row to the blocks on its left.
+ * Errors: EMB_ERR_STATE (bins of another level, missing level). */
 emb_status emb_voxelize(emb_forest f, emb_bins b, int32_t level, uint64_t *d_solid_mask, void *stream);
 
 /* -------------------------------------------------------------- refine ---- */
@@ -199,6 +200,24 @@ emb_status emb_voxelize(emb_forest f, emb_bins b, int32_t level, uint64_t *d_sol
  * Errors: EMB_ERR_BAD_INPUT (band < 1), EMB_ERR_STATE, EMB_ERR_RANGE. */
 emb_status emb_refine_flags(emb_forest f, emb_bins b, int32_t level, int32_t band, uint8_t *d_flags,
                             void *stream);
+
+/* The paper's own refinement rules for `level` < max_level (Sec. 3.4, "Refinement
+ * Flagging and Propagation", Eq. N_prop), an alternative to emb_refine_flags.
+ * From the level's masks (emb_voxelize first): a block is solid if one of its cells
+ * is solid, fully fluid otherwise; solid blocks with a fully fluid neighbour form the
+ * solid boundary and are marked; every block next to one is marked; then
+ * N_prop = 1 + floor(d_spec R / sqrt(2)) propagation rounds (Eq. N_prop with the
+ * block length 1/(R 2^L): its 2^L factors cancel) mark each unmarked block next to a
+ * marked one, fully fluid blocks in every round and solid blocks in the first only
+ * (two layers into the body).  Blocks on the refinement interface (an in-domain
+ * neighbour position without a block of the level) are never marked.  d_spec:
+ * near-wall distance in units of the unit domain, >= 0.  Unlike the distance rule,
+ * unrefined blocks may contain surface; the voxelizer and the cut links handle that
+ * (a neighbour cell in a missing block counts as fluid).  d_flags: one uint8 per
+ * level block, overwritten.  Needs no bins.
+ * Errors: EMB_ERR_BAD_INPUT (d_spec negative or not finite, null d_flags),
+ * EMB_ERR_STATE (level not the finest built, or not voxelized). */
+emb_status emb_refine_flags_paper(emb_forest f, int32_t level, double d_spec, uint8_t *d_flags, void *stream);
 
 /* ------------------------------------------------------------ cut links ---- */
 /* Number of cut links at the finest level for `lattice` (19 or 27): pairs

@@ -44,7 +44,7 @@ struct BMesh {
     // scratch sized for the largest level / the triangle count
     uint32_t *flag = nullptr, *pos = nullptr;       // T + 1
     unsigned long long *s_acc = nullptr;            // max blocks
-    unsigned int *p_acc = nullptr;
+    unsigned int *p_acc = nullptr, *t_acc = nullptr;
     uint32_t *cnt = nullptr, *rank = nullptr;       // max blocks + 1
     uint32_t *pc = nullptr;                         // max bitmap words + 1
     uint64_t *tmp = nullptr;                        // scan scratch
@@ -187,6 +187,7 @@ static emb_status alloc_mesh(BMesh &B)
     BTRY(balloc(B, &B.pos, T + 1));
     BTRY(balloc(B, &B.s_acc, nmax));
     BTRY(balloc(B, &B.p_acc, nmax));
+    BTRY(balloc(B, &B.t_acc, nmax));
     BTRY(balloc(B, &B.cnt, nmax + 1));
     BTRY(balloc(B, &B.rank, nmax + 1));
     BTRY(balloc(B, &B.pc, wmax + 1));
@@ -228,7 +229,7 @@ static emb_status enqueue_mesh(BMesh &B, int tri_block, cudaStream_t s)
         const LevelGeom g = level_geom(&B.geo, L);
         BTRY(emb_enq_filter(rec, T, g, B.flag, B.pos, BL.flist, B.tmp, tri_block, s));
         BTRY(emb_expect_u32(B.pos + T, (uint64_t)BL.nf, s));
-        BTRY(emb_enq_voxelize(rec, T, BL.flist, BL.nf, B.pos + T, nullptr, g, lv, B.s_acc, B.p_acc, B.bq, tri_block, s));
+        BTRY(emb_enq_voxelize(rec, T, BL.flist, BL.nf, B.pos + T, nullptr, g, lv, B.s_acc, B.p_acc, B.t_acc, B.bq, tri_block, s));
         if (L < B.Lf) {
             const long long dil = emb_refine_dilation(&B.geo, L, B.band);
             if (dil < 0) return EMB_ERR_RANGE;

@@ -909,8 +909,15 @@ extern "C" emb_status emb_cutlinks(emb_forest f, emb_bins b, int32_t lattice, in
                                    int32_t *d_tri, int64_t capacity, int64_t *d_count, void *stream)
 {
     if (!f || !b || (lattice != 19 && lattice != 27) || capacity < 0) return EMB_ERR_BAD_INPUT;
-    if (b->f != f || b->level != f->max_level || !b->off) return EMB_ERR_STATE;
+    if (b->f != f || b->level != f->max_level || f->top != f->max_level) return EMB_ERR_STATE;
     cudaStream_t s = emb_stream(stream);
+    if (f->lv[f->max_level].n == 0) {
+        // an empty finest level (nothing was refined down to it): no links
+        if (d_count) EMB_CUDA_TRY(cudaMemsetAsync(d_count, 0, sizeof(int64_t), s));
+        f->n_links = 0;
+        return EMB_OK;
+    }
+    if (!b->off) return EMB_ERR_STATE;
     {
         // complete bins (a pair list that proved too small is redone here)
         const emb_status rb = emb_bins_sync(b);

@@ -23,16 +23,6 @@ __global__ void k_flags_u32(const uint8_t *__restrict__ f, int64_t n, uint32_t *
     if (i < n) out[i] = f[i] ? 1u : 0u;
 }
 
-__device__ __forceinline__ int64_t lower_bound_u64(const uint64_t *__restrict__ a, int64_t n, uint64_t v)
-{
-    int64_t lo = 0, hi = n;
-    while (lo < hi) {
-        int64_t mid = (lo + hi) >> 1;
-        if (a[mid] < v) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
-}
 
 __global__ void k_make_children(const uint64_t *__restrict__ key, int64_t n, const uint8_t *__restrict__ flags,
                                 const uint32_t *__restrict__ rank, uint64_t *__restrict__ ckey, int64_t Cn)

@@ -188,7 +188,7 @@ emb_status emb_enq_bin_scatter(const uint2 *list_bs, const uint32_t *list_tri, c
                                uint64_t list_cap, const uint32_t *off, uint32_t *ent, uint64_t ent_cap, cudaStream_t s);
 emb_status emb_enq_voxelize(const int4 *rec, int64_t T, const uint32_t *flist, int64_t nf, const uint32_t *d_nf,
                             const uint32_t *keep, LevelGeom g, const EmbLevel &lv, unsigned long long *s_acc,
-                            unsigned int *p_acc, const EmbBigQ &Q, int block, cudaStream_t s);
+                            unsigned int *p_acc, unsigned int *t_acc, const EmbBigQ &Q, int block, cudaStream_t s);
 emb_status emb_enq_refine(const int4 *rec, int64_t T, LevelGeom g, long long dil, const EmbLevel &lv, uint8_t *flags,
                           unsigned long long *fbits, const EmbBigQ &Q, cudaStream_t s);
 long long emb_refine_dilation(const emb_forest_s *f, int L, int band);
@@ -283,6 +283,18 @@ __device__ __forceinline__ int32_t emb_lookup(const EmbLookup &l, int64_t bx, in
         return (int32_t)(__ldg(l.wpre + (lin >> 6)) + __popcll(w & ((1ull << sh) - 1ull)));
     }
     return emb_hash_find(l.hkey, l.hval, l.hcap, emb_key(bx, by, bz));
+}
+
+// First index in the ascending a[0, n) whose value is not below v.
+static __device__ __forceinline__ int64_t lower_bound_u64(const uint64_t *__restrict__ a, int64_t n, uint64_t v)
+{
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (a[mid] < v) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
 }
 
 // floor(a / 2^s) and ceil(a / 2^s) for signed a (arithmetic shifts; the cell and

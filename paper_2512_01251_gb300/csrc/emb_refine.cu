@@ -14,6 +14,8 @@
 // against the 32 triangles; triangles left out of the union are walked by their
 // own lane, or in queued chunks by whole warps when they have many candidate
 // blocks.  Flags are idempotent byte stores.
+#include <math.h>
+
 #include "emb_internal.cuh"
 
 #ifndef REFINE_MINB
@@ -285,4 +287,98 @@ extern "C" emb_status emb_refine_flags(emb_forest f, emb_bins b, int32_t level, 
     if (fbits) cudaFreeAsync(fbits, s);
     emb_bigq_free(Q, s);
     return rc;
+}
+
+// ---------------------------------------------------------------------------
+// the paper's refinement rules (Sec. 3.4, "Refinement Flagging and Propagation")
+// ---------------------------------------------------------------------------
+// Block classes from the masks: solid (a solid cell), fully fluid (none).  cls bit 0:
+// solid; bit 1: solid-boundary (solid with a fully fluid neighbour of the level);
+// bit 2: eligible (every in-domain neighbour position holds a block of the level,
+// always at the root: refining a block on the refinement interface breaks 2:1).
+// The solid-boundary blocks are the first marks.
+__global__ void k_pf_classify(const uint64_t *__restrict__ key, const uint64_t *__restrict__ mask,
+                              const int32_t *__restrict__ nbr, int64_t n, int64_t nb, int root,
+                              uint8_t *__restrict__ cls, uint8_t *__restrict__ marks)
+{
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n) return;
+    const uint64_t k = key[b];
+    const int64_t bx = (int64_t)(k & EMB_KEY_MASK), by = (int64_t)((k >> EMB_KEY_BITS) & EMB_KEY_MASK),
+                  bz = (int64_t)(k >> (2 * EMB_KEY_BITS));
+    const bool solid = mask[b] != 0;
+    bool eligible = true, fluid_nbr = false;
+    for (int d = 1; d < 27; ++d) {
+        int cx, cy, cz;
+        emb_dir(d, cx, cy, cz);
+        const int64_t x = bx + cx, y = by + cy, z = bz + cz;
+        if (x < 0 || y < 0 || z < 0 || x >= nb || y >= nb || z >= nb) continue;
+        const int32_t j = nbr[b * 26 + d - 1];
+        if (j < 0) {
+            if (!root) eligible = false;
+        } else if (mask[j] == 0) {
+            fluid_nbr = true;
+        }
+    }
+    const bool sb = solid && fluid_nbr;
+    cls[b] = (uint8_t)((solid ? 1 : 0) | (sb ? 2 : 0) | (eligible ? 4 : 0));
+    marks[b] = (uint8_t)(sb && eligible);
+}
+
+// One propagation step: out = in, plus every eligible block in scope next to a block
+// whose `want` bits are set in cls (the adjacency step: want = solid-boundary, every
+// class in scope) or that is marked in `in` (the propagation rounds: want = 0, scope =
+// fully fluid blocks, and solid ones in the first round).
+__global__ void k_pf_step(const int32_t *__restrict__ nbr, int64_t n, const uint8_t *__restrict__ cls, int want,
+                          int solid_in_scope, const uint8_t *__restrict__ in, uint8_t *__restrict__ out)
+{
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n) return;
+    uint8_t m = in[b];
+    const uint8_t c = cls[b];
+    if (!m && (c & 4) && (!(c & 1) || solid_in_scope)) {
+        for (int d = 0; d < 26 && !m; ++d) {
+            const int32_t j = nbr[b * 26 + d];
+            if (j >= 0 && (want ? (cls[j] & want) : in[j])) m = 1;
+        }
+    }
+    out[b] = m;
+}
+
+extern "C" emb_status emb_refine_flags_paper(emb_forest f, int32_t level, double d_spec, uint8_t *d_flags, void *stream)
+{
+    if (!f || !(d_spec >= 0.0) || d_spec > 1e6) return EMB_ERR_BAD_INPUT;
+    if (level < 0 || level != f->top || level >= f->max_level) return EMB_ERR_STATE;
+    EmbLevel &lv = f->lv[level];
+    if (!lv.mask_valid) return EMB_ERR_STATE;
+    if (lv.n == 0) return EMB_OK;
+    if (!d_flags) return EMB_ERR_BAD_INPUT;
+    cudaStream_t s = emb_stream(stream);
+    // Eq. N_prop: 1 + floor(2^-L d_spec / (sqrt(2) Dx_{b,L})), Dx_{b,L} = 4 Dx_L = 1 / (R 2^L)
+    // for d_spec in units of the unit domain: the 2^L factors cancel
+    const double np_d = floor((d_spec * (double)f->R) / sqrt(2.0));
+    if (np_d > 1e6) return EMB_ERR_BAD_INPUT;
+    const int nprop = 1 + (int)np_d;
+    emb_status rc = emb_build_neighbors(lv, s);
+    if (rc != EMB_OK) return rc;
+    uint8_t *cls = nullptr, *tmp = nullptr;
+    EMB_CUDA_TRY(cudaMallocAsync(&cls, lv.n, s));
+    EMB_CUDA_TRY(cudaMallocAsync(&tmp, lv.n, s));
+    const int grid = emb_grid(lv.n, 256);
+    EMB_LAUNCH((k_pf_classify), grid, 256, 0, s)(lv.key, lv.mask, lv.nbr, lv.n, lv.nb_axis, level == 0 ? 1 : 0, cls,
+                                                 d_flags);
+    // blocks next to the solid boundary (both classes), then the rounds, ping-pong
+    EMB_LAUNCH((k_pf_step), grid, 256, 0, s)(lv.nbr, lv.n, cls, 2, 1, d_flags, tmp);
+    uint8_t *a = tmp, *b = d_flags;
+    for (int r = 0; r < nprop; ++r) {
+        EMB_LAUNCH((k_pf_step), grid, 256, 0, s)(lv.nbr, lv.n, cls, 0, r == 0 ? 1 : 0, a, b);
+        uint8_t *t = a;
+        a = b;
+        b = t;
+    }
+    if (a != d_flags) EMB_CUDA_TRY(cudaMemcpyAsync(d_flags, a, lv.n, cudaMemcpyDeviceToDevice, s));
+    EMB_CUDA_TRY(cudaGetLastError());
+    EMB_CUDA_TRY(cudaFreeAsync(cls, s));
+    EMB_CUDA_TRY(cudaFreeAsync(tmp, s));
+    return EMB_OK;
 }

@@ -11,9 +11,11 @@
 //     the line's block parity (bit of p).
 //   k_xscan (one thread per x-row of blocks): walking the row from +x to -x,
 //     solid = s XOR (parity of every crossing in the blocks further along +x).
-// Rows are contiguous and x-ordered in the level's block list.  Unrefined gaps
-// between blocks of a row contain no surface (the refine rule guarantees it), so
-// the row scan sees every crossing.  Block-local parity plays the role of the
+// Rows are contiguous and x-ordered in the level's block list.  Under the distance
+// refine rule, unrefined gaps between blocks of a row contain no surface; under the
+// paper's block-layer rule they may, and a crossing in a gap joins the line parity of
+// the next block of the row (or a tail word of the row's last block that the row scan
+// starts from), so the scan sees every crossing either way.  Block-local parity plays the role of the
 // paper's internal propagation, and the suffix scan that of Alg. 4's
 // neighbour-to-neighbour walk along +x.
 #include "emb_internal.cuh"
@@ -56,11 +58,34 @@ __device__ __forceinline__ unsigned long long vox_items(const VoxTri &V)
     return (unsigned long long)(V.j1 - V.j0 + 1) * (unsigned long long)(V.k1 - V.k0 + 1);
 }
 
+// Parity sinks of one voxelization: per block the cell bits s and the line parity p,
+// and per block the row tail t (crossings beyond the last block of its row, read by
+// the row scan of that last block); the level's sorted keys locate them.
+struct VoxAcc {
+    unsigned long long *s;
+    unsigned int *p, *t;
+    const uint64_t *key;
+    int64_t n;
+};
+
+// A crossing inside a block position the level does not have (a region left coarser by
+// the refinement rule): it flips every cell of the row to its left, so it joins the line
+// parity of the next block of the row to its right, or the row tail of the row's last
+// block when there is none.
+__device__ __noinline__ void vox_gap(const VoxAcc &acc, long long bx, long long by, long long bz, int line)
+{
+    const uint64_t row = (uint64_t)emb_key(0, by, bz) >> EMB_KEY_BITS;
+    const int64_t nx = lower_bound_u64(acc.key, acc.n, emb_key(bx + 1, by, bz));
+    if (nx < acc.n && (acc.key[nx] >> EMB_KEY_BITS) == row) atomicXor(acc.p + nx, 1u << line);
+    else if (nx > 0 && (acc.key[nx - 1] >> EMB_KEY_BITS) == row) atomicXor(acc.t + nx - 1, 1u << line);
+}
+
 // The crossing of line (j, k) with the triangle, if any, recorded in its owner block.
 __device__ __forceinline__ void vox_line(const VoxTri &V, const LevelGeom &g, const EmbLookup &lk, long long j,
-                                         long long k, unsigned long long *__restrict__ s_acc,
-                                         unsigned int *__restrict__ p_acc, int *st)
+                                         long long k, const VoxAcc &acc, int *st)
 {
+    unsigned long long *__restrict__ s_acc = acc.s;
+    unsigned int *__restrict__ p_acc = acc.p;
     const int4 A = V.A, B = V.B, C = V.C;
     const int sx = V.sx;
     const int pz = (int)((2 * k + 1) * g.half), py = (int)((2 * j + 1) * g.half);
@@ -77,7 +102,7 @@ __device__ __forceinline__ void vox_line(const VoxTri &V, const LevelGeom &g, co
         if (sgn_i128(Dlo - mul128(V.nx, g.W)) * sx >= 0) continue;  // x_hit >= lo + W
         const int32_t id = emb_lookup(lk, bx, j >> 2, k >> 2);
         if (id < 0) {
-            emb_set_status(st, EMB_ERR_STATE);  // a crossing outside every block
+            vox_gap(acc, bx, j >> 2, k >> 2, (int)((j & 3) + 4 * (k & 3)));
             return;
         }
         // cell q of this line (centre lo + (2q+1) half) lies before the crossing iff
@@ -98,7 +123,7 @@ __device__ __forceinline__ void vox_line(const VoxTri &V, const LevelGeom &g, co
 
 __global__ void k_vox(const int4 *__restrict__ rec, int64_t T, const uint32_t *__restrict__ flist, int64_t nf,
                       const uint32_t *__restrict__ d_nf, const uint32_t *__restrict__ keep, LevelGeom g, EmbLookup lk,
-                      unsigned long long *__restrict__ s_acc, unsigned int *__restrict__ p_acc, EmbBigQ Q, int *st)
+                      VoxAcc acc, EmbBigQ Q, int *st)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     // nf: the planned count of a replay or the exact one; d_nf: the count this replay found
@@ -111,13 +136,12 @@ __global__ void k_vox(const int4 *__restrict__ rec, int64_t T, const uint32_t *_
     const unsigned long long items = vox_items(V);
     if (items > EMB_BIG_ITEMS && emb_bigq_push(Q, t, items)) return;
     for (long long k = V.k0; k <= V.k1; ++k)
-        for (long long j = V.j0; j <= V.j1; ++j) vox_line(V, g, lk, j, k, s_acc, p_acc, st);
+        for (long long j = V.j0; j <= V.j1; ++j) vox_line(V, g, lk, j, k, acc, st);
 }
 
 // The queued chunks of large triangles, one warp per chunk (lines in j-major order).
 __global__ void __launch_bounds__(EMB_BIG_BLOCK) k_vox_big(const int4 *__restrict__ rec, LevelGeom g, EmbLookup lk,
-                                                           unsigned long long *__restrict__ s_acc,
-                                                           unsigned int *__restrict__ p_acc, EmbBigQ Q, int *st)
+                                                           VoxAcc acc, EmbBigQ Q, int *st)
 {
     const int lane = threadIdx.x & 31;
     const unsigned long long nq = emb_bigq_count(Q);
@@ -136,7 +160,7 @@ __global__ void __launch_bounds__(EMB_BIG_BLOCK) k_vox_big(const int4 *__restric
         long long jj = (long long)(first % nj), kk = (long long)(first / nj);
         const long long dj = (long long)(32 % nj), dk = (long long)(32 / nj);
         for (unsigned long long it = first; it < i1; it += 32) {
-            vox_line(V, g, lk, V.j0 + jj, V.k0 + kk, s_acc, p_acc, st);
+            vox_line(V, g, lk, V.j0 + jj, V.k0 + kk, acc, st);
             jj += dj;
             kk += dk;
             if (jj >= (long long)nj) {
@@ -159,13 +183,14 @@ __device__ __forceinline__ unsigned long long spread_lines(unsigned int p)
 }
 
 __global__ void k_xscan(const uint64_t *__restrict__ key, int64_t n, const unsigned long long *__restrict__ s_acc,
-                        const unsigned int *__restrict__ p_acc, uint64_t *__restrict__ mask)
+                        const unsigned int *__restrict__ p_acc, const unsigned int *__restrict__ t_acc,
+                        uint64_t *__restrict__ mask)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     uint64_t row = key[i] >> EMB_KEY_BITS;
     if (i + 1 < n && (key[i + 1] >> EMB_KEY_BITS) == row) return;  // only the row's last (+x-most) block walks
-    unsigned int acc = 0;
+    unsigned int acc = t_acc[i];  // crossings beyond the row's last block
     for (int64_t j = i; j >= 0 && (key[j] >> EMB_KEY_BITS) == row; --j) {
         mask[j] = s_acc[j] ^ spread_lines(acc);
         acc ^= p_acc[j];
@@ -175,20 +200,22 @@ __global__ void k_xscan(const uint64_t *__restrict__ key, int64_t n, const unsig
 // Enqueue only: s_acc (n uint64) and p_acc (n uint32) are scratch; writes lv.mask.
 emb_status emb_enq_voxelize(const int4 *rec, int64_t T, const uint32_t *flist, int64_t nf, const uint32_t *d_nf,
                             const uint32_t *keep, LevelGeom g, const EmbLevel &lv, unsigned long long *s_acc,
-                            unsigned int *p_acc, const EmbBigQ &Q, int block, cudaStream_t s)
+                            unsigned int *p_acc, unsigned int *t_acc, const EmbBigQ &Q, int block, cudaStream_t s)
 {
     int *st = emb_status_word();
     if (!st) return EMB_ERR_CUDA;
     if (lv.n == 0) return EMB_OK;
     EMB_CUDA_TRY(cudaMemsetAsync(s_acc, 0, lv.n * sizeof(unsigned long long), s));
     EMB_CUDA_TRY(cudaMemsetAsync(p_acc, 0, lv.n * sizeof(unsigned int), s));
+    EMB_CUDA_TRY(cudaMemsetAsync(t_acc, 0, lv.n * sizeof(unsigned int), s));
+    const VoxAcc acc = {s_acc, p_acc, t_acc, lv.key, lv.n};
     if (nf > 0) {
         const EmbLookup lk = emb_lookup_of(lv);
         if (Q.cap) EMB_CUDA_TRY(cudaMemsetAsync(Q.n, 0, sizeof(unsigned long long), s));
-        EMB_LAUNCH((k_vox), emb_grid(nf, block), block, 0, s)(rec, T, flist, nf, d_nf, keep, g, lk, s_acc, p_acc, Q, st);
-        if (Q.cap) EMB_LAUNCH((k_vox_big), EMB_BIG_GRID, EMB_BIG_BLOCK, 0, s)(rec, g, lk, s_acc, p_acc, Q, st);
+        EMB_LAUNCH((k_vox), emb_grid(nf, block), block, 0, s)(rec, T, flist, nf, d_nf, keep, g, lk, acc, Q, st);
+        if (Q.cap) EMB_LAUNCH((k_vox_big), EMB_BIG_GRID, EMB_BIG_BLOCK, 0, s)(rec, g, lk, acc, Q, st);
     }
-    EMB_LAUNCH((k_xscan), emb_grid(lv.n, 256), 256, 0, s)(lv.key, lv.n, s_acc, p_acc, lv.mask);
+    EMB_LAUNCH((k_xscan), emb_grid(lv.n, 256), 256, 0, s)(lv.key, lv.n, s_acc, p_acc, t_acc, lv.mask);
     EMB_CUDA_TRY(cudaGetLastError());
     return EMB_OK;
 }
@@ -206,21 +233,23 @@ extern "C" emb_status emb_voxelize(emb_forest f, emb_bins b, int32_t level, uint
     }
     if (!lv.mask) EMB_CUDA_TRY(cudaMallocAsync(&lv.mask, lv.n * sizeof(uint64_t), s));
     unsigned long long *s_acc = nullptr;
-    unsigned int *p_acc = nullptr;
+    unsigned int *p_acc = nullptr, *t_acc = nullptr;
     EMB_CUDA_TRY(cudaMallocAsync(&s_acc, lv.n * sizeof(unsigned long long), s));
     EMB_CUDA_TRY(cudaMallocAsync(&p_acc, lv.n * sizeof(unsigned int), s));
+    EMB_CUDA_TRY(cudaMallocAsync(&t_acc, lv.n * sizeof(unsigned int), s));
     EmbBigQ Q;
     emb_status rc = emb_bigq_alloc(Q, b->m->T, s);
     if (rc != EMB_OK) return rc;
     // the filtered count stays on the device: the grid covers every triangle and stops at it
     rc = emb_enq_voxelize(b->m->rec, b->m->T, b->flist, b->known ? b->nf : b->m->T, (const uint32_t *)b->dcount, b->keep,
-                          g, lv, s_acc, p_acc, Q, 128, s);
+                          g, lv, s_acc, p_acc, t_acc, Q, 128, s);
     emb_bigq_free(Q, s);
     if (rc != EMB_OK) return rc;
     if (d_solid_mask)
         EMB_CUDA_TRY(cudaMemcpyAsync(d_solid_mask, lv.mask, lv.n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
     EMB_CUDA_TRY(cudaFreeAsync(s_acc, s));
     EMB_CUDA_TRY(cudaFreeAsync(p_acc, s));
+    EMB_CUDA_TRY(cudaFreeAsync(t_acc, s));
     lv.mask_valid = 1;
     if (level == f->top) f->n_links = -1;
     return EMB_OK;

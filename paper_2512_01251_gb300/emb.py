@@ -224,6 +224,15 @@ def emb_refine_flags(forest: Forest, bins: Bins, level: int, band: int, out: tor
     return out
 
 
+def emb_refine_flags_paper(forest: Forest, level: int, d_spec: float, out: torch.Tensor | None = None, stream=None):
+    """The paper's block-layer refinement rules (Sec. 3.4, Eq. N_prop); d_spec in units of the unit domain."""
+    if out is None:
+        out = torch.empty(max(1, emb_forest_num_blocks(forest, level)), dtype=torch.uint8, device="cuda")
+    _check(load().emb_refine_flags_paper(forest.h, int(level), float(d_spec), _ptr(out), _stream(stream)),
+           "emb_refine_flags_paper")
+    return out[:emb_forest_num_blocks(forest, level)]
+
+
 def emb_cutlinks_count(forest: Forest, lattice: int, stream=None) -> int:
     out = ctypes.c_int64(0)
     _check(load().emb_cutlinks_count(forest.h, int(lattice), ctypes.byref(out), _stream(stream)), "emb_cutlinks_count")
@@ -315,12 +324,14 @@ class Embedding:
 
 def embed(verts: torch.Tensor, tris: torch.Tensor, R: int, levels: int, band: int = 2, lattice: int = 19,
           check_watertight: bool = True, mesh: Mesh | None = None, keep_bins: bool = False,
-          check_status: bool = True, stream=None, bin_mode: int = EMB_BIN_FILTER_COMPACT) -> Embedding:
+          check_status: bool = True, stream=None, bin_mode: int = EMB_BIN_FILTER_COMPACT,
+          d_spec: float | None = None) -> Embedding:
     """Embed a closed mesh into a forest with root R^3 blocks and levels 0..levels.
 
     Per level: emb_bin, emb_voxelize, then (below the finest level)
     emb_refine_flags and emb_forest_refine; at the finest level the cut-link
-    table of `lattice` (19 or 27).
+    table of `lattice` (19 or 27).  With d_spec, the refinement follows the
+    paper's block-layer rules (emb_refine_flags_paper) instead of `band`.
     """
     if mesh is None:
         mesh = emb_mesh_create(verts, tris, R, check_watertight, stream)
@@ -330,7 +341,8 @@ def embed(verts: torch.Tensor, tris: torch.Tensor, R: int, levels: int, band: in
         bins = emb_bin(mesh, forest, L, lattice, stream, mode=bin_mode)
         E.masks.append(emb_voxelize(forest, bins, L, stream=stream))
         if L < levels:
-            fl = emb_refine_flags(forest, bins, L, band, stream=stream)
+            fl = (emb_refine_flags(forest, bins, L, band, stream=stream) if d_spec is None
+                  else emb_refine_flags_paper(forest, L, d_spec, stream=stream))
             E.flags.append(fl)
             emb_forest_refine(forest, L, fl, stream)
         else:
