@@ -10,6 +10,11 @@ Parity status of each function (see also the module functions' docstrings):
   * ``build_forest``, ``masks``, ``refine_flags``, ``cut_links`` — pinned by
     closed forms, half-space representations, clipping and invariants
     (tests/test_oracle_pins.py).
+  * ``lbm_step`` (one step on the finest level with Bouzidi bounce-back from the
+    link table) — pinned by the rest state, a pulse streaming one cell, a pulse
+    bounced by a halfway wall, and mass conservation in a cavity with halfway walls
+    (tests/test_oracle_lbm.py).  The D3Q19/D3Q27 weights and BGK are the textbook
+    ones (the paper cites its LBM and prints neither).
   * ``paper_flags``, ``build_forest_paper``, ``n_prop`` (the paper's block-layer
     refinement rules) — pinned by the closed form of a block-aligned box and the
     2:1 invariant (tests/test_oracle_paper_policy.py).
@@ -529,3 +534,82 @@ def grad_verts_from_gq(links_, gq, X, tris, R, levels, blocks_f, n_verts):
     for j, lam in enumerate((lamA, lamB, lamC)):
         np.add.at(g, t[:, j], (gq * lam)[:, None] * base)
     return g
+
+
+# --------------------------------------------------------------------------- #
+# One lattice-Boltzmann step on the finest level: the table's consumer
+# --------------------------------------------------------------------------- #
+def lattice_weights(lattice: int) -> np.ndarray:
+    """D3Q19 / D3Q27 weights in the direction order of directions() (rest, axes, edges,
+    corners): 1/3, 1/18, 1/36 and 8/27, 2/27, 1/54, 1/216."""
+    C = directions()[:lattice]
+    kind = np.abs(C).sum(axis=1)
+    table = {0: 1 / 3, 1: 1 / 18, 2: 1 / 36} if lattice == 19 else {0: 8 / 27, 1: 2 / 27, 2: 1 / 54, 3: 1 / 216}
+    return np.array([table[int(k)] for k in kind], dtype=np.float64)
+
+
+def equilibrium(rho: np.ndarray, u: np.ndarray, lattice: int) -> np.ndarray:
+    """(Q, n) second-order equilibrium w_i rho (1 + 3 c.u + 9/2 (c.u)^2 - 3/2 u.u)."""
+    C = directions()[:lattice].astype(np.float64)
+    w = lattice_weights(lattice)
+    cu = u @ C.T
+    usq = (u * u).sum(axis=1)
+    return (w[None, :] * rho[:, None] * (1 + 3 * cu + 4.5 * cu * cu - 1.5 * usq[:, None])).T
+
+
+def lbm_sources(R, levels, blocks_f, mask_f, lattice):
+    """For every finest cell x and direction i: the cell x - c_i if it is a fluid cell of
+    the level, -1 if it is solid, -2 if its block is missing (edge of the level)."""
+    C = directions()[:lattice]
+    idx = _block_index(blocks_f)
+    bits = unpack_masks(mask_f)
+    n = len(blocks_f) * 64
+    t = np.arange(64)
+    loc = np.stack([t % 4, (t // 4) % 4, t // 16], axis=1)
+    src = np.full((lattice, n), -2, dtype=np.int64)
+    for b, blk in enumerate(np.asarray(blocks_f, dtype=np.int64).tolist()):
+        g = 4 * np.array(blk)[None, :] + loc
+        for i in range(lattice):
+            s_ = g - C[i]
+            bb = np.floor_divide(s_, 4)
+            ll = s_ - 4 * bb
+            for c in range(64):
+                j = idx.get(tuple(bb[c].tolist()))
+                if j is None:
+                    continue
+                tt = int(ll[c, 0] + 4 * ll[c, 1] + 16 * ll[c, 2])
+                src[i, b * 64 + c] = -1 if bits[j, tt] else j * 64 + tt
+    return src
+
+
+def lbm_step(R, levels, blocks_f, mask_f, links_, pop, omega: float, lattice: int) -> np.ndarray:
+    """One step from post-collision populations pop (Q, n_cells) at t to those at t + 1:
+    1. pull streaming: f_i(x) = f*_i(x - c_i) when x - c_i is a fluid cell of the level,
+       f*_i(x) when its block is missing (zero gradient at the edge of the level; the
+       coupling to coarser levels is out of scope);
+    2. at every cut link (x, d, q), the population entering x against c_d, where
+       x - c_{-d} = x + c_d is solid: the linear Bouzidi rule (bouzidi_incoming) on f*;
+    3. BGK collision f* = f - omega (f - f_eq(rho, u)) at fluid cells; solid cells are 0.
+    """
+    pop = np.asarray(pop, dtype=np.float64)
+    n = pop.shape[1]
+    src = lbm_sources(R, levels, blocks_f, mask_f, lattice)
+    fluid = unpack_masks(mask_f).reshape(-1) == 0
+    pre = np.zeros_like(pop)
+    for i in range(lattice):
+        ok = src[i] >= 0
+        pre[i, ok] = pop[i, src[i, ok]]
+        edge = src[i] == -2
+        pre[i, edge] = pop[i, edge]
+    partner = partner_cells(R, levels, blocks_f, mask_f, links_["cell"], links_["dir"])
+    _, f_i, f_opp, f_p, has = _link_pops(links_, pop, partner)
+    inc = bouzidi_incoming(links_["q"], f_i, f_p, f_opp, has)
+    opp = np.array([opposite(int(d)) for d in links_["dir"]], dtype=np.int64)
+    pre[opp, links_["cell"]] = inc
+    C = directions()[:lattice].astype(np.float64)
+    rho = pre.sum(axis=0)
+    rs = np.where(rho != 0, rho, 1.0)
+    u = (C.T @ pre).T / rs[:, None]
+    out = pre - omega * (pre - equilibrium(rho, u, lattice))
+    out[:, ~fluid] = 0.0
+    return out
