@@ -376,6 +376,7 @@ def run_ours(args):
         line["fwd_bwd"] = fwd_bwd_leg(P)
         line["batched"] = batch_leg(P)
         line["ablation"] = ablation_leg(P, verts, tris, w, lattice)
+        line["lbm"] = lbm_leg(P)
         units_s, secs = oracle_sample(v, t, w, lattice, 6, seed=7)
         line["cpu_baseline"] = dict(value=units_s / secs, unit=UNIT, cores=omp_threads(), kind="oracle",
                                     sample=("6 surface blocks of the finest level: 64 cell states each, the states "
@@ -444,6 +445,53 @@ def fwd_bwd_leg(P, reps=10):
                 forward_ms=round(fmed, 4), backward_ms=round(bmed, 4), backward_over_forward=round(bmed / fmed, 3),
                 embed_ms=round(emed, 4), backward_over_embed=round(bmed / emed, 3),
                 forward="emb_cutlinks + emb_mex_force", backward="emb_mex_force_backward + emb_cutlinks_backward")
+
+
+def lbm_leg(P, reps=20):
+    """The link table's consumer on the differentiation workload (diff_112k, D3Q19): one
+    lattice-Boltzmann step on the finest level, timed per pass with CUDA events (median):
+    pull streaming and BGK collision over every cell, the Bouzidi pass over the cut links,
+    and the momentum-exchange force.  'boundary_share' = (Bouzidi + force) / whole."""
+    import torch
+
+    from synth import populations
+    w = workload("diff_112k")
+    v, t = w.build_mesh()
+    E = P.embed(torch.from_numpy(v).cuda(), torch.from_numpy(t).cuda(), w.R, w.levels, w.band, 19)
+    nblk = P.emb_forest_num_blocks(E.forest, w.levels)
+    ncell = nblk * 64
+    pop = torch.from_numpy(populations(ncell, seed=w.extra["pop_seed"])).cuda()
+    out, pre = torch.empty_like(pop), torch.empty_like(pop)
+    F = torch.empty(3, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    calls = {
+        "stream": lambda: P.emb_lbm_step(E.forest, 19, E.links, 1.2, pop, out=out, pre=pre, phases=1),
+        "bouzidi": lambda: P.emb_lbm_step(E.forest, 19, E.links, 1.2, pop, out=out, pre=pre, phases=2),
+        "collide": lambda: P.emb_lbm_step(E.forest, 19, E.links, 1.2, pop, out=out, pre=pre, phases=4),
+        "force": lambda: P.emb_mex_force(E.forest, 19, E.links["cell"], E.links["dir"], E.links["q"], pop, out=F),
+        "step": lambda: P.emb_lbm_step(E.forest, 19, E.links, 1.2, pop, out=out, pre=pre, phases=7),
+    }
+    ms = {}
+    for name, fn in calls.items():
+        fn()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        ms[name] = round(statistics.median(ts), 4)
+    hbm = peaks()[0].get("hbm_gbs", 6800.0)
+    cell_bytes = 19 * 4 * 2  # one population read and one written per direction and cell
+    gbps = {k: ncell * cell_bytes / (ms[k] / 1e3) / 1e9 for k in ("stream", "collide")}
+    whole = ms["step"] + ms["force"]
+    return dict(workload=f"diff_112k: {len(t)} triangles, {ncell} finest cells, {E.links['q'].numel()} cut links, D3Q19",
+                ms=ms, boundary_share=round((ms["bouzidi"] + ms["force"]) / whole, 4),
+                stream_GBps=round(gbps["stream"], 1), collide_GBps=round(gbps["collide"], 1),
+                hbm_frac=dict(stream=round(gbps["stream"] / hbm, 3), collide=round(gbps["collide"] / hbm, 3)),
+                timing=f"CUDA events, median of {reps}; bytes = 2 x 19 x 4 per cell and pass")
 
 
 def ablation_leg(P, verts, tris, w, lattice, reps=3):

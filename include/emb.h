@@ -278,6 +278,29 @@ emb_status emb_mex_force_noalloc(emb_forest f, int32_t lattice, const int32_t *d
                                  const float *d_q, int64_t n, const float *d_pop, int64_t pop_stride, float *d_F,
                                  void *stream);
 
+/* ------------------------------------------------------------- solver ---- */
+/* One lattice-Boltzmann step on the finest level, the consumer of the link table
+ * (Sec. 2.2: interpolated bounce-back with the link fractions q; the paper cites
+ * the method and prints no formula).  Populations are SoA float32, pop[i * stride
+ * + cell] for the lattice's directions (order of emb_directions), cell = block *
+ * 64 + x + 4 y + 16 z on the finest level; d_pop holds post-collision values at t,
+ * d_pop_out receives them at t + 1, d_pre is caller scratch of the same size; the
+ * three buffers must differ.  phases (bits, 7 = the whole step): 1 pull streaming
+ * into d_pre (from the cell x - c_i when it is a fluid cell of the level, the cell's
+ * own value when its block is missing: zero gradient at the edge of the level, the
+ * coupling to coarser levels being out of scope); 2 at every cut link (x, d, q),
+ * the population entering x against c_d by the linear Bouzidi rule of
+ * emb_mex_force; 4 BGK collision with relaxation omega in [0, 2) and the standard
+ * D3Q19 / D3Q27 weights at fluid cells, 0 at solid ones.  The link table is the one
+ * of emb_cutlinks for this forest and lattice.  Enqueues only (builds the finest
+ * neighbour table on first use).
+ * Errors: EMB_ERR_BAD_INPUT (lattice, omega, phases, stride, aliasing, null
+ * pointers; device status for a link outside the level), EMB_ERR_STATE (no finest
+ * masks). */
+emb_status emb_lbm_step(emb_forest f, int32_t lattice, const int32_t *d_cell, const uint8_t *d_dir, const float *d_q,
+                        int64_t n_links, float omega, const float *d_pop, float *d_pre, float *d_pop_out,
+                        int64_t pop_stride, int32_t phases, void *stream);
+
 /* Adjoint of the link table with respect to the vertex positions (world
  * units): d_gverts (V x 3 float32, overwritten) = sum_k d_gq[k] dq_k/dV with
  * dq/dV_j = lambda_j n / (h n.c) for the three vertices of link k's triangle

@@ -47,6 +47,7 @@ SIGNATURES = {
     "emb_mex_force_backward": (I32, [P, I32, P, P, P, I64, P, I64, P, P, P]),
     "emb_mex_force_noalloc": (I32, [P, I32, P, P, P, I64, P, I64, P, P]),
     "emb_cutlinks_backward": (I32, [P, P, P, P, P, P, I64, P, P, P]),
+    "emb_lbm_step": (I32, [P, I32, P, P, P, I64, ctypes.c_float, P, P, P, I64, I32, P]),
     "emb_batch_create": (I32, [P, P, P, P, I32, P, ctypes.POINTER(P)]),
     "emb_batch_run": (I32, [P, P]),
     "emb_batch_capture": (I32, [P, P]),

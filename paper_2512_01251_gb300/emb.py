@@ -286,6 +286,21 @@ def emb_mex_force_backward(forest: Forest, lattice: int, cell, dir, q, pop: torc
     return out
 
 
+def emb_lbm_step(forest: Forest, lattice: int, links: dict, omega: float, pop: torch.Tensor,
+                 out: torch.Tensor | None = None, pre: torch.Tensor | None = None, phases: int = 7, stream=None):
+    """One lattice-Boltzmann step on the finest level with Bouzidi bounce-back from the link table.
+    pop: (lattice, stride) float32 post-collision populations; returns those one step later."""
+    if out is None:
+        out = torch.empty_like(pop)
+    if pre is None:
+        pre = torch.empty_like(pop)
+    n = links["q"].numel()
+    _check(load().emb_lbm_step(forest.h, int(lattice), _ptr(links["cell"]), _ptr(links["dir"]), _ptr(links["q"]), n,
+                               float(omega), _ptr(pop), _ptr(pre), _ptr(out), pop.shape[1], int(phases),
+                               _stream(stream)), "emb_lbm_step")
+    return out
+
+
 def emb_cutlinks_backward(mesh: Mesh, forest: Forest, cell, dir, q, tri, gq: torch.Tensor,
                           out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     if out is None:

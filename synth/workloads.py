@@ -120,16 +120,19 @@ D3Q27_DIRS = np.array(
      [1, 1, 1], [-1, -1, -1], [1, 1, -1], [-1, -1, 1], [1, -1, 1], [-1, 1, -1], [-1, 1, 1], [1, -1, -1]],
     dtype=np.int64)
 D3Q19_WEIGHTS = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12, dtype=np.float64)
+D3Q27_WEIGHTS = np.array([8 / 27] + [2 / 27] * 6 + [1 / 54] * 12 + [1 / 216] * 8, dtype=np.float64)
 
 
-def populations(n_cells: int, seed: int, u=(0.05, 0.0, 0.0), noise: float = 0.01) -> np.ndarray:
-    """D3Q19 populations [19, n_cells] float32: equilibrium(rho=1, u) * (1 + noise N(0,1))."""
+def populations(n_cells: int, seed: int, u=(0.05, 0.0, 0.0), noise: float = 0.01, lattice: int = 19) -> np.ndarray:
+    """Populations [lattice, n_cells] float32 (D3Q19 or D3Q27): a uniform flow state,
+    equilibrium(rho=1, u) * (1 + noise N(0,1)) per population."""
     rng = np.random.default_rng(seed)
-    c = D3Q27_DIRS[:19].astype(np.float64)
+    c = D3Q27_DIRS[:lattice].astype(np.float64)
+    w = D3Q19_WEIGHTS if lattice == 19 else D3Q27_WEIGHTS
     u = np.asarray(u, dtype=np.float64)
     cu = c @ u
-    feq = D3Q19_WEIGHTS * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * float(u @ u))
-    z = rng.standard_normal((19, n_cells))
+    feq = w * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * float(u @ u))
+    z = rng.standard_normal((lattice, n_cells))
     return (feq[:, None] * (1.0 + noise * z)).astype(np.float32)
 
 
