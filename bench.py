@@ -205,6 +205,17 @@ def peaks():
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def reduce_over_ranks(dist, total_ms: float, units: float, device: str):
+    """Whole-job numbers of N replicas: the slowest rank's time and the sum of the units
+    all ranks embedded (one all-reduce each; the only collective of the run)."""
+    import torch
+    tt = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    uu = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(uu)
+    return float(tt.item()), float(uu.item())
+
+
 def run_ours(args):
     import torch
 
@@ -314,12 +325,7 @@ def run_ours(args):
     last = (mesh, forest, masks, links, stats, info.get("bins"))
     total_ms = sum(step_ms)
     if dist is not None:
-        tt = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
-        uu = torch.tensor([units], dtype=torch.float64, device="cuda")
-        dist.all_reduce(uu)
-        units = float(uu.item())
+        total_ms, units = reduce_over_ranks(dist, total_ms, units, "cuda")
     value = units / (total_ms / 1e3)
 
     # ---- breakdown, roofline of the dominant call
