@@ -337,7 +337,8 @@ emb_status emb_cutlinks_backward(emb_mesh m, emb_forest f, const int32_t *d_cell
  * the fastest; h_choice (4 int32, may be NULL) receives the chosen stream count
  * (1..16), thread-block size of the triangle-parallel kernels (128, 256 or 512),
  * resident link CTAs per SM (0 = as many as fit) and link placement (0 joint,
- * 1 per mesh).  It synchronises and drops a captured graph.  emb_batch_configure
+ * 1 per mesh on its pipeline's stream, 2 per mesh on a low-priority stream of its
+ * own, so that the link kernels yield SMs to the pipelines still running).  It synchronises and drops a captured graph.  emb_batch_configure
  * sets such a 4-value shape directly (host array; EMB_ERR_BAD_INPUT outside the
  * ranges above) and drops a captured graph; it enqueues nothing.
  *

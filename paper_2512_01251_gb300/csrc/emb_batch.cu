@@ -70,13 +70,16 @@ struct BMesh {
 
 struct emb_batch_s {
     std::vector<BMesh> m;
-    cudaStream_t st[BATCH_MAX_STREAMS] = {};
-    cudaEvent_t ev_fork = nullptr, ev_join[BATCH_MAX_STREAMS] = {};
+    cudaStream_t st[BATCH_MAX_STREAMS] = {};   // pipelines (highest priority)
+    cudaStream_t lst[BATCH_MAX_STREAMS] = {};  // link launches of placement 2 (lowest priority)
+    cudaEvent_t ev_fork = nullptr, ev_join[BATCH_MAX_STREAMS] = {}, ev_ljoin[BATCH_MAX_STREAMS] = {};
+    cudaEvent_t ev_mesh[EMB_MAX_BATCH] = {};    // a mesh's pipeline is done
     unsigned int *next = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     // launch shape (autotuned): streams, block size of the triangle-parallel
-    // kernels, link CTAs per SM (0 = as many as fit), link placement (0 joint, 1 per mesh)
+    // kernels, link CTAs per SM (0 = as many as fit), link placement (0 joint, 1 per
+    // mesh on its pipeline's stream, 2 per mesh on a low-priority stream of its own)
     int nstreams = 8, tri_block = 256, link_ctas = 0, per_mesh_links = 1;
     int device = 0;
 };
@@ -270,8 +273,12 @@ extern "C" void emb_batch_destroy(emb_batch b)
     if (b->graph) cudaGraphDestroy(b->graph);
     for (int i = 0; i < BATCH_MAX_STREAMS; ++i) {
         if (b->st[i]) cudaStreamDestroy(b->st[i]);
+        if (b->lst[i]) cudaStreamDestroy(b->lst[i]);
         if (b->ev_join[i]) cudaEventDestroy(b->ev_join[i]);
+        if (b->ev_ljoin[i]) cudaEventDestroy(b->ev_ljoin[i]);
     }
+    for (int j = 0; j < EMB_MAX_BATCH; ++j)
+        if (b->ev_mesh[j]) cudaEventDestroy(b->ev_mesh[j]);
     if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     if (b->next) cudaFree(b->next);
     for (BMesh &B : b->m) free_mesh(B);
@@ -306,11 +313,17 @@ extern "C" emb_status emb_batch_create(const emb_mesh *meshes, const int32_t *le
     if (rc == EMB_OK && cudaMalloc(&b->next, sizeof(unsigned int)) != cudaSuccess) rc = EMB_ERR_CUDA;
     if (rc == EMB_OK) rc = emb_link_emit_init();  // kernel attributes are set outside of any capture
     if (rc == EMB_OK && !emb_status_word()) rc = EMB_ERR_CUDA;
+    int prio_least = 0, prio_greatest = 0;
+    if (rc == EMB_OK && cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest) != cudaSuccess) rc = EMB_ERR_CUDA;
     for (int i = 0; i < BATCH_MAX_STREAMS && rc == EMB_OK; ++i) {
-        if (cudaStreamCreateWithFlags(&b->st[i], cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&b->ev_join[i], cudaEventDisableTiming) != cudaSuccess)
+        if (cudaStreamCreateWithPriority(&b->st[i], cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&b->lst[i], cudaStreamNonBlocking, prio_least) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->ev_join[i], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->ev_ljoin[i], cudaEventDisableTiming) != cudaSuccess)
             rc = EMB_ERR_CUDA;
     }
+    for (int j = 0; j < n && rc == EMB_OK; ++j)
+        if (cudaEventCreateWithFlags(&b->ev_mesh[j], cudaEventDisableTiming) != cudaSuccess) rc = EMB_ERR_CUDA;
     if (rc == EMB_OK && cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess) rc = EMB_ERR_CUDA;
     if (rc == EMB_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = EMB_ERR_CUDA;
     if (rc != EMB_OK) {
@@ -362,7 +375,10 @@ static emb_status batch_enqueue(emb_batch b, cudaStream_t s)
 {
     const int K = b->nstreams < 1 ? 1 : (b->nstreams > BATCH_MAX_STREAMS ? BATCH_MAX_STREAMS : b->nstreams);
     EMB_CUDA_TRY(cudaEventRecord(b->ev_fork, s));
-    for (int i = 0; i < K; ++i) EMB_CUDA_TRY(cudaStreamWaitEvent(b->st[i], b->ev_fork, 0));
+    for (int i = 0; i < K; ++i) {
+        EMB_CUDA_TRY(cudaStreamWaitEvent(b->st[i], b->ev_fork, 0));
+        if (b->per_mesh_links == 2) EMB_CUDA_TRY(cudaStreamWaitEvent(b->lst[i], b->ev_fork, 0));
+    }
     // meshes by decreasing planned work, each to the stream with the least work so far
     std::vector<int> order(b->m.size());
     for (size_t j = 0; j < order.size(); ++j) order[j] = (int)j;
@@ -384,12 +400,23 @@ static emb_status batch_enqueue(emb_batch b, cudaStream_t s)
             LinkTable one;
             one.n = 1;
             one.m[0] = link_mesh(B);
-            BTRY(emb_enq_link_emit(one, B.next, b->link_ctas, b->st[k], B.nwork > 0 ? B.nwork : 1));
+            cudaStream_t ls = b->st[k];
+            if (b->per_mesh_links == 2) {
+                // the link kernel yields SMs to the latency-bound pipelines of other meshes
+                ls = b->lst[k];
+                EMB_CUDA_TRY(cudaEventRecord(b->ev_mesh[order[q]], b->st[k]));
+                EMB_CUDA_TRY(cudaStreamWaitEvent(ls, b->ev_mesh[order[q]], 0));
+            }
+            BTRY(emb_enq_link_emit(one, B.next, b->link_ctas, ls, B.nwork > 0 ? B.nwork : 1));
         }
     }
     for (int i = 0; i < K; ++i) {
         EMB_CUDA_TRY(cudaEventRecord(b->ev_join[i], b->st[i]));
         EMB_CUDA_TRY(cudaStreamWaitEvent(s, b->ev_join[i], 0));
+        if (b->per_mesh_links == 2) {
+            EMB_CUDA_TRY(cudaEventRecord(b->ev_ljoin[i], b->lst[i]));
+            EMB_CUDA_TRY(cudaStreamWaitEvent(s, b->ev_ljoin[i], 0));
+        }
     }
     if (b->per_mesh_links) return EMB_OK;
     LinkTable tab;
@@ -428,7 +455,15 @@ extern "C" emb_status emb_batch_capture(emb_batch b, void *stream)
     }
     if (e != cudaSuccess) return EMB_ERR_CUDA;
     b->graph = g;
-    EMB_CUDA_TRY(cudaGraphInstantiate(&b->exec, g, 0));
+    // kernels keep the priority of the stream they were captured from (where the
+    // driver takes per-node priorities; otherwise the graph runs at its launch stream's)
+    cudaError_t ie = cudaGraphInstantiate(&b->exec, g, cudaGraphInstantiateFlagUseNodePriority);
+    if (ie != cudaSuccess) {
+        emb_note_cuda_error(ie, "cudaGraphInstantiate(UseNodePriority)", __FILE__, __LINE__);
+        (void)cudaGetLastError();
+        b->exec = nullptr;
+        EMB_CUDA_TRY(cudaGraphInstantiate(&b->exec, g, 0));
+    }
     return EMB_OK;
 }
 
@@ -447,9 +482,9 @@ extern "C" emb_status emb_batch_autotune(emb_batch b, void *stream, int32_t *h_c
     struct Cand {
         int nstreams, tri_block, link_ctas, per_mesh;
     };
-    const Cand cands[] = {{1, 256, 0, 0},  {8, 256, 0, 0},  {16, 256, 0, 0}, {8, 256, 2, 0},  {16, 128, 0, 0},
-                          {4, 256, 0, 1},  {8, 256, 0, 1},  {16, 256, 0, 1}, {16, 128, 0, 1}, {16, 512, 0, 1},
-                          {16, 256, 2, 1}, {8, 128, 2, 1}};
+    const Cand cands[] = {{1, 256, 0, 0},  {16, 256, 0, 0}, {16, 128, 0, 0}, {8, 256, 0, 1}, {16, 256, 0, 1},
+                          {16, 256, 2, 1}, {16, 128, 2, 1}, {16, 256, 0, 2}, {16, 256, 1, 2}, {16, 256, 2, 2},
+                          {16, 128, 1, 2}, {16, 128, 2, 2}, {8, 256, 2, 2}};
     const int nc = (int)(sizeof(cands) / sizeof(cands[0]));
     cudaEvent_t e0, e1;
     EMB_CUDA_TRY(cudaEventCreate(&e0));
@@ -500,8 +535,8 @@ extern "C" emb_status emb_batch_configure(emb_batch b, const int32_t *h_choice)
 {
     if (!b || !h_choice) return EMB_ERR_BAD_INPUT;
     const int ns = h_choice[0], tb = h_choice[1], lc = h_choice[2], pm = h_choice[3];
-    if (ns < 1 || ns > BATCH_MAX_STREAMS || (tb != 128 && tb != 256 && tb != 512) || lc < 0 || lc > 64 ||
-        (pm != 0 && pm != 1))
+    if (ns < 1 || ns > BATCH_MAX_STREAMS || (tb != 128 && tb != 256 && tb != 512) || lc < 0 || lc > 64 || pm < 0 ||
+        pm > 2)
         return EMB_ERR_BAD_INPUT;
     b->nstreams = ns;
     b->tri_block = tb;

@@ -402,7 +402,7 @@ def emb_batch_launch(batch: Batch, stream=None):
 
 
 def emb_batch_autotune(batch: Batch, stream=None) -> tuple:
-    """(streams, tri_block, link CTAs per SM, per-mesh link placement) of the fastest shape."""
+    """(streams, tri_block, link CTAs per SM, link placement 0/1/2) of the fastest shape."""
     c = (ctypes.c_int32 * 4)()
     _check(load().emb_batch_autotune(batch.h, _stream(stream), c), "emb_batch_autotune")
     return tuple(c)

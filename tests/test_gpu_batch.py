@@ -77,14 +77,14 @@ def test_batch_replay_graph_and_autotune_match_per_call_path():
         for j in range(len(cases)):
             _same(plain[j], _batch_result(P, B, j), j)
         choice = P.emb_batch_autotune(B, s)
-        assert choice[0] >= 1 and choice[1] in (128, 256, 512) and choice[3] in (0, 1)
+        assert choice[0] >= 1 and choice[1] in (128, 256, 512) and choice[3] in (0, 1, 2)
         P.emb_batch_run(B, s)
         s.synchronize()
         assert P.emb_status_get(s) == P.EMB_OK
         for j in range(len(cases)):
             _same(plain[j], _batch_result(P, B, j), j)
         # both link placements, each replayed and captured
-        for shape in ((3, 128, 0, 0), (5, 512, 1, 1), (16, 256, 0, 1)):
+        for shape in ((3, 128, 0, 0), (5, 512, 1, 1), (16, 256, 0, 1), (7, 256, 2, 2), (16, 128, 0, 2)):
             P.emb_batch_configure(B, *shape)
             P.emb_batch_run(B, s)
             s.synchronize()
@@ -102,7 +102,7 @@ def test_batch_replay_graph_and_autotune_match_per_call_path():
         with pytest.raises(P.EmbError):
             P.emb_batch_configure(B, 4, 96, 0, 1)
         with pytest.raises(P.EmbError):
-            P.emb_batch_configure(B, 4, 256, 0, 2)
+            P.emb_batch_configure(B, 4, 256, 0, 3)
 
 
 def test_batch_mesh_matches_oracle(orc):
