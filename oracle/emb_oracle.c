@@ -267,3 +267,12 @@ int orc_line_hits(const i64 *tri9, const i64 *P, int dir)
     i64 n[3], nc;
     return line_hits(tri9, tri9 + 3, tri9 + 6, P, DIR[dir], n, &nc);
 }
+
+/* out[i * T + t] = 1 iff triangle t overlaps the closed box [lo_i, hi_i]: the
+ * (box, triangle) incidence of the per-block bins (Alg. 2). */
+void orc_box_pairs(const i64 *tri, i64 T, const i64 *lo, const i64 *hi, i64 N, uint8_t *out)
+{
+#pragma omp parallel for schedule(dynamic, 4)
+    for (i64 i = 0; i < N; ++i)
+        for (i64 t = 0; t < T; ++t) out[i * T + t] = (uint8_t)orc_sat(tri + 9 * t, lo + 3 * i, hi + 3 * i);
+}

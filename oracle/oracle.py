@@ -15,6 +15,12 @@ Parity status of each function (see also the module functions' docstrings):
     bounced by a halfway wall, and mass conservation in a cavity with halfway walls
     (tests/test_oracle_lbm.py).  The D3Q19/D3Q27 weights and BGK are the textbook
     ones (the paper cites its LBM and prints neither).
+  * ``xfilter`` and ``finest_bins`` (the binning step's two outputs) — pinned by
+    the closed form of an axis-aligned box, the single crossing of a line through
+    an edge shared by two triangles, the invariance of every solid mask under the
+    filter, the exact reach of the half-cell dilation, a corner that only a true
+    overlap test rejects, and the coverage of every cut link
+    (tests/test_oracle_bins.py).
   * ``paper_flags``, ``build_forest_paper``, ``n_prop`` (the paper's block-layer
     refinement rules) — pinned by the closed form of a block-aligned box and the
     2:1 invariant (tests/test_oracle_paper_policy.py).
@@ -64,6 +70,7 @@ def lib():
         L.orc_solid.argtypes = [P, i64, P, i64, ctypes.c_int, P]
         L.orc_links.argtypes = [P, i64, P, P, i64, i64, P, P, P]
         L.orc_boxes_any.argtypes = [P, i64, P, P, i64, P]
+        L.orc_box_pairs.argtypes = [P, i64, P, P, i64, P]
         L.orc_sat.argtypes = [P, P, P]
         L.orc_sat.restype = ctypes.c_int
         L.orc_segment_hit.argtypes = [P, P, ctypes.c_int, i64, P]
@@ -184,6 +191,67 @@ def boxes_any(tri9: np.ndarray, lo: np.ndarray, hi: np.ndarray) -> np.ndarray:
 
 def sat(tri9_one, lo, hi) -> bool:
     return bool(lib().orc_sat(_p(_c64(tri9_one)), _p(_c64(lo)), _p(_c64(hi))))
+
+
+def cells_per_axis(R: int, L: int) -> int:
+    return 4 * R << L
+
+
+def xfilter(tri9: np.ndarray, R: int, L: int) -> np.ndarray:
+    """Sec. 3.3, step 1 (the 1-D ray indicator of Alg. 1): the ids, ascending, of the
+    triangles that the +x line through the centre of some level-L cell crosses.  The
+    line is the perturbed one of ``solid``, so a triangle the filter drops takes part
+    in no crossing parity of the level.  Brute force over the centre lines inside the
+    triangle's y-z bounding box (no other line can meet it)."""
+    tri9 = _c64(tri9)
+    h = h_units(R, L)
+    half = h // 2
+    n = cells_per_axis(R, L)
+    keep = []
+    for t in range(len(tri9)):
+        ys, zs = tri9[t, 1::3], tri9[t, 2::3]
+        j0, j1 = max(0, -(-(int(ys.min()) - half) // h)), min(n - 1, (int(ys.max()) - half) // h)
+        k0, k1 = max(0, -(-(int(zs.min()) - half) // h)), min(n - 1, (int(zs.max()) - half) // h)
+        hit = False
+        for k in range(k0, k1 + 1):
+            for j in range(j0, j1 + 1):
+                P = np.array([half, (2 * j + 1) * half, (2 * k + 1) * half], dtype=np.int64)
+                if lib().orc_line_hits(_p(tri9[t]), _p(P), 1):
+                    hit = True
+                    break
+            if hit:
+                break
+        if hit:
+            keep.append(t)
+    return np.array(keep, dtype=np.int64)
+
+
+def degenerate(tri9: np.ndarray) -> np.ndarray:
+    """True for triangles with a zero normal (collinear vertices)."""
+    t = _c64(tri9).astype(object)
+    u, v = t[:, 3:6] - t[:, 0:3], t[:, 6:9] - t[:, 0:3]
+    n = np.stack([u[:, 1] * v[:, 2] - u[:, 2] * v[:, 1], u[:, 2] * v[:, 0] - u[:, 0] * v[:, 2],
+                  u[:, 0] * v[:, 1] - u[:, 1] * v[:, 0]], axis=1)
+    return np.all(n == 0, axis=1).astype(bool)
+
+
+def finest_bins(tri9: np.ndarray, R: int, L: int, blocks: np.ndarray) -> list:
+    """Alg. 2 at the finest level: per block, the ids (ascending) of the non-degenerate
+    triangles that overlap the closed block box dilated by half a cell.  A link starts
+    at a cell centre, half a cell inside its block, and reaches one cell further, so
+    it stays inside that box (Alg. 2 dilates by a whole cell; half suffices)."""
+    tri9 = _c64(tri9)
+    h = h_units(R, L)
+    W = 4 * h
+    blocks = _c64(blocks).reshape(-1, 3)
+    lo = _c64(blocks * W - h // 2)
+    hi = _c64((blocks + 1) * W + h // 2)
+    T = len(tri9)
+    inc = np.zeros((len(blocks), T), dtype=np.uint8)
+    if len(blocks) and T:
+        lib().orc_box_pairs(_p(tri9), T, _p(lo), _p(hi), len(blocks), _p(inc))
+    ok = ~degenerate(tri9) if T else np.zeros(0, dtype=bool)
+    return [np.nonzero(inc[i].astype(bool) & ok)[0].astype(np.int64) for i in range(len(blocks))]
 
 
 # --------------------------------------------------------------------------- #
