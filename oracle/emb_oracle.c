@@ -26,6 +26,7 @@
  * is replaced by P + (e, e^2, e^3) with e -> 0+, so a point never lies on a
  * plane, edge or vertex of the mesh and every decision is unique.
  */
+#include <math.h>
 #include <stdint.h>
 #include <string.h>
 
@@ -275,4 +276,88 @@ void orc_box_pairs(const i64 *tri, i64 T, const i64 *lo, const i64 *hi, i64 N, u
 #pragma omp parallel for schedule(dynamic, 4)
     for (i64 i = 0; i < N; ++i)
         for (i64 t = 0; t < T; ++t) out[i * T + t] = (uint8_t)orc_sat(tri + 9 * t, lo + 3 * i, hi + 3 * i);
+}
+
+/* ---------------------------------------------------------------------- */
+/* The paper's guard-cell voxelizer (Sec. 3.4, "Partial Surface            */
+/* Voxelization", Alg. 3): single-precision nearest-hit classification of  */
+/* each cell from the faces of its block's bin.  Plain IEEE binary32        */
+/* arithmetic, one rounding per operation in the order written (the file is */
+/* compiled with -ffp-contract=off, so no multiply-add is fused).           */
+/* ---------------------------------------------------------------------- */
+#define GUARD_EPS 1.1920928955078125e-7f /* 2^-23, the binary32 machine epsilon */
+
+/* Does the face (yz projection a, b, c) touch the thin box around the x-line
+ * through (py, pz)?  The box spans the domain along x, so only the axes of the
+ * yz projection can separate: y, z and the three edge normals.  Half-width in y
+ * and z: GUARD_EPS.  Touching counts as overlap. */
+static int guard_in_face(const float *ty, const float *tz, float py, float pz)
+{
+    float y[3], z[3];
+    for (int i = 0; i < 3; ++i) {
+        y[i] = ty[i] - py;
+        z[i] = tz[i] - pz;
+    }
+    float ylo = y[0], yhi = y[0], zlo = z[0], zhi = z[0];
+    for (int i = 1; i < 3; ++i) {
+        if (y[i] < ylo) ylo = y[i];
+        if (y[i] > yhi) yhi = y[i];
+        if (z[i] < zlo) zlo = z[i];
+        if (z[i] > zhi) zhi = z[i];
+    }
+    if (ylo > GUARD_EPS || yhi < -GUARD_EPS) return 0;
+    if (zlo > GUARD_EPS || zhi < -GUARD_EPS) return 0;
+    for (int i = 0; i < 3; ++i) {
+        int k = (i + 1) % 3;
+        float ey = y[k] - y[i];
+        float ez = z[k] - z[i];
+        float r = GUARD_EPS * (fabsf(ey) + fabsf(ez));
+        float lo = 0.0f, hi = 0.0f;
+        for (int m = 0; m < 3; ++m) {
+            float p = z[m] * ey - y[m] * ez; /* projection on the edge normal (-ez, ey) */
+            if (m == 0 || p < lo) lo = p;
+            if (m == 0 || p > hi) hi = p;
+        }
+        if (lo > r || hi < -r) return 0;
+    }
+    return 1;
+}
+
+/* state[i * 64 + t] for cell t of block i (t = x + 4 y + 16 z): 0 no face hit,
+ * 1 solid, 2 guard.  Cell centre (2 g + 1) / (2 n) per axis (n cells per axis,
+ * g the global cell index), one division.  Faces in ascending id order from the
+ * CSR bins; for each, the unit normal n = (v2 - v1) x (v3 - v1) / |...|, the
+ * signed distance d = ((v1 - c) . n) / n_x along x, and the point-in-face test;
+ * the nearest accepted face (strictly smaller |d|, starting from 1) decides:
+ * solid if n_x d > 0, guard otherwise. */
+void orc_guard_surface(const float *verts, const int32_t *tris, const i64 *blocks, i64 N, const i64 *off,
+                       const i64 *ent, i64 ncell, uint8_t *state)
+{
+#pragma omp parallel for schedule(dynamic, 4)
+    for (i64 i = 0; i < N; ++i) {
+        for (int t = 0; t < 64; ++t) {
+            i64 g[3] = {4 * blocks[3 * i] + (t & 3), 4 * blocks[3 * i + 1] + ((t >> 2) & 3),
+                        4 * blocks[3 * i + 2] + (t >> 4)};
+            float c[3];
+            for (int a = 0; a < 3; ++a) c[a] = (float)(2 * g[a] + 1) / (float)(2 * ncell);
+            float dmin = 1.0f;
+            int st = 0;
+            for (i64 e = off[i]; e < off[i + 1]; ++e) {
+                const int32_t *tv = tris + 3 * ent[e];
+                const float *v1 = verts + 3 * tv[0], *v2 = verts + 3 * tv[1], *v3 = verts + 3 * tv[2];
+                float u[3] = {v2[0] - v1[0], v2[1] - v1[1], v2[2] - v1[2]};
+                float w[3] = {v3[0] - v1[0], v3[1] - v1[1], v3[2] - v1[2]};
+                float n[3] = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0]};
+                float len = sqrtf(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+                for (int a = 0; a < 3; ++a) n[a] = n[a] / len;
+                float d = ((v1[0] - c[0]) * n[0] + (v1[1] - c[1]) * n[1] + (v1[2] - c[2]) * n[2]) / n[0];
+                if (!(fabsf(d) < dmin)) continue;
+                float ty[3] = {v1[1], v2[1], v3[1]}, tz[3] = {v1[2], v2[2], v3[2]};
+                if (!guard_in_face(ty, tz, c[1], c[2])) continue;
+                dmin = fabsf(d);
+                st = n[0] * d > 0.0f ? 1 : 2;
+            }
+            state[i * 64 + t] = (uint8_t)st;
+        }
+    }
 }

@@ -21,6 +21,13 @@ Parity status of each function (see also the module functions' docstrings):
     filter, the exact reach of the half-cell dilation, a corner that only a true
     overlap test rejects, and the coverage of every cut link
     (tests/test_oracle_bins.py).
+  * ``guard_voxelize`` (the paper's single-precision guard-cell voxelizer, built as
+    an ablation of the exact one) — pinned by closed forms: a box whose faces lie
+    between cell centres gives exactly its inside, with every block present and
+    with the interior left unrefined (holes entered from the solid side); a box
+    whose faces lie on centre planes gives the half-open set the nearest-face rule
+    implies (tests/test_oracle_guard.py).  The box half-width of the point-in-face
+    test (the binary32 epsilon) is a reading with no closed form to pin it.
   * ``paper_flags``, ``build_forest_paper``, ``n_prop`` (the paper's block-layer
     refinement rules) — pinned by the closed form of a block-aligned box and the
     2:1 invariant (tests/test_oracle_paper_policy.py).
@@ -53,7 +60,7 @@ def build(force: bool = False) -> str:
     """Compile the C core with gcc (OpenMP) into oracle/liboracle.so."""
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-o", tmp, _SRC])
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -71,6 +78,7 @@ def lib():
         L.orc_links.argtypes = [P, i64, P, P, i64, i64, P, P, P]
         L.orc_boxes_any.argtypes = [P, i64, P, P, i64, P]
         L.orc_box_pairs.argtypes = [P, i64, P, P, i64, P]
+        L.orc_guard_surface.argtypes = [P, P, P, i64, P, P, i64, P]
         L.orc_sat.argtypes = [P, P, P]
         L.orc_sat.restype = ctypes.c_int
         L.orc_segment_hit.argtypes = [P, P, ctypes.c_int, i64, P]
@@ -413,6 +421,107 @@ def balanced_2to1(blocks_by_level, R: int) -> bool:
                 if q not in fine and (q[0] // 2, q[1] // 2, q[2] // 2) not in coarse:
                     return False
     return True
+
+
+# --------------------------------------------------------------------------- #
+# The paper's guard-cell voxelizer (Sec. 3.4, "Partial Surface Voxelization" with
+# Alg. 3, and "External Cell Flag Propagation"), on the finest level of a forest
+# --------------------------------------------------------------------------- #
+FLUID, SOLID, GUARD = 0, 1, 2
+
+
+def guard_surface(verts, tris, R: int, L: int, blocks: np.ndarray) -> np.ndarray:
+    """(n, 64) cell states before propagation: each cell takes the nearest face of its
+    block's bin crossed by its x-line (binary32, C core ``orc_guard_surface``):
+    SOLID if the centre is behind that face (n_x d > 0), GUARD if in front, FLUID if no
+    face of the bin is hit."""
+    v = np.ascontiguousarray(np.asarray(verts, dtype=np.float32))
+    t = np.ascontiguousarray(np.asarray(tris, dtype=np.int32))
+    tri9 = tri_coords(int_coords(v, R), t)
+    blocks = _c64(blocks).reshape(-1, 3)
+    bins = finest_bins(tri9, R, L, blocks)
+    off = _c64(np.concatenate([[0], np.cumsum([len(b) for b in bins])]).astype(np.int64))
+    ent = _c64(np.concatenate(bins).astype(np.int64) if len(bins) else np.zeros(0, np.int64))
+    state = np.zeros((len(blocks), 64), dtype=np.uint8)
+    if len(blocks):
+        lib().orc_guard_surface(_p(v), _p(t), _p(blocks), len(blocks), _p(off), _p(ent), cells_per_axis(R, L),
+                                _p(state))
+    return state
+
+
+def guard_internal(state: np.ndarray) -> np.ndarray:
+    """Internal propagation along x inside each block: three rounds in which every cell
+    looks at its two x-neighbours of the previous round; a FLUID cell next to a GUARD
+    becomes GUARD, then a cell that is not GUARD next to a SOLID becomes SOLID.  Three
+    rounds carry a flag across a row of four cells."""
+    H = state.reshape(-1, 4, 4, 4).copy()  # (block, z, y, x)
+    for _ in range(3):
+        left = np.full_like(H, FLUID)
+        right = np.full_like(H, FLUID)
+        left[..., 1:] = H[..., :-1]
+        right[..., :-1] = H[..., 1:]
+        new = H.copy()
+        new[(H == FLUID) & ((left == GUARD) | (right == GUARD))] = GUARD
+        new[(new != GUARD) & ((left == SOLID) | (right == SOLID))] = SOLID
+        H = new
+    return H.reshape(-1, 64)
+
+
+def guard_external(state: np.ndarray, R: int, L: int, blocks_by_level, masks_by_level) -> np.ndarray:
+    """External propagation along +x, then (levels L > 0) along -x.  Each maximal run of
+    consecutive blocks along the direction is walked from its first block, row by row:
+    the status is the row's cell on the face ahead; a run whose first block borders a
+    hole left by a coarser block with a solid cell starts from the solid (the row's
+    non-guard cells turn SOLID unless the status is GUARD); in each following block a
+    SOLID status turns the row's non-guard cells SOLID, and the status is read again."""
+    H = state.reshape(-1, 4, 4, 4).copy()
+    blocks = _c64(blocks_by_level[L]).reshape(-1, 3)
+    index = {tuple(b): i for i, b in enumerate(blocks.tolist())}
+    coarse = [{tuple(b): i for i, b in enumerate(_c64(blocks_by_level[l]).reshape(-1, 3).tolist())} for l in range(L)]
+    nb = R << L
+
+    def hole_is_solid(p):
+        for l in range(L - 1, -1, -1):
+            q = tuple(c >> (L - l) for c in p)
+            j = coarse[l].get(q)
+            if j is not None:
+                return bool(np.asarray(masks_by_level[l], dtype=np.uint64)[j] != 0)
+        return False
+
+    for step in ([1, -1] if L > 0 else [1]):
+        face = 3 if step > 0 else 0
+        for i, b in enumerate(blocks.tolist()):
+            before = (b[0] - step, b[1], b[2])
+            if before in index:
+                continue  # not the first block of its run
+            special = 0 <= before[0] < nb and hole_is_solid(before)
+            run = [i]
+            nxt = (b[0] + step, b[1], b[2])
+            while nxt in index:
+                run.append(index[nxt])
+                nxt = (nxt[0] + step, nxt[1], nxt[2])
+            for z in range(4):
+                for y in range(4):
+                    status = H[i, z, y, face]
+                    if special and status != GUARD:
+                        row = H[i, z, y]
+                        row[row != GUARD] = SOLID
+                        status = SOLID
+                    for j in run[1:]:
+                        if status == SOLID:
+                            row = H[j, z, y]
+                            row[row != GUARD] = SOLID
+                        status = H[j, z, y, face]
+    return H.reshape(-1, 64)
+
+
+def guard_voxelize(verts, tris, R: int, L: int, blocks_by_level, masks_by_level):
+    """The guard-cell voxelizer on level L of a forest: (solid words, guard words) per
+    block after both propagations; the paper then turns the guards back into fluid, so
+    the solid words are its cell masks.  masks_by_level[l] for l < L decide the holes."""
+    st = guard_surface(verts, tris, R, L, blocks_by_level[L])
+    st = guard_external(guard_internal(st), R, L, blocks_by_level, masks_by_level)
+    return pack_masks(st == SOLID), pack_masks(st == GUARD)
 
 
 def cell_centres(R: int, L: int, blocks: np.ndarray) -> np.ndarray:
