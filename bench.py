@@ -387,6 +387,7 @@ def run_ours(args):
         line["ablation"] = ablation_leg(P, verts, tris, w, lattice)
         line["lbm"] = lbm_leg(P)
         line["moving"] = moving_leg(P)
+        line["guard_ablation"] = guard_leg(P, verts, tris, w, lattice)
         units_s, secs = oracle_sample(v, t, w, lattice, 6, seed=7)
         line["cpu_baseline"] = dict(value=units_s / secs, unit=UNIT, cores=omp_threads(), kind="oracle",
                                     sample=("6 surface blocks of the finest level: 64 cell states each, the states "
@@ -579,6 +580,48 @@ def ablation_leg(P, verts, tris, w, lattice, reps=3):
     out["triangles"] = len(tris)
     out["timing"] = "emb_bin + emb_voxelize per level, CUDA events, median of %d" % reps
     return out
+
+
+def guard_leg(P, v, t, w, lattice, reps=10):
+    """The paper's guard-cell voxelizer (binary32 nearest face, internal and external
+    propagation) against the exact parity voxelizer on the finest level of the bench
+    workload: median CUDA-event time of each on the same bins, and the cells on which
+    the two disagree."""
+    import torch
+    stream = torch.cuda.current_stream()
+    E = P.embed(v, t, w.R, w.levels, w.band, lattice, keep_bins=True, check_watertight=False)
+    L = w.levels
+    fin = E.bins[-1]
+    exact = E.masks[L].clone()
+    n = exact.numel()
+    solid = torch.empty(n, dtype=torch.int64, device="cuda")
+    guard = torch.empty(n, dtype=torch.int64, device="cuda")
+    vox = torch.empty(n, dtype=torch.int64, device="cuda")
+
+    def timed(fn):
+        runs = []
+        for rep in range(reps + 2):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            if rep >= 2:
+                runs.append(a.elapsed_time(b))
+        return statistics.median(runs)
+
+    g_ms = timed(lambda: P.emb_voxelize_guard(E.forest, fin, solid, guard))
+    e_ms = timed(lambda: P.emb_voxelize(E.forest, fin, L, vox))
+    st = P.emb_status_get()
+
+    def popc(x):
+        return int(np.unpackbits(x.cpu().numpy().view(np.uint8)).sum())
+
+    return dict(level=L, blocks=n, guard_ms=round(g_ms, 4), exact_ms=round(e_ms, 4),
+                solid_cells_exact=popc(exact), guard_cells=popc(guard),
+                cells_differing=popc(solid ^ exact), solid_only_in_guard=popc(solid & ~exact),
+                solid_only_in_exact=popc(exact & ~solid), exact_rerun_identical=bool(torch.equal(vox, exact)),
+                status=st, timing=f"CUDA events, median of {reps}; both on the finest bins of the step")
 
 
 def batch_leg(P, reps=5):

@@ -190,6 +190,31 @@ emb_status emb_bins_copy(emb_bins b, uint32_t *d_filtered, uint32_t *d_off, uint
  * Errors: EMB_ERR_STATE (bins of another level, missing level). */
 emb_status emb_voxelize(emb_forest f, emb_bins b, int32_t level, uint64_t *d_solid_mask, void *stream);
 
+/* The paper's own voxelizer, for the ablation of the exact one above (Sec. 3.4,
+ * "Partial Surface Voxelization" with Alg. 3, and "External Cell Flag
+ * Propagation"), on the finest level of the forest (`b` = its bins):
+ *  (1) every cell takes the nearest face of its block's bin that its +x line meets,
+ *      in binary32: signed distance d = ((v1 - c) . n) / n_x to the face's plane
+ *      (n the unit normal), point-in-face by overlap of the face with a box of
+ *      half-width 2^-23 around the line, equal |d| to the lowest face id; the cell
+ *      is solid if n_x d > 0, a guard otherwise, untouched if no face is met;
+ *  (2) internal propagation along x inside each block (three rounds: a fluid cell
+ *      next to a guard becomes a guard, then a non-guard cell next to a solid
+ *      becomes solid);
+ *  (3) external propagation along +x, then (max_level > 0) along -x: each run of
+ *      consecutive blocks is walked from its first block, a solid status turning
+ *      the next block's row solid except at guards; a run whose first block borders
+ *      a hole left by a coarser block with a solid cell (the masks of the coarser
+ *      levels decide) starts from the solid.
+ * d_solid_mask gets the solid cells (the paper's masks once guards turn back into
+ * fluid), d_guard_mask the guard cells, one uint64 per finest block each, distinct
+ * device buffers owned by the caller.  The forest's own masks are not changed.
+ * Enqueues only (after completing the bins, as emb_cutlinks does).
+ * Errors: EMB_ERR_BAD_INPUT (NULL or equal outputs), EMB_ERR_STATE (bins of another
+ * level, coarser masks missing; on the device: a bin entry outside the mesh). */
+emb_status emb_voxelize_guard(emb_forest f, emb_bins b, uint64_t *d_solid_mask, uint64_t *d_guard_mask,
+                              void *stream);
+
 /* -------------------------------------------------------------- refine ---- */
 /* Near-wall refinement flags of `level` < max_level (Sec. 3.4, "Refinement
  * Flagging"; near-wall criterion d_spec): flag = some triangle overlaps the

@@ -39,6 +39,7 @@ SIGNATURES = {
     "emb_bins_stats": (I32, [P, PI64, PI64]),
     "emb_bins_copy": (I32, [P, P, P, P, P]),
     "emb_voxelize": (I32, [P, P, I32, P, P]),
+    "emb_voxelize_guard": (I32, [P, P, P, P, P]),
     "emb_refine_flags": (I32, [P, P, I32, I32, P, P]),
     "emb_refine_flags_paper": (I32, [P, I32, ctypes.c_double, P, P]),
     "emb_cutlinks_count": (I32, [P, I32, PI64, P]),

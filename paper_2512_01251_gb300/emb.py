@@ -215,6 +215,20 @@ def emb_voxelize(forest: Forest, bins: Bins, level: int, out: torch.Tensor | Non
     return out
 
 
+def emb_voxelize_guard(forest: Forest, bins: Bins, out_solid: torch.Tensor | None = None,
+                       out_guard: torch.Tensor | None = None, stream=None):
+    """The paper's guard-cell voxelizer on the finest level (the ablation of the exact
+    one): (solid words, guard words) as int64 tensors holding the uint64 patterns."""
+    n = emb_forest_num_blocks(forest, bins.level)
+    if out_solid is None:
+        out_solid = torch.empty(max(n, 1), dtype=torch.int64, device="cuda")
+    if out_guard is None:
+        out_guard = torch.empty(max(n, 1), dtype=torch.int64, device="cuda")
+    _check(load().emb_voxelize_guard(forest.h, bins.h, _ptr(out_solid), _ptr(out_guard), _stream(stream)),
+           "emb_voxelize_guard")
+    return out_solid[:n], out_guard[:n]
+
+
 def emb_refine_flags(forest: Forest, bins: Bins, level: int, band: int, out: torch.Tensor | None = None,
                      stream=None):
     if out is None:
