@@ -27,7 +27,7 @@
 
 #include "emb_internal.cuh"
 
-#define BATCH_MAX_STREAMS 16
+#define BATCH_MAX_STREAMS 32
 
 struct BLevel {
     EmbLevel lv;                     // key, hash, bitmap, mask (+ nbr at the finest level)
@@ -167,10 +167,11 @@ static emb_status alloc_mesh(BMesh &B)
         const int64_t nw = emb_bitmap_words(lv.nb_axis);
         wmax = nw > wmax ? nw : wmax;
         BTRY(balloc(B, &lv.key, lv.n + 1));
-        lv.hcap = emb_hash_capacity(lv.n);
-        BTRY(balloc(B, &lv.hkey, lv.hcap));
-        BTRY(balloc(B, &lv.hval, lv.hcap));
-        if (nw > 0) {
+        if (nw == 0) {  // the level is looked up through its hash
+            lv.hcap = emb_hash_capacity(lv.n);
+            BTRY(balloc(B, &lv.hkey, lv.hcap));
+            BTRY(balloc(B, &lv.hval, lv.hcap));
+        } else {
             BTRY(balloc(B, &lv.bits, nw));
             BTRY(balloc(B, &lv.wpre, nw + 1));
         }
@@ -230,28 +231,24 @@ static emb_status enqueue_mesh(BMesh &B, int tri_block, cudaStream_t s)
         BLevel &BL = B.L[L];
         EmbLevel &lv = BL.lv;
         const LevelGeom g = level_geom(&B.geo, L);
-        BTRY(emb_enq_filter(rec, T, g, B.flag, B.pos, BL.flist, B.tmp, tri_block, s));
-        BTRY(emb_expect_u32(B.pos + T, (uint64_t)BL.nf, s));
+        BTRY(emb_enq_filter(rec, T, g, B.flag, B.pos, BL.flist, B.tmp, tri_block, s, (uint64_t)BL.nf));
         BTRY(emb_enq_voxelize(rec, T, BL.flist, BL.nf, B.pos + T, nullptr, g, lv, B.s_acc, B.p_acc, B.t_acc, B.bq, tri_block, s));
         if (L < B.Lf) {
             const long long dil = emb_refine_dilation(&B.geo, L, B.band);
             if (dil < 0) return EMB_ERR_RANGE;
             BTRY(emb_enq_refine(rec, T, g, dil, lv, BL.flags, B.fbits, B.bq, s));
-            BTRY(emb_enq_flag_ranks(lv, BL.flags, B.cnt, B.rank, B.tmp, s));
-            BTRY(emb_expect_u32(B.rank + lv.n, (uint64_t)BL.F, s));
+            BTRY(emb_enq_flag_ranks(lv, BL.flags, B.cnt, B.rank, B.tmp, s, (uint64_t)BL.F));
             EmbLevel &C = B.L[L + 1].lv;
             BTRY(emb_enq_children(lv, BL.flags, B.rank, C.key, C.n, true, s));
             BTRY(emb_enq_level_index(C, B.pc, B.tmp, s));
         } else {
             BTRY(emb_enq_bin_pairs(rec, T, g, lv, B.cnt, B.bin_off, B.list_bs, B.list_tri, B.list_n, (uint64_t)B.pairs,
-                                   B.tmp, B.bq, s));
-            BTRY(emb_expect_u32(B.bin_off + lv.n, (uint64_t)B.pairs, s));
+                                   B.tmp, B.bq, s, (uint64_t)B.pairs));
             BTRY(emb_enq_bin_scatter(B.list_bs, B.list_tri, B.list_n, (uint64_t)B.pairs, B.bin_off, B.bin_ent,
                                      (uint64_t)B.pairs, s));
             BTRY(emb_enq_neighbors(lv, s));
-            BTRY(emb_enq_link_prep(lv, B.lattice, B.cand, B.cnt, B.rank, B.work_n, B.work, B.blk_off, B.tmp, s));
-            BTRY(emb_expect_u32(B.work_n + lv.n, (uint64_t)B.nwork, s));
-            BTRY(emb_expect_u32(B.blk_off + lv.n, (uint64_t)B.links, s));
+            BTRY(emb_enq_link_prep(lv, B.lattice, B.cand, B.cnt, B.rank, B.work_n, B.work, B.blk_off, B.tmp, s,
+                                   (uint64_t)B.nwork, (uint64_t)B.links));
             BTRY(emb_enq_link_split(lv, B.work, B.work_n + lv.n, B.cand, B.blk_off, B.bin_off, B.witem, B.extra,
                                     B.extra_n, (uint32_t)emb_link_extra_capacity(lv.n), s));
         }

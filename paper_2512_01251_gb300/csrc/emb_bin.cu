@@ -310,10 +310,10 @@ __global__ void __launch_bounds__(EMB_BIG_BLOCK) k_bin_pairs_big(const int4 *__r
 // Step 1 (enqueue only): flag, pos, flist hold T + 1 uint32; the kept count ends at
 // pos[T]; tmp is scan scratch for T entries.
 emb_status emb_enq_filter(const int4 *rec, int64_t T, LevelGeom g, uint32_t *flag, uint32_t *pos, uint32_t *flist,
-                          uint64_t *tmp, int block, cudaStream_t s)
+                          uint64_t *tmp, int block, cudaStream_t s, uint64_t expect)
 {
     EMB_LAUNCH((k_xfilter), emb_grid(T, block), block, 0, s)(rec, T, g, flag);
-    emb_status rc = emb_scan_into(flag, pos, T, tmp, s);
+    emb_status rc = emb_scan_into_expect(flag, pos, T, tmp, expect, s);
     if (rc != EMB_OK) return rc;
     EMB_LAUNCH((k_compact), emb_grid(T, 256), 256, 0, s)(flag, pos, T, flist);
     EMB_CUDA_TRY(cudaGetLastError());
@@ -339,7 +339,7 @@ __global__ void k_bin_scatter(const uint2 *__restrict__ bs, const uint32_t *__re
 // list holds list_cap entries (list_n counts the requests); tmp: scan scratch for n.
 emb_status emb_enq_bin_pairs(const int4 *rec, int64_t T, LevelGeom g, const EmbLevel &lv, uint32_t *cnt, uint32_t *off,
                              uint2 *list_bs, uint32_t *list_tri, unsigned long long *list_n, uint64_t list_cap,
-                             uint64_t *tmp, const EmbBigQ &Q, cudaStream_t s)
+                             uint64_t *tmp, const EmbBigQ &Q, cudaStream_t s, uint64_t expect)
 {
     EMB_CUDA_TRY(cudaMemsetAsync(cnt, 0, (lv.n + 1) * sizeof(uint32_t), s));
     EMB_CUDA_TRY(cudaMemsetAsync(list_n, 0, sizeof(unsigned long long), s));
@@ -350,7 +350,7 @@ emb_status emb_enq_bin_pairs(const int4 *rec, int64_t T, LevelGeom g, const EmbL
         EMB_LAUNCH((k_bin_pairs), emb_grid(T, 32 * EMB_WU_WARPS), 32 * EMB_WU_WARPS, 0, s)(rec, T, g, g.half, lk, cnt, PL,
                                                                                            Q);
     if (Q.cap) EMB_LAUNCH((k_bin_pairs_big), EMB_BIG_GRID, EMB_BIG_BLOCK, 0, s)(rec, g, g.half, lk, cnt, PL, Q);
-    return emb_scan_into(cnt, off, lv.n, tmp, s);
+    return emb_scan_into_expect(cnt, off, lv.n, tmp, expect, s);
 }
 
 // Scatter half: ent holds ent_cap entries.

@@ -159,8 +159,24 @@ __global__ void k_scan_sums(uint64_t *__restrict__ tile_sum, int64_t ntiles, uin
     if (threadIdx.x == 0) *total = carry;
 }
 
+// Writes the tile's exclusive sums from its offset `run`; entry n receives the total,
+// which is checked against `expect` unless that is EMB_NO_EXPECT.
+__device__ __forceinline__ void scan_write_tile(const uint32_t v[SCAN_ITEMS], int64_t base, int64_t n, uint64_t run,
+                                                uint32_t *__restrict__ out, uint64_t expect, int *st)
+{
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        if (base + i <= n) {  // entry n receives the total
+            if (run > 0xFFFFFFFFull) emb_set_status(st, EMB_ERR_CAPACITY);
+            out[base + i] = (uint32_t)run;
+            if (base + i == n && expect != EMB_NO_EXPECT && run != expect) emb_set_status(st, EMB_ERR_STATE);
+        }
+        run += v[i];
+    }
+}
+
 __global__ void k_scan_apply(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int64_t n,
-                             const uint64_t *__restrict__ tile_off, int *st)
+                             const uint64_t *__restrict__ tile_off, uint64_t expect, int *st)
 {
     __shared__ uint64_t tot;
     int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
@@ -171,31 +187,64 @@ __global__ void k_scan_apply(const uint32_t *__restrict__ in, uint32_t *__restri
         v[i] = base + i < n ? in[base + i] : 0u;
         s += v[i];
     }
-    uint64_t run = tile_off[blockIdx.x] + block_excl_scan(s, &tot);
+    const uint64_t run = tile_off[blockIdx.x] + block_excl_scan(s, &tot);
+    scan_write_tile(v, base, n, run, out, expect, st);
+}
+
+// Apply with the scan of the tile sums folded in: each tile adds up the sums of the
+// tiles before it (few enough to read them all), and the last tile stores the total
+// after the sums.  With one tile it is the whole scan in one launch.
+__global__ void k_scan_apply_fused(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int64_t n,
+                                   uint64_t *__restrict__ tile_sum, int64_t ntiles, uint64_t expect, int *st)
+{
+    __shared__ uint64_t tot, before;
+    uint64_t part = 0;
+    for (int64_t i = threadIdx.x; i < (int64_t)blockIdx.x; i += SCAN_BLOCK) part += tile_sum[i];
+    block_excl_scan(part, &before);
+    const uint64_t off = before;
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    uint32_t v[SCAN_ITEMS];
+    uint64_t s = 0;
 #pragma unroll
     for (int i = 0; i < SCAN_ITEMS; ++i) {
-        if (base + i <= n) {  // entry n receives the total
-            if (run > 0xFFFFFFFFull) emb_set_status(st, EMB_ERR_CAPACITY);
-            out[base + i] = (uint32_t)run;
-        }
-        run += v[i];
+        v[i] = base + i < n ? in[base + i] : 0u;
+        s += v[i];
     }
+    const uint64_t run = off + block_excl_scan(s, &tot);
+    if (threadIdx.x == 0 && (int64_t)blockIdx.x == ntiles - 1) tile_sum[ntiles] = off + tot;
+    scan_write_tile(v, base, n, run, out, expect, st);
 }
 
 int64_t emb_scan_tmp_words(int64_t n) { return (n + 1 + SCAN_TILE - 1) / SCAN_TILE + 1; }
 
-// d_out gets n + 1 entries: exclusive prefix sums and, at index n, the total.
-// tmp: emb_scan_tmp_words(n) uint64 words of scratch.  Enqueues only.
-emb_status emb_scan_into(const uint32_t *d_in, uint32_t *d_out, int64_t n, uint64_t *tmp, cudaStream_t s)
+// Above this many tiles the tile sums get a scan of their own.
+#define SCAN_FUSE_TILES 1024
+
+// d_out gets n + 1 entries: exclusive prefix sums and, at index n, the total (also in
+// tmp[ntiles]); a total other than `expect` raises EMB_ERR_STATE on the device.
+// tmp: emb_scan_tmp_words(n) uint64 words of scratch.  Enqueues only: one launch up
+// to SCAN_TILE entries, two up to SCAN_FUSE_TILES tiles, three beyond.
+emb_status emb_scan_into_expect(const uint32_t *d_in, uint32_t *d_out, int64_t n, uint64_t *tmp, uint64_t expect,
+                                cudaStream_t s)
 {
     int *st = emb_status_word();
     if (!st) return EMB_ERR_CUDA;
     int64_t ntiles = (n + 1 + SCAN_TILE - 1) / SCAN_TILE;
-    EMB_LAUNCH((k_scan_tile_sums), (int)ntiles, SCAN_BLOCK, 0, s)(d_in, n, tmp);
-    EMB_LAUNCH((k_scan_sums), 1, SCAN_BLOCK, 0, s)(tmp, ntiles, tmp + ntiles);
-    EMB_LAUNCH((k_scan_apply), (int)ntiles, SCAN_BLOCK, 0, s)(d_in, d_out, n, tmp, st);
+    if (ntiles <= SCAN_FUSE_TILES) {
+        if (ntiles > 1) EMB_LAUNCH((k_scan_tile_sums), (int)ntiles, SCAN_BLOCK, 0, s)(d_in, n, tmp);
+        EMB_LAUNCH((k_scan_apply_fused), (int)ntiles, SCAN_BLOCK, 0, s)(d_in, d_out, n, tmp, ntiles, expect, st);
+    } else {
+        EMB_LAUNCH((k_scan_tile_sums), (int)ntiles, SCAN_BLOCK, 0, s)(d_in, n, tmp);
+        EMB_LAUNCH((k_scan_sums), 1, SCAN_BLOCK, 0, s)(tmp, ntiles, tmp + ntiles);
+        EMB_LAUNCH((k_scan_apply), (int)ntiles, SCAN_BLOCK, 0, s)(d_in, d_out, n, tmp, expect, st);
+    }
     EMB_CUDA_TRY(cudaGetLastError());
     return EMB_OK;
+}
+
+emb_status emb_scan_into(const uint32_t *d_in, uint32_t *d_out, int64_t n, uint64_t *tmp, cudaStream_t s)
+{
+    return emb_scan_into_expect(d_in, d_out, n, tmp, EMB_NO_EXPECT, s);
 }
 
 emb_status emb_scan_u32(const uint32_t *d_in, uint32_t *d_out, int64_t n, uint64_t *h_total, cudaStream_t s)
@@ -210,21 +259,6 @@ emb_status emb_scan_u32(const uint32_t *d_in, uint32_t *d_out, int64_t n, uint64
         EMB_CUDA_TRY(cudaStreamSynchronize(s));
     }
     EMB_CUDA_TRY(cudaFreeAsync(tmp, s));
-    return EMB_OK;
-}
-
-// Raises EMB_ERR_STATE when a count recomputed on the device differs from the planned one.
-__global__ void k_expect_u32(const uint32_t *__restrict__ got, uint64_t expect, int *st)
-{
-    if (threadIdx.x == 0 && blockIdx.x == 0 && (uint64_t)*got != expect) emb_set_status(st, EMB_ERR_STATE);
-}
-
-emb_status emb_expect_u32(const uint32_t *d_got, uint64_t expect, cudaStream_t s)
-{
-    int *st = emb_status_word();
-    if (!st) return EMB_ERR_CUDA;
-    EMB_LAUNCH((k_expect_u32), 1, 32, 0, s)(d_got, expect, st);
-    EMB_CUDA_TRY(cudaGetLastError());
     return EMB_OK;
 }
 
@@ -281,16 +315,19 @@ int64_t emb_bitmap_words(int64_t nb)
     return cells <= EMB_BITMAP_MAX_BITS ? (cells + 63) / 64 : 0;
 }
 
-// Hash and rank bitmap of a level whose keys are in place; buffers sized by
-// emb_hash_capacity / emb_bitmap_words; pc: words + 1 uint32, tmp: scan scratch.
+// Rank bitmap of a level whose keys are in place or, where the level's dense positions
+// exceed EMB_BITMAP_MAX_BITS, its hash (lookups use whichever exists); buffers sized by
+// emb_bitmap_words / emb_hash_capacity; pc: words + 1 uint32, tmp: scan scratch.
 emb_status emb_enq_level_index(EmbLevel &lv, uint32_t *pc, uint64_t *tmp, cudaStream_t s)
 {
     int *st = emb_status_word();
     if (!st) return EMB_ERR_CUDA;
-    EMB_CUDA_TRY(cudaMemsetAsync(lv.hkey, 0xFF, lv.hcap * sizeof(uint64_t), s));
-    if (lv.n > 0) EMB_LAUNCH((k_hash_insert), emb_grid(lv.n, 256), 256, 0, s)(lv.key, lv.n, lv.hkey, lv.hval, lv.hcap, st);
     int64_t nw = emb_bitmap_words(lv.nb_axis);
-    if (lv.bits && nw > 0) {
+    if (!(lv.bits && nw > 0)) {
+        EMB_CUDA_TRY(cudaMemsetAsync(lv.hkey, 0xFF, lv.hcap * sizeof(uint64_t), s));
+        if (lv.n > 0)
+            EMB_LAUNCH((k_hash_insert), emb_grid(lv.n, 256), 256, 0, s)(lv.key, lv.n, lv.hkey, lv.hval, lv.hcap, st);
+    } else {
         EMB_CUDA_TRY(cudaMemsetAsync(lv.bits, 0, nw * sizeof(uint64_t), s));
         if (lv.n > 0)
             EMB_LAUNCH((k_bits_set), emb_grid(lv.n, 256), 256, 0, s)(lv.key, lv.n, lv.nb_axis, (unsigned long long *)lv.bits);
@@ -310,10 +347,15 @@ emb_status emb_build_hash(EmbLevel &lv, cudaStream_t s)
     if (lv.wpre) EMB_CUDA_TRY(cudaFreeAsync(lv.wpre, s));
     lv.bits = nullptr;
     lv.wpre = nullptr;
-    lv.hcap = emb_hash_capacity(lv.n);
-    EMB_CUDA_TRY(cudaMallocAsync(&lv.hkey, lv.hcap * sizeof(uint64_t), s));
-    EMB_CUDA_TRY(cudaMallocAsync(&lv.hval, lv.hcap * sizeof(int32_t), s));
+    lv.hkey = nullptr;
+    lv.hval = nullptr;
+    lv.hcap = 0;
     int64_t nw = emb_bitmap_words(lv.nb_axis);
+    if (nw == 0) {
+        lv.hcap = emb_hash_capacity(lv.n);
+        EMB_CUDA_TRY(cudaMallocAsync(&lv.hkey, lv.hcap * sizeof(uint64_t), s));
+        EMB_CUDA_TRY(cudaMallocAsync(&lv.hval, lv.hcap * sizeof(int32_t), s));
+    }
     uint32_t *pc = nullptr;
     uint64_t *tmp = nullptr;
     if (nw > 0) {

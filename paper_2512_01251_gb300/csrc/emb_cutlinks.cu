@@ -747,7 +747,8 @@ static void free_candidates(emb_forest f, cudaStream_t s)
 // work-list scan, count at work_n[n]), work (n), blk_off (n + 1: link offsets,
 // total at blk_off[n]), tmp (scan scratch for n).
 emb_status emb_enq_link_prep(const EmbLevel &lv, int lattice, uint64_t *cand, uint32_t *cnt, uint32_t *flag,
-                             uint32_t *work_n, uint32_t *work, uint32_t *blk_off, uint64_t *tmp, cudaStream_t s)
+                             uint32_t *work_n, uint32_t *work, uint32_t *blk_off, uint64_t *tmp, cudaStream_t s,
+                             uint64_t expect_work, uint64_t expect_links)
 {
     EMB_CUDA_TRY(cudaMemsetAsync(cnt, 0, (lv.n + 1) * sizeof(uint32_t), s));
     EMB_CUDA_TRY(cudaMemsetAsync(flag, 0, (lv.n + 1) * sizeof(uint32_t), s));
@@ -755,11 +756,11 @@ emb_status emb_enq_link_prep(const EmbLevel &lv, int lattice, uint64_t *cand, ui
         EMB_LAUNCH((k_link_cand), emb_grid(lv.n, 128), 128, 0, s)(lv.mask, lv.nbr, lv.n, lattice, cand, cnt);
         EMB_LAUNCH((k_nonempty), emb_grid(lv.n, 256), 256, 0, s)(cnt, lv.n, flag);
     }
-    emb_status rc = emb_scan_into(flag, work_n, lv.n, tmp, s);
+    emb_status rc = emb_scan_into_expect(flag, work_n, lv.n, tmp, expect_work, s);
     if (rc != EMB_OK) return rc;
     if (lv.n > 0) EMB_LAUNCH((k_compact_ids), emb_grid(lv.n, 256), 256, 0, s)(flag, work_n, lv.n, work);
     EMB_CUDA_TRY(cudaGetLastError());
-    return emb_scan_into(cnt, blk_off, lv.n, tmp, s);
+    return emb_scan_into_expect(cnt, blk_off, lv.n, tmp, expect_links, s);
 }
 
 // Work items (thread per block with links): block b with l links, a bin of nt

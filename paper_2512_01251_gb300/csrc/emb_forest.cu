@@ -125,10 +125,10 @@ extern "C" void emb_forest_destroy(emb_forest f)
 //      of flagged blocks F ends at rank[P.n]; tmp is scan scratch for P.n entries;
 //  (2) the 8 F children keys, written in (z, y, x) order into ckey.
 emb_status emb_enq_flag_ranks(const EmbLevel &P, const uint8_t *d_flags, uint32_t *cnt, uint32_t *rank, uint64_t *tmp,
-                              cudaStream_t s)
+                              cudaStream_t s, uint64_t expect)
 {
     if (P.n > 0) EMB_LAUNCH((k_flags_u32), emb_grid(P.n, 256), 256, 0, s)(d_flags, P.n, cnt);
-    return emb_scan_into(cnt, rank, P.n, tmp, s);
+    return emb_scan_into_expect(cnt, rank, P.n, tmp, expect, s);
 }
 
 // Keys [8 F, Cn) of a planned replay that flagged fewer blocks than its plan: the

@@ -158,9 +158,12 @@ static inline LevelGeom level_geom(const emb_forest_s *f, int L)
 // only enqueues, with emb_scan_tmp_words(n) words of caller scratch.
 emb_status emb_scan_u32(const uint32_t *d_in, uint32_t *d_out, int64_t n, uint64_t *h_total, cudaStream_t s);
 emb_status emb_scan_into(const uint32_t *d_in, uint32_t *d_out, int64_t n, uint64_t *tmp, cudaStream_t s);
+// emb_scan_into that also checks the total against a planned count (EMB_ERR_STATE on the
+// device when they differ), for planned replays; EMB_NO_EXPECT skips the check.
+#define EMB_NO_EXPECT 0xFFFFFFFFFFFFFFFFull
+emb_status emb_scan_into_expect(const uint32_t *d_in, uint32_t *d_out, int64_t n, uint64_t *tmp, uint64_t expect,
+                                cudaStream_t s);
 int64_t emb_scan_tmp_words(int64_t n);
-// Device check that a count recomputed during a planned replay equals the plan.
-emb_status emb_expect_u32(const uint32_t *d_got, uint64_t expect, cudaStream_t s);
 // Level index (hash + rank bitmap) and neighbour table.
 int64_t emb_hash_capacity(int64_t n);
 int64_t emb_bitmap_words(int64_t nb);
@@ -173,17 +176,17 @@ int emb_sm_count();
 // Forest steps (enqueue only; buffers supplied by the caller).
 emb_status emb_enq_root_keys(int64_t R, uint64_t *key, cudaStream_t s);
 emb_status emb_enq_flag_ranks(const EmbLevel &P, const uint8_t *d_flags, uint32_t *cnt, uint32_t *rank, uint64_t *tmp,
-                              cudaStream_t s);
+                              cudaStream_t s, uint64_t expect = EMB_NO_EXPECT);
 emb_status emb_enq_children(const EmbLevel &P, const uint8_t *d_flags, const uint32_t *rank, uint64_t *ckey, int64_t Cn,
                             bool planned, cudaStream_t s);
 // Binning, voxelization and refine flags (enqueue only).
 struct LevelGeom;
 emb_status emb_enq_filter(const int4 *rec, int64_t T, LevelGeom g, uint32_t *flag, uint32_t *pos, uint32_t *flist,
-                          uint64_t *tmp, int block, cudaStream_t s);
+                          uint64_t *tmp, int block, cudaStream_t s, uint64_t expect = EMB_NO_EXPECT);
 struct EmbBigQ;
 emb_status emb_enq_bin_pairs(const int4 *rec, int64_t T, LevelGeom g, const EmbLevel &lv, uint32_t *cnt, uint32_t *off,
                              uint2 *list_bs, uint32_t *list_tri, unsigned long long *list_n, uint64_t list_cap,
-                             uint64_t *tmp, const EmbBigQ &Q, cudaStream_t s);
+                             uint64_t *tmp, const EmbBigQ &Q, cudaStream_t s, uint64_t expect = EMB_NO_EXPECT);
 emb_status emb_enq_bin_scatter(const uint2 *list_bs, const uint32_t *list_tri, const unsigned long long *list_n,
                                uint64_t list_cap, const uint32_t *off, uint32_t *ent, uint64_t ent_cap, cudaStream_t s);
 emb_status emb_enq_voxelize(const int4 *rec, int64_t T, const uint32_t *flist, int64_t nf, const uint32_t *d_nf,
@@ -225,7 +228,8 @@ struct LinkTable {
     LinkMesh m[EMB_MAX_BATCH];
 };
 emb_status emb_enq_link_prep(const EmbLevel &lv, int lattice, uint64_t *cand, uint32_t *cnt, uint32_t *flag,
-                             uint32_t *work_n, uint32_t *work, uint32_t *blk_off, uint64_t *tmp, cudaStream_t s);
+                             uint32_t *work_n, uint32_t *work, uint32_t *blk_off, uint64_t *tmp, cudaStream_t s,
+                             uint64_t expect_work = EMB_NO_EXPECT, uint64_t expect_links = EMB_NO_EXPECT);
 emb_status emb_enq_link_split(const EmbLevel &lv, const uint32_t *work, const uint32_t *work_n, const uint64_t *cand,
                               const uint32_t *blk_off, const uint32_t *bin_off, uint2 *witem, uint2 *extra,
                               unsigned long long *extra_n, uint32_t extra_cap, cudaStream_t s);

@@ -163,3 +163,15 @@ def test_capacity_and_state_errors():
     with pytest.raises(P.EmbError) as e:
         P.emb_forest_root(1 << 10, 9)  # k + level beyond the integer frame
     assert e.value.code == P.EMB_ERR_RANGE
+
+
+def test_deep_forest_looked_up_through_the_hash(orc):
+    # R = 32 with 6 levels: the finest level has 2048^3 block positions, more than the
+    # rank bitmap covers (2^32), so its blocks are found through the level hash (the
+    # coarser levels use bitmaps); a small body keeps the refined region small
+    from synth.meshes import icosphere
+    v, t = icosphere(1, radius=0.004, centre=(0.5013, 0.4987, 0.5021))
+    o = orc.embed(v, t, 32, 6, 2, 19)
+    _, g = gpu_embed(v, t, 32, 6, 2, 19)
+    compare_full(g, o, 6)
+    assert len(g["links"]["q"]) > 1000
