@@ -112,7 +112,7 @@ __global__ void k_link_cand(const uint64_t *__restrict__ mask, const int32_t *__
 // sends its cell through an exact per-cell scan of the whole bin instead.
 #define LE_WARPS 4
 #define LE_TILE 32
-#define LE_BCAP 28
+#define LE_BCAP 20
 // A block is split into about (links x bin triangles) / LE_SPLIT_COST parts, at
 // most one per three links and LE_SPLIT_MAX in all.
 #define LE_SPLIT_COST 16384
@@ -127,7 +127,7 @@ struct TriT {
 struct LeWarp {
     TriT tile[LE_TILE];
     uint2 hit[LE_BCAP][32];  // per slot: (bin-local index | direction << 24, q bits)
-    int best[27][32];        // per (direction, slot): index of the nearest hit during resolution
+    signed char best[27][32];  // per (direction, slot): index of the nearest hit during resolution
     int hcnt[32];
     uint32_t cm[32];         // candidate directions of each slot's cell
 };
@@ -363,7 +363,7 @@ __device__ __noinline__ bool pair_cross_wide(const TriT &T, long long px, long l
 }
 
 #ifndef LE_MINB
-#define LE_MINB 4
+#define LE_MINB 6
 #endif
 __global__ void __launch_bounds__(LE_WARPS * 32, LE_MINB) k_link_emit(const __grid_constant__ LinkTable tab,
                                                                 unsigned int *__restrict__ next, int *st)
