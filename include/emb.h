@@ -358,8 +358,9 @@ emb_status emb_cutlinks_backward(emb_mesh m, emb_forest f, const int32_t *d_cell
  * emb_batch_capture records emb_batch_run into a CUDA graph; emb_batch_launch
  * replays that graph on `stream`.
  *
- * emb_batch_autotune times a small set of launch shapes on this batch and keeps
- * the fastest; h_choice (4 int32, may be NULL) receives the chosen stream count
+ * emb_batch_autotune times a small set of launch shapes on this batch (as captured
+ * graphs when `stream` can be captured, else as stream launches) and keeps the
+ * fastest; h_choice (4 int32, may be NULL) receives the chosen stream count
  * (1..32), thread-block size of the triangle-parallel kernels (128, 256 or 512),
  * resident link CTAs per SM (0 = as many as fit) and link placement (0 joint,
  * 1 per mesh on its pipeline's stream, 2 per mesh on a low-priority stream of its

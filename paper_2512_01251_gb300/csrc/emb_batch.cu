@@ -479,9 +479,13 @@ extern "C" emb_status emb_batch_autotune(emb_batch b, void *stream, int32_t *h_c
     struct Cand {
         int nstreams, tri_block, link_ctas, per_mesh;
     };
-    const Cand cands[] = {{1, 256, 0, 0},  {16, 256, 0, 0}, {16, 128, 0, 0}, {8, 256, 0, 1}, {16, 256, 0, 1},
-                          {16, 256, 2, 1}, {16, 128, 2, 1}, {16, 256, 0, 2}, {16, 256, 1, 2}, {16, 256, 2, 2},
-                          {16, 128, 1, 2}, {16, 128, 2, 2}, {8, 256, 2, 2}};
+    const Cand cands[] = {{1, 256, 0, 0},   {16, 256, 0, 0},  {16, 128, 0, 0}, {8, 256, 0, 1},  {16, 256, 0, 1},
+                          {16, 256, 2, 1},  {16, 128, 2, 1},  {16, 256, 0, 2}, {16, 256, 1, 2}, {16, 256, 2, 2},
+                          {16, 128, 1, 2},  {16, 128, 2, 2},  {8, 256, 2, 2},  {32, 256, 0, 1}, {32, 256, 2, 1},
+                          {32, 256, 0, 2},  {32, 256, 2, 2},  {24, 256, 2, 2}};
+    // shapes are timed the way they will run: as captured graphs where the stream can be
+    // captured, else as stream launches
+    const bool graphs = s != nullptr;
     const int nc = (int)(sizeof(cands) / sizeof(cands[0]));
     cudaEvent_t e0, e1;
     EMB_CUDA_TRY(cudaEventCreate(&e0));
@@ -493,11 +497,17 @@ extern "C" emb_status emb_batch_autotune(emb_batch b, void *stream, int32_t *h_c
         b->tri_block = cands[i].tri_block;
         b->link_ctas = cands[i].link_ctas;
         b->per_mesh_links = cands[i].per_mesh;
-        BTRY(batch_enqueue(b, s));  // warm-up
+        if (graphs) {
+            BTRY(emb_batch_capture(b, s));
+            BTRY(emb_batch_launch(b, s));  // warm-up
+        } else {
+            BTRY(batch_enqueue(b, s));  // warm-up
+        }
         float tot = 0;
         for (int r = 0; r < 3; ++r) {
             EMB_CUDA_TRY(cudaEventRecord(e0, s));
-            BTRY(batch_enqueue(b, s));
+            if (graphs) BTRY(emb_batch_launch(b, s));
+            else BTRY(batch_enqueue(b, s));
             EMB_CUDA_TRY(cudaEventRecord(e1, s));
             EMB_CUDA_TRY(cudaEventSynchronize(e1));
             float ms = 0;
@@ -518,6 +528,10 @@ extern "C" emb_status emb_batch_autotune(emb_batch b, void *stream, int32_t *h_c
     if (b->exec) {  // a captured graph no longer matches the chosen shape
         cudaGraphExecDestroy(b->exec);
         b->exec = nullptr;
+    }
+    if (b->graph) {
+        cudaGraphDestroy(b->graph);
+        b->graph = nullptr;
     }
     if (h_choice) {
         h_choice[0] = b->nstreams;

@@ -538,21 +538,22 @@ __global__ void __launch_bounds__(LE_WARPS * 32, LE_MINB) k_link_emit(const __gr
                         // line tests for the 13 direction pairs (odd index d and its opposite d + 1)
                         uint32_t line = 0, degen = 0;
 #pragma unroll
+                        // all 13 lines, without branches (the lanes hold different cells, so a
+                        // per-direction branch would diverge); non-candidates are masked off
+#pragma unroll
                         for (int r = 0; r < 13; ++r) {
                             const int d = 2 * r + 1;
-                            if (!(ccm & (3u << d))) continue;
                             int cx, cy, cz;
                             emb_dir(d, cx, cy, cz);
                             const int NC = cx * nx + cy * ny + cz * nz;
                             const int V1 = cx * m1x + cy * m1y + cz * m1z;
                             const int V2 = cx * m2x + cy * m2y + cz * m2z;
                             const int V3 = cx * m3x + cy * m3y + cz * m3z;
-                            if (NC == 0) continue;  // line parallel to the face: never crosses
-                            if (V1 == 0 || V2 == 0 || V3 == 0) {
-                                degen |= 1u << d;
-                                continue;
-                            }
-                            if (((V1 ^ NC) | (V2 ^ NC) | (V3 ^ NC)) >= 0) line |= 1u << d;
+                            const uint32_t ok = ((ccm >> d) & 3u) != 0u && NC != 0;  // a parallel line never crosses
+                            const uint32_t zero = (V1 == 0) | (V2 == 0) | (V3 == 0);
+                            const uint32_t same = ((V1 ^ NC) | (V2 ^ NC) | (V3 ^ NC)) >= 0;
+                            degen |= (ok & zero) << d;
+                            line |= (ok & (zero ^ 1u) & same) << d;
                         }
                         // members of line-hit pairs that are candidates: the segment ends must straddle the plane
                         uint32_t mm = (line | (line << 1)) & ccm;
