@@ -14,6 +14,7 @@ on bounded samples of the same workload on this host's cores.
 from __future__ import annotations
 
 import argparse
+import gc
 import hashlib
 import json
 import math
@@ -297,6 +298,10 @@ def run_ours(args):
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
+    # the per-call path reads counts back between its launches: keep the Python garbage
+    # collector from pausing the host inside a timed step (collected after the region)
+    gc.collect()
+    gc.disable()
     clocks.start()
     l0 = P.emb_launch_count()
     step_ms, per_call = [], {}
@@ -316,6 +321,7 @@ def run_ours(args):
     launches = P.emb_launch_count() - l0
     torch.cuda.synchronize()
     clk = clocks.stop()
+    gc.enable()
     if dist is not None:
         dist.barrier()
     st = P.emb_status_get()
