@@ -110,6 +110,10 @@ __global__ void k_link_cand(const uint64_t *__restrict__ mask, const int32_t *__
 // face) and writes the links at the cell's offset in the table, which the
 // direction words fix whichever warp handles the cell.  A bucket that overflows
 // sends its cell through an exact per-cell scan of the whole bin instead.
+// Sizes: 4 warps per CTA; a warp's tile of 32 triangles, 20 hit slots per cell and the
+// byte-wide best-hit indices take 9 KB of shared memory, so six CTAs fit on an SM (with
+// 80 registers a thread).  Fewer hit slots let more CTAs fit but send many more cells of
+// a D3Q27 workload through the per-cell rescan, which costs far more than it saves.
 #define LE_WARPS 4
 #define LE_TILE 32
 #define LE_BCAP 20
