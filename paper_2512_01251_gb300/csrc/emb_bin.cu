@@ -118,11 +118,13 @@ __device__ __forceinline__ void bin_block(const int4 &A, const int4 &B, const in
     PL.put(atomicAdd(PL.n, 1ull), (uint32_t)id, slot, t);
 }
 
-// The (triangle, block) pairs of 32 consecutive triangles, visited warp-cooperatively
-// over the union of their candidate blocks (see emb_internal.cuh); a lane whose
-// triangle is left out of the union walks its own candidates, or queues them in
-// chunks when there are many.  Degenerate triangles (zero normal) are never
-// crossed by a link and are left out.
+// The (triangle, candidate block) pairs of 32 consecutive triangles, spread evenly over
+// the warp's lanes by a prefix sum of the lanes' candidate counts, so that every lane
+// tests one pair per round (a triangle with very many candidates goes to the chunk queue
+// instead), with one list append per warp and round.  (Visiting the union of the 32
+// triangles' candidate blocks instead, one lane per block against all 32 triangles,
+// measured slower here: the lanes' overlap tests diverge.)  Degenerate triangles (zero
+// normal) are never crossed by a link and are left out.
 __global__ void __launch_bounds__(EMB_WU_WARPS * 32) k_bin_pairs(const int4 *__restrict__ rec, int64_t T, LevelGeom g,
                                                                  long long dil, EmbLookup lk, uint32_t *__restrict__ cnt,
                                                                  PairList PL, EmbBigQ Q)
@@ -138,72 +140,8 @@ __global__ void __launch_bounds__(EMB_WU_WARPS * 32) k_bin_pairs(const int4 *__r
     S.A[lane] = A;
     S.B[lane] = B;
     S.C[lane] = C;
-    S.lo[0][lane] = valid ? min(A.x, min(B.x, C.x)) : 0x7fffffff;
-    S.hi[0][lane] = valid ? max(A.x, max(B.x, C.x)) : -0x7fffffff;
-    S.lo[1][lane] = min(A.y, min(B.y, C.y));
-    S.hi[1][lane] = max(A.y, max(B.y, C.y));
-    S.lo[2][lane] = min(A.z, min(B.z, C.z));
-    S.hi[2][lane] = max(A.z, max(B.z, C.z));
     __syncwarp();
-    int u0[3], u1[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        u0[d] = __reduce_min_sync(0xffffffffu, (int)min(b0[d], (long long)0x7fffffff));
-        u1[d] = __reduce_max_sync(0xffffffffu, (int)b1[d]);
-    }
-    const long long nx = u1[0] - u0[0] + 1, ny = u1[1] - u0[1] + 1, nz = u1[2] - u0[2] + 1;
-    if (nx <= 0 || ny <= 0 || nz <= 0) return;
-    const long long total = nx * ny * nz;
-    // per-triangle candidates summed over the warp: the union pays off only when it is much smaller
     const unsigned long long own = valid ? box_items(b0, b1) : 0;
-    const unsigned own_sum = __reduce_add_sync(0xffffffffu, (unsigned)min(own, 1ull << 20));
-    if (total <= EMB_WU_MAX && 4 * total <= (long long)own_sum) {
-        // total <= EMB_WU_MAX: decode the union index in 32-bit arithmetic; the loop
-        // bound is uniform so that the list appends can be aggregated over the warp
-        const unsigned ux = (unsigned)nx, uxy = (unsigned)(nx * ny);
-        for (unsigned c0 = 0; c0 < (unsigned)total; c0 += 32) {
-            const unsigned c = c0 + lane;
-            uint32_t hits = 0;
-            int32_t id = -1;
-            if (c < (unsigned)total) {
-                const unsigned cz = c / uxy, cr = c - cz * uxy, cy = cr / ux;
-                const long long bx = u0[0] + (long long)(cr - cy * ux), by = u0[1] + (long long)cy,
-                                bz = u0[2] + (long long)cz;
-                id = emb_lookup(lk, bx, by, bz);
-                if (id >= 0) {
-                    const long long lx = bx * g.W - dil, ly = by * g.W - dil, lz = bz * g.W - dil;
-                    const long long hx = lx + g.W + 2 * dil, hy = ly + g.W + 2 * dil, hz = lz + g.W + 2 * dil;
-                    for (int j = 0; j < 32; ++j)
-                        if (wu_overlap(S, j, lx, ly, lz, hx, hy, hz)) hits |= 1u << j;
-                }
-            }
-            const uint32_t k = (uint32_t)__popc(hits);
-            uint32_t incl = k;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += v;
-            }
-            const uint32_t wtot = __shfl_sync(0xffffffffu, incl, 31);
-            if (wtot == 0) continue;
-            unsigned long long base = 0;
-            if (lane == 31) base = atomicAdd(PL.n, (unsigned long long)wtot);
-            base = __shfl_sync(0xffffffffu, base, 31) + (incl - k);
-            if (k) {
-                uint32_t slot = atomicAdd(cnt + id, k);
-                while (hits) {
-                    const int j = __ffs(hits) - 1;
-                    hits &= hits - 1;
-                    PL.put(base++, (uint32_t)id, slot++, (uint32_t)(t0 + j));
-                }
-            }
-        }
-        return;
-    }
-    // large or loose union: the warp's (triangle, candidate block) pairs, spread evenly
-    // over the lanes by a prefix sum of the lanes' candidate counts (a triangle with
-    // very many candidates goes to the chunk queue instead), with one list append
-    // per warp and round
     const bool mine = valid && own > 0 && !(own > EMB_BIG_ITEMS && emb_bigq_push(Q, (uint32_t)t, own));
     const uint32_t k = mine ? (uint32_t)own : 0u;
     uint32_t incl = k;
