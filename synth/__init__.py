@@ -1,4 +1,4 @@
-"""Seeded synthetic inputs shared by the tests, the bench and the oracle driver.
+"""Seeded synthetic inputs shared by the tests, the bench and the oracle.
 
 This package only *generates* inputs: closed triangle meshes snapped to the
 2^-20 grid, lattice populations and per-link weights.  It holds none of the
