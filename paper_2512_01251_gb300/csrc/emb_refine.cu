@@ -9,11 +9,12 @@
 // rho_L = max(band, rho_{L+1}/2 + 5/2), which keeps all 26 neighbours of every
 // refined block present (2:1 balance) and leaves unrefined blocks surface-free.
 //
-// Warp-cooperative over 32 consecutive triangles (see emb_internal.cuh): each
-// candidate block of the warp's union range is looked up once and tested
-// against the 32 triangles; triangles left out of the union are walked by their
-// own lane, or in queued chunks by whole warps when they have many candidate
-// blocks.  Flags are idempotent byte stores.
+// Warp-cooperative over 32 consecutive triangles (see emb_internal.cuh): when the
+// union of their candidate blocks is at most an eighth of their summed candidates,
+// each block of the union is looked up once and tested against the 32 triangles;
+// otherwise the warp's (triangle, candidate block) pairs are spread evenly over its
+// lanes, and a triangle with very many candidates goes in queued chunks to whole
+// warps.  Flags are idempotent byte stores.
 #include <math.h>
 
 #include "emb_internal.cuh"
@@ -75,9 +76,9 @@ __device__ __forceinline__ void refine_block(const int4 &A, const int4 &B, const
     }
 }
 
-// The less common paths, kept out of line so that the kernel's main path needs few
+// The less common path, kept out of line so that the kernel's main path needs few
 // registers and more warps stay resident to cover the latency of the record loads:
-// a union block not yet flagged, tested against the warp's 32 triangles ...
+// a union block not yet flagged, tested against the warp's 32 triangles.
 static __device__ __noinline__ void refine_union_block(const WuTri &S, long long bx, long long by, long long bz,
                                                        unsigned long long pos, const LevelGeom &g, long long dil,
                                                        const EmbLookup &lk, uint8_t *__restrict__ flags,
@@ -96,15 +97,6 @@ static __device__ __noinline__ void refine_union_block(const WuTri &S, long long
     }
 }
 
-// ... and a triangle walking its own candidate blocks.
-static __device__ __noinline__ void refine_own(const int4 A, const int4 B, const int4 C, const long long *b0,
-                                               const long long *b1, const LevelGeom &g, long long dil,
-                                               const EmbLookup &lk, uint8_t *__restrict__ flags, const FlagBits &fb)
-{
-    for (long long bz = b0[2]; bz <= b1[2]; ++bz)
-        for (long long by = b0[1]; by <= b1[1]; ++by)
-            for (long long bx = b0[0]; bx <= b1[0]; ++bx) refine_block(A, B, C, bx, by, bz, g, dil, lk, flags, fb);
-}
 
 // Persistent warps over tiles of 32 consecutive triangles; each warp loads the
 // records of its next tile before it works on the current one, so that the loads
@@ -182,9 +174,39 @@ __global__ void __launch_bounds__(EMB_WU_WARPS * 32, REFINE_MINB) k_refine(const
             }
             continue;
         }
-        // large or loose union: each lane takes its own triangle, queued in chunks when it has many candidates
-        if (valid && !(own > EMB_BIG_ITEMS && emb_bigq_push(Q, (uint32_t)t, own)))
-            refine_own(A, B, C, b0, b1, g, dil, lk, flags, fb);
+        // large or loose union: the warp's (triangle, candidate block) pairs spread evenly over
+        // the lanes (a triangle with very many candidates goes to the chunk queue instead)
+        const bool mine = valid && own > 0 && !(own > EMB_BIG_ITEMS && emb_bigq_push(Q, (uint32_t)t, own));
+        const uint32_t k = mine ? (uint32_t)own : 0u;
+        uint32_t incl = k;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const uint32_t wtot = __shfl_sync(0xffffffffu, incl, 31);
+        const int ox = (int)b0[0], oy = (int)b0[1], oz = (int)b0[2];
+        const int onx = mine ? (int)(b1[0] - b0[0] + 1) : 1, ony = mine ? (int)(b1[1] - b0[1] + 1) : 1;
+        for (uint32_t s0 = 0; s0 < wtot; s0 += 32) {
+            const uint32_t gi = s0 + lane;
+            int lo = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                const uint32_t v = __shfl_sync(0xffffffffu, incl, lo + step - 1);
+                if (v <= gi) lo += step;
+            }
+            const int ti = lo > 31 ? 31 : lo;
+            const uint32_t first = __shfl_sync(0xffffffffu, incl, ti) - __shfl_sync(0xffffffffu, k, ti);
+            const int bx0 = __shfl_sync(0xffffffffu, ox, ti), by0 = __shfl_sync(0xffffffffu, oy, ti),
+                      bz0 = __shfl_sync(0xffffffffu, oz, ti), nbx = __shfl_sync(0xffffffffu, onx, ti),
+                      nby = __shfl_sync(0xffffffffu, ony, ti);
+            if (gi < wtot) {
+                const uint32_t r = gi - first, cx = r % (uint32_t)nbx, rr = r / (uint32_t)nbx, cy = rr % (uint32_t)nby,
+                               cz = rr / (uint32_t)nby;
+                refine_block(S.A[ti], S.B[ti], S.C[ti], bx0 + (long long)cx, by0 + (long long)cy, bz0 + (long long)cz, g,
+                             dil, lk, flags, fb);
+            }
+        }
     }
 }
 
