@@ -78,3 +78,18 @@ def test_workloads(orc, name):
     w = workload(name)
     v, t = w.build_mesh()
     _compare(orc, v, t, w.R, w.levels, w.band)
+
+
+def test_guard_rejects_bins_of_another_level():
+    import torch
+
+    import paper_2512_01251_gb300 as P
+    w = workload("icosphere_320")
+    v, t = w.build_mesh()
+    E = P.embed(torch.from_numpy(v), torch.from_numpy(t), w.R, w.levels, w.band, 19, keep_bins=True)
+    with pytest.raises(P.EmbError) as e:
+        P.emb_voxelize_guard(E.forest, E.bins[0])  # the root's bins: only the finest level has block bins
+    assert e.value.code == P.EMB_ERR_STATE
+    s, g = P.emb_voxelize_guard(E.forest, E.bins[-1])
+    assert s.numel() == g.numel() == E.masks[-1].numel()
+    assert P.emb_status_get() == P.EMB_OK
