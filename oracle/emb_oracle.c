@@ -11,8 +11,8 @@
  *   - a cell is solid iff its centre lies inside the closed oriented surface
  *     (Sec. 3.4 "Partial Surface Voxelization": the centre decides the cell's
  *     type; Sec. 3.2: solid cells have their centre inside the geometry),
- *     decided by the parity of ray crossings (the "standard intersection parity
- *     test" of Sec. 3.3.1);
+ *     decided by the parity of ray crossings (Sec. 3.3.1 names the crossing-count
+ *     parity as the usual inside test);
  *   - a cut link runs from a fluid cell centre P to a solid lattice neighbour
  *     P + h c; its length q is the distance along the link to the nearest face
  *     crossing, divided by the link length (Sec. 3.4 "Link-Length Computation");
