@@ -441,12 +441,13 @@ __device__ __forceinline__ void line_range(long long mn, long long mx, int lh, l
 // warp-cooperative visit of (triangle, block) overlaps
 // ---------------------------------------------------------------------------
 // A warp takes 32 consecutive triangles (neighbours in a mesh's storage order
-// are usually neighbours in space), forms the union of the block ranges their
-// dilated boxes can touch, and lets each lane test whole blocks of that union
-// against all 32 triangles.  This trades 32 independent lookups per candidate
-// block for one.  When the union is large (above EMB_WU_MAX blocks) or loose
-// (more than a quarter of the warp's summed per-triangle candidates), the warp
-// falls back to the per-triangle enumeration.
+// are usually neighbours in space) and stages them in shared memory.  The refine
+// kernel may form the union of the block ranges their dilated boxes can touch and
+// let each lane test whole blocks of that union against all 32 triangles, which
+// trades 32 independent lookups per candidate block for one; when the union is
+// large (above EMB_WU_MAX blocks) or loose (more than an eighth of the warp's
+// summed per-triangle candidates), and always in the finest-level binning, the
+// warp's (triangle, candidate block) pairs are spread evenly over its lanes instead.
 #define EMB_WU_WARPS 4
 #define EMB_WU_MAX 2048
 
