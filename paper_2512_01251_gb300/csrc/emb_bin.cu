@@ -118,10 +118,51 @@ __device__ __forceinline__ void bin_block(const int4 &A, const int4 &B, const in
     PL.put(atomicAdd(PL.n, 1ull), (uint32_t)id, slot, t);
 }
 
+// Appends the pairs of the lanes with `hit` to the pair list (one list append per warp)
+// and takes each pair's slot in its block.
+__device__ __forceinline__ void bin_append(bool hit, int32_t id, uint32_t tri, int lane, uint32_t *__restrict__ cnt,
+                                           const PairList &PL)
+{
+    const unsigned hm = __ballot_sync(0xffffffffu, hit);
+    if (!hm) return;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(PL.n, (unsigned long long)__popc(hm));
+    base = __shfl_sync(0xffffffffu, base, 0) + (unsigned long long)__popc(hm & ((1u << lane) - 1u));
+    if (hit) PL.put(base, (uint32_t)id, atomicAdd(cnt + id, 1u), tri);
+}
+
+// Per warp: (triangle lane, bx, by, bz) and block id of pairs whose triangle has no vertex
+// in the dilated block, waiting for the separating-axis test.
+struct SatQueue {
+    int4 e[EMB_WU_WARPS][64];
+    int32_t id[EMB_WU_WARPS][64];
+};
+
+// The separating-axis test of the first n queued pairs, one per lane.
+__device__ __forceinline__ void bin_sat_batch(const SatQueue &Q2, int w, int n, int lane, const WuTri &S, int64_t t0,
+                                              const LevelGeom &g, long long dil, uint32_t *__restrict__ cnt,
+                                              const PairList &PL)
+{
+    bool hit = false;
+    int32_t id = -1;
+    int ti = 0;
+    if (lane < n) {
+        const int4 e = Q2.e[w][lane];
+        id = Q2.id[w][lane];
+        ti = e.x;
+        const long long lx = (long long)e.y * g.W - dil, ly = (long long)e.z * g.W - dil, lz = (long long)e.w * g.W - dil;
+        const long long hx = lx + g.W + 2 * dil, hy = ly + g.W + 2 * dil, hz = lz + g.W + 2 * dil;
+        hit = emb_tri_box(S.A[ti], S.B[ti], S.C[ti], lx, ly, lz, hx, hy, hz);
+    }
+    bin_append(hit, id, (uint32_t)(t0 + ti), lane, cnt, PL);
+}
+
 // The (triangle, candidate block) pairs of 32 consecutive triangles, spread evenly over
 // the warp's lanes by a prefix sum of the lanes' candidate counts, so that every lane
 // tests one pair per round (a triangle with very many candidates goes to the chunk queue
-// instead), with one list append per warp and round.  (Visiting the union of the 32
+// instead), with one list append per warp and round.  A pair whose triangle has a vertex
+// in the dilated block is decided at once; the others wait in a per-warp queue and take
+// the full separating-axis test 32 at a time, so that the lanes run it together.  (Visiting the union of the 32
 // triangles' candidate blocks instead, one lane per block against all 32 triangles,
 // measured slower here: the lanes' overlap tests diverge.)  Degenerate triangles (zero
 // normal) are never crossed by a link and are left out.
@@ -130,8 +171,10 @@ __global__ void __launch_bounds__(EMB_WU_WARPS * 32) k_bin_pairs(const int4 *__r
                                                                  PairList PL, EmbBigQ Q)
 {
     __shared__ WuTri tiles[EMB_WU_WARPS];
+    __shared__ SatQueue Q2;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WuTri &S = tiles[w];
+    int qn = 0;  // pairs queued for the full overlap test (warp-uniform)
     const int64_t t0 = ((int64_t)blockIdx.x * EMB_WU_WARPS + w) * 32;
     const int64_t t = t0 + lane;
     long long b0[3] = {1ll << 40, 1ll << 40, 1ll << 40}, b1[3] = {-1, -1, -1};
@@ -166,28 +209,54 @@ __global__ void __launch_bounds__(EMB_WU_WARPS * 32) k_bin_pairs(const int4 *__r
         const int bx0 = __shfl_sync(0xffffffffu, ox, ti), by0 = __shfl_sync(0xffffffffu, oy, ti),
                   bz0 = __shfl_sync(0xffffffffu, oz, ti), nbx = __shfl_sync(0xffffffffu, onx, ti),
                   nby = __shfl_sync(0xffffffffu, ony, ti);
-        bool hit = false;
+        bool hit = false, need = false;
         int32_t id = -1;
+        int bxi = 0, byi = 0, bzi = 0;
         if (gi < wtot) {
             const uint32_t r = gi - first, cx = r % (uint32_t)nbx, rr = r / (uint32_t)nbx, cy = rr % (uint32_t)nby,
                            cz = rr / (uint32_t)nby;
-            const long long bx = bx0 + (long long)cx, by = by0 + (long long)cy, bz = bz0 + (long long)cz;
-            id = emb_lookup(lk, bx, by, bz);
+            bxi = bx0 + (int)cx;
+            byi = by0 + (int)cy;
+            bzi = bz0 + (int)cz;
+            id = emb_lookup(lk, bxi, byi, bzi);
             if (id >= 0) {
-                const int4 TA = S.A[ti], TB = S.B[ti], TC = S.C[ti];
-                const long long lx = bx * g.W - dil, ly = by * g.W - dil, lz = bz * g.W - dil;
+                const long long lx = (long long)bxi * g.W - dil, ly = (long long)byi * g.W - dil,
+                                lz = (long long)bzi * g.W - dil;
                 const long long hx = lx + g.W + 2 * dil, hy = ly + g.W + 2 * dil, hz = lz + g.W + 2 * dil;
-                hit = emb_point_in_box(TA, lx, ly, lz, hx, hy, hz) || emb_point_in_box(TB, lx, ly, lz, hx, hy, hz) ||
-                      emb_point_in_box(TC, lx, ly, lz, hx, hy, hz) || emb_tri_box(TA, TB, TC, lx, ly, lz, hx, hy, hz);
+                hit = emb_point_in_box(S.A[ti], lx, ly, lz, hx, hy, hz) ||
+                      emb_point_in_box(S.B[ti], lx, ly, lz, hx, hy, hz) ||
+                      emb_point_in_box(S.C[ti], lx, ly, lz, hx, hy, hz);
+                need = !hit;
             }
         }
-        const unsigned hm = __ballot_sync(0xffffffffu, hit);
-        if (!hm) continue;
-        unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(PL.n, (unsigned long long)__popc(hm));
-        base = __shfl_sync(0xffffffffu, base, 0) + (unsigned long long)__popc(hm & ((1u << lane) - 1u));
-        if (hit) PL.put(base, (uint32_t)id, atomicAdd(cnt + id, 1u), (uint32_t)(t0 + ti));
+        bin_append(hit, id, (uint32_t)(t0 + ti), lane, cnt, PL);
+        // pairs that need the full overlap test wait until a whole warp's worth is queued
+        const unsigned nm = __ballot_sync(0xffffffffu, need);
+        if (need) {
+            const int pos = qn + __popc(nm & ((1u << lane) - 1u));
+            Q2.e[w][pos] = make_int4(ti, bxi, byi, bzi);
+            Q2.id[w][pos] = id;
+        }
+        qn += __popc(nm);
+        __syncwarp();
+        if (qn >= 32) {
+            bin_sat_batch(Q2, w, 32, lane, S, t0, g, dil, cnt, PL);
+            int4 e = make_int4(0, 0, 0, 0);
+            int32_t idn = 0;
+            if (lane < qn - 32) {
+                e = Q2.e[w][32 + lane];
+                idn = Q2.id[w][32 + lane];
+            }
+            __syncwarp();
+            if (lane < qn - 32) {
+                Q2.e[w][lane] = e;
+                Q2.id[w][lane] = idn;
+            }
+            qn -= 32;
+            __syncwarp();
+        }
     }
+    if (qn > 0) bin_sat_batch(Q2, w, qn, lane, S, t0, g, dil, cnt, PL);
 }
 
 // Decomposition of candidate index i of the box [b0, b1] (x fastest) and its step by 32.
