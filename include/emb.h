@@ -111,7 +111,8 @@ void emb_forest_destroy(emb_forest f);
 
 /* Creates level+1 from the refinement flags of `level` (d_flags: one uint8 per
  * level block, nonzero = refine): 8 children per flagged block, numbered in
- * (z, y, x) order, plus their coordinate hash.  This is the forest harness
+ * (z, y, x) order, plus their lookup index (a rank bitmap of the level's dense block
+ * positions, or a hash where there are more than 2^32 of them).  This is the forest harness
  * (the paper delegates it to its AMR pipeline, Sec. 3.2 steps 1-8); it keeps no
  * ghost/interface metadata.  Synchronises once to read the child count.
  * Errors: EMB_ERR_STATE (level not the current finest, or beyond max_level). */
