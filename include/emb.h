@@ -258,7 +258,10 @@ emb_status emb_cutlinks_count(emb_forest f, int32_t lattice, int64_t *h_count, v
  * length (in [0,1]), d_tri = that face's triangle id (lowest id on exact ties).
  * Ordered by (cell, dir).  `b` must be the bins of the finest level.  If the
  * count exceeds `capacity`, nothing is written, *d_count (device int64) still
- * receives the required size and the device status becomes EMB_ERR_CAPACITY. */
+ * receives the required size and the device status becomes EMB_ERR_CAPACITY.
+ * A finest-level bin may hold at most 2^24 triangles (16,777,216 faces overlapping
+ * one block); the links of a block with a larger bin are not written and the device
+ * status becomes EMB_ERR_CAPACITY (refine further so that the bins shrink). */
 emb_status emb_cutlinks(emb_forest f, emb_bins b, int32_t lattice, int32_t *d_cell, uint8_t *d_dir,
                         float *d_q, int32_t *d_tri, int64_t capacity, int64_t *d_count, void *stream);
 
@@ -299,7 +302,10 @@ emb_status emb_mex_force_backward(emb_forest f, int32_t lattice, const int32_t *
  *     (cudaGetSymbolAddress) with that device current; make that first call
  *     before any stream capture;
  *   - all calls share the one array, so calls that overlap on the GPU (other
- *     streams, other threads) race: serialise them. */
+ *     streams, other threads) race: serialise them;
+ *   - the looked-up address belongs to the device's primary context: after
+ *     cudaDeviceReset (or anything else that destroys that context) the next call
+ *     looks it up again, because the library keys its cache on the context. */
 emb_status emb_mex_force_noalloc(emb_forest f, int32_t lattice, const int32_t *d_cell, const uint8_t *d_dir,
                                  const float *d_q, int64_t n, const float *d_pop, int64_t pop_stride, float *d_F,
                                  void *stream);

@@ -191,17 +191,50 @@ extern "C" emb_status emb_mex_force_backward(emb_forest f, int32_t lattice, cons
 static __device__ __align__(256) double g_mex_noalloc_part[3 * EMB_NOALLOC_MEX_PARTS];
 
 static std::mutex g_mex_noalloc_mu;
-static double *g_mex_noalloc_ptr[64] = {nullptr};  // device address of the array, per device
+static double *g_mex_noalloc_ptr[64] = {nullptr};        // device address of the array, per device
+static unsigned long long g_mex_noalloc_ctx[64] = {0};   // id of the context it was looked up in
 
-// The array's device address for the current device, looked up once per device.
-// In host code the array's name is only a host-side stand-in, so the address must
-// come from cudaGetSymbolAddress with the device current.
+// Unique id of the calling thread's current context (0 when none is current or the
+// driver entry points are unavailable).  Context ids are never reused within a
+// process, so a reset device (a new primary context) is told apart from the old one.
+typedef int (*emb_pfn_ctx_get_current)(void **);
+typedef int (*emb_pfn_ctx_get_id)(void *, unsigned long long *);
+static unsigned long long current_ctx_id()
+{
+    static emb_pfn_ctx_get_current get_cur = nullptr;
+    static emb_pfn_ctx_get_id get_id = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *a = nullptr, *b = nullptr;
+        cudaDriverEntryPointQueryResult qa, qb;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) == cudaSuccess &&
+            qa == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) == cudaSuccess &&
+            qb == cudaDriverEntryPointSuccess) {
+            get_cur = (emb_pfn_ctx_get_current)a;
+            get_id = (emb_pfn_ctx_get_id)b;
+        }
+    }
+    if (!get_cur || !get_id) return 0;
+    void *ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_cur(&ctx) != 0 || !ctx) return 0;
+    if (get_id(ctx, &id) != 0) return 0;
+    return id;
+}
+
+// The array's device address for the current device, looked up once per device
+// (and again if that device's context was replaced, e.g. by cudaDeviceReset).  In
+// host code the array's name is only a host-side stand-in, so the address must come
+// from cudaGetSymbolAddress with the device current.
 static emb_status mex_noalloc_scratch(double **out)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return EMB_ERR_CUDA;
     std::lock_guard<std::mutex> lk(g_mex_noalloc_mu);
-    if (!g_mex_noalloc_ptr[dev]) {
+    const unsigned long long ctx = current_ctx_id();
+    if (!g_mex_noalloc_ptr[dev] || ctx == 0 || ctx != g_mex_noalloc_ctx[dev]) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_mex_noalloc_part);
         if (e != cudaSuccess || !p) {
@@ -209,6 +242,8 @@ static emb_status mex_noalloc_scratch(double **out)
             return EMB_ERR_CUDA;
         }
         g_mex_noalloc_ptr[dev] = (double *)p;
+        // the lookup made the device's primary context current if it was not yet
+        g_mex_noalloc_ctx[dev] = ctx ? ctx : current_ctx_id();
     }
     *out = g_mex_noalloc_ptr[dev];
     return EMB_OK;

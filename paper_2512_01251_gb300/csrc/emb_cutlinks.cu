@@ -117,6 +117,9 @@ __global__ void k_link_cand(const uint64_t *__restrict__ mask, const int32_t *__
 #define LE_WARPS 4
 #define LE_TILE 32
 #define LE_BCAP 20
+// Largest finest-level bin the link kernel takes (hit records hold the bin-local
+// triangle index in 24 bits); a larger bin sets EMB_ERR_CAPACITY.
+#define EMB_BIN_MAX_ENTRIES (1u << 24)
 // A block is split into about (links x bin triangles) / LE_SPLIT_COST parts, at
 // most one per three links and LE_SPLIT_MAX in all.
 #define LE_SPLIT_COST 16384
@@ -434,6 +437,11 @@ __global__ void __launch_bounds__(LE_WARPS * 32, LE_MINB) k_link_emit(const __gr
         // reports that through its count checks; its passes must stay in bounds)
         const uint32_t e1 = (uint64_t)M.bin_off[b + 1] < M.ent_cap ? M.bin_off[b + 1] : (uint32_t)M.ent_cap;
         const uint32_t e0 = M.bin_off[b] < e1 ? M.bin_off[b] : e1;
+        if (e1 - e0 > EMB_BIN_MAX_ENTRIES) {
+            // a hit record keeps the bin-local triangle index in 24 bits
+            if (lane == 0) emb_set_status(st, EMB_ERR_CAPACITY);
+            continue;
+        }
         const int lh = __ffsll(h) - 1;  // h is a power of two
         const long long LIM = 1ll << 14;
         // this item's cells with links: ranks [kb0, kb1) among the set bits of bmask
@@ -529,8 +537,15 @@ __global__ void __launch_bounds__(LE_WARPS * 32, LE_MINB) k_link_emit(const __gr
                                     l2 = T.loz - pz, h2 = T.hiz - pz;
                     const bool narrow = l0 > -LIM && h0 < LIM && l1 > -LIM && h1 < LIM && l2 > -LIM && h2 < LIM;
                     if (narrow) {
-                        // all vertex offsets below 2^14 in magnitude: moments < 2^29, their signed sums
-                        // over the components of c below 2^31, n = m1 + m2 + m3, D below 2^47
+                        // Every vertex offset a, b, q lies in (-2^14, 2^14), so in 32-bit integers:
+                        //   moment components (a x b etc.): |a_y b_z - a_z b_y| < 2 * 2^28 = 2^29;
+                        //   V_k = c . m_k over the at most three nonzero components of c: < 3 * 2^29 < 2^31;
+                        //   n = m1 + m2 + m3 per component: < 3 * 2^29 < 2^31.
+                        // c . n is NOT formed in 32 bits: for a corner direction it reaches 9 * 2^29 > 2^31.
+                        // The line test needs only the signs of V1, V2, V3 (n = m1 + m2 + m3, so c . n =
+                        // V1 + V2 + V3, which has their common sign when they agree and are nonzero, and a
+                        // line parallel to the face cannot have three nonzero V of one sign); the crossing
+                        // parameter takes c . n in 64 bits.  D = n . a < 3 * 2^31 * 2^14 < 2^47.
                         const int ax = (int)(T.ax - px), ay = (int)(T.ay - py), az = (int)(T.az - pz);
                         const int bx = (int)(T.bx - px), by = (int)(T.by - py), bz = (int)(T.bz - pz);
                         const int qx = (int)(T.cx - px), qy = (int)(T.cy - py), qz = (int)(T.cz - pz);
@@ -539,23 +554,23 @@ __global__ void __launch_bounds__(LE_WARPS * 32, LE_MINB) k_link_emit(const __gr
                         const int m3x = qy * az - qz * ay, m3y = qz * ax - qx * az, m3z = qx * ay - qy * ax;
                         const int nx = m1x + m2x + m3x, ny = m1y + m2y + m3y, nz = m1z + m2z + m3z;
                         const long long D = (long long)nx * ax + (long long)ny * ay + (long long)nz * az;
-                        // line tests for the 13 direction pairs (odd index d and its opposite d + 1)
-                        uint32_t line = 0, degen = 0;
-#pragma unroll
+                        // line tests for the 13 direction pairs (odd index d and its opposite d + 1):
                         // all 13 lines, without branches (the lanes hold different cells, so a
                         // per-direction branch would diverge); non-candidates are masked off
+                        uint32_t line = 0, degen = 0;
 #pragma unroll
                         for (int r = 0; r < 13; ++r) {
                             const int d = 2 * r + 1;
                             int cx, cy, cz;
                             emb_dir(d, cx, cy, cz);
-                            const int NC = cx * nx + cy * ny + cz * nz;
                             const int V1 = cx * m1x + cy * m1y + cz * m1z;
                             const int V2 = cx * m2x + cy * m2y + cz * m2z;
                             const int V3 = cx * m3x + cy * m3y + cz * m3z;
-                            const uint32_t ok = ((ccm >> d) & 3u) != 0u && NC != 0;  // a parallel line never crosses
+                            const uint32_t ok = ((ccm >> d) & 3u) != 0u;
                             const uint32_t zero = (V1 == 0) | (V2 == 0) | (V3 == 0);
-                            const uint32_t same = ((V1 ^ NC) | (V2 ^ NC) | (V3 ^ NC)) >= 0;
+                            const uint32_t same = ((V1 ^ V2) | (V1 ^ V3)) >= 0;
+                            // a zero V (the perturbation decides) goes to the exact per-direction test,
+                            // which also rejects a line parallel to the face
                             degen |= (ok & zero) << d;
                             line |= (ok & (zero ^ 1u) & same) << d;
                         }
@@ -566,7 +581,8 @@ __global__ void __launch_bounds__(LE_WARPS * 32, LE_MINB) k_link_emit(const __gr
                             mm &= mm - 1;
                             int cx, cy, cz;
                             emb_dir(d, cx, cy, cz);
-                            const long long nc = (long long)(cx * nx + cy * ny + cz * nz);
+                            // |c . n| < 9 * 2^29 and h c . n < 2^18 * 2^33: both fit 64 bits
+                            const long long nc = (long long)cx * nx + (long long)cy * ny + (long long)cz * nz;
                             const int sn = nc > 0 ? 1 : -1;
                             if (side_sign64(D, nx, ny, nz) != sn) continue;           // t <= 0
                             if (side_sign64(D - h * nc, nx, ny, nz) != -sn) continue;  // t >= 1

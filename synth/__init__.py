@@ -13,6 +13,7 @@ from .meshes import (  # noqa: F401
     axis_box,
     tetrahedron,
     octahedron,
+    corner_face_tetrahedra,
     signed_volume,
 )
 from .workloads import (  # noqa: F401

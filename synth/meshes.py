@@ -262,3 +262,24 @@ def octahedron(centre, radii):
                 n = np.cross(p[b] - p[a], p[cc] - p[a])
                 tris.append([a, b, cc] if np.dot(n, p[a] - c) > 0 else [a, cc, b])
     return snap(p / _GRID), np.array(tris, dtype=np.int32)
+
+
+def corner_face_tetrahedra(centres, signs, a: int, delta: int, depth: int):
+    """Tetrahedra whose large face is perpendicular to a corner direction c = signs[i].
+
+    For each integer point P = centres[i] (2^-20 units) the face has its centroid at
+    G = P + delta c and its vertices at G + a u_k, with u_k = c * (1,-1,0), c * (0,1,-1),
+    c * (-1,0,1) (componentwise), so every vertex lies within a + |delta| of P on each
+    axis while the face normal is 3 a^2 c.  The fourth vertex is G + depth c.  The
+    segment from P along c meets the face at its centroid, at parameter delta / h for a
+    link of length h.  Returns one mesh (verts, tris) holding all the tetrahedra.
+    """
+    vs, ts = [], []
+    for P, c in zip(np.asarray(centres, dtype=np.int64), np.asarray(signs, dtype=np.int64)):
+        G = P + delta * c
+        u = np.array([[1, -1, 0], [0, 1, -1], [-1, 0, 1]], dtype=np.int64) * c[None, :]
+        pts = np.concatenate([G[None, :] + a * u, (G + depth * c)[None, :]])
+        v, t = tetrahedron(pts)
+        ts.append(t + 4 * len(vs))
+        vs.append(v)
+    return np.concatenate(vs).astype(np.float32), np.concatenate(ts).astype(np.int32)

@@ -175,3 +175,19 @@ def test_deep_forest_looked_up_through_the_hash(orc):
     _, g = gpu_embed(v, t, 32, 6, 2, 19)
     compare_full(g, o, 6)
     assert len(g["links"]["q"]) > 1000
+
+
+def test_corner_faces_beyond_int32(orc):
+    """Faces perpendicular to the four D3Q27 corner lines with every vertex within
+    2^14 of a finest cell centre, where c . n = 9 a^2 exceeds 2^31: the link kernel's
+    narrow 32-bit path must still find each crossing (q = 1/8 at the face centroid)."""
+    import corner_case as K
+    v, t = K.mesh()
+    o = orc.embed(v, t, K.R, K.LEVELS, K.BAND, K.LATTICE)
+    _, g = gpu_embed(v, t, K.R, K.LEVELS, K.BAND, K.LATTICE)
+    compare_full(g, o, K.LEVELS)
+    P = orc.cell_centres(K.R, K.LEVELS, g["blocks"][-1])
+    for i in range(4):
+        cell = int(np.nonzero((P == K.centres()[i][None, :]).all(axis=1))[0][0])
+        sel = (g["links"]["cell"] == cell) & (g["links"]["dir"] == K.direction_index(K.SIGNS[i]))
+        assert sel.sum() == 1 and abs(float(g["links"]["q"][sel][0]) - 0.125) <= 2e-6
