@@ -54,13 +54,17 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _SRC = os.path.join(_HERE, "emb_oracle.c")
+_SRC_LINES = os.path.join(_HERE, "emb_oracle_lines.c")
 
 
 def build(force: bool = False) -> str:
-    """Compile the C core with gcc (OpenMP) into oracle/liboracle.so."""
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+    """Compile the C core (brute force and sorted-line tiers) with gcc (OpenMP) into
+    oracle/liboracle.so."""
+    srcs = [_SRC, _SRC_LINES]
+    if force or not os.path.exists(_LIB_PATH) or any(os.path.getmtime(_LIB_PATH) < os.path.getmtime(x) for x in srcs):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-ffp-contract=off", "-o", tmp,
+                               *srcs, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -86,6 +90,11 @@ def lib():
         L.orc_line_hits.argtypes = [P, P, ctypes.c_int]
         L.orc_line_hits.restype = ctypes.c_int
         L.orc_directions.argtypes = [P]
+        L.orc_lines_flags.argtypes = [P, i64, P, i64, i64, i64, i64, P]
+        L.orc_lines_masks.argtypes = [P, i64, P, i64, i64, i64, P]
+        L.orc_lines_links.argtypes = [P, i64, P, i64, P, i64, i64, ctypes.c_int]
+        L.orc_lines_links.restype = i64
+        L.orc_lines_links_take.argtypes = [P, P, P, P, P]
         _lib = L
     return _lib
 
@@ -599,6 +608,71 @@ def embed(verts, tris, R: int, levels: int, band: int = 2, lattice: int = 19, d_
     else:
         blocks, flags, m = build_forest_paper(tri9, R, levels, d_spec)
         lk = cut_links(tri9, R, levels, blocks[levels], m[levels], lattice, existing_only=True)
+    return dict(X=X, tri9=tri9, blocks=blocks, flags=flags, masks=m, links=lk)
+
+
+# --------------------------------------------------------------------------- #
+# Tier B: the same definitions along sorted lattice lines (emb_oracle_lines.c)
+# --------------------------------------------------------------------------- #
+def _block_keys(blocks: np.ndarray, nb: int) -> np.ndarray:
+    b = _c64(blocks).reshape(-1, 3)
+    return _c64((b[:, 2] * nb + b[:, 1]) * nb + b[:, 0])
+
+
+def lines_flags(tri9, R, L, levels, band, blocks) -> np.ndarray:
+    """refine_flags, triangle-major: each triangle visits the blocks of the level whose
+    dilated box can meet its bounding box."""
+    tri9 = _c64(tri9)
+    blocks = _c64(blocks).reshape(-1, 3)
+    nb = R << L
+    out = np.zeros(len(blocks), dtype=np.uint8)
+    if len(blocks):
+        lib().orc_lines_flags(_p(tri9), len(tri9), _p(_block_keys(blocks, nb)), len(blocks), nb,
+                              4 * h_units(R, L), dilation(R, L, levels, band), _p(out))
+    return out
+
+
+def lines_masks(tri9, R, L, blocks) -> np.ndarray:
+    """masks, from the sorted crossings of the level's +x centre lines."""
+    tri9 = _c64(tri9)
+    blocks = _c64(blocks).reshape(-1, 3)
+    out = np.zeros(len(blocks), dtype=np.uint64)
+    if len(blocks):
+        lib().orc_lines_masks(_p(tri9), len(tri9), _p(blocks), len(blocks), h_units(R, L) // 2, cells_per_axis(R, L),
+                              _p(out))
+    return out
+
+
+def lines_links(tri9, R, levels, blocks_f, mask_f, lattice: int) -> dict:
+    """cut_links, with the crossings found triangle-major (one direction per thread)."""
+    tri9 = _c64(tri9)
+    blocks_f = _c64(blocks_f).reshape(-1, 3)
+    m = np.ascontiguousarray(mask_f, dtype=np.uint64)
+    n = lib().orc_lines_links(_p(tri9), len(tri9), _p(blocks_f), len(blocks_f), _p(m), h_units(R, levels) // 2,
+                              cells_per_axis(R, levels), int(lattice))
+    cell = np.zeros(n, dtype=np.int64)
+    d = np.zeros(n, dtype=np.int32)
+    q = np.zeros(n, dtype=np.float64)
+    tri = np.zeros(n, dtype=np.int64)
+    nc = np.zeros(n, dtype=np.int32)
+    lib().orc_lines_links_take(_p(cell), _p(d), _p(q), _p(tri), _p(nc))
+    return dict(cell=cell, dir=d.astype(np.int64), q=q, tri=tri, ncross=nc)
+
+
+def embed_lines(verts, tris, R: int, levels: int, band: int = 2, lattice: int = 19):
+    """The whole path (forest, masks per level, refine flags, cut links) by the
+    sorted-line tier; same results as ``embed`` (checked against it wherever both run),
+    fast enough for meshes of millions of triangles."""
+    X = int_coords(verts, R)
+    tri9 = tri_coords(X, tris)
+    blocks = [root_blocks(R)]
+    flags = []
+    for L in range(levels):
+        f = lines_flags(tri9, R, L, levels, band, blocks[L])
+        flags.append(f)
+        blocks.append(children(blocks[L], f))
+    m = [lines_masks(tri9, R, L, blocks[L]) for L in range(levels + 1)]
+    lk = lines_links(tri9, R, levels, blocks[levels], m[levels], lattice)
     return dict(X=X, tri9=tri9, blocks=blocks, flags=flags, masks=m, links=lk)
 
 

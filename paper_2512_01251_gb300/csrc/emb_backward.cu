@@ -155,7 +155,7 @@ extern "C" emb_status emb_mex_force(emb_forest f, int32_t lattice, const int32_t
     int nparts = (int)(np64 < 1184 ? np64 : 1184);
     if (nparts < 1) nparts = 1;
     double *part = nullptr;
-    EMB_CUDA_TRY(cudaMallocAsync(&part, 3 * nparts * sizeof(double), s));
+    EMB_CUDA_TRY(emb_malloc_async(&part, 3 * nparts * sizeof(double), s));
     EMB_LAUNCH((k_mex_partial), nparts, MEX_BLOCK, 0, s)(d_cell, d_dir, d_q, n, d_pop, pop_stride, lv.nbr, lv.mask, part);
     EMB_LAUNCH((k_mex_final), 1, MEX_BLOCK, 0, s)(part, nparts, d_F);
     EMB_CUDA_TRY(cudaGetLastError());
@@ -400,7 +400,7 @@ extern "C" emb_status emb_cutlinks_backward(emb_mesh m, emb_forest f, const int3
                  a_v = (size_t)(m->V + 1) * sizeof(uint32_t), a_tmp = emb_scan_tmp_words(m->V) * sizeof(uint64_t);
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
     char *scratch = nullptr;
-    EMB_CUDA_TRY(cudaMallocAsync((void **)&scratch, up(a_val) + 2 * up(a_ent) + 2 * up(a_v) + up(a_tmp), s));
+    EMB_CUDA_TRY(emb_malloc_async((void **)&scratch, up(a_val) + 2 * up(a_ent) + 2 * up(a_v) + up(a_tmp), s));
     float *val = (float *)scratch;
     int32_t *vid = (int32_t *)(scratch + up(a_val));
     uint32_t *slot = (uint32_t *)(scratch + up(a_val) + up(a_ent));

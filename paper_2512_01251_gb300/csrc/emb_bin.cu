@@ -385,17 +385,17 @@ static emb_status bin_finest(emb_bins b, uint64_t list_cap, uint64_t ent_cap, cu
     char *list = nullptr;
     EmbBigQ Q = {nullptr, nullptr, 0};
     const size_t a_bs = ((size_t)list_cap * sizeof(uint2) + 255) & ~(size_t)255;
-    if (cudaMallocAsync(&cnt, (lv.n + 1) * sizeof(uint32_t), s) != cudaSuccess ||
-        cudaMallocAsync(&tmp, emb_scan_tmp_words(lv.n) * sizeof(uint64_t), s) != cudaSuccess ||
-        cudaMallocAsync((void **)&list, 256 + a_bs + (size_t)list_cap * sizeof(uint32_t), s) != cudaSuccess)
+    if (emb_malloc_async(&cnt, (lv.n + 1) * sizeof(uint32_t), s) != cudaSuccess ||
+        emb_malloc_async(&tmp, emb_scan_tmp_words(lv.n) * sizeof(uint64_t), s) != cudaSuccess ||
+        emb_malloc_async((void **)&list, 256 + a_bs + (size_t)list_cap * sizeof(uint32_t), s) != cudaSuccess)
         rc = EMB_ERR_CUDA;
-    if (rc == EMB_OK && !b->off && cudaMallocAsync(&b->off, (lv.n + 1) * sizeof(uint32_t), s) != cudaSuccess)
+    if (rc == EMB_OK && !b->off && emb_malloc_async(&b->off, (lv.n + 1) * sizeof(uint32_t), s) != cudaSuccess)
         rc = EMB_ERR_CUDA;
     if (rc == EMB_OK && b->ent_cap != ent_cap) {
         if (b->ent) cudaFreeAsync(b->ent, s);
         b->ent = nullptr;
         b->ent_cap = ent_cap;
-        if (cudaMallocAsync(&b->ent, ((size_t)ent_cap + 1) * sizeof(uint32_t), s) != cudaSuccess) rc = EMB_ERR_CUDA;
+        if (emb_malloc_async(&b->ent, ((size_t)ent_cap + 1) * sizeof(uint32_t), s) != cudaSuccess) rc = EMB_ERR_CUDA;
     }
     if (rc == EMB_OK) rc = emb_bigq_alloc(Q, m->T, s);
     unsigned long long *ln = (unsigned long long *)list;
@@ -456,11 +456,11 @@ extern "C" emb_status emb_bin_ex(emb_mesh m, emb_forest f, int32_t level, int32_
     // step 1: exact x-line filter, compacted in ascending order
     // every buffer is stream-ordered on s: the bins are freed the same way, without a
     // device synchronisation (the flags of the mode without compaction live in the bins)
-    if (cudaMallocAsync(&flag, (m->T + 1) * sizeof(uint32_t), s) != cudaSuccess ||
-        cudaMallocAsync(&pos, (m->T + 1) * sizeof(uint32_t), s) != cudaSuccess ||
-        cudaMallocAsync(&tmp, emb_scan_tmp_words(m->T) * sizeof(uint64_t), s) != cudaSuccess ||
-        cudaMallocAsync(&b->flist, (m->T + 1) * sizeof(uint32_t), s) != cudaSuccess ||
-        cudaMallocAsync(&b->dcount, 16, s) != cudaSuccess) {
+    if (emb_malloc_async(&flag, (m->T + 1) * sizeof(uint32_t), s) != cudaSuccess ||
+        emb_malloc_async(&pos, (m->T + 1) * sizeof(uint32_t), s) != cudaSuccess ||
+        emb_malloc_async(&tmp, emb_scan_tmp_words(m->T) * sizeof(uint64_t), s) != cudaSuccess ||
+        emb_malloc_async(&b->flist, (m->T + 1) * sizeof(uint32_t), s) != cudaSuccess ||
+        emb_malloc_async(&b->dcount, 16, s) != cudaSuccess) {
         emb_bins_destroy(b);
         return EMB_ERR_CUDA;
     }

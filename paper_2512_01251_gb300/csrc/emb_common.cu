@@ -35,6 +35,36 @@ int *emb_status_word()
 
 cudaStream_t emb_stream(void *s) { return (cudaStream_t)s; }
 
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[64] = {nullptr};
+
+cudaError_t emb_malloc_raw(void **p, size_t bytes, cudaStream_t s)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    cudaMemPool_t pool;
+    {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        if (!g_pool[dev]) {
+            cudaMemPoolProps props = {};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            cudaMemPool_t np = nullptr;
+            e = cudaMemPoolCreate(&np, &props);
+            if (e != cudaSuccess) return e;
+            uint64_t keep = UINT64_MAX;  // never trimmed at synchronisations
+            e = cudaMemPoolSetAttribute(np, cudaMemPoolAttrReleaseThreshold, &keep);
+            if (e != cudaSuccess) return e;
+            g_pool[dev] = np;
+        }
+        pool = g_pool[dev];
+    }
+    return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
 static std::atomic<long long> g_launches{0};
 
 void emb_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -251,7 +281,7 @@ emb_status emb_scan_u32(const uint32_t *d_in, uint32_t *d_out, int64_t n, uint64
 {
     uint64_t *tmp = nullptr;
     int64_t ntiles = (n + 1 + SCAN_TILE - 1) / SCAN_TILE;
-    EMB_CUDA_TRY(cudaMallocAsync(&tmp, emb_scan_tmp_words(n) * sizeof(uint64_t), s));
+    EMB_CUDA_TRY(emb_malloc_async(&tmp, emb_scan_tmp_words(n) * sizeof(uint64_t), s));
     emb_status rc = emb_scan_into(d_in, d_out, n, tmp, s);
     if (rc != EMB_OK) return rc;
     if (h_total) {
@@ -353,16 +383,16 @@ emb_status emb_build_hash(EmbLevel &lv, cudaStream_t s)
     int64_t nw = emb_bitmap_words(lv.nb_axis);
     if (nw == 0) {
         lv.hcap = emb_hash_capacity(lv.n);
-        EMB_CUDA_TRY(cudaMallocAsync(&lv.hkey, lv.hcap * sizeof(uint64_t), s));
-        EMB_CUDA_TRY(cudaMallocAsync(&lv.hval, lv.hcap * sizeof(int32_t), s));
+        EMB_CUDA_TRY(emb_malloc_async(&lv.hkey, lv.hcap * sizeof(uint64_t), s));
+        EMB_CUDA_TRY(emb_malloc_async(&lv.hval, lv.hcap * sizeof(int32_t), s));
     }
     uint32_t *pc = nullptr;
     uint64_t *tmp = nullptr;
     if (nw > 0) {
-        EMB_CUDA_TRY(cudaMallocAsync(&lv.bits, nw * sizeof(uint64_t), s));
-        EMB_CUDA_TRY(cudaMallocAsync(&lv.wpre, (nw + 1) * sizeof(uint32_t), s));
-        EMB_CUDA_TRY(cudaMallocAsync(&pc, (nw + 1) * sizeof(uint32_t), s));
-        EMB_CUDA_TRY(cudaMallocAsync(&tmp, emb_scan_tmp_words(nw) * sizeof(uint64_t), s));
+        EMB_CUDA_TRY(emb_malloc_async(&lv.bits, nw * sizeof(uint64_t), s));
+        EMB_CUDA_TRY(emb_malloc_async(&lv.wpre, (nw + 1) * sizeof(uint32_t), s));
+        EMB_CUDA_TRY(emb_malloc_async(&pc, (nw + 1) * sizeof(uint32_t), s));
+        EMB_CUDA_TRY(emb_malloc_async(&tmp, emb_scan_tmp_words(nw) * sizeof(uint64_t), s));
     }
     emb_status rc = emb_enq_level_index(lv, pc, tmp, s);
     if (pc) EMB_CUDA_TRY(cudaFreeAsync(pc, s));
@@ -398,7 +428,7 @@ emb_status emb_enq_neighbors(EmbLevel &lv, cudaStream_t s)
 emb_status emb_build_neighbors(EmbLevel &lv, cudaStream_t s)
 {
     if (lv.nbr) return EMB_OK;
-    EMB_CUDA_TRY(cudaMallocAsync(&lv.nbr, (lv.n * 26 + 1) * sizeof(int32_t), s));
+    EMB_CUDA_TRY(emb_malloc_async(&lv.nbr, (lv.n * 26 + 1) * sizeof(int32_t), s));
     return emb_enq_neighbors(lv, s);
 }
 
@@ -417,7 +447,7 @@ emb_status emb_bigq_alloc(EmbBigQ &Q, int64_t T, cudaStream_t s)
     Q.n = nullptr;
     Q.cap = (uint32_t)emb_bigq_capacity(T);
     char *p = nullptr;
-    EMB_CUDA_TRY(cudaMallocAsync((void **)&p, 256 + (size_t)Q.cap * sizeof(uint2), s));
+    EMB_CUDA_TRY(emb_malloc_async((void **)&p, 256 + (size_t)Q.cap * sizeof(uint2), s));
     Q.n = (unsigned long long *)p;
     Q.q = (uint2 *)(p + 256);
     return EMB_OK;

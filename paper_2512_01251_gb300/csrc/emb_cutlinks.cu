@@ -895,16 +895,16 @@ static emb_status build_candidates(emb_forest f, int lattice, cudaStream_t s)
     emb_status rc = emb_build_neighbors(lv, s);
     if (rc != EMB_OK) return rc;
     free_candidates(f, s);
-    EMB_CUDA_TRY(cudaMallocAsync(&f->cand, (lv.n * 26 + 1) * sizeof(uint64_t), s));
-    EMB_CUDA_TRY(cudaMallocAsync(&f->blk_off, (lv.n + 1) * sizeof(uint32_t), s));
-    EMB_CUDA_TRY(cudaMallocAsync(&f->work_n, (lv.n + 1) * sizeof(uint32_t), s));
-    EMB_CUDA_TRY(cudaMallocAsync(&f->work, (lv.n + 1) * sizeof(uint32_t), s));
+    EMB_CUDA_TRY(emb_malloc_async(&f->cand, (lv.n * 26 + 1) * sizeof(uint64_t), s));
+    EMB_CUDA_TRY(emb_malloc_async(&f->blk_off, (lv.n + 1) * sizeof(uint32_t), s));
+    EMB_CUDA_TRY(emb_malloc_async(&f->work_n, (lv.n + 1) * sizeof(uint32_t), s));
+    EMB_CUDA_TRY(emb_malloc_async(&f->work, (lv.n + 1) * sizeof(uint32_t), s));
     if (!f->next) EMB_CUDA_TRY(cudaMalloc(&f->next, sizeof(unsigned int)));
     uint32_t *cnt = nullptr, *flag = nullptr;
     uint64_t *tmp = nullptr;
-    EMB_CUDA_TRY(cudaMallocAsync(&cnt, (lv.n + 1) * sizeof(uint32_t), s));
-    EMB_CUDA_TRY(cudaMallocAsync(&flag, (lv.n + 1) * sizeof(uint32_t), s));
-    EMB_CUDA_TRY(cudaMallocAsync(&tmp, emb_scan_tmp_words(lv.n) * sizeof(uint64_t), s));
+    EMB_CUDA_TRY(emb_malloc_async(&cnt, (lv.n + 1) * sizeof(uint32_t), s));
+    EMB_CUDA_TRY(emb_malloc_async(&flag, (lv.n + 1) * sizeof(uint32_t), s));
+    EMB_CUDA_TRY(emb_malloc_async(&tmp, emb_scan_tmp_words(lv.n) * sizeof(uint64_t), s));
     rc = emb_enq_link_prep(lv, lattice, f->cand, cnt, flag, f->work_n, f->work, f->blk_off, tmp, s);
     if (rc != EMB_OK) return rc;
     uint32_t total = 0;
@@ -980,7 +980,7 @@ extern "C" emb_status emb_cutlinks(emb_forest f, emb_bins b, int32_t lattice, in
     const int64_t xcap = emb_link_extra_capacity(lv.n);
     char *sp = nullptr;
     const size_t a_w = ((size_t)(lv.n + 1) * sizeof(uint2) + 255) & ~(size_t)255;
-    EMB_CUDA_TRY(cudaMallocAsync((void **)&sp, 256 + a_w + (size_t)xcap * sizeof(uint2), s));
+    EMB_CUDA_TRY(emb_malloc_async((void **)&sp, 256 + a_w + (size_t)xcap * sizeof(uint2), s));
     unsigned long long *xn = (unsigned long long *)sp;
     uint2 *witem = (uint2 *)(sp + 256);
     uint2 *extra = (uint2 *)(sp + 256 + a_w);

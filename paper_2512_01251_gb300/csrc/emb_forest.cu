@@ -91,7 +91,7 @@ extern "C" emb_status emb_forest_root(int32_t R, int32_t max_level, void *stream
     EmbLevel &lv = f->lv[0];
     lv.n = (int64_t)R * R * R;
     lv.nb_axis = R;
-    if (cudaMallocAsync(&lv.key, lv.n * sizeof(uint64_t), s) != cudaSuccess) {
+    if (emb_malloc_async(&lv.key, lv.n * sizeof(uint64_t), s) != cudaSuccess) {
         emb_forest_destroy(f);
         return EMB_ERR_CUDA;
     }
@@ -167,9 +167,9 @@ extern "C" emb_status emb_forest_refine(emb_forest f, int32_t level, const uint8
     free_level(C);
     uint32_t *cnt = nullptr, *rank = nullptr;
     uint64_t *tmp = nullptr;
-    EMB_CUDA_TRY(cudaMallocAsync(&cnt, (P.n + 1) * sizeof(uint32_t), s));
-    EMB_CUDA_TRY(cudaMallocAsync(&rank, (P.n + 1) * sizeof(uint32_t), s));
-    EMB_CUDA_TRY(cudaMallocAsync(&tmp, emb_scan_tmp_words(P.n) * sizeof(uint64_t), s));
+    EMB_CUDA_TRY(emb_malloc_async(&cnt, (P.n + 1) * sizeof(uint32_t), s));
+    EMB_CUDA_TRY(emb_malloc_async(&rank, (P.n + 1) * sizeof(uint32_t), s));
+    EMB_CUDA_TRY(emb_malloc_async(&tmp, emb_scan_tmp_words(P.n) * sizeof(uint64_t), s));
     emb_status rc = emb_enq_flag_ranks(P, d_flags, cnt, rank, tmp, s);
     if (rc != EMB_OK) return rc;
     uint32_t F = 0;
@@ -177,7 +177,7 @@ extern "C" emb_status emb_forest_refine(emb_forest f, int32_t level, const uint8
     EMB_CUDA_TRY(cudaStreamSynchronize(s));
     C.n = 8 * (int64_t)F;
     C.nb_axis = P.nb_axis * 2;
-    EMB_CUDA_TRY(cudaMallocAsync(&C.key, (C.n + 1) * sizeof(uint64_t), s));
+    EMB_CUDA_TRY(emb_malloc_async(&C.key, (C.n + 1) * sizeof(uint64_t), s));
     rc = emb_enq_children(P, d_flags, rank, C.key, C.n, false, s);
     if (rc != EMB_OK) return rc;
     EMB_CUDA_TRY(cudaFreeAsync(cnt, s));

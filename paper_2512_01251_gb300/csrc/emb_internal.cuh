@@ -36,6 +36,16 @@ void emb_count_launch();
 #define EMB_STRIP(...) __VA_ARGS__
 #define EMB_LAUNCH(kern, ...) emb_count_launch(), EMB_STRIP kern<<<__VA_ARGS__>>>
 int *emb_status_word();  // device pointer of the current device's status word (lazily created)
+// Stream-ordered allocation from the library's memory pool of the current device.  The
+// pool keeps freed memory for reuse instead of returning it to the driver at every
+// synchronisation (the default pool's behaviour), so a call that follows a host
+// synchronisation does not map fresh pages for its scratch.
+cudaError_t emb_malloc_raw(void **p, size_t bytes, cudaStream_t s);
+template <class T>
+static inline cudaError_t emb_malloc_async(T **p, size_t bytes, cudaStream_t s)
+{
+    return emb_malloc_raw((void **)p, bytes, s);
+}
 cudaStream_t emb_stream(void *s);
 
 __device__ __forceinline__ void emb_set_status(int *st, int code)

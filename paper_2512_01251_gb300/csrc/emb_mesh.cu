@@ -134,7 +134,10 @@ extern "C" emb_status emb_mesh_create(const float *d_verts, const int32_t *d_tri
     unsigned long long *hk = nullptr;
     emb_status rc = EMB_OK;
     int herr = 0;
-    if (cudaMalloc(&m->rec, (size_t)T * 3 * sizeof(int4)) != cudaSuccess || cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
+    // records and the error word from the library's pool (stream-ordered on s; the
+    // synchronisation below completes them before the mesh is used on any stream)
+    if (emb_malloc_async(&m->rec, (size_t)T * 3 * sizeof(int4), s) != cudaSuccess ||
+        emb_malloc_async(&err, sizeof(int), s) != cudaSuccess) {
         rc = EMB_ERR_CUDA;
         goto done;
     }
@@ -143,7 +146,7 @@ extern "C" emb_status emb_mesh_create(const float *d_verts, const int32_t *d_tri
     if (check_watertight) {
         int64_t cap = 1024;
         while (cap < 6 * T) cap <<= 1;
-        if (cudaMallocAsync(&hk, cap * sizeof(unsigned long long), s) != cudaSuccess) {
+        if (emb_malloc_async(&hk, cap * sizeof(unsigned long long), s) != cudaSuccess) {
             rc = EMB_ERR_CUDA;
             goto done;
         }
@@ -160,7 +163,7 @@ extern "C" emb_status emb_mesh_create(const float *d_verts, const int32_t *d_tri
     if (herr & (MESH_ERR_ID | MESH_ERR_SNAP)) rc = EMB_ERR_BAD_INPUT;
     else if (herr) rc = EMB_ERR_NOT_WATERTIGHT;
 done:
-    if (err) cudaFree(err);
+    if (err) cudaFreeAsync(err, s);
     if (rc != EMB_OK) {
         emb_mesh_destroy(m);
         return rc;

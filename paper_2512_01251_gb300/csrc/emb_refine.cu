@@ -305,7 +305,7 @@ extern "C" emb_status emb_refine_flags(emb_forest f, emb_bins b, int32_t level, 
     if (rc != EMB_OK) return rc;
     unsigned long long *fbits = nullptr;
     const int64_t nw = emb_bitmap_words(lv.nb_axis);
-    if (nw > 0 && cudaMallocAsync(&fbits, nw * sizeof(unsigned long long), s) != cudaSuccess) fbits = nullptr;
+    if (nw > 0 && emb_malloc_async(&fbits, nw * sizeof(unsigned long long), s) != cudaSuccess) fbits = nullptr;
     rc = emb_enq_refine(b->m->rec, b->m->T, level_geom(f, level), dil, lv, d_flags, fbits, Q, s);
     if (fbits) cudaFreeAsync(fbits, s);
     emb_bigq_free(Q, s);
@@ -385,8 +385,8 @@ extern "C" emb_status emb_refine_flags_paper(emb_forest f, int32_t level, double
     emb_status rc = emb_build_neighbors(lv, s);
     if (rc != EMB_OK) return rc;
     uint8_t *cls = nullptr, *tmp = nullptr;
-    EMB_CUDA_TRY(cudaMallocAsync(&cls, lv.n, s));
-    EMB_CUDA_TRY(cudaMallocAsync(&tmp, lv.n, s));
+    EMB_CUDA_TRY(emb_malloc_async(&cls, lv.n, s));
+    EMB_CUDA_TRY(emb_malloc_async(&tmp, lv.n, s));
     const int grid = emb_grid(lv.n, 256);
     EMB_LAUNCH((k_pf_classify), grid, 256, 0, s)(lv.key, lv.mask, lv.nbr, lv.n, lv.nb_axis, level == 0 ? 1 : 0, cls,
                                                  d_flags);

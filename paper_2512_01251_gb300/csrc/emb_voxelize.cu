@@ -231,12 +231,12 @@ extern "C" emb_status emb_voxelize(emb_forest f, emb_bins b, int32_t level, uint
         lv.mask_valid = 1;
         return EMB_OK;
     }
-    if (!lv.mask) EMB_CUDA_TRY(cudaMallocAsync(&lv.mask, lv.n * sizeof(uint64_t), s));
+    if (!lv.mask) EMB_CUDA_TRY(emb_malloc_async(&lv.mask, lv.n * sizeof(uint64_t), s));
     unsigned long long *s_acc = nullptr;
     unsigned int *p_acc = nullptr, *t_acc = nullptr;
-    EMB_CUDA_TRY(cudaMallocAsync(&s_acc, lv.n * sizeof(unsigned long long), s));
-    EMB_CUDA_TRY(cudaMallocAsync(&p_acc, lv.n * sizeof(unsigned int), s));
-    EMB_CUDA_TRY(cudaMallocAsync(&t_acc, lv.n * sizeof(unsigned int), s));
+    EMB_CUDA_TRY(emb_malloc_async(&s_acc, lv.n * sizeof(unsigned long long), s));
+    EMB_CUDA_TRY(emb_malloc_async(&p_acc, lv.n * sizeof(unsigned int), s));
+    EMB_CUDA_TRY(emb_malloc_async(&t_acc, lv.n * sizeof(unsigned int), s));
     EmbBigQ Q;
     emb_status rc = emb_bigq_alloc(Q, b->m->T, s);
     if (rc != EMB_OK) return rc;
