@@ -38,8 +38,11 @@ METRIC = "cells+cut links embedded/s at 7.2M tris; batched & fwd+bwd vs plain, s
 UNIT = "units/s"
 WORKLOAD = "star_7m"
 # Nominal 32-bit ALU instruction slots charged per (link, triangle) exact segment test
-# (three Pluecker signs in 64-bit arithmetic plus the normal dot product).
+# (three Pluecker signs in 64-bit arithmetic plus the normal dot product), and per cut
+# link for its exact crossing parameter (the int128 plane offsets and the rational
+# comparisons between crossings).
 KAPPA_SEG = 48
+KAPPA_Q = 60
 
 
 def parse():
@@ -99,31 +102,81 @@ def oracle_sample(v, t, w, lattice, n_blocks, seed):
     return units, time.perf_counter() - t0
 
 
+def oracle_lines_full(v, t, w, lattice):
+    """The whole workload by the sorted-line oracle tier (every block, mask, flag and
+    link).  Returns (units, seconds)."""
+    from oracle import oracle as O
+    O.lib()
+    t0 = time.perf_counter()
+    r = O.embed_lines(v, t, w.R, w.levels, w.band, lattice)
+    secs = time.perf_counter() - t0
+    return 64 * sum(len(b) for b in r["blocks"]) + len(r["links"]["q"]), secs
+
+
+def oracle_slab(tri9, w, lattice, z0, z1):
+    """The sorted-line tier on the root-block layers z0 <= bz < z1 of the workload: it
+    runs on the triangles whose z-range meets those layers widened by three root blocks
+    (more than the reach of any refine dilation, mask line or link of a block in the
+    layers, so their results are the whole workload's), and only the blocks and links
+    inside the layers are counted.  Returns (units, seconds)."""
+    from oracle import oracle as O
+    O.lib()
+    W0 = 4 * O.h_units(w.R, 0)
+    t0 = time.perf_counter()
+    zs = tri9[:, 2::3]
+    sel = (zs.max(axis=1) >= z0 * W0 - 3 * W0) & (zs.min(axis=1) <= z1 * W0 + 3 * W0)
+    r = O.embed_lines_tri9(tri9[sel], w.R, w.levels, w.band, lattice)
+    secs = time.perf_counter() - t0
+    units = 0
+    for L, b in enumerate(r["blocks"]):
+        units += 64 * int(((b[:, 2] >= z0 << L) & (b[:, 2] < z1 << L)).sum())
+    bf = r["blocks"][-1][r["links"]["cell"] // 64]
+    units += int(((bf[:, 2] >= z0 << w.levels) & (bf[:, 2] < z1 << w.levels)).sum())
+    return units, secs
+
+
 def omp_threads():
     n = os.environ.get("OMP_NUM_THREADS")
     return int(n) if n else os.cpu_count()
 
 
+def body_layers(tri9, w):
+    """Root-block layers (bz) that the mesh's z-range touches."""
+    from oracle import oracle as O
+    W0 = 4 * O.h_units(w.R, 0)
+    return int(tri9[:, 2::3].min() // W0), int(tri9[:, 2::3].max() // W0) + 1
+
+
 def run_reference(args):
+    """The oracle arm: each step is the sorted-line oracle tier on two root-block layers
+    of the workload (a bounded sample: the layers the step takes move through the body),
+    on this host's cores.  Value = units embedded in the sampled layers per second."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    from oracle import oracle as O
+    O.lib()
     w = workload(args.workload)
     lattice = max(w.lattices)
     v, t, cfg = workload_config(w, lattice)
-    per_step = 1
+    tri9 = O.tri_coords(O.int_coords(v, w.R), t)
+    z_lo, z_hi = body_layers(tri9, w)
+    span = 2
+    starts = list(range(z_lo, z_hi, span))
     for i in range(args.warmup):
-        oracle_sample(v, t, w, lattice, per_step, seed=1000 + i)
+        z0 = starts[i % len(starts)]
+        oracle_slab(tri9, w, lattice, z0, z0 + span)
     units = 0
     secs = 0.0
     for i in range(args.steps):
-        u, s = oracle_sample(v, t, w, lattice, per_step, seed=2000 + i)
+        z0 = starts[i % len(starts)]
+        u, s_ = oracle_slab(tri9, w, lattice, z0, z0 + span)
         units += u
-        secs += s
+        secs += s_
     val = units / secs
-    sample = (f"{per_step} surface block(s) of the finest level per step: 64 cell states, the states of all "
-              f"lattice neighbours of their fluid cells, and q of every cut link, each by brute force over all "
-              f"{len(t)} triangles")
+    sample = (f"per step {span} root-block layers (z) of the workload, cycling through the {z_hi - z_lo} layers the "
+              f"body spans: every block, mask, refine flag and cut link inside them by the sorted-line oracle tier "
+              f"(exact integer predicates, FP64 q) on {omp_threads()} host threads")
     line = dict(impl="reference", metric=METRIC, value=val, unit=UNIT, n_gpus=args.gpus, steps=args.steps,
                 warmup=args.warmup, ms_per_step=1e3 * secs / args.steps, higher_is_better=True, scaling="weak",
                 vs_baseline=None, dtype="int64", data="synthetic", config=cfg,
@@ -227,6 +280,55 @@ def reduce_over_ranks(dist, total_ms: float, units: float, device: str):
     uu = torch.tensor([units], dtype=torch.float64, device=device)
     dist.all_reduce(uu)
     return float(tt.item()), float(uu.item())
+
+
+def step_roofline(med, T, level_blocks, stats, n_links, tests, hbm_gbs, alu_tops, step_ms, replay_ms=None):
+    """Roofline of the whole step: per call, T_roof = max(algorithmic bytes / HBM peak,
+    algorithmic ops / ALU peak); summed over the calls of a step and divided by the
+    measured step time.  Bytes per call (B = blocks of the level, T triangles, nf the
+    filtered triangles, pairs the finest bin entries):
+      mesh records      96 T (indices, vertex gather, records out)
+      bin L             48 T + 4 T + 4 nf (records, filter flags, kept ids); at the finest
+                        level also 8 pairs + 4 B (pair counts and fill, offsets)
+      voxelize L        52 nf + 8 B + 32 B (kept records and ids, masks, line parities in and out)
+      refine flags L    48 T + B
+      forest refine L   9 B + 8 B_next (flags and keys in, child keys out)
+      cut links         27 x 8 B + 4 pairs + 48 nf + 13 links (mask words, bins, records,
+                        the table), ops = tests x KAPPA_SEG + links x KAPPA_Q
+    Only the cut links carry an op count (the exact segment tests it must run); for the
+    other calls the bytes bound is used, which makes their roofline time a lower bound."""
+    lf = len(level_blocks) - 1
+    rows = {}
+
+    def add(name, ms, by, ops=0.0):
+        if ms is None:
+            return
+        t_roof = max(by / (hbm_gbs * 1e9), ops / (alu_tops * 1e12)) * 1e3
+        rows[name] = dict(ms=round(ms, 4), bytes=int(by), ops=float(ops), roof_ms=round(t_roof, 4),
+                          frac=round(t_roof / ms, 4) if ms > 0 else None,
+                          bound="alu" if ops / (alu_tops * 1e12) > by / (hbm_gbs * 1e9) else "hbm")
+
+    add("mesh", med.get("mesh"), 96 * T)
+    for L in range(lf + 1):
+        B = level_blocks[L]
+        nf, pairs = stats[L]
+        by = 48 * T + 4 * T + 4 * nf + ((8 * pairs + 4 * B) if L == lf else 0)
+        add(f"bin{L}", med.get(f"bin{L}"), by)
+        add(f"voxelize{L}", med.get(f"voxelize{L}"), 52 * nf + 40 * B)
+        if L < lf:
+            add(f"refine_flags{L}", med.get(f"refine_flags{L}"), 48 * T + B)
+            add(f"forest_refine{L}", med.get(f"forest_refine{L}"), 9 * B + 8 * level_blocks[L + 1])
+    cl_ms = (med.get("cutlinks_count") or 0.0) + (med.get("cutlinks_emit") or 0.0)
+    Bf = level_blocks[lf]
+    add("cutlinks", cl_ms, 27 * 8 * Bf + 4 * stats[lf][1] + 48 * stats[lf][0] + 13 * n_links,
+        tests * KAPPA_SEG + n_links * KAPPA_Q)
+    t_roof = sum(r["roof_ms"] for r in rows.values())
+    out = dict(step_roof_ms=round(t_roof, 4), step_ms=round(step_ms, 4), step_frac=round(t_roof / step_ms, 4),
+               per_call=rows)
+    if replay_ms:
+        out["replay_ms"] = round(replay_ms, 4)
+        out["replay_frac"] = round(t_roof / replay_ms, 4)
+    return out
 
 
 def run_ours(args):
@@ -363,14 +465,14 @@ def run_ours(args):
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
     clk_mhz = (clk or {}).get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
     alu_peak = sm_count * 128 * clk_mhz * 1e6 / 1e12  # Tops/s of 32-bit ALU slots
-    achieved = tests * KAPPA_SEG / (emit_ms / 1e3) / 1e12
+    achieved = (tests * KAPPA_SEG + n_links * KAPPA_Q) / (emit_ms / 1e3) / 1e12
     traffic = measured_traffic("k_link_emit", ["emb_cutlinks.cu"])
     roofline = dict(kernel="k_link_emit (emb_cutlinks)", bound="alu", achieved=achieved, peak=alu_peak,
                     unit="Tops/s", frac=achieved / alu_peak,
                     traffic=(traffic or {}).get("bytes_per_launch"),
-                    basis=(f"{tests} (link, bin triangle) exact segment tests x {KAPPA_SEG} 32-bit ALU slots / "
-                           f"median launch time; peak = {sm_count} SMs x 128 lanes x {clk_mhz:.0f} MHz "
-                           f"(SM clock sampled under load; {pk_src} peaks file for HBM)"))
+                    basis=(f"({tests} (link, bin triangle) exact segment tests x {KAPPA_SEG} + {n_links} links x "
+                           f"{KAPPA_Q}) 32-bit ALU slots / median launch time; peak = {sm_count} SMs x 128 lanes x "
+                           f"{clk_mhz:.0f} MHz (SM clock sampled under load; {pk_src} peaks file for HBM)"))
     hbm = pk.get("hbm_gbs", 6800.0)
     T = len(t)
     level_blocks = [P.emb_forest_num_blocks(forest, L) for L in range(lf + 1)]
@@ -407,6 +509,9 @@ def run_ours(args):
                                  ci95_median=[srt[j], srt[k]], n=nst)
     line["four_calls"] = dict(ms=round(four, 4),
                              units_per_s=(64 * sum(level_blocks) + n_links) / (four / 1e3) if four else None)
+    # the whole step against its roofline (the replay leg below adds the graph-replay time)
+    roofline["step"] = step_roofline(med, T, level_blocks, stats, n_links, tests, hbm, alu_peak,
+                                     line["step_ms_stats"]["median"])
 
     if rank == 0 and not args.no_extras:
         legs = None if args.legs == "all" else set(args.legs.split(","))
@@ -430,13 +535,21 @@ def run_ours(args):
             line["guard_ablation"] = guard_leg(P, verts, tris, w, lattice)
         if want("replay"):
             line["replay"] = replay_leg(P, verts, tris, w, lattice, line["ms_per_step"])
+            line["roofline"]["step"] = step_roofline(med, T, level_blocks, stats, n_links, tests, hbm, alu_peak,
+                                                     line["step_ms_stats"]["median"], line["replay"]["ms"])
         if want("cpu_baseline"):
-            units_s, secs = oracle_sample(v, t, w, lattice, 6, seed=7)
-            line["cpu_baseline"] = dict(value=units_s / secs, unit=UNIT, cores=omp_threads(), kind="oracle",
-                                        sample=("6 surface blocks of the finest level: 64 cell states each, the "
-                                                "states of all lattice neighbours of their fluid cells and q of every "
-                                                f"cut link, each by brute force over all {len(t)} triangles; "
-                                                f"{units_s} units in {secs:.1f} s"))
+            units_b, secs_b = oracle_lines_full(v, t, w, lattice)
+            units_a, secs_a = oracle_sample(v, t, w, lattice, 4, seed=7)
+            full_units = 64 * sum(level_blocks) + n_links
+            line["cpu_baseline"] = dict(
+                value=units_b / secs_b, unit=UNIT, cores=omp_threads(), kind="oracle",
+                sample=(f"the whole workload ({units_b} units) by the sorted-line oracle tier: every block, mask, "
+                        f"refine flag and cut link, exact integer predicates, FP64 q; {secs_b:.1f} s"),
+                brute_force=dict(value=units_a / secs_a, unit=UNIT, cores=omp_threads(),
+                                 sample=(f"extrapolated: 4 surface blocks of the finest level by brute force over all "
+                                         f"{len(t)} triangles ({units_a} units in {secs_a:.1f} s); at that rate the "
+                                         f"full step of {full_units} units would take "
+                                         f"{full_units / (units_a / secs_a) / 3600:.0f} h")))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -664,7 +664,14 @@ def embed_lines(verts, tris, R: int, levels: int, band: int = 2, lattice: int = 
     sorted-line tier; same results as ``embed`` (checked against it wherever both run),
     fast enough for meshes of millions of triangles."""
     X = int_coords(verts, R)
-    tri9 = tri_coords(X, tris)
+    out = embed_lines_tri9(tri_coords(X, tris), R, levels, band, lattice)
+    out["X"] = X
+    return out
+
+
+def embed_lines_tri9(tri9, R: int, levels: int, band: int = 2, lattice: int = 19):
+    """embed_lines from triangle records in frame units ((T, 9) int64)."""
+    tri9 = _c64(tri9)
     blocks = [root_blocks(R)]
     flags = []
     for L in range(levels):
@@ -673,7 +680,7 @@ def embed_lines(verts, tris, R: int, levels: int, band: int = 2, lattice: int = 
         blocks.append(children(blocks[L], f))
     m = [lines_masks(tri9, R, L, blocks[L]) for L in range(levels + 1)]
     lk = lines_links(tri9, R, levels, blocks[levels], m[levels], lattice)
-    return dict(X=X, tri9=tri9, blocks=blocks, flags=flags, masks=m, links=lk)
+    return dict(tri9=tri9, blocks=blocks, flags=flags, masks=m, links=lk)
 
 
 # --------------------------------------------------------------------------- #

@@ -66,3 +66,30 @@ def test_leg_selection(monkeypatch):
     assert a.legs == "batched,replay" and a.steps == 10 and a.warmup == 3 and a.gpus == 1
     monkeypatch.setattr(sys, "argv", ["bench.py"])
     assert b.parse().legs == "all"
+
+
+def test_oracle_slabs_partition_the_workload():
+    """The reference arm's layer samples: slabs of root-block layers covering the domain
+    add up to exactly the units of the whole workload."""
+    b = _bench()
+    from oracle import oracle as O
+    from synth import workload
+    w = workload("star_20k")
+    v, t = w.build_mesh()
+    full, _ = b.oracle_lines_full(v, t, w, 27)
+    tri9 = O.tri_coords(O.int_coords(v, w.R), t)
+    parts = sum(b.oracle_slab(tri9, w, 27, z0, z0 + 3)[0] for z0 in range(0, w.R, 3))
+    assert parts == full
+
+
+def test_step_roofline_sums_the_calls():
+    b = _bench()
+    med = {"mesh": 0.3, "bin0": 0.5, "bin1": 1.0, "voxelize0": 0.1, "voxelize1": 0.2, "refine_flags0": 0.4,
+           "forest_refine0": 0.1, "cutlinks_count": 0.5, "cutlinks_emit": 4.0}
+    r = b.step_roofline(med, 1000, [8, 64], [(500, 0), (400, 3000)], 20000, 10 ** 9, 6000.0, 40.0, 8.0, 6.0)
+    assert set(r["per_call"]) == {"mesh", "bin0", "bin1", "voxelize0", "voxelize1", "refine_flags0", "forest_refine0",
+                                  "cutlinks"}
+    lk = r["per_call"]["cutlinks"]
+    assert lk["bound"] == "alu" and abs(lk["roof_ms"] - (10 ** 9 * 48 + 20000 * 60) / 40e12 * 1e3) < 1e-3
+    assert abs(r["step_roof_ms"] - sum(x["roof_ms"] for x in r["per_call"].values())) < 1e-3
+    assert abs(r["step_frac"] - r["step_roof_ms"] / 8.0) < 1e-3 and abs(r["replay_frac"] - r["step_roof_ms"] / 6.0) < 1e-3
