@@ -75,6 +75,29 @@ emb_status emb_directions(int32_t *h_out);
  * launched in the process so far, counted on the host at each launch site. */
 emb_status emb_launch_count(int64_t *h_out);
 
+/* Diagnostics for tests: evaluates the library's exact device predicates on n
+ * caller-given queries (no counterpart in the paper; these are the decisions of
+ * Sec. 3.3-3.4 taken in isolation, so that they can be checked against a host
+ * evaluation on adversarial and extreme inputs).  d_in: n x 15 int64 per query
+ * (device): a triangle A, B, C in frame units (9 values, each in [0, 2^25)), then
+ *   EMB_PROBE_XLINE:   [9] unused, [10] y, [11] z of a +x line; hit = the perturbed
+ *                      line crosses the triangle (filter and voxelizer test);
+ *   EMB_PROBE_SEGMENT: [9..11] P, [12] direction 1..26, [13] h > 0; hit = the
+ *                      perturbed segment P -> P + h c crosses the triangle, q = its
+ *                      parameter rounded to float (the link kernel's exact rescan);
+ *   EMB_PROBE_PAIR:    same query through the link kernel's per-pair path (32-bit
+ *                      moments when every vertex is within 2^14 of P);
+ *   EMB_PROBE_BOX:     [9..11] lo, [12..14] hi; hit = the triangle meets the closed
+ *                      box (binning and refine-flag test).
+ * d_hit: n int32 (0, 1, or -1 for a direction or h out of range); d_q: n floats (-1
+ * where not hit).  Points and box corners within 2^25 of the triangle.  Enqueues only.
+ * Errors: EMB_ERR_BAD_INPUT (kind, n < 0, null pointers with n > 0). */
+#define EMB_PROBE_XLINE 0
+#define EMB_PROBE_SEGMENT 1
+#define EMB_PROBE_PAIR 2
+#define EMB_PROBE_BOX 3
+emb_status emb_probe_predicates(int32_t kind, const int64_t *d_in, int64_t n, int32_t *d_hit, float *d_q, void *stream);
+
 /* ---------------------------------------------------------------- mesh ---- */
 /* Geometry input (Sec. 3.1): a closed, oriented triangle mesh given as an index
  * list.  d_verts: V x 3 float32, each coordinate a multiple of 2^-20 strictly

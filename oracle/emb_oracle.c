@@ -361,3 +361,38 @@ void orc_guard_surface(const float *verts, const int32_t *tris, const i64 *block
         }
     }
 }
+
+/* ---------------------------------------------------------------------- */
+/* one triangle per query (tests of single decisions in bulk)              */
+/* ---------------------------------------------------------------------- */
+/* out[i] = the perturbed line through pts[i] along DIR[dirs[i]] crosses triangle tri[i]. */
+void orc_each_line(const i64 *tri, const i64 *pts, const int32_t *dirs, i64 N, uint8_t *out)
+{
+#pragma omp parallel for schedule(static)
+    for (i64 i = 0; i < N; ++i) {
+        i64 n[3], nc;
+        const i64 *A = tri + 9 * i;
+        out[i] = (uint8_t)line_hits(A, A + 3, A + 6, pts + 3 * i, DIR[dirs[i]], n, &nc);
+    }
+}
+
+/* hit[i] = the perturbed segment pts[i] -> pts[i] + h[i] DIR[dirs[i]] crosses triangle
+ * tri[i]; t[i] = its parameter in FP64 (-1 if not). */
+void orc_each_segment(const i64 *tri, const i64 *pts, const int32_t *dirs, const i64 *h, i64 N, uint8_t *hit,
+                      double *t)
+{
+#pragma omp parallel for schedule(static)
+    for (i64 i = 0; i < N; ++i) {
+        i128 Nn, Mm;
+        const i64 *A = tri + 9 * i;
+        hit[i] = (uint8_t)segment_hit(A, A + 3, A + 6, pts + 3 * i, DIR[dirs[i]], h[i], &Nn, &Mm);
+        t[i] = hit[i] ? (double)Nn / ((double)Mm * (double)h[i]) : -1.0;
+    }
+}
+
+/* out[i] = triangle tri[i] overlaps the closed box [lo[i], hi[i]]. */
+void orc_each_box(const i64 *tri, const i64 *lo, const i64 *hi, i64 N, uint8_t *out)
+{
+#pragma omp parallel for schedule(static)
+    for (i64 i = 0; i < N; ++i) out[i] = (uint8_t)orc_sat(tri + 9 * i, lo + 3 * i, hi + 3 * i);
+}

@@ -90,6 +90,9 @@ def lib():
         L.orc_line_hits.argtypes = [P, P, ctypes.c_int]
         L.orc_line_hits.restype = ctypes.c_int
         L.orc_directions.argtypes = [P]
+        L.orc_each_line.argtypes = [P, P, P, i64, P]
+        L.orc_each_segment.argtypes = [P, P, P, P, i64, P, P]
+        L.orc_each_box.argtypes = [P, P, P, i64, P]
         L.orc_lines_flags.argtypes = [P, i64, P, i64, i64, i64, i64, P]
         L.orc_lines_masks.argtypes = [P, i64, P, i64, i64, i64, P]
         L.orc_lines_links.argtypes = [P, i64, P, i64, P, i64, i64, ctypes.c_int]
@@ -208,6 +211,38 @@ def boxes_any(tri9: np.ndarray, lo: np.ndarray, hi: np.ndarray) -> np.ndarray:
 
 def sat(tri9_one, lo, hi) -> bool:
     return bool(lib().orc_sat(_p(_c64(tri9_one)), _p(_c64(lo)), _p(_c64(hi))))
+
+
+def each_line(tri9, pts, dirs) -> np.ndarray:
+    """One query per triangle: the perturbed line through pts[i] along DIR[dirs[i]] crosses tri9[i]."""
+    tri9, pts = _c64(tri9).reshape(-1, 9), _c64(pts).reshape(-1, 3)
+    d = np.ascontiguousarray(dirs, dtype=np.int32)
+    out = np.zeros(len(tri9), dtype=np.uint8)
+    if len(tri9):
+        lib().orc_each_line(_p(tri9), _p(pts), _p(d), len(tri9), _p(out))
+    return out
+
+
+def each_segment(tri9, pts, dirs, h):
+    """One query per triangle: (hit, t in FP64) of the perturbed segment pts[i] -> pts[i] + h[i] c."""
+    tri9, pts = _c64(tri9).reshape(-1, 9), _c64(pts).reshape(-1, 3)
+    d = np.ascontiguousarray(dirs, dtype=np.int32)
+    hh = _c64(np.broadcast_to(np.asarray(h, dtype=np.int64), (len(tri9),)))
+    hit = np.zeros(len(tri9), dtype=np.uint8)
+    t = np.zeros(len(tri9), dtype=np.float64)
+    if len(tri9):
+        lib().orc_each_segment(_p(tri9), _p(pts), _p(d), _p(hh), len(tri9), _p(hit), _p(t))
+    return hit, t
+
+
+def each_box(tri9, lo, hi) -> np.ndarray:
+    """One query per triangle: tri9[i] overlaps the closed box [lo[i], hi[i]]."""
+    tri9 = _c64(tri9).reshape(-1, 9)
+    lo, hi = _c64(lo).reshape(-1, 3), _c64(hi).reshape(-1, 3)
+    out = np.zeros(len(tri9), dtype=np.uint8)
+    if len(tri9):
+        lib().orc_each_box(_p(tri9), _p(lo), _p(hi), len(tri9), _p(out))
+    return out
 
 
 def cells_per_axis(R: int, L: int) -> int:

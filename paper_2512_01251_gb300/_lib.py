@@ -23,6 +23,7 @@ SIGNATURES = {
     "emb_status_get": (I32, [P, PI32]),
     "emb_directions": (I32, [PI32]),
     "emb_launch_count": (I32, [PI64]),
+    "emb_probe_predicates": (I32, [I32, P, I64, P, P, P]),
     "emb_mesh_create": (I32, [P, P, I64, I64, I32, I32, P, ctypes.POINTER(P)]),
     "emb_mesh_destroy": (None, [P]),
     "emb_mesh_update": (I32, [P, P, I64, P]),

@@ -369,6 +369,150 @@ __device__ __noinline__ bool pair_cross_wide(const TriT &T, long long px, long l
     return true;
 }
 
+// All crossings of one (triangle, cell centre P) pair on the candidate directions ccm:
+// emit(d, q) for every direction d whose perturbed segment P -> P + h c_d crosses the
+// triangle, q = t rounded to float.  When every vertex lies within 2^14 of P the
+// moments fit 32-bit integers and D fits 64 bits; otherwise the moments are formed
+// in 64 bits by widening products and D in 128 bits.  A zero Pluecker value sends
+// its direction through the exact per-direction test with the full tie-break.
+template <class Emit>
+__device__ __forceinline__ void link_pair(const TriT &T, long long px, long long py, long long pz, uint32_t ccm,
+                                          long long h, Emit emit)
+{
+    const long long LIM = 1ll << 14;
+    const long long l0 = T.lox - px, h0 = T.hix - px, l1 = T.loy - py, h1 = T.hiy - py,
+                    l2 = T.loz - pz, h2 = T.hiz - pz;
+    const bool narrow = l0 > -LIM && h0 < LIM && l1 > -LIM && h1 < LIM && l2 > -LIM && h2 < LIM;
+    if (narrow) {
+        // Every vertex offset a, b, q lies in (-2^14, 2^14), so in 32-bit integers:
+        //   moment components (a x b etc.): |a_y b_z - a_z b_y| < 2 * 2^28 = 2^29;
+        //   V_k = c . m_k over the at most three nonzero components of c: < 3 * 2^29 < 2^31;
+        //   n = m1 + m2 + m3 per component: < 3 * 2^29 < 2^31.
+        // c . n is NOT formed in 32 bits: for a corner direction it reaches 9 * 2^29 > 2^31.
+        // The line test needs only the signs of V1, V2, V3 (n = m1 + m2 + m3, so c . n =
+        // V1 + V2 + V3, which has their common sign when they agree and are nonzero, and a
+        // line parallel to the face cannot have three nonzero V of one sign); the crossing
+        // parameter takes c . n in 64 bits.  D = n . a < 3 * 2^31 * 2^14 < 2^47.
+        const int ax = (int)(T.ax - px), ay = (int)(T.ay - py), az = (int)(T.az - pz);
+        const int bx = (int)(T.bx - px), by = (int)(T.by - py), bz = (int)(T.bz - pz);
+        const int qx = (int)(T.cx - px), qy = (int)(T.cy - py), qz = (int)(T.cz - pz);
+        const int m1x = ay * bz - az * by, m1y = az * bx - ax * bz, m1z = ax * by - ay * bx;
+        const int m2x = by * qz - bz * qy, m2y = bz * qx - bx * qz, m2z = bx * qy - by * qx;
+        const int m3x = qy * az - qz * ay, m3y = qz * ax - qx * az, m3z = qx * ay - qy * ax;
+        const int nx = m1x + m2x + m3x, ny = m1y + m2y + m3y, nz = m1z + m2z + m3z;
+        const long long D = (long long)nx * ax + (long long)ny * ay + (long long)nz * az;
+        // line tests for the 13 direction pairs (odd index d and its opposite d + 1):
+        // all 13 lines, without branches (the lanes hold different cells, so a
+        // per-direction branch would diverge); non-candidates are masked off
+        uint32_t line = 0, degen = 0;
+#pragma unroll
+        for (int r = 0; r < 13; ++r) {
+            const int d = 2 * r + 1;
+            int cx, cy, cz;
+            emb_dir(d, cx, cy, cz);
+            const int V1 = cx * m1x + cy * m1y + cz * m1z;
+            const int V2 = cx * m2x + cy * m2y + cz * m2z;
+            const int V3 = cx * m3x + cy * m3y + cz * m3z;
+            const uint32_t ok = ((ccm >> d) & 3u) != 0u;
+            const uint32_t zero = (V1 == 0) | (V2 == 0) | (V3 == 0);
+            const uint32_t same = ((V1 ^ V2) | (V1 ^ V3)) >= 0;
+            // a zero V (the perturbation decides) goes to the exact per-direction test,
+            // which also rejects a line parallel to the face
+            degen |= (ok & zero) << d;
+            line |= (ok & (zero ^ 1u) & same) << d;
+        }
+        // members of line-hit pairs that are candidates: the segment ends must straddle the plane
+        uint32_t mm = (line | (line << 1)) & ccm;
+        while (mm) {
+            const int d = __ffs(mm) - 1;
+            mm &= mm - 1;
+            int cx, cy, cz;
+            emb_dir(d, cx, cy, cz);
+            // |c . n| < 9 * 2^29 and h c . n < 2^18 * 2^33: both fit 64 bits
+            const long long nc = (long long)cx * nx + (long long)cy * ny + (long long)cz * nz;
+            const int sn = nc > 0 ? 1 : -1;
+            if (side_sign64(D, nx, ny, nz) != sn) continue;           // t <= 0
+            if (side_sign64(D - h * nc, nx, ny, nz) != -sn) continue;  // t >= 1
+            const long long N = sn > 0 ? D : -D, Mq = nc > 0 ? nc : -nc;
+            const float q = __fdiv_rn((float)N, (float)Mq * (float)h);
+            emit(d, q);
+        }
+        // a zero Pluecker value: resolve the pair's directions exactly
+        mm = (degen | (degen << 1)) & ccm;
+        while (mm) {
+            const int d = __ffs(mm) - 1;
+            mm &= mm - 1;
+            int cx, cy, cz;
+            emb_dir(d, cx, cy, cz);
+            float q;
+            if (!pair_cross_wide(T, px, py, pz, cx, cy, cz, h, &q)) continue;
+            emit(d, q);
+        }
+    } else {
+        // coordinates are below 2^25, so offsets fit 32 bits: moments (below 2^51)
+        // and their signed sums in 64 bits from widening products, D in 128 bits
+        const int ax = (int)(T.ax - px), ay = (int)(T.ay - py), az = (int)(T.az - pz);
+        const int bx = (int)(T.bx - px), by = (int)(T.by - py), bz = (int)(T.bz - pz);
+        const int qx = (int)(T.cx - px), qy = (int)(T.cy - py), qz = (int)(T.cz - pz);
+        const long long m1x = (long long)ay * bz - (long long)az * by,
+                        m1y = (long long)az * bx - (long long)ax * bz,
+                        m1z = (long long)ax * by - (long long)ay * bx;
+        const long long m2x = (long long)by * qz - (long long)bz * qy,
+                        m2y = (long long)bz * qx - (long long)bx * qz,
+                        m2z = (long long)bx * qy - (long long)by * qx;
+        const long long m3x = (long long)qy * az - (long long)qz * ay,
+                        m3y = (long long)qz * ax - (long long)qx * az,
+                        m3z = (long long)qx * ay - (long long)qy * ax;
+        const long long nx = m1x + m2x + m3x, ny = m1y + m2y + m3y, nz = m1z + m2z + m3z;
+        uint32_t line = 0, degen = 0;
+#pragma unroll
+        for (int r = 0; r < 13; ++r) {
+            const int d = 2 * r + 1;
+            if (!(ccm & (3u << d))) continue;
+            int cx, cy, cz;
+            emb_dir(d, cx, cy, cz);
+            const long long NC = cx * nx + cy * ny + cz * nz;
+            const long long V1 = cx * m1x + cy * m1y + cz * m1z;
+            const long long V2 = cx * m2x + cy * m2y + cz * m2z;
+            const long long V3 = cx * m3x + cy * m3y + cz * m3z;
+            if (NC == 0) continue;
+            if (V1 == 0 || V2 == 0 || V3 == 0) {
+                degen |= 1u << d;
+                continue;
+            }
+            if (((V1 ^ NC) | (V2 ^ NC) | (V3 ^ NC)) >= 0) line |= 1u << d;
+        }
+        uint32_t mm = (line | (line << 1)) & ccm;
+        if (mm) {
+            const i128 D = mul128(nx, ax) + mul128(ny, ay) + mul128(nz, az);
+            while (mm) {
+                const int d = __ffs(mm) - 1;
+                mm &= mm - 1;
+                int cx, cy, cz;
+                emb_dir(d, cx, cy, cz);
+                const long long nc = cx * nx + cy * ny + cz * nz;
+                const int sn = nc > 0 ? 1 : -1;
+                if (side_sign(D, nx, ny, nz) != sn) continue;                  // t <= 0
+                if (side_sign(D - mul128(h, nc), nx, ny, nz) != -sn) continue;  // t >= 1
+                const i128 N = sn > 0 ? D : -D;
+                const long long Mq = nc > 0 ? nc : -nc;
+                const float q = __fdiv_rn(i128_to_float(N), (float)Mq * (float)h);
+                emit(d, q);
+            }
+        }
+        mm = (degen | (degen << 1)) & ccm;
+        while (mm) {
+            const int d = __ffs(mm) - 1;
+            mm &= mm - 1;
+            int cx, cy, cz;
+            emb_dir(d, cx, cy, cz);
+            float q;
+            if (!pair_cross_wide(T, px, py, pz, cx, cy, cz, h, &q)) continue;
+            emit(d, q);
+        }
+    }
+}
+
 #ifndef LE_MINB
 #define LE_MINB 6
 #endif
@@ -443,7 +587,6 @@ __global__ void __launch_bounds__(LE_WARPS * 32, LE_MINB) k_link_emit(const __gr
             continue;
         }
         const int lh = __ffsll(h) - 1;  // h is a power of two
-        const long long LIM = 1ll << 14;
         // this item's cells with links: ranks [kb0, kb1) among the set bits of bmask
         const int kb0 = (int)(E.y & 0xFFu), kb1 = min(nbc, (int)((E.y >> 8) & 0xFFu));
         for (int cb = kb0; cb < kb1; cb += 32) {
@@ -533,141 +676,10 @@ __global__ void __launch_bounds__(LE_WARPS * 32, LE_MINB) k_link_emit(const __gr
                                     pz = Z0 + (2 * (cell >> 4) + 1) * half;
                     const uint32_t ccm = S.cm[slot];
                     const uint32_t local = e - e0 + (uint32_t)ti;
-                    const long long l0 = T.lox - px, h0 = T.hix - px, l1 = T.loy - py, h1 = T.hiy - py,
-                                    l2 = T.loz - pz, h2 = T.hiz - pz;
-                    const bool narrow = l0 > -LIM && h0 < LIM && l1 > -LIM && h1 < LIM && l2 > -LIM && h2 < LIM;
-                    if (narrow) {
-                        // Every vertex offset a, b, q lies in (-2^14, 2^14), so in 32-bit integers:
-                        //   moment components (a x b etc.): |a_y b_z - a_z b_y| < 2 * 2^28 = 2^29;
-                        //   V_k = c . m_k over the at most three nonzero components of c: < 3 * 2^29 < 2^31;
-                        //   n = m1 + m2 + m3 per component: < 3 * 2^29 < 2^31.
-                        // c . n is NOT formed in 32 bits: for a corner direction it reaches 9 * 2^29 > 2^31.
-                        // The line test needs only the signs of V1, V2, V3 (n = m1 + m2 + m3, so c . n =
-                        // V1 + V2 + V3, which has their common sign when they agree and are nonzero, and a
-                        // line parallel to the face cannot have three nonzero V of one sign); the crossing
-                        // parameter takes c . n in 64 bits.  D = n . a < 3 * 2^31 * 2^14 < 2^47.
-                        const int ax = (int)(T.ax - px), ay = (int)(T.ay - py), az = (int)(T.az - pz);
-                        const int bx = (int)(T.bx - px), by = (int)(T.by - py), bz = (int)(T.bz - pz);
-                        const int qx = (int)(T.cx - px), qy = (int)(T.cy - py), qz = (int)(T.cz - pz);
-                        const int m1x = ay * bz - az * by, m1y = az * bx - ax * bz, m1z = ax * by - ay * bx;
-                        const int m2x = by * qz - bz * qy, m2y = bz * qx - bx * qz, m2z = bx * qy - by * qx;
-                        const int m3x = qy * az - qz * ay, m3y = qz * ax - qx * az, m3z = qx * ay - qy * ax;
-                        const int nx = m1x + m2x + m3x, ny = m1y + m2y + m3y, nz = m1z + m2z + m3z;
-                        const long long D = (long long)nx * ax + (long long)ny * ay + (long long)nz * az;
-                        // line tests for the 13 direction pairs (odd index d and its opposite d + 1):
-                        // all 13 lines, without branches (the lanes hold different cells, so a
-                        // per-direction branch would diverge); non-candidates are masked off
-                        uint32_t line = 0, degen = 0;
-#pragma unroll
-                        for (int r = 0; r < 13; ++r) {
-                            const int d = 2 * r + 1;
-                            int cx, cy, cz;
-                            emb_dir(d, cx, cy, cz);
-                            const int V1 = cx * m1x + cy * m1y + cz * m1z;
-                            const int V2 = cx * m2x + cy * m2y + cz * m2z;
-                            const int V3 = cx * m3x + cy * m3y + cz * m3z;
-                            const uint32_t ok = ((ccm >> d) & 3u) != 0u;
-                            const uint32_t zero = (V1 == 0) | (V2 == 0) | (V3 == 0);
-                            const uint32_t same = ((V1 ^ V2) | (V1 ^ V3)) >= 0;
-                            // a zero V (the perturbation decides) goes to the exact per-direction test,
-                            // which also rejects a line parallel to the face
-                            degen |= (ok & zero) << d;
-                            line |= (ok & (zero ^ 1u) & same) << d;
-                        }
-                        // members of line-hit pairs that are candidates: the segment ends must straddle the plane
-                        uint32_t mm = (line | (line << 1)) & ccm;
-                        while (mm) {
-                            const int d = __ffs(mm) - 1;
-                            mm &= mm - 1;
-                            int cx, cy, cz;
-                            emb_dir(d, cx, cy, cz);
-                            // |c . n| < 9 * 2^29 and h c . n < 2^18 * 2^33: both fit 64 bits
-                            const long long nc = (long long)cx * nx + (long long)cy * ny + (long long)cz * nz;
-                            const int sn = nc > 0 ? 1 : -1;
-                            if (side_sign64(D, nx, ny, nz) != sn) continue;           // t <= 0
-                            if (side_sign64(D - h * nc, nx, ny, nz) != -sn) continue;  // t >= 1
-                            const long long N = sn > 0 ? D : -D, Mq = nc > 0 ? nc : -nc;
-                            const float q = __fdiv_rn((float)N, (float)Mq * (float)h);
-                            const int kk = atomicAdd(&S.hcnt[slot], 1);
-                            if (kk < LE_BCAP) S.hit[kk][slot] = make_uint2(local | ((uint32_t)d << 24), __float_as_uint(q));
-                        }
-                        // a zero Pluecker value: resolve the pair's directions exactly
-                        mm = (degen | (degen << 1)) & ccm;
-                        while (mm) {
-                            const int d = __ffs(mm) - 1;
-                            mm &= mm - 1;
-                            int cx, cy, cz;
-                            emb_dir(d, cx, cy, cz);
-                            float q;
-                            if (!pair_cross_wide(T, px, py, pz, cx, cy, cz, h, &q)) continue;
-                            const int kk = atomicAdd(&S.hcnt[slot], 1);
-                            if (kk < LE_BCAP) S.hit[kk][slot] = make_uint2(local | ((uint32_t)d << 24), __float_as_uint(q));
-                        }
-                    } else {
-                        // coordinates are below 2^25, so offsets fit 32 bits: moments (below 2^51)
-                        // and their signed sums in 64 bits from widening products, D in 128 bits
-                        const int ax = (int)(T.ax - px), ay = (int)(T.ay - py), az = (int)(T.az - pz);
-                        const int bx = (int)(T.bx - px), by = (int)(T.by - py), bz = (int)(T.bz - pz);
-                        const int qx = (int)(T.cx - px), qy = (int)(T.cy - py), qz = (int)(T.cz - pz);
-                        const long long m1x = (long long)ay * bz - (long long)az * by,
-                                        m1y = (long long)az * bx - (long long)ax * bz,
-                                        m1z = (long long)ax * by - (long long)ay * bx;
-                        const long long m2x = (long long)by * qz - (long long)bz * qy,
-                                        m2y = (long long)bz * qx - (long long)bx * qz,
-                                        m2z = (long long)bx * qy - (long long)by * qx;
-                        const long long m3x = (long long)qy * az - (long long)qz * ay,
-                                        m3y = (long long)qz * ax - (long long)qx * az,
-                                        m3z = (long long)qx * ay - (long long)qy * ax;
-                        const long long nx = m1x + m2x + m3x, ny = m1y + m2y + m3y, nz = m1z + m2z + m3z;
-                        uint32_t line = 0, degen = 0;
-#pragma unroll
-                        for (int r = 0; r < 13; ++r) {
-                            const int d = 2 * r + 1;
-                            if (!(ccm & (3u << d))) continue;
-                            int cx, cy, cz;
-                            emb_dir(d, cx, cy, cz);
-                            const long long NC = cx * nx + cy * ny + cz * nz;
-                            const long long V1 = cx * m1x + cy * m1y + cz * m1z;
-                            const long long V2 = cx * m2x + cy * m2y + cz * m2z;
-                            const long long V3 = cx * m3x + cy * m3y + cz * m3z;
-                            if (NC == 0) continue;
-                            if (V1 == 0 || V2 == 0 || V3 == 0) {
-                                degen |= 1u << d;
-                                continue;
-                            }
-                            if (((V1 ^ NC) | (V2 ^ NC) | (V3 ^ NC)) >= 0) line |= 1u << d;
-                        }
-                        uint32_t mm = (line | (line << 1)) & ccm;
-                        if (mm) {
-                            const i128 D = mul128(nx, ax) + mul128(ny, ay) + mul128(nz, az);
-                            while (mm) {
-                                const int d = __ffs(mm) - 1;
-                                mm &= mm - 1;
-                                int cx, cy, cz;
-                                emb_dir(d, cx, cy, cz);
-                                const long long nc = cx * nx + cy * ny + cz * nz;
-                                const int sn = nc > 0 ? 1 : -1;
-                                if (side_sign(D, nx, ny, nz) != sn) continue;                  // t <= 0
-                                if (side_sign(D - mul128(h, nc), nx, ny, nz) != -sn) continue;  // t >= 1
-                                const i128 N = sn > 0 ? D : -D;
-                                const long long Mq = nc > 0 ? nc : -nc;
-                                const float q = __fdiv_rn(i128_to_float(N), (float)Mq * (float)h);
-                                const int kk = atomicAdd(&S.hcnt[slot], 1);
-                                if (kk < LE_BCAP) S.hit[kk][slot] = make_uint2(local | ((uint32_t)d << 24), __float_as_uint(q));
-                            }
-                        }
-                        mm = (degen | (degen << 1)) & ccm;
-                        while (mm) {
-                            const int d = __ffs(mm) - 1;
-                            mm &= mm - 1;
-                            int cx, cy, cz;
-                            emb_dir(d, cx, cy, cz);
-                            float q;
-                            if (!pair_cross_wide(T, px, py, pz, cx, cy, cz, h, &q)) continue;
-                            const int kk = atomicAdd(&S.hcnt[slot], 1);
-                            if (kk < LE_BCAP) S.hit[kk][slot] = make_uint2(local | ((uint32_t)d << 24), __float_as_uint(q));
-                        }
-                    }
+                    link_pair(T, px, py, pz, ccm, h, [&](int d, float q) {
+                        const int kk = atomicAdd(&S.hcnt[slot], 1);
+                        if (kk < LE_BCAP) S.hit[kk][slot] = make_uint2(local | ((uint32_t)d << 24), __float_as_uint(q));
+                    });
                 }
                 __syncwarp();
             }
@@ -995,6 +1007,99 @@ extern "C" emb_status emb_cutlinks(emb_forest f, emb_bins b, int32_t lattice, in
     }
     cudaFreeAsync(sp, s);
     if (rc != EMB_OK) return rc;
+    EMB_CUDA_TRY(cudaGetLastError());
+    return EMB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Predicate probe: the device predicates of the path on caller-given queries
+// ---------------------------------------------------------------------------
+// One thread per query of 15 int64 (layout in emb.h, emb_probe_predicates).
+__global__ void k_probe(int kind, const long long *__restrict__ in, int64_t n, int32_t *__restrict__ hit,
+                        float *__restrict__ qout)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const long long *r = in + 15 * i;
+    const int4 A = make_int4((int)r[0], (int)r[1], (int)r[2], 0), B = make_int4((int)r[3], (int)r[4], (int)r[5], 0),
+               C = make_int4((int)r[6], (int)r[7], (int)r[8], 0);
+    int h_ = 0;
+    float q_ = -1.0f;
+    if (kind == EMB_PROBE_XLINE) {
+        // the x-line test of the filter and the voxelizer
+        const long long nx = ((long long)B.y - A.y) * ((long long)C.z - A.z) - ((long long)B.z - A.z) * ((long long)C.y - A.y);
+        if (nx != 0) {
+            const int sx = nx > 0 ? 1 : -1, py = (int)r[10], pz = (int)r[11];
+            h_ = emb_orient_yz(A.y, A.z, B.y, B.z, py, pz) == sx && emb_orient_yz(B.y, B.z, C.y, C.z, py, pz) == sx &&
+                 emb_orient_yz(C.y, C.z, A.y, A.z, py, pz) == sx;
+        }
+    } else if (kind == EMB_PROBE_BOX) {
+        // the overlap test of the binning and the refine flags (closed box [lo, hi])
+        h_ = emb_point_in_box(A, r[9], r[10], r[11], r[12], r[13], r[14]) ||
+             emb_point_in_box(B, r[9], r[10], r[11], r[12], r[13], r[14]) ||
+             emb_point_in_box(C, r[9], r[10], r[11], r[12], r[13], r[14]) ||
+             emb_tri_box(A, B, C, r[9], r[10], r[11], r[12], r[13], r[14]);
+    } else {
+        const long long px = r[9], py = r[10], pz = r[11], h = r[13];
+        const int d = (int)r[12];
+        if (r[12] < 1 || r[12] > 26 || h <= 0) {
+            h_ = -1;  // not a query of this kind
+        } else if (kind == EMB_PROBE_SEGMENT) {
+            // the exact per-direction test of the link kernel's rescan path
+            const long long ax = A.x - px, ay = A.y - py, az = A.z - pz;
+            const long long bx = B.x - px, by = B.y - py, bz = B.z - pz;
+            const long long qx = C.x - px, qy = C.y - py, qz = C.z - pz;
+            const long long ux = bx - ax, uy = by - ay, uz = bz - az, vx = qx - ax, vy = qy - ay, vz = qz - az;
+            const long long nx = uy * vz - uz * vy, ny = uz * vx - ux * vz, nz = ux * vy - uy * vx;
+            const long long m1x = ay * bz - az * by, m1y = az * bx - ax * bz, m1z = ax * by - ay * bx;
+            const long long m2x = by * qz - bz * qy, m2y = bz * qx - bx * qz, m2z = bx * qy - by * qx;
+            const long long m3x = qy * az - qz * ay, m3y = qz * ax - qx * az, m3z = qx * ay - qy * ax;
+            int cx, cy, cz;
+            emb_dir(d, cx, cy, cz);
+            i128 D = 0;
+            bool haveD = false;
+            if (seg_cross(cx, cy, cz, h, ax, ay, az, bx, by, bz, qx, qy, qz, nx, ny, nz, m1x, m1y, m1z, m2x, m2y, m2z,
+                          m3x, m3y, m3z, D, haveD)) {
+                const long long nc = cdot(cx, cy, cz, nx, ny, nz);
+                const i128 N = nc > 0 ? D : -D;
+                const long long M = nc > 0 ? nc : -nc;
+                h_ = 1;
+                q_ = __fdiv_rn(i128_to_float(N), (float)M * (float)h);
+            }
+        } else {
+            // the link kernel's per-pair path (32-bit moments within 2^14 of P, else 64-bit)
+            TriT T;
+            T.ax = A.x; T.ay = A.y; T.az = A.z;
+            T.bx = B.x; T.by = B.y; T.bz = B.z;
+            T.cx = C.x; T.cy = C.y; T.cz = C.z;
+            T.id = 0;
+            T.lox = min(A.x, min(B.x, C.x)); T.hix = max(A.x, max(B.x, C.x));
+            T.loy = min(A.y, min(B.y, C.y)); T.hiy = max(A.y, max(B.y, C.y));
+            T.loz = min(A.z, min(B.z, C.z)); T.hiz = max(A.z, max(B.z, C.z));
+            const long long ux = (long long)B.x - A.x, uy = (long long)B.y - A.y, uz = (long long)B.z - A.z;
+            const long long vx = (long long)C.x - A.x, vy = (long long)C.y - A.y, vz = (long long)C.z - A.z;
+            T.nx = uy * vz - uz * vy;
+            T.ny = uz * vx - ux * vz;
+            T.nz = ux * vy - uy * vx;
+            link_pair(T, px, py, pz, 1u << d, h, [&](int dd, float qq) {
+                if (dd == d) {
+                    h_ = 1;
+                    q_ = qq;
+                }
+            });
+        }
+    }
+    hit[i] = h_;
+    qout[i] = q_;
+}
+
+extern "C" emb_status emb_probe_predicates(int32_t kind, const int64_t *d_in, int64_t n, int32_t *d_hit, float *d_q,
+                                           void *stream)
+{
+    if (kind < EMB_PROBE_XLINE || kind > EMB_PROBE_BOX || n < 0) return EMB_ERR_BAD_INPUT;
+    if (n == 0) return EMB_OK;
+    if (!d_in || !d_hit || !d_q) return EMB_ERR_BAD_INPUT;
+    EMB_LAUNCH((k_probe), emb_grid(n, 128), 128, 0, emb_stream(stream))(kind, (const long long *)d_in, n, d_hit, d_q);
     EMB_CUDA_TRY(cudaGetLastError());
     return EMB_OK;
 }

@@ -108,6 +108,21 @@ def emb_directions() -> list:
     return [tuple(buf[3 * i:3 * i + 3]) for i in range(27)]
 
 
+EMB_PROBE_XLINE, EMB_PROBE_SEGMENT, EMB_PROBE_PAIR, EMB_PROBE_BOX = 0, 1, 2, 3
+
+
+def emb_probe_predicates(kind: int, queries: torch.Tensor, stream=None):
+    """The library's device predicates on (n, 15) int64 queries (layout in emb.h):
+    returns (hit int32, q float32) tensors."""
+    queries = queries.to(device="cuda", dtype=torch.int64).contiguous()
+    n = queries.shape[0]
+    hit = torch.empty(n, dtype=torch.int32, device="cuda")
+    q = torch.empty(n, dtype=torch.float32, device="cuda")
+    _check(load().emb_probe_predicates(int(kind), _ptr(queries), n, _ptr(hit), _ptr(q), _stream(stream)),
+           "emb_probe_predicates")
+    return hit, q
+
+
 def emb_mesh_create(verts: torch.Tensor, tris: torch.Tensor, R: int, check_watertight: bool = True,
                     stream=None) -> Mesh:
     verts = verts.to(device="cuda", dtype=torch.float32).contiguous()
