@@ -369,42 +369,41 @@ __device__ __noinline__ bool pair_cross_wide(const TriT &T, long long px, long l
     return true;
 }
 
-// All crossings of one (triangle, cell centre P) pair on the candidate directions ccm:
-// emit(d, q) for every direction d whose perturbed segment P -> P + h c_d crosses the
-// triangle, q = t rounded to float.  When every vertex lies within 2^14 of P the
-// moments fit 32-bit integers and D fits 64 bits; otherwise the moments are formed
-// in 64 bits by widening products and D in 128 bits.  A zero Pluecker value sends
-// its direction through the exact per-direction test with the full tie-break.
-template <class Emit>
-__device__ __forceinline__ void link_pair(const TriT &T, long long px, long long py, long long pz, uint32_t ccm,
-                                          long long h, Emit emit)
+// Pair (triangle, cell centre P) tests, in two halves: the line tests of every
+// candidate direction, then the segment ends of the lines that cross.
+//
+// pair_lines: the candidate directions (bits of ccm) whose perturbed line through P
+// crosses the triangle (hd), and those with a zero Pluecker value, which need the exact
+// per-direction test (dd).  When every vertex lies within 2^14 of P the moments fit
+// 32-bit integers; otherwise they are formed in 64 bits by widening products.
+__device__ __forceinline__ bool pair_narrow(const TriT &T, long long px, long long py, long long pz)
 {
     const long long LIM = 1ll << 14;
-    const long long l0 = T.lox - px, h0 = T.hix - px, l1 = T.loy - py, h1 = T.hiy - py,
-                    l2 = T.loz - pz, h2 = T.hiz - pz;
-    const bool narrow = l0 > -LIM && h0 < LIM && l1 > -LIM && h1 < LIM && l2 > -LIM && h2 < LIM;
-    if (narrow) {
+    return T.lox - px > -LIM && T.hix - px < LIM && T.loy - py > -LIM && T.hiy - py < LIM && T.loz - pz > -LIM &&
+           T.hiz - pz < LIM;
+}
+
+__device__ __forceinline__ void pair_lines(const TriT &T, long long px, long long py, long long pz, uint32_t ccm,
+                                           uint32_t &hd, uint32_t &dd)
+{
+    uint32_t line = 0, degen = 0;
+    if (pair_narrow(T, px, py, pz)) {
         // Every vertex offset a, b, q lies in (-2^14, 2^14), so in 32-bit integers:
         //   moment components (a x b etc.): |a_y b_z - a_z b_y| < 2 * 2^28 = 2^29;
-        //   V_k = c . m_k over the at most three nonzero components of c: < 3 * 2^29 < 2^31;
-        //   n = m1 + m2 + m3 per component: < 3 * 2^29 < 2^31.
-        // c . n is NOT formed in 32 bits: for a corner direction it reaches 9 * 2^29 > 2^31.
-        // The line test needs only the signs of V1, V2, V3 (n = m1 + m2 + m3, so c . n =
-        // V1 + V2 + V3, which has their common sign when they agree and are nonzero, and a
-        // line parallel to the face cannot have three nonzero V of one sign); the crossing
-        // parameter takes c . n in 64 bits.  D = n . a < 3 * 2^31 * 2^14 < 2^47.
+        //   V_k = c . m_k over the at most three nonzero components of c: < 3 * 2^29 < 2^31.
+        // c . n = V1 + V2 + V3 is NOT formed in 32 bits: for a corner direction it reaches
+        // 9 * 2^29 > 2^31.  The line test needs only the signs of V1, V2, V3 (when they
+        // agree and are nonzero their sum has that sign, and a line parallel to the face
+        // cannot have three nonzero V of one sign).
         const int ax = (int)(T.ax - px), ay = (int)(T.ay - py), az = (int)(T.az - pz);
         const int bx = (int)(T.bx - px), by = (int)(T.by - py), bz = (int)(T.bz - pz);
         const int qx = (int)(T.cx - px), qy = (int)(T.cy - py), qz = (int)(T.cz - pz);
         const int m1x = ay * bz - az * by, m1y = az * bx - ax * bz, m1z = ax * by - ay * bx;
         const int m2x = by * qz - bz * qy, m2y = bz * qx - bx * qz, m2z = bx * qy - by * qx;
         const int m3x = qy * az - qz * ay, m3y = qz * ax - qx * az, m3z = qx * ay - qy * ax;
-        const int nx = m1x + m2x + m3x, ny = m1y + m2y + m3y, nz = m1z + m2z + m3z;
-        const long long D = (long long)nx * ax + (long long)ny * ay + (long long)nz * az;
         // line tests for the 13 direction pairs (odd index d and its opposite d + 1):
         // all 13 lines, without branches (the lanes hold different cells, so a
         // per-direction branch would diverge); non-candidates are masked off
-        uint32_t line = 0, degen = 0;
 #pragma unroll
         for (int r = 0; r < 13; ++r) {
             const int d = 2 * r + 1;
@@ -421,36 +420,9 @@ __device__ __forceinline__ void link_pair(const TriT &T, long long px, long long
             degen |= (ok & zero) << d;
             line |= (ok & (zero ^ 1u) & same) << d;
         }
-        // members of line-hit pairs that are candidates: the segment ends must straddle the plane
-        uint32_t mm = (line | (line << 1)) & ccm;
-        while (mm) {
-            const int d = __ffs(mm) - 1;
-            mm &= mm - 1;
-            int cx, cy, cz;
-            emb_dir(d, cx, cy, cz);
-            // |c . n| < 9 * 2^29 and h c . n < 2^18 * 2^33: both fit 64 bits
-            const long long nc = (long long)cx * nx + (long long)cy * ny + (long long)cz * nz;
-            const int sn = nc > 0 ? 1 : -1;
-            if (side_sign64(D, nx, ny, nz) != sn) continue;           // t <= 0
-            if (side_sign64(D - h * nc, nx, ny, nz) != -sn) continue;  // t >= 1
-            const long long N = sn > 0 ? D : -D, Mq = nc > 0 ? nc : -nc;
-            const float q = __fdiv_rn((float)N, (float)Mq * (float)h);
-            emit(d, q);
-        }
-        // a zero Pluecker value: resolve the pair's directions exactly
-        mm = (degen | (degen << 1)) & ccm;
-        while (mm) {
-            const int d = __ffs(mm) - 1;
-            mm &= mm - 1;
-            int cx, cy, cz;
-            emb_dir(d, cx, cy, cz);
-            float q;
-            if (!pair_cross_wide(T, px, py, pz, cx, cy, cz, h, &q)) continue;
-            emit(d, q);
-        }
     } else {
         // coordinates are below 2^25, so offsets fit 32 bits: moments (below 2^51)
-        // and their signed sums in 64 bits from widening products, D in 128 bits
+        // and their signed sums in 64 bits from widening products
         const int ax = (int)(T.ax - px), ay = (int)(T.ay - py), az = (int)(T.az - pz);
         const int bx = (int)(T.bx - px), by = (int)(T.by - py), bz = (int)(T.bz - pz);
         const int qx = (int)(T.cx - px), qy = (int)(T.cy - py), qz = (int)(T.cz - pz);
@@ -464,7 +436,6 @@ __device__ __forceinline__ void link_pair(const TriT &T, long long px, long long
                         m3y = (long long)qz * ax - (long long)qx * az,
                         m3z = (long long)qx * ay - (long long)qy * ax;
         const long long nx = m1x + m2x + m3x, ny = m1y + m2y + m3y, nz = m1z + m2z + m3z;
-        uint32_t line = 0, degen = 0;
 #pragma unroll
         for (int r = 0; r < 13; ++r) {
             const int d = 2 * r + 1;
@@ -482,35 +453,74 @@ __device__ __forceinline__ void link_pair(const TriT &T, long long px, long long
             }
             if (((V1 ^ NC) | (V2 ^ NC) | (V3 ^ NC)) >= 0) line |= 1u << d;
         }
-        uint32_t mm = (line | (line << 1)) & ccm;
-        if (mm) {
-            const i128 D = mul128(nx, ax) + mul128(ny, ay) + mul128(nz, az);
-            while (mm) {
-                const int d = __ffs(mm) - 1;
-                mm &= mm - 1;
-                int cx, cy, cz;
-                emb_dir(d, cx, cy, cz);
-                const long long nc = cx * nx + cy * ny + cz * nz;
-                const int sn = nc > 0 ? 1 : -1;
-                if (side_sign(D, nx, ny, nz) != sn) continue;                  // t <= 0
-                if (side_sign(D - mul128(h, nc), nx, ny, nz) != -sn) continue;  // t >= 1
-                const i128 N = sn > 0 ? D : -D;
-                const long long Mq = nc > 0 ? nc : -nc;
-                const float q = __fdiv_rn(i128_to_float(N), (float)Mq * (float)h);
-                emit(d, q);
-            }
-        }
-        mm = (degen | (degen << 1)) & ccm;
+    }
+    // members of line-hit pairs that are candidates
+    hd = (line | (line << 1)) & ccm;
+    dd = (degen | (degen << 1)) & ccm;
+}
+
+// pair_segments: emit(d, q) for every direction d of hd whose segment P -> P + h c_d has
+// its ends on opposite sides of the plane (perturbed), and for every direction of dd
+// that the exact per-direction test finds crossed; q = t rounded to float.
+template <class Emit>
+__device__ __forceinline__ void pair_segments(const TriT &T, long long px, long long py, long long pz, uint32_t hd,
+                                              uint32_t dd, long long h, Emit emit)
+{
+    const long long ax = T.ax - px, ay = T.ay - py, az = T.az - pz;
+    uint32_t mm = hd;
+    if (mm && pair_narrow(T, px, py, pz)) {
+        // n = m1 + m2 + m3 per component < 3 * 2^29, so D = n . a < 9 * 2^29 * 2^14 < 2^47,
+        // |c . n| < 9 * 2^29 and h c . n < 2^18 * 2^33: all fit 64 bits
+        const long long D = T.nx * ax + T.ny * ay + T.nz * az;
         while (mm) {
             const int d = __ffs(mm) - 1;
             mm &= mm - 1;
             int cx, cy, cz;
             emb_dir(d, cx, cy, cz);
-            float q;
-            if (!pair_cross_wide(T, px, py, pz, cx, cy, cz, h, &q)) continue;
-            emit(d, q);
+            const long long nc = (long long)cx * T.nx + (long long)cy * T.ny + (long long)cz * T.nz;
+            const int sn = nc > 0 ? 1 : -1;
+            if (side_sign64(D, T.nx, T.ny, T.nz) != sn) continue;           // t <= 0
+            if (side_sign64(D - h * nc, T.nx, T.ny, T.nz) != -sn) continue;  // t >= 1
+            const long long N = sn > 0 ? D : -D, Mq = nc > 0 ? nc : -nc;
+            emit(d, __fdiv_rn((float)N, (float)Mq * (float)h));
+        }
+    } else if (mm) {
+        const i128 D = mul128(T.nx, ax) + mul128(T.ny, ay) + mul128(T.nz, az);
+        while (mm) {
+            const int d = __ffs(mm) - 1;
+            mm &= mm - 1;
+            int cx, cy, cz;
+            emb_dir(d, cx, cy, cz);
+            const long long nc = cx * T.nx + cy * T.ny + cz * T.nz;
+            const int sn = nc > 0 ? 1 : -1;
+            if (side_sign(D, T.nx, T.ny, T.nz) != sn) continue;                  // t <= 0
+            if (side_sign(D - mul128(h, nc), T.nx, T.ny, T.nz) != -sn) continue;  // t >= 1
+            const i128 N = sn > 0 ? D : -D;
+            const long long Mq = nc > 0 ? nc : -nc;
+            emit(d, __fdiv_rn(i128_to_float(N), (float)Mq * (float)h));
         }
     }
+    // a zero Pluecker value: resolve the pair's directions exactly
+    mm = dd;
+    while (mm) {
+        const int d = __ffs(mm) - 1;
+        mm &= mm - 1;
+        int cx, cy, cz;
+        emb_dir(d, cx, cy, cz);
+        float q;
+        if (!pair_cross_wide(T, px, py, pz, cx, cy, cz, h, &q)) continue;
+        emit(d, q);
+    }
+}
+
+// All crossings of one pair on the candidate directions ccm (both halves in one call).
+template <class Emit>
+__device__ __forceinline__ void link_pair(const TriT &T, long long px, long long py, long long pz, uint32_t ccm,
+                                          long long h, Emit emit)
+{
+    uint32_t hd, dd;
+    pair_lines(T, px, py, pz, ccm, hd, dd);
+    pair_segments(T, px, py, pz, hd, dd, h, emit);
 }
 
 #ifndef LE_MINB

@@ -76,28 +76,6 @@ __device__ __forceinline__ void refine_block(const int4 &A, const int4 &B, const
     }
 }
 
-// The less common path, kept out of line so that the kernel's main path needs few
-// registers and more warps stay resident to cover the latency of the record loads:
-// a union block not yet flagged, tested against the warp's 32 triangles.
-static __device__ __noinline__ void refine_union_block(const WuTri &S, long long bx, long long by, long long bz,
-                                                       unsigned long long pos, const LevelGeom &g, long long dil,
-                                                       const EmbLookup &lk, uint8_t *__restrict__ flags,
-                                                       const FlagBits &fb)
-{
-    const int32_t id = emb_lookup(lk, bx, by, bz);
-    if (id < 0 || flags[id]) return;
-    const long long lx = bx * g.W - dil, ly = by * g.W - dil, lz = bz * g.W - dil;
-    const long long hx = lx + g.W + 2 * dil, hy = ly + g.W + 2 * dil, hz = lz + g.W + 2 * dil;
-    for (int j = 0; j < 32; ++j) {
-        if (wu_overlap(S, j, lx, ly, lz, hx, hy, hz)) {
-            flags[id] = 1;
-            if (fb.w) fb.set(pos);
-            return;
-        }
-    }
-}
-
-
 // Persistent warps over tiles of 32 consecutive triangles; each warp loads the
 // records of its next tile before it works on the current one, so that the loads
 // are in flight during the work (a warp otherwise spends most of its life after its
@@ -162,15 +140,39 @@ __global__ void __launch_bounds__(EMB_WU_WARPS * 32, REFINE_MINB) k_refine(const
         const unsigned long long own = valid ? refine_items(b0, b1) : 0;
         const unsigned own_sum = __reduce_add_sync(0xffffffffu, (unsigned)min(own, 1ull << 20));
         if (total <= EMB_WU_MAX && 8 * total <= (long long)own_sum) {
-            // total <= EMB_WU_MAX: decode the union index in 32-bit arithmetic
+            // total <= EMB_WU_MAX: decode the union index in 32-bit arithmetic.  Each lane
+            // takes a union block; the blocks that exist and are not flagged yet are then
+            // tested one at a time by the whole warp, each lane against its own triangle.
             const unsigned ux = (unsigned)nx, uxy = (unsigned)(nx * ny);
-            for (unsigned c = lane; c < (unsigned)total; c += 32) {
-                const unsigned cz = c / uxy, cr = c - cz * uxy, cy = cr / ux;
-                const long long bx = u0[0] + (long long)(cr - cy * ux), by = u0[1] + (long long)cy,
-                                bz = u0[2] + (long long)cz;
+            for (unsigned c0 = 0; c0 < (unsigned)total; c0 += 32) {
+                const unsigned c = c0 + lane;
+                long long bx = 0, by = 0, bz = 0;
                 unsigned long long pos = 0;
-                if (fb.w && fb.test(bx, by, bz, pos)) continue;  // the common case: one cached load
-                refine_union_block(S, bx, by, bz, pos, g, dil, lk, flags, fb);
+                int32_t id = -1;
+                if (c < (unsigned)total) {
+                    const unsigned cz = c / uxy, cr = c - cz * uxy, cy = cr / ux;
+                    bx = u0[0] + (long long)(cr - cy * ux);
+                    by = u0[1] + (long long)cy;
+                    bz = u0[2] + (long long)cz;
+                    if (!(fb.w && fb.test(bx, by, bz, pos))) {  // the common case: one cached load
+                        id = emb_lookup(lk, bx, by, bz);
+                        if (id >= 0 && flags[id]) id = -1;
+                    }
+                }
+                unsigned m = __ballot_sync(0xffffffffu, id >= 0);
+                while (m) {
+                    const int src = __ffs(m) - 1;
+                    m &= m - 1;
+                    const long long lx = __shfl_sync(0xffffffffu, bx, src) * g.W - dil,
+                                    ly = __shfl_sync(0xffffffffu, by, src) * g.W - dil,
+                                    lz = __shfl_sync(0xffffffffu, bz, src) * g.W - dil;
+                    const bool hit = wu_overlap(S, lane, lx, ly, lz, lx + g.W + 2 * dil, ly + g.W + 2 * dil,
+                                                lz + g.W + 2 * dil);
+                    if (__any_sync(0xffffffffu, hit) && lane == src) {
+                        flags[id] = 1;
+                        if (fb.w) fb.set(pos);
+                    }
+                }
             }
             continue;
         }
