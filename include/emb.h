@@ -53,9 +53,12 @@ typedef int32_t emb_status;
 #define EMB_ERR_NOT_WATERTIGHT (-2) /* an edge is not shared by exactly two oppositely oriented faces */
 #define EMB_ERR_CAPACITY (-3)       /* caller buffer too small; the required size was written */
 #define EMB_ERR_CUDA (-4)           /* a CUDA runtime call failed */
-#define EMB_ERR_TIMEOUT (-5)        /* a bounded device wait gave up */
+#define EMB_ERR_TIMEOUT (-5)        /* a bounded device wait gave up (reserved: no call of this
+                                       library waits on the device) */
 #define EMB_ERR_RANGE (-6)          /* the level is too fine for the integer frame */
 #define EMB_ERR_STATE (-7)          /* call order violated, or an internal invariant failed */
+#define EMB_ERR_BOUNDS (-8)         /* a library built with -DEMB_CHECK found an index out of
+                                       range (the access was skipped; device status only) */
 
 typedef struct emb_mesh_s *emb_mesh;
 typedef struct emb_forest_s *emb_forest;

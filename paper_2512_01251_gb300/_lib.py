@@ -9,7 +9,8 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "lib", "libemb.so")
+# EMB_LIBRARY=check selects the bounds-mode build (lib/libemb_check.so, see build.py)
+LIB_PATH = os.path.join(HERE, "lib", "libemb_check.so" if os.environ.get("EMB_LIBRARY") == "check" else "libemb.so")
 
 P = ctypes.c_void_p
 I32 = ctypes.c_int32

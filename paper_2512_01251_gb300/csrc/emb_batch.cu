@@ -365,6 +365,7 @@ static LinkMesh link_mesh(BMesh &B)
     M.o_tri = B.o_tri;
     M.g = level_geom(&B.geo, B.Lf);
     M.cap = (uint32_t)B.links;
+    M.nblk = fin.n;
     return M;
 }
 

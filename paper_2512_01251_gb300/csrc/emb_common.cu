@@ -95,6 +95,7 @@ extern "C" const char *emb_status_string(emb_status s)
     case EMB_ERR_TIMEOUT: return "EMB_ERR_TIMEOUT";
     case EMB_ERR_RANGE: return "EMB_ERR_RANGE";
     case EMB_ERR_STATE: return "EMB_ERR_STATE";
+    case EMB_ERR_BOUNDS: return "EMB_ERR_BOUNDS";
     default: return "EMB_ERR_UNKNOWN";
     }
 }

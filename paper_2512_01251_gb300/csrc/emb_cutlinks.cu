@@ -43,7 +43,7 @@ __device__ __forceinline__ uint64_t shift_axis(uint64_t cur, uint64_t nxt, int a
 // a fluid cell with a solid neighbour is within one link of the surface, and the
 // refine rule makes every block within that reach exist.
 __global__ void k_link_cand(const uint64_t *__restrict__ mask, const int32_t *__restrict__ nbr, int64_t n, int lattice,
-                            uint64_t *__restrict__ cand, uint32_t *__restrict__ blk_cnt)
+                            uint64_t *__restrict__ cand, uint32_t *__restrict__ blk_cnt, int *st)
 {
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= n) return;
@@ -54,7 +54,7 @@ __global__ void k_link_cand(const uint64_t *__restrict__ mask, const int32_t *__
         int cx, cy, cz;
         emb_dir(i, cx, cy, cz);
         const int32_t id = nbr[b * 26 + i - 1];
-        W[(cx + 1) + 3 * (cy + 1) + 9 * (cz + 1)] = id >= 0 ? mask[id] : 0ull;
+        W[(cx + 1) + 3 * (cy + 1) + 9 * (cz + 1)] = id >= 0 && emb_ck((uint64_t)id, (uint64_t)n, st) ? mask[id] : 0ull;
     }
     const uint64_t fluid = ~W[13];
     uint32_t count = 0;
@@ -112,8 +112,9 @@ __global__ void k_link_cand(const uint64_t *__restrict__ mask, const int32_t *__
 // sends its cell through an exact per-cell scan of the whole bin instead.
 // Sizes: 4 warps per CTA; a warp's tile of 32 triangles, 20 hit slots per cell and the
 // byte-wide best-hit indices take 9 KB of shared memory, so six CTAs fit on an SM (with
-// 80 registers a thread).  Fewer hit slots let more CTAs fit but send many more cells of
-// a D3Q27 workload through the per-cell rescan, which costs far more than it saves.
+// 80 registers a thread; five CTAs with 96 registers measured 12 % slower in the bench
+// step).  Fewer hit slots let more CTAs fit but send many more cells of a D3Q27 workload
+// through the per-cell rescan, which costs far more than it saves.
 #define LE_WARPS 4
 #define LE_TILE 32
 #define LE_BCAP 20
@@ -561,6 +562,7 @@ __global__ void __launch_bounds__(LE_WARPS * 32, LE_MINB) k_link_emit(const __gr
         const uint2 E = local < s_ext[mj] ? M.extra[local] : M.witem[local - s_ext[mj]];
         if (E.x == EMB_BIG_NONE) continue;
         const int64_t b = E.x;
+        if (!emb_ck((uint64_t)b, (uint64_t)M.nblk, st)) continue;
         const uint32_t base = M.blk_off[b];
         // candidate directions of cells lane and 32 + lane: lane d < 26 holds direction
         // word d + 1; a 32 x 32 bit transpose of the low and of the high halves gives
@@ -712,6 +714,7 @@ __global__ void __launch_bounds__(LE_WARPS * 32, LE_MINB) k_link_emit(const __gr
                             emb_dir(d, cx, cy, cz);
                             const int tn = (int)bin_ent[e0 + (hv.x & 0xFFFFFFu)];
                             const int to = (int)bin_ent[e0 + (S.hit[prev][lane].x & 0xFFFFFFu)];
+                            if (!emb_ck((uint32_t)tn, M.T, st) || !emb_ck((uint32_t)to, M.T, st)) continue;
                             i128 Nn, No;
                             long long Mn, Mo;
                             tri_NM(rec, tn, px, py, pz, cx, cy, cz, Nn, Mn);
@@ -796,7 +799,8 @@ emb_status emb_enq_link_prep(const EmbLevel &lv, int lattice, uint64_t *cand, ui
     EMB_CUDA_TRY(cudaMemsetAsync(cnt, 0, (lv.n + 1) * sizeof(uint32_t), s));
     EMB_CUDA_TRY(cudaMemsetAsync(flag, 0, (lv.n + 1) * sizeof(uint32_t), s));
     if (lv.n > 0) {
-        EMB_LAUNCH((k_link_cand), emb_grid(lv.n, 128), 128, 0, s)(lv.mask, lv.nbr, lv.n, lattice, cand, cnt);
+        EMB_LAUNCH((k_link_cand), emb_grid(lv.n, 128), 128, 0, s)(lv.mask, lv.nbr, lv.n, lattice, cand, cnt,
+                                                                  emb_status_word());
         EMB_LAUNCH((k_nonempty), emb_grid(lv.n, 256), 256, 0, s)(cnt, lv.n, flag);
     }
     emb_status rc = emb_scan_into_expect(flag, work_n, lv.n, tmp, expect_work, s);
@@ -998,6 +1002,7 @@ extern "C" emb_status emb_cutlinks(emb_forest f, emb_bins b, int32_t lattice, in
     M.o_tri = d_tri;
     M.g = level_geom(f, f->max_level);
     M.cap = (uint32_t)(capacity < 0xFFFFFFFFll ? capacity : 0xFFFFFFFFll);
+    M.nblk = lv.n;
     // parts of heavy blocks
     const int64_t xcap = emb_link_extra_capacity(lv.n);
     char *sp = nullptr;

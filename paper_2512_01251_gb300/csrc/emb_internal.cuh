@@ -53,6 +53,22 @@ __device__ __forceinline__ void emb_set_status(int *st, int code)
     atomicCAS(st, 0, code);
 }
 
+// Bounds mode.  A library built with -DEMB_CHECK checks each index that a kernel
+// derives from data (block ids from the level index or the neighbour table, work-item
+// blocks, bin triangle ids) before it is used: one out of range records
+// EMB_ERR_BOUNDS in the device status word and the access is skipped, so a bad index
+// shows up as a status instead of a fault.  The default build compiles the checks out.
+#ifdef EMB_CHECK
+__device__ __forceinline__ bool emb_ck(uint64_t i, uint64_t n, int *st)
+{
+    if (i < n) return true;
+    if (st) emb_set_status(st, EMB_ERR_BOUNDS);
+    return false;
+}
+#else
+__device__ __forceinline__ bool emb_ck(uint64_t, uint64_t, int *) { return true; }
+#endif
+
 // ---------------------------------------------------------------------------
 // handles
 // ---------------------------------------------------------------------------
@@ -90,6 +106,8 @@ struct EmbLookup {
     const uint64_t *bits;
     const uint32_t *wpre;
     int64_t nb;
+    int64_t n;  // blocks of the level (ids below n)
+    int *st;    // device status word (bounds mode)
 };
 
 static inline EmbLookup emb_lookup_of(const EmbLevel &lv)
@@ -101,6 +119,8 @@ static inline EmbLookup emb_lookup_of(const EmbLevel &lv)
     l.bits = lv.bits;
     l.wpre = lv.wpre;
     l.nb = lv.nb_axis;
+    l.n = lv.n;
+    l.st = emb_status_word();
     return l;
 }
 
@@ -232,6 +252,7 @@ struct LinkMesh {
     int32_t *o_tri;
     LevelGeom g;
     uint32_t cap;              // capacity of the output table
+    int64_t nblk;              // finest blocks (bounds mode)
 };
 struct LinkTable {
     int n;
@@ -289,14 +310,19 @@ __device__ __forceinline__ int32_t emb_hash_find(const uint64_t *__restrict__ hk
 // Block id at (bx, by, bz) of a level, or -1 (coordinates must lie in [0, nb)).
 __device__ __forceinline__ int32_t emb_lookup(const EmbLookup &l, int64_t bx, int64_t by, int64_t bz)
 {
+    int32_t id;
     if (l.bits) {
         const int64_t lin = (bz * l.nb + by) * l.nb + bx;
+        if (!emb_ck((uint64_t)lin, (uint64_t)l.nb * l.nb * l.nb, l.st)) return -1;
         const uint64_t w = __ldg(l.bits + (lin >> 6));
         const int sh = (int)(lin & 63);
         if (!((w >> sh) & 1ull)) return -1;
-        return (int32_t)(__ldg(l.wpre + (lin >> 6)) + __popcll(w & ((1ull << sh) - 1ull)));
+        id = (int32_t)(__ldg(l.wpre + (lin >> 6)) + __popcll(w & ((1ull << sh) - 1ull)));
+    } else {
+        id = emb_hash_find(l.hkey, l.hval, l.hcap, emb_key(bx, by, bz));
     }
-    return emb_hash_find(l.hkey, l.hval, l.hcap, emb_key(bx, by, bz));
+    if (id >= 0 && !emb_ck((uint64_t)id, (uint64_t)l.n, l.st)) return -1;
+    return id;
 }
 
 // First index in the ascending a[0, n) whose value is not below v.

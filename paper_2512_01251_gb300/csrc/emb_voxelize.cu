@@ -114,6 +114,7 @@ __device__ __forceinline__ void vox_line(const VoxTri &V, const LevelGeom &g, co
             if (sgn_i128(Dq) == sx) bits |= 1ull << q;
         }
         const int line = (int)((j & 3) + 4 * (k & 3));
+        if (!emb_ck((uint64_t)id, (uint64_t)acc.n, st)) return;
         if (bits) atomicXor(s_acc + id, bits << (4 * line));
         atomicXor(p_acc + id, 1u << line);
         return;

@@ -23,6 +23,7 @@ EMB_ERR_CUDA = -4
 EMB_ERR_TIMEOUT = -5
 EMB_ERR_RANGE = -6
 EMB_ERR_STATE = -7
+EMB_ERR_BOUNDS = -8
 
 
 class EmbError(RuntimeError):
