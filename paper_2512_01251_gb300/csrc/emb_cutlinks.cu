@@ -385,7 +385,7 @@ __device__ __forceinline__ bool pair_narrow(const TriT &T, long long px, long lo
 }
 
 __device__ __forceinline__ void pair_lines(const TriT &T, long long px, long long py, long long pz, uint32_t ccm,
-                                           uint32_t &hd, uint32_t &dd)
+                                           uint32_t uni, uint32_t &hd, uint32_t &dd)
 {
     uint32_t line = 0, degen = 0;
     if (pair_narrow(T, px, py, pz)) {
@@ -422,8 +422,12 @@ __device__ __forceinline__ void pair_lines(const TriT &T, long long px, long lon
             line |= (ok & (zero ^ 1u) & same) << d;
         }
     } else {
-        // coordinates are below 2^25, so offsets fit 32 bits: moments (below 2^51)
-        // and their signed sums in 64 bits from widening products
+        // Coordinates are below 2^25, so offsets fit 32 bits; the moments come from
+        // widening products (below 2^53) and V_k = c . m_k stays below 3 * 2^53 < 2^55.
+        // The 13 lines are tested branch-free as in the 32-bit path (the lanes hold
+        // different cells), skipping only the lines no cell of the warp's chunk needs
+        // (uni, warp-uniform; a D3Q19 table needs no corner line).  This path carries
+        // the frames whose cell is 2^14 units or more (odd roots, coarse levels).
         const int ax = (int)(T.ax - px), ay = (int)(T.ay - py), az = (int)(T.az - pz);
         const int bx = (int)(T.bx - px), by = (int)(T.by - py), bz = (int)(T.bz - pz);
         const int qx = (int)(T.cx - px), qy = (int)(T.cy - py), qz = (int)(T.cz - pz);
@@ -436,23 +440,20 @@ __device__ __forceinline__ void pair_lines(const TriT &T, long long px, long lon
         const long long m3x = (long long)qy * az - (long long)qz * ay,
                         m3y = (long long)qz * ax - (long long)qx * az,
                         m3z = (long long)qx * ay - (long long)qy * ax;
-        const long long nx = m1x + m2x + m3x, ny = m1y + m2y + m3y, nz = m1z + m2z + m3z;
 #pragma unroll
         for (int r = 0; r < 13; ++r) {
             const int d = 2 * r + 1;
-            if (!(ccm & (3u << d))) continue;
+            if (!((uni >> d) & 3u)) continue;
             int cx, cy, cz;
             emb_dir(d, cx, cy, cz);
-            const long long NC = cx * nx + cy * ny + cz * nz;
             const long long V1 = cx * m1x + cy * m1y + cz * m1z;
             const long long V2 = cx * m2x + cy * m2y + cz * m2z;
             const long long V3 = cx * m3x + cy * m3y + cz * m3z;
-            if (NC == 0) continue;
-            if (V1 == 0 || V2 == 0 || V3 == 0) {
-                degen |= 1u << d;
-                continue;
-            }
-            if (((V1 ^ NC) | (V2 ^ NC) | (V3 ^ NC)) >= 0) line |= 1u << d;
+            const uint32_t ok = ((ccm >> d) & 3u) != 0u;
+            const uint32_t zero = (V1 == 0) | (V2 == 0) | (V3 == 0);
+            const uint32_t same = ((V1 ^ V2) | (V1 ^ V3)) >= 0;
+            degen |= (ok & zero) << d;
+            line |= (ok & (zero ^ 1u) & same) << d;
         }
     }
     // members of line-hit pairs that are candidates
@@ -517,10 +518,10 @@ __device__ __forceinline__ void pair_segments(const TriT &T, long long px, long 
 // All crossings of one pair on the candidate directions ccm (both halves in one call).
 template <class Emit>
 __device__ __forceinline__ void link_pair(const TriT &T, long long px, long long py, long long pz, uint32_t ccm,
-                                          long long h, Emit emit)
+                                          uint32_t uni, long long h, Emit emit)
 {
     uint32_t hd, dd;
-    pair_lines(T, px, py, pz, ccm, hd, dd);
+    pair_lines(T, px, py, pz, ccm, uni, hd, dd);
     pair_segments(T, px, py, pz, hd, dd, h, emit);
 }
 
@@ -616,6 +617,8 @@ __global__ void __launch_bounds__(LE_WARPS * 32, LE_MINB) k_link_emit(const __gr
             const uint32_t off = t < 32 ? ex_lo : ex_hi;
             S.cm[lane] = cm;
             S.hcnt[lane] = 0;
+            // the directions some cell of the chunk needs
+            const uint32_t cmu = __reduce_or_sync(0xffffffffu, cm);
             __syncwarp();
             for (uint32_t e = e0; e < e1; e += LE_TILE) {
                 // stage triangle `lane` of this tile and the chunk cells its reach box touches
@@ -688,7 +691,7 @@ __global__ void __launch_bounds__(LE_WARPS * 32, LE_MINB) k_link_emit(const __gr
                                     pz = Z0 + (2 * (cell >> 4) + 1) * half;
                     const uint32_t ccm = S.cm[slot];
                     const uint32_t local = e - e0 + (uint32_t)ti;
-                    link_pair(T, px, py, pz, ccm, h, [&](int d, float q) {
+                    link_pair(T, px, py, pz, ccm, cmu, h, [&](int d, float q) {
                         const int kk = atomicAdd(&S.hcnt[slot], 1);
                         if (kk < LE_BCAP) S.hit[kk][slot] = make_uint2(local | ((uint32_t)d << 24), __float_as_uint(q));
                     });
@@ -1096,7 +1099,7 @@ __global__ void k_probe(int kind, const long long *__restrict__ in, int64_t n, i
             T.nx = uy * vz - uz * vy;
             T.ny = uz * vx - ux * vz;
             T.nz = ux * vy - uy * vx;
-            link_pair(T, px, py, pz, 1u << d, h, [&](int dd, float qq) {
+            link_pair(T, px, py, pz, 1u << d, 1u << d, h, [&](int dd, float qq) {
                 if (dd == d) {
                     h_ = 1;
                     q_ = qq;
