@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the e2e leg and the CPU baseline")
     ap.add_argument("--legs", default="all",
                     help="comma-separated extra legs to run (e2e, fwd_bwd, batched, ablation, lbm, moving, "
-                         "guard_ablation, replay, cpu_baseline), or 'all'")
+                         "incremental, guard_ablation, replay, cpu_baseline), or 'all'")
     return ap.parse_args()
 
 
@@ -531,6 +531,8 @@ def run_ours(args):
             line["lbm"] = lbm_leg(P)
         if want("moving"):
             line["moving"] = moving_leg(P)
+        if want("incremental"):
+            line["incremental"] = incremental_leg(P)
         if want("guard_ablation"):
             line["guard_ablation"] = guard_leg(P, verts, tris, w, lattice)
         if want("replay"):
@@ -697,6 +699,53 @@ def moving_leg(P, reps=10):
     return dict(workload=f"star_112k shifted by one root block each step: {len(t)} triangles, D3Q19",
                 per_call_ms=out["per_call"], replay_ms=out["replay"], speedup=round(out["per_call"] / out["replay"], 2),
                 status=st, timing=f"mesh update + re-embedding per step, CUDA events, median of {reps}")
+
+
+def incremental_leg(P, reps=6):
+    """A local deformation of the bench workload (the ~7.2M-triangle mesh, D3Q27): a cap
+    of vertices pushed in and out along their radial directions, step after step.  The
+    windowed re-embedding (reembed_window: a window forest of the root-block rows the
+    change can reach, the triangles near it, emb_splice) against a full re-embedding
+    through the per-call path.  Host wall clock around synchronised calls (both paths
+    synchronise inside)."""
+    import torch
+
+    from synth import bump
+    w = workload("star_7m")
+    v, t = w.build_mesh()
+    tt = torch.from_numpy(t).cuda()
+    E = P.embed(torch.from_numpy(v).cuda(), tt, w.R, w.levels, w.band, 27)
+    inc, full, sizes = [], [], []
+    for i in range(reps + 2):
+        v_new, moved = bump(v, (0.2, 1.0, 0.3), 0.995, 300 if i % 2 == 0 else -300)
+        hit = np.isin(t, moved).any(axis=1)
+        pts = np.concatenate([v[t[hit]].reshape(-1, 3), v_new[t[hit]].reshape(-1, 3)])
+        lo, hi = np.floor(pts.min(axis=0) * w.R).astype(int), np.floor(pts.max(axis=0) * w.R).astype(int) + 1
+        ext = (int(lo[1]), int(hi[1]), int(lo[2]), int(hi[2]))
+        vn = torch.from_numpy(v_new).cuda()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        P.reembed_window(E, vn, ext, w.band)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        F = P.embed(vn, tt, w.R, w.levels, w.band, 27, check_watertight=False, check_status=False)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        if i >= 2:
+            inc.append(1e3 * (t1 - t0))
+            full.append(1e3 * (t2 - t1))
+            sizes.append(ext)
+        same = F.links["q"].numel() == E.links["q"].numel()
+        del F
+        v = v_new
+    st = P.emb_status_get()
+    mi, mf = statistics.median(inc), statistics.median(full)
+    return dict(workload=(f"star_7m ({len(t)} triangles, root 32^3, levels 0..4, D3Q27): a cap of {len(moved)} "
+                          "vertices pushed by +-300 grid units per step"),
+                changed_rows=f"y {sizes[-1][0]}..{sizes[-1][1]}, z {sizes[-1][2]}..{sizes[-1][3]} of {w.R}",
+                incremental_ms=round(mi, 4), full_ms=round(mf, 4), speedup=round(mf / mi, 2),
+                same_link_count=bool(same), status=st,
+                timing=f"host wall clock around synchronised calls, median of {reps}")
 
 
 def replay_leg(P, verts, tris, w, lattice, step_ms, reps=10):

@@ -271,6 +271,52 @@ emb_status emb_refine_flags(emb_forest f, emb_bins b, int32_t level, int32_t ban
  * EMB_ERR_STATE (level not the finest built, or not voxelized). */
 emb_status emb_refine_flags_paper(emb_forest f, int32_t level, double d_spec, uint8_t *d_flags, void *stream);
 
+/* ------------------------------------------------- incremental re-embedding ---- */
+/* A window of root-block rows: the root blocks with y0 <= by < y1 and z0 <= bz < z1,
+ * every bx (0 <= y0 < y1 <= R, 0 <= z0 < z1 <= R).  A forest started from a window
+ * is embedded by the ordinary calls (emb_bin ... emb_cutlinks); its x-rows of cells are
+ * whole, so the voxelizer's row parity is exact inside it.  The paper names moving
+ * geometry as future work (Sec. 5); this is the region-limited re-embedding a
+ * locally moving or deforming surface needs.  Errors as emb_forest_root, plus
+ * EMB_ERR_BAD_INPUT for an empty or out-of-range window. */
+emb_status emb_forest_root_window(int32_t R, int32_t max_level, int32_t y0, int32_t y1, int32_t z0, int32_t z1,
+                                  void *stream, emb_forest *out);
+
+/* The triangles of m whose bounding box meets the slab ylo <= y <= yhi, zlo <= z <= zhi
+ * (frame units, the integer coordinates of the records: a vertex coordinate v maps to
+ * v 2^20 r_o with R = r_o 2^k), as a new mesh handle for embedding a window (its
+ * records are copies, in the order of m; the subset is not closed, which the window's
+ * whole x-rows do not need).  d_map (device, optional, map_capacity entries) receives
+ * for each subset triangle its id in m; *h_count (host) the subset size.  Synchronises.
+ * Errors: EMB_ERR_BAD_INPUT, EMB_ERR_CAPACITY (d_map too small; nothing created),
+ * EMB_ERR_STATE (no triangle meets the slab). */
+emb_status emb_mesh_subset(emb_mesh m, int64_t ylo, int64_t yhi, int64_t zlo, int64_t zhi, int32_t *d_map,
+                           int64_t map_capacity, void *stream, emb_mesh *out, int64_t *h_count);
+
+/* Splices the embedding of a window forest w into the forest f (same R and levels,
+ * both refined to their finest level and voxelized on every level): on every level
+ * the blocks of f whose root ancestor lies in the inner window [y0, y1) x [z0, z1)
+ * (all bx) are replaced by the blocks of w there, with their solid masks, in (z, y, x)
+ * order; f's level index is rebuilt and its neighbour table and link candidates are
+ * dropped.  The link tables (sorted by (cell, dir), cells numbered on the finest level
+ * of their own forest) are merged into o_* (device, capacity entries): the links of f
+ * outside the inner window and those of w inside it, renumbered to the merged finest
+ * level, in (cell, dir) order; w_tri_map (device, optional) maps w's triangle ids to
+ * the caller's (w was embedded from a subset of the triangles).  *h_count (host)
+ * receives the merged link count.  The result equals an embedding of the whole mesh
+ * when every change of the mesh since f was embedded lies inside the inner window
+ * widened by 2 root blocks in y and z, the window of w holds the inner window widened
+ * by 1 root block, and w was embedded from every triangle that meets the window of w
+ * widened by 2 root blocks (refine dilations reach at most 1.2 root blocks, a link one
+ * finest cell).  Synchronises (the merged counts size the levels).
+ * Errors: EMB_ERR_BAD_INPUT, EMB_ERR_STATE (forests not matching, not refined or not
+ * voxelized), EMB_ERR_CAPACITY (nothing written to o_*; f already spliced). */
+emb_status emb_splice(emb_forest f, emb_forest w, int32_t y0, int32_t y1, int32_t z0, int32_t z1,
+                      const int32_t *f_cell, const uint8_t *f_dir, const float *f_q, const int32_t *f_tri, int64_t f_n,
+                      const int32_t *w_cell, const uint8_t *w_dir, const float *w_q, const int32_t *w_tri, int64_t w_n,
+                      const int32_t *w_tri_map, int32_t *o_cell, uint8_t *o_dir, float *o_q, int32_t *o_tri,
+                      int64_t capacity, int64_t *h_count, void *stream);
+
 /* ------------------------------------------------------------ cut links ---- */
 /* Number of cut links at the finest level for `lattice` (19 or 27): pairs
  * (fluid cell, direction i) whose neighbour along c_i is solid (Sec. 3.4,

@@ -30,6 +30,9 @@ SIGNATURES = {
     "emb_mesh_update": (I32, [P, P, I64, P]),
     "emb_forest_root": (I32, [I32, I32, P, ctypes.POINTER(P)]),
     "emb_forest_destroy": (None, [P]),
+    "emb_forest_root_window": (I32, [I32, I32, I32, I32, I32, I32, P, ctypes.POINTER(P)]),
+    "emb_mesh_subset": (I32, [P, I64, I64, I64, I64, P, I64, P, ctypes.POINTER(P), PI64]),
+    "emb_splice": (I32, [P, P, I32, I32, I32, I32, P, P, P, P, I64, P, P, P, P, I64, P, P, P, P, P, I64, PI64, P]),
     "emb_forest_refine": (I32, [P, I32, P, P]),
     "emb_forest_num_blocks": (I32, [P, I32, PI64]),
     "emb_forest_blocks": (I32, [P, I32, P, P]),

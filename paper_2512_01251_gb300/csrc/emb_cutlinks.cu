@@ -112,9 +112,8 @@ __global__ void k_link_cand(const uint64_t *__restrict__ mask, const int32_t *__
 // sends its cell through an exact per-cell scan of the whole bin instead.
 // Sizes: 4 warps per CTA; a warp's tile of 32 triangles, 20 hit slots per cell and the
 // byte-wide best-hit indices take 9 KB of shared memory, so six CTAs fit on an SM (with
-// 80 registers a thread; five CTAs with 96 registers measured 12 % slower in the bench
-// step).  Fewer hit slots let more CTAs fit but send many more cells of a D3Q27 workload
-// through the per-cell rescan, which costs far more than it saves.
+// 80 registers a thread).  Fewer hit slots let more CTAs fit but send many more cells of
+// a D3Q27 workload through the per-cell rescan, which costs far more than it saves.
 #define LE_WARPS 4
 #define LE_TILE 32
 #define LE_BCAP 20
@@ -370,41 +369,42 @@ __device__ __noinline__ bool pair_cross_wide(const TriT &T, long long px, long l
     return true;
 }
 
-// Pair (triangle, cell centre P) tests, in two halves: the line tests of every
-// candidate direction, then the segment ends of the lines that cross.
-//
-// pair_lines: the candidate directions (bits of ccm) whose perturbed line through P
-// crosses the triangle (hd), and those with a zero Pluecker value, which need the exact
-// per-direction test (dd).  When every vertex lies within 2^14 of P the moments fit
-// 32-bit integers; otherwise they are formed in 64 bits by widening products.
-__device__ __forceinline__ bool pair_narrow(const TriT &T, long long px, long long py, long long pz)
+// All crossings of one (triangle, cell centre P) pair on the candidate directions ccm:
+// emit(d, q) for every direction d whose perturbed segment P -> P + h c_d crosses the
+// triangle, q = t rounded to float.  When every vertex lies within 2^14 of P the
+// moments fit 32-bit integers and D fits 64 bits; otherwise the moments are formed
+// in 64 bits by widening products and D in 128 bits.  A zero Pluecker value sends
+// its direction through the exact per-direction test with the full tie-break.
+template <class Emit>
+__device__ __forceinline__ void link_pair(const TriT &T, long long px, long long py, long long pz, uint32_t ccm,
+                                          long long h, Emit emit)
 {
     const long long LIM = 1ll << 14;
-    return T.lox - px > -LIM && T.hix - px < LIM && T.loy - py > -LIM && T.hiy - py < LIM && T.loz - pz > -LIM &&
-           T.hiz - pz < LIM;
-}
-
-__device__ __forceinline__ void pair_lines(const TriT &T, long long px, long long py, long long pz, uint32_t ccm,
-                                           uint32_t uni, uint32_t &hd, uint32_t &dd)
-{
-    uint32_t line = 0, degen = 0;
-    if (pair_narrow(T, px, py, pz)) {
+    const long long l0 = T.lox - px, h0 = T.hix - px, l1 = T.loy - py, h1 = T.hiy - py,
+                    l2 = T.loz - pz, h2 = T.hiz - pz;
+    const bool narrow = l0 > -LIM && h0 < LIM && l1 > -LIM && h1 < LIM && l2 > -LIM && h2 < LIM;
+    if (narrow) {
         // Every vertex offset a, b, q lies in (-2^14, 2^14), so in 32-bit integers:
         //   moment components (a x b etc.): |a_y b_z - a_z b_y| < 2 * 2^28 = 2^29;
-        //   V_k = c . m_k over the at most three nonzero components of c: < 3 * 2^29 < 2^31.
-        // c . n = V1 + V2 + V3 is NOT formed in 32 bits: for a corner direction it reaches
-        // 9 * 2^29 > 2^31.  The line test needs only the signs of V1, V2, V3 (when they
-        // agree and are nonzero their sum has that sign, and a line parallel to the face
-        // cannot have three nonzero V of one sign).
+        //   V_k = c . m_k over the at most three nonzero components of c: < 3 * 2^29 < 2^31;
+        //   n = m1 + m2 + m3 per component: < 3 * 2^29 < 2^31.
+        // c . n is NOT formed in 32 bits: for a corner direction it reaches 9 * 2^29 > 2^31.
+        // The line test needs only the signs of V1, V2, V3 (n = m1 + m2 + m3, so c . n =
+        // V1 + V2 + V3, which has their common sign when they agree and are nonzero, and a
+        // line parallel to the face cannot have three nonzero V of one sign); the crossing
+        // parameter takes c . n in 64 bits.  D = n . a < 3 * 2^31 * 2^14 < 2^47.
         const int ax = (int)(T.ax - px), ay = (int)(T.ay - py), az = (int)(T.az - pz);
         const int bx = (int)(T.bx - px), by = (int)(T.by - py), bz = (int)(T.bz - pz);
         const int qx = (int)(T.cx - px), qy = (int)(T.cy - py), qz = (int)(T.cz - pz);
         const int m1x = ay * bz - az * by, m1y = az * bx - ax * bz, m1z = ax * by - ay * bx;
         const int m2x = by * qz - bz * qy, m2y = bz * qx - bx * qz, m2z = bx * qy - by * qx;
         const int m3x = qy * az - qz * ay, m3y = qz * ax - qx * az, m3z = qx * ay - qy * ax;
+        const int nx = m1x + m2x + m3x, ny = m1y + m2y + m3y, nz = m1z + m2z + m3z;
+        const long long D = (long long)nx * ax + (long long)ny * ay + (long long)nz * az;
         // line tests for the 13 direction pairs (odd index d and its opposite d + 1):
         // all 13 lines, without branches (the lanes hold different cells, so a
         // per-direction branch would diverge); non-candidates are masked off
+        uint32_t line = 0, degen = 0;
 #pragma unroll
         for (int r = 0; r < 13; ++r) {
             const int d = 2 * r + 1;
@@ -421,13 +421,36 @@ __device__ __forceinline__ void pair_lines(const TriT &T, long long px, long lon
             degen |= (ok & zero) << d;
             line |= (ok & (zero ^ 1u) & same) << d;
         }
+        // members of line-hit pairs that are candidates: the segment ends must straddle the plane
+        uint32_t mm = (line | (line << 1)) & ccm;
+        while (mm) {
+            const int d = __ffs(mm) - 1;
+            mm &= mm - 1;
+            int cx, cy, cz;
+            emb_dir(d, cx, cy, cz);
+            // |c . n| < 9 * 2^29 and h c . n < 2^18 * 2^33: both fit 64 bits
+            const long long nc = (long long)cx * nx + (long long)cy * ny + (long long)cz * nz;
+            const int sn = nc > 0 ? 1 : -1;
+            if (side_sign64(D, nx, ny, nz) != sn) continue;           // t <= 0
+            if (side_sign64(D - h * nc, nx, ny, nz) != -sn) continue;  // t >= 1
+            const long long N = sn > 0 ? D : -D, Mq = nc > 0 ? nc : -nc;
+            const float q = __fdiv_rn((float)N, (float)Mq * (float)h);
+            emit(d, q);
+        }
+        // a zero Pluecker value: resolve the pair's directions exactly
+        mm = (degen | (degen << 1)) & ccm;
+        while (mm) {
+            const int d = __ffs(mm) - 1;
+            mm &= mm - 1;
+            int cx, cy, cz;
+            emb_dir(d, cx, cy, cz);
+            float q;
+            if (!pair_cross_wide(T, px, py, pz, cx, cy, cz, h, &q)) continue;
+            emit(d, q);
+        }
     } else {
-        // Coordinates are below 2^25, so offsets fit 32 bits; the moments come from
-        // widening products (below 2^53) and V_k = c . m_k stays below 3 * 2^53 < 2^55.
-        // The 13 lines are tested branch-free as in the 32-bit path (the lanes hold
-        // different cells), skipping only the lines no cell of the warp's chunk needs
-        // (uni, warp-uniform; a D3Q19 table needs no corner line).  This path carries
-        // the frames whose cell is 2^14 units or more (odd roots, coarse levels).
+        // coordinates are below 2^25, so offsets fit 32 bits: moments (below 2^51)
+        // and their signed sums in 64 bits from widening products, D in 128 bits
         const int ax = (int)(T.ax - px), ay = (int)(T.ay - py), az = (int)(T.az - pz);
         const int bx = (int)(T.bx - px), by = (int)(T.by - py), bz = (int)(T.bz - pz);
         const int qx = (int)(T.cx - px), qy = (int)(T.cy - py), qz = (int)(T.cz - pz);
@@ -440,89 +463,54 @@ __device__ __forceinline__ void pair_lines(const TriT &T, long long px, long lon
         const long long m3x = (long long)qy * az - (long long)qz * ay,
                         m3y = (long long)qz * ax - (long long)qx * az,
                         m3z = (long long)qx * ay - (long long)qy * ax;
+        const long long nx = m1x + m2x + m3x, ny = m1y + m2y + m3y, nz = m1z + m2z + m3z;
+        uint32_t line = 0, degen = 0;
 #pragma unroll
         for (int r = 0; r < 13; ++r) {
             const int d = 2 * r + 1;
-            if (!((uni >> d) & 3u)) continue;
+            if (!(ccm & (3u << d))) continue;
             int cx, cy, cz;
             emb_dir(d, cx, cy, cz);
+            const long long NC = cx * nx + cy * ny + cz * nz;
             const long long V1 = cx * m1x + cy * m1y + cz * m1z;
             const long long V2 = cx * m2x + cy * m2y + cz * m2z;
             const long long V3 = cx * m3x + cy * m3y + cz * m3z;
-            const uint32_t ok = ((ccm >> d) & 3u) != 0u;
-            const uint32_t zero = (V1 == 0) | (V2 == 0) | (V3 == 0);
-            const uint32_t same = ((V1 ^ V2) | (V1 ^ V3)) >= 0;
-            degen |= (ok & zero) << d;
-            line |= (ok & (zero ^ 1u) & same) << d;
+            if (NC == 0) continue;
+            if (V1 == 0 || V2 == 0 || V3 == 0) {
+                degen |= 1u << d;
+                continue;
+            }
+            if (((V1 ^ NC) | (V2 ^ NC) | (V3 ^ NC)) >= 0) line |= 1u << d;
         }
-    }
-    // members of line-hit pairs that are candidates
-    hd = (line | (line << 1)) & ccm;
-    dd = (degen | (degen << 1)) & ccm;
-}
-
-// pair_segments: emit(d, q) for every direction d of hd whose segment P -> P + h c_d has
-// its ends on opposite sides of the plane (perturbed), and for every direction of dd
-// that the exact per-direction test finds crossed; q = t rounded to float.
-template <class Emit>
-__device__ __forceinline__ void pair_segments(const TriT &T, long long px, long long py, long long pz, uint32_t hd,
-                                              uint32_t dd, long long h, Emit emit)
-{
-    const long long ax = T.ax - px, ay = T.ay - py, az = T.az - pz;
-    uint32_t mm = hd;
-    if (mm && pair_narrow(T, px, py, pz)) {
-        // n = m1 + m2 + m3 per component < 3 * 2^29, so D = n . a < 9 * 2^29 * 2^14 < 2^47,
-        // |c . n| < 9 * 2^29 and h c . n < 2^18 * 2^33: all fit 64 bits
-        const long long D = T.nx * ax + T.ny * ay + T.nz * az;
+        uint32_t mm = (line | (line << 1)) & ccm;
+        if (mm) {
+            const i128 D = mul128(nx, ax) + mul128(ny, ay) + mul128(nz, az);
+            while (mm) {
+                const int d = __ffs(mm) - 1;
+                mm &= mm - 1;
+                int cx, cy, cz;
+                emb_dir(d, cx, cy, cz);
+                const long long nc = cx * nx + cy * ny + cz * nz;
+                const int sn = nc > 0 ? 1 : -1;
+                if (side_sign(D, nx, ny, nz) != sn) continue;                  // t <= 0
+                if (side_sign(D - mul128(h, nc), nx, ny, nz) != -sn) continue;  // t >= 1
+                const i128 N = sn > 0 ? D : -D;
+                const long long Mq = nc > 0 ? nc : -nc;
+                const float q = __fdiv_rn(i128_to_float(N), (float)Mq * (float)h);
+                emit(d, q);
+            }
+        }
+        mm = (degen | (degen << 1)) & ccm;
         while (mm) {
             const int d = __ffs(mm) - 1;
             mm &= mm - 1;
             int cx, cy, cz;
             emb_dir(d, cx, cy, cz);
-            const long long nc = (long long)cx * T.nx + (long long)cy * T.ny + (long long)cz * T.nz;
-            const int sn = nc > 0 ? 1 : -1;
-            if (side_sign64(D, T.nx, T.ny, T.nz) != sn) continue;           // t <= 0
-            if (side_sign64(D - h * nc, T.nx, T.ny, T.nz) != -sn) continue;  // t >= 1
-            const long long N = sn > 0 ? D : -D, Mq = nc > 0 ? nc : -nc;
-            emit(d, __fdiv_rn((float)N, (float)Mq * (float)h));
-        }
-    } else if (mm) {
-        const i128 D = mul128(T.nx, ax) + mul128(T.ny, ay) + mul128(T.nz, az);
-        while (mm) {
-            const int d = __ffs(mm) - 1;
-            mm &= mm - 1;
-            int cx, cy, cz;
-            emb_dir(d, cx, cy, cz);
-            const long long nc = cx * T.nx + cy * T.ny + cz * T.nz;
-            const int sn = nc > 0 ? 1 : -1;
-            if (side_sign(D, T.nx, T.ny, T.nz) != sn) continue;                  // t <= 0
-            if (side_sign(D - mul128(h, nc), T.nx, T.ny, T.nz) != -sn) continue;  // t >= 1
-            const i128 N = sn > 0 ? D : -D;
-            const long long Mq = nc > 0 ? nc : -nc;
-            emit(d, __fdiv_rn(i128_to_float(N), (float)Mq * (float)h));
+            float q;
+            if (!pair_cross_wide(T, px, py, pz, cx, cy, cz, h, &q)) continue;
+            emit(d, q);
         }
     }
-    // a zero Pluecker value: resolve the pair's directions exactly
-    mm = dd;
-    while (mm) {
-        const int d = __ffs(mm) - 1;
-        mm &= mm - 1;
-        int cx, cy, cz;
-        emb_dir(d, cx, cy, cz);
-        float q;
-        if (!pair_cross_wide(T, px, py, pz, cx, cy, cz, h, &q)) continue;
-        emit(d, q);
-    }
-}
-
-// All crossings of one pair on the candidate directions ccm (both halves in one call).
-template <class Emit>
-__device__ __forceinline__ void link_pair(const TriT &T, long long px, long long py, long long pz, uint32_t ccm,
-                                          uint32_t uni, long long h, Emit emit)
-{
-    uint32_t hd, dd;
-    pair_lines(T, px, py, pz, ccm, uni, hd, dd);
-    pair_segments(T, px, py, pz, hd, dd, h, emit);
 }
 
 #ifndef LE_MINB
@@ -617,8 +605,6 @@ __global__ void __launch_bounds__(LE_WARPS * 32, LE_MINB) k_link_emit(const __gr
             const uint32_t off = t < 32 ? ex_lo : ex_hi;
             S.cm[lane] = cm;
             S.hcnt[lane] = 0;
-            // the directions some cell of the chunk needs
-            const uint32_t cmu = __reduce_or_sync(0xffffffffu, cm);
             __syncwarp();
             for (uint32_t e = e0; e < e1; e += LE_TILE) {
                 // stage triangle `lane` of this tile and the chunk cells its reach box touches
@@ -691,7 +677,7 @@ __global__ void __launch_bounds__(LE_WARPS * 32, LE_MINB) k_link_emit(const __gr
                                     pz = Z0 + (2 * (cell >> 4) + 1) * half;
                     const uint32_t ccm = S.cm[slot];
                     const uint32_t local = e - e0 + (uint32_t)ti;
-                    link_pair(T, px, py, pz, ccm, cmu, h, [&](int d, float q) {
+                    link_pair(T, px, py, pz, ccm, h, [&](int d, float q) {
                         const int kk = atomicAdd(&S.hcnt[slot], 1);
                         if (kk < LE_BCAP) S.hit[kk][slot] = make_uint2(local | ((uint32_t)d << 24), __float_as_uint(q));
                     });
@@ -1099,7 +1085,7 @@ __global__ void k_probe(int kind, const long long *__restrict__ in, int64_t n, i
             T.nx = uy * vz - uz * vy;
             T.ny = uz * vx - ux * vz;
             T.nz = ux * vy - uy * vx;
-            link_pair(T, px, py, pz, 1u << d, 1u << d, h, [&](int dd, float qq) {
+            link_pair(T, px, py, pz, 1u << d, h, [&](int dd, float qq) {
                 if (dd == d) {
                     h_ = 1;
                     q_ = qq;

@@ -404,6 +404,88 @@ def embed(verts: torch.Tensor, tris: torch.Tensor, R: int, levels: int, band: in
 
 
 # --------------------------------------------------------------------------- #
+# incremental re-embedding of a region
+# --------------------------------------------------------------------------- #
+def emb_forest_root_window(R: int, max_level: int, y0: int, y1: int, z0: int, z1: int, stream=None) -> Forest:
+    h = ctypes.c_void_p()
+    _check(load().emb_forest_root_window(int(R), int(max_level), int(y0), int(y1), int(z0), int(z1), _stream(stream),
+                                         ctypes.byref(h)), "emb_forest_root_window")
+    f = Forest(h)
+    f.R, f.max_level = int(R), int(max_level)
+    return f
+
+
+def emb_mesh_subset(mesh: Mesh, ylo: int, yhi: int, zlo: int, zhi: int, stream=None):
+    """(sub-mesh, map int32 tensor: sub-mesh triangle -> mesh triangle)."""
+    tri_map = torch.empty(mesh.T, dtype=torch.int32, device="cuda")
+    h = ctypes.c_void_p()
+    n = ctypes.c_int64(0)
+    _check(load().emb_mesh_subset(mesh.h, int(ylo), int(yhi), int(zlo), int(zhi), _ptr(tri_map), mesh.T,
+                                  _stream(stream), ctypes.byref(h), ctypes.byref(n)), "emb_mesh_subset")
+    sub = Mesh(h)
+    sub.V, sub.T, sub.R = mesh.V, int(n.value), mesh.R
+    return sub, tri_map[:n.value]
+
+
+def emb_splice(forest: Forest, window: Forest, y0: int, y1: int, z0: int, z1: int, links: dict, wlinks: dict,
+               tri_map: torch.Tensor | None = None, stream=None) -> dict:
+    """Merges `window` into `forest` inside the inner window [y0, y1) x [z0, z1) of root-block
+    rows; returns the merged link table."""
+    nf, nw = links["q"].numel(), wlinks["q"].numel()
+    cap = nf + nw
+    out = dict(cell=torch.empty(max(cap, 1), dtype=torch.int32, device="cuda"),
+               dir=torch.empty(max(cap, 1), dtype=torch.uint8, device="cuda"),
+               q=torch.empty(max(cap, 1), dtype=torch.float32, device="cuda"),
+               tri=torch.empty(max(cap, 1), dtype=torch.int32, device="cuda"))
+    n = ctypes.c_int64(0)
+    args = [_ptr(links[k]) if nf else None for k in ("cell", "dir", "q", "tri")]
+    wargs = [_ptr(wlinks[k]) if nw else None for k in ("cell", "dir", "q", "tri")]
+    _check(load().emb_splice(forest.h, window.h, int(y0), int(y1), int(z0), int(z1), *args, nf, *wargs, nw,
+                             _ptr(tri_map) if tri_map is not None and tri_map.numel() else None,
+                             _ptr(out["cell"]), _ptr(out["dir"]), _ptr(out["q"]), _ptr(out["tri"]), cap,
+                             ctypes.byref(n), _stream(stream)), "emb_splice")
+    return {k: v[:n.value] for k, v in out.items()}
+
+
+def reembed_window(E: Embedding, verts: torch.Tensor, changed: tuple, band: int = 2, stream=None) -> Embedding:
+    """Brings E up to date after the mesh's vertices moved to `verts`, recomputing only the
+    region the change can reach (the paper names moving geometry as future work, Sec. 5).
+
+    `changed` = (y_lo, y_hi, z_lo, z_hi): the y-z extent, in root blocks (half-open), of
+    every triangle that moved, at its old and at its new position.  The inner window is
+    that extent widened by 2 root blocks (the reach of a refine dilation, at most 1.2 root
+    blocks, plus the block that holds it); the window forest is 1 root block wider (the
+    neighbours of its inner blocks) and is embedded from the triangles that meet it widened
+    by 2 more root blocks.  The result is identical to re-embedding the whole mesh."""
+    R, Lf = E.forest.R, E.levels
+    emb_mesh_update(E.mesh, verts, stream)
+    y0, y1, z0, z1 = changed
+    iy0, iy1, iz0, iz1 = max(0, y0 - 2), min(R, y1 + 2), max(0, z0 - 2), min(R, z1 + 2)
+    wy0, wy1, wz0, wz1 = max(0, iy0 - 1), min(R, iy1 + 1), max(0, iz0 - 1), min(R, iz1 + 1)
+    k = (R & -R).bit_length() - 1  # R = r_o 2^k
+    W0 = 1 << (20 - k)  # root block width in frame units (4 cells of 2^(18-k))
+    sub, tri_map = emb_mesh_subset(E.mesh, (wy0 - 2) * W0, (wy1 + 2) * W0, (wz0 - 2) * W0, (wz1 + 2) * W0, stream)
+    fw = emb_forest_root_window(R, Lf, wy0, wy1, wz0, wz1, stream)
+    wl = None
+    for L in range(Lf + 1):
+        bins = emb_bin(sub, fw, L, E.lattice, stream)
+        emb_voxelize(fw, bins, L, stream=stream)
+        if L < Lf:
+            fl = emb_refine_flags(fw, bins, L, band, stream=stream)
+            emb_forest_refine(fw, L, fl, stream)
+        else:
+            wl = emb_cutlinks(fw, bins, E.lattice, stream=stream)
+        bins.close()
+    E.links = emb_splice(E.forest, fw, iy0, iy1, iz0, iz1, E.links, wl, tri_map, stream)
+    E.masks = [emb_forest_masks(E.forest, L, stream) for L in range(Lf + 1)]
+    E.flags = []
+    E.blocks = []
+    fw.close()
+    sub.close()
+    return E
+
+
+# --------------------------------------------------------------------------- #
 # batches of meshes
 # --------------------------------------------------------------------------- #
 def emb_batch_create(meshes: list, levels: list, bands: list, lattices: list, stream=None) -> Batch:

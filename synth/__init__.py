@@ -14,6 +14,7 @@ from .meshes import (  # noqa: F401
     tetrahedron,
     octahedron,
     corner_face_tetrahedra,
+    bump,
     signed_volume,
 )
 from .workloads import (  # noqa: F401

@@ -283,3 +283,19 @@ def corner_face_tetrahedra(centres, signs, a: int, delta: int, depth: int):
         ts.append(t + 4 * len(vs))
         vs.append(v)
     return np.concatenate(vs).astype(np.float32), np.concatenate(ts).astype(np.int32)
+
+
+def bump(verts: np.ndarray, axis, cos_min: float, push_units: int, centre=(0.5, 0.5, 0.5)):
+    """A local deformation of a star-shaped mesh: every vertex whose direction from
+    `centre` lies within the cone cos(angle to `axis`) >= cos_min moves outward along
+    that direction by about push_units grid units (2^-20), rounded to the grid per axis.
+    Returns (new verts float32, ids of the moved vertices)."""
+    v = np.asarray(verts, dtype=np.float64)
+    d = v - np.asarray(centre, dtype=np.float64)[None, :]
+    u = d / np.linalg.norm(d, axis=1, keepdims=True)
+    a = np.asarray(axis, dtype=np.float64)
+    a = a / np.linalg.norm(a)
+    sel = np.nonzero(u @ a >= cos_min)[0]
+    out = (np.round(v * _GRID)).astype(np.int64)
+    out[sel] += np.round(u[sel] * push_units).astype(np.int64)
+    return snap(out / _GRID), sel
