@@ -134,7 +134,10 @@ struct TriT {
 struct LeWarp {
     TriT tile[LE_TILE];
     uint2 hit[LE_BCAP][32];  // per slot: (bin-local index | direction << 24, q bits)
-    signed char best[27][32];  // per (direction, slot): index of the nearest hit during resolution
+    union {
+        signed char best[27][32];  // resolution: per (direction, slot) the index of the nearest hit
+        uint2 hq[32];              // tile passes: queued pairs (tile index | cell << 5 | slot << 11, line hits)
+    };
     int hcnt[32];
     uint32_t cm[32];         // candidate directions of each slot's cell
 };
@@ -346,6 +349,28 @@ __device__ __forceinline__ int side_sign64(long long X, long long nx, long long 
     return nz > 0 ? -1 : 1;
 }
 
+// Segment ends of a line hit of the narrow path (every vertex offset from P within
+// 2^14, so |n| < 3 * 2^29 per component): direction d's line is known to cross the
+// triangle, at t = D / (h c . n) with D = n . (A - P).  The link crosses iff t lies in
+// (0, 1) under the perturbation; then q = t rounded to float.  D < 3 * 2^31 * 2^14 and
+// h c . n < 2^18 * 9 * 2^29 fit 64 bits.
+__device__ __forceinline__ bool hit_segment(const TriT &T, long long px, long long py, long long pz, int d, long long h,
+                                            float *q)
+{
+    const int nx = (int)T.nx, ny = (int)T.ny, nz = (int)T.nz;
+    const long long D = (long long)nx * (int)(T.ax - px) + (long long)ny * (int)(T.ay - py) +
+                        (long long)nz * (int)(T.az - pz);
+    int cx, cy, cz;
+    emb_dir(d, cx, cy, cz);
+    const long long nc = (long long)cx * nx + (long long)cy * ny + (long long)cz * nz;
+    const int sn = nc > 0 ? 1 : -1;
+    if (side_sign64(D, nx, ny, nz) != sn) return false;           // t <= 0
+    if (side_sign64(D - h * nc, nx, ny, nz) != -sn) return false;  // t >= 1
+    const long long N = sn > 0 ? D : -D, Mq = nc > 0 ? nc : -nc;
+    *q = __fdiv_rn((float)N, (float)Mq * (float)h);
+    return true;
+}
+
 // Exact segment test for a pair whose vertices are not all within 2^14 of P
 // (128-bit plane offsets, 64-bit Pluecker products); returns t = N / (h M).
 __device__ __noinline__ bool pair_cross_wide(const TriT &T, long long px, long long py, long long pz, int cx, int cy,
@@ -375,10 +400,14 @@ __device__ __noinline__ bool pair_cross_wide(const TriT &T, long long px, long l
 // moments fit 32-bit integers and D fits 64 bits; otherwise the moments are formed
 // in 64 bits by widening products and D in 128 bits.  A zero Pluecker value sends
 // its direction through the exact per-direction test with the full tie-break.
-template <class Emit>
+// With DEFER the narrow path does not test the segment ends of its line hits: it
+// returns them in `deferred` (directions whose line crosses the triangle; the caller
+// finishes them with hit_segment), so that a warp can test them 32 at a time.
+template <bool DEFER, class Emit>
 __device__ __forceinline__ void link_pair(const TriT &T, long long px, long long py, long long pz, uint32_t ccm,
-                                          long long h, Emit emit)
+                                          long long h, Emit emit, uint32_t &deferred)
 {
+    deferred = 0;
     const long long LIM = 1ll << 14;
     const long long l0 = T.lox - px, h0 = T.hix - px, l1 = T.loy - py, h1 = T.hiy - py,
                     l2 = T.loz - pz, h2 = T.hiz - pz;
@@ -423,6 +452,10 @@ __device__ __forceinline__ void link_pair(const TriT &T, long long px, long long
         }
         // members of line-hit pairs that are candidates: the segment ends must straddle the plane
         uint32_t mm = (line | (line << 1)) & ccm;
+        if (DEFER) {
+            deferred = mm;
+            mm = 0;
+        }
         while (mm) {
             const int d = __ffs(mm) - 1;
             mm &= mm - 1;
@@ -657,6 +690,45 @@ __global__ void __launch_bounds__(LE_WARPS * 32, LE_MINB) k_link_emit(const __gr
                     if (lane >= o) incl += tt;
                 }
                 const int total = __shfl_sync(0xffffffffu, incl, 31);
+                // the segment-end tests of the narrow path's line hits, queued per pair in
+                // S.hq and run 32 hits at a time: lane g takes hit g of the queue
+                int qn = 0;
+                auto flush = [&]() {
+                    __syncwarp();
+                    const uint2 qe = lane < qn ? S.hq[lane] : make_uint2(0u, 0u);
+                    const int nq = __popc(qe.y);
+                    int qi = nq;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int tt = __shfl_up_sync(0xffffffffu, qi, o);
+                        if (lane >= o) qi += tt;
+                    }
+                    const int qt = __shfl_sync(0xffffffffu, qi, 31);
+                    for (int g0 = 0; g0 < qt; g0 += 32) {
+                        const int g = g0 + lane;
+                        int ei = 0;
+#pragma unroll
+                        for (int step = 16; step >= 1; step >>= 1) {
+                            const int v = __shfl_sync(0xffffffffu, qi, ei + step - 1);
+                            if (v <= g) ei += step;
+                        }
+                        ei = ei > 31 ? 31 : ei;
+                        const int qex = __shfl_sync(0xffffffffu, qi - nq, ei);
+                        const uint32_t qm = __shfl_sync(0xffffffffu, qe.y, ei), qx = __shfl_sync(0xffffffffu, qe.x, ei);
+                        if (g >= qt) continue;
+                        const int d = select64(qm, g - qex);
+                        const int ti = (int)(qx & 31u), cell = (int)((qx >> 5) & 63u), slot = (int)(qx >> 11);
+                        const long long px = X0 + (2 * (cell & 3) + 1) * half, py = Y0 + (2 * ((cell >> 2) & 3) + 1) * half,
+                                        pz = Z0 + (2 * (cell >> 4) + 1) * half;
+                        float q;
+                        if (!hit_segment(S.tile[ti], px, py, pz, d, h, &q)) continue;
+                        const int kk = atomicAdd(&S.hcnt[slot], 1);
+                        if (kk < LE_BCAP)
+                            S.hit[kk][slot] = make_uint2((e - e0 + (uint32_t)ti) | ((uint32_t)d << 24), __float_as_uint(q));
+                    }
+                    __syncwarp();
+                    qn = 0;
+                };
                 for (int s0 = 0; s0 < total; s0 += 32) {
                     const int gidx = s0 + lane;
                     int lo = 0;
@@ -669,35 +741,49 @@ __global__ void __launch_bounds__(LE_WARPS * 32, LE_MINB) k_link_emit(const __gr
                     const int excl_i = __shfl_sync(0xffffffffu, incl - np, ti);
                     const unsigned long long pmi = ((unsigned long long)__shfl_sync(0xffffffffu, (unsigned)(pm >> 32), ti) << 32) |
                                                    (unsigned long long)__shfl_sync(0xffffffffu, (unsigned)pm, ti);
-                    if (gidx >= total) continue;
-                    const int cell = select64(pmi, gidx - excl_i);
-                    const int slot = __popcll(cmask & ((1ull << cell) - 1ull));
-                    const TriT &T = S.tile[ti];
-                    const long long px = X0 + (2 * (cell & 3) + 1) * half, py = Y0 + (2 * ((cell >> 2) & 3) + 1) * half,
-                                    pz = Z0 + (2 * (cell >> 4) + 1) * half;
-                    const uint32_t ccm = S.cm[slot];
-                    const uint32_t local = e - e0 + (uint32_t)ti;
-                    link_pair(T, px, py, pz, ccm, h, [&](int d, float q) {
-                        const int kk = atomicAdd(&S.hcnt[slot], 1);
-                        if (kk < LE_BCAP) S.hit[kk][slot] = make_uint2(local | ((uint32_t)d << 24), __float_as_uint(q));
-                    });
+                    uint32_t dm = 0, qx = 0;
+                    if (gidx < total) {
+                        const int cell = select64(pmi, gidx - excl_i);
+                        const int slot = __popcll(cmask & ((1ull << cell) - 1ull));
+                        const TriT &T = S.tile[ti];
+                        const long long px = X0 + (2 * (cell & 3) + 1) * half,
+                                        py = Y0 + (2 * ((cell >> 2) & 3) + 1) * half, pz = Z0 + (2 * (cell >> 4) + 1) * half;
+                        const uint32_t ccm = S.cm[slot];
+                        const uint32_t local = e - e0 + (uint32_t)ti;
+                        link_pair<true>(
+                            T, px, py, pz, ccm, h,
+                            [&](int d, float q) {
+                                const int kk = atomicAdd(&S.hcnt[slot], 1);
+                                if (kk < LE_BCAP)
+                                    S.hit[kk][slot] = make_uint2(local | ((uint32_t)d << 24), __float_as_uint(q));
+                            },
+                            dm);
+                        qx = (uint32_t)ti | ((uint32_t)cell << 5) | ((uint32_t)slot << 11);
+                    }
+                    const unsigned qb = __ballot_sync(0xffffffffu, dm != 0);
+                    if (qn + __popc(qb) > 32) flush();
+                    if (dm) S.hq[qn + __popc(qb & ((1u << lane) - 1u))] = make_uint2(qx, dm);
+                    qn += __popc(qb);
                 }
+                if (qn) flush();  // before the next tile replaces S.tile
                 __syncwarp();
             }
             // resolve: the owner lane of each cell keeps, per direction, the nearest crossing
+            // (`got` marks the directions with a kept hit)
+            const int nh = active ? S.hcnt[lane] : 0;
+            uint32_t got = 0;
             if (active) {
                 const long long px = X0 + (2 * (t & 3) + 1) * half, py = Y0 + (2 * ((t >> 2) & 3) + 1) * half,
                                 pz = Z0 + (2 * (t >> 4) + 1) * half;
-                const int nh = S.hcnt[lane];
                 if (nh > LE_BCAP) {
                     emit_cell_slow(M, e0, e1, px, py, pz, h, cm, base + off, b * 64 + t, st);
                 } else {
-                    for (int d = 0; d < 27; ++d) S.best[d][lane] = -1;
                     for (int k = 0; k < nh; ++k) {
                         const uint2 hv = S.hit[k][lane];
-                        const int d = (int)(hv.x >> 24), prev = S.best[d][lane];
-                        bool better = prev < 0;
+                        const int d = (int)(hv.x >> 24);
+                        bool better = !((got >> d) & 1u);
                         if (!better) {
+                            const int prev = S.best[d][lane];
                             // several faces cross this link: compare t exactly
                             int cx, cy, cz;
                             emb_dir(d, cx, cy, cz);
@@ -711,35 +797,58 @@ __global__ void __launch_bounds__(LE_WARPS * 32, LE_MINB) k_link_emit(const __gr
                             const i128 l = Nn * (i128)Mo, rr = No * (i128)Mn;
                             better = l < rr || (l == rr && tn < to);
                         }
-                        if (better) S.best[d][lane] = k;
-                    }
-                    uint32_t mm = cm;
-                    uint32_t o = base + off;
-                    while (mm) {
-                        const int d = __ffs(mm) - 1;
-                        mm &= mm - 1;
-                        if (o >= M.cap) {
-                            emb_set_status(st, EMB_ERR_CAPACITY);
-                            ++o;
-                            continue;
+                        if (better) {
+                            S.best[d][lane] = (signed char)k;
+                            got |= 1u << d;
                         }
-                        int tr = -1;
-                        float q = -1.0f;
-                        const int k = S.best[d][lane];
-                        if (k >= 0) {
-                            const uint2 hv = S.hit[k][lane];
-                            tr = (int)bin_ent[e0 + (hv.x & 0xFFFFFFu)];
-                            q = __uint_as_float(hv.y);
-                        } else {
-                            emb_set_status(st, EMB_ERR_STATE);  // a fluid-to-solid link must cross the surface
-                        }
-                        M.o_cell[o] = (int32_t)(b * 64 + t);
-                        M.o_dir[o] = (uint8_t)d;
-                        M.o_q[o] = q;
-                        M.o_tri[o] = tr;
-                        ++o;
                     }
                 }
+            }
+            __syncwarp();
+            // write the chunk's links: they are consecutive in the table (slot s holds links
+            // off_s .. off_s + popc(cm_s) - 1 of the block), so the lanes take them in turn
+            // and the stores coalesce; a cell written by the overflow path above is skipped
+            const int nl = __popc(cm);
+            int lincl = nl;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int tt = __shfl_up_sync(0xffffffffu, lincl, o);
+                if (lane >= o) lincl += tt;
+            }
+            const int ltotal = __shfl_sync(0xffffffffu, lincl, 31);
+            const uint32_t o_first = base + __shfl_sync(0xffffffffu, off, 0);
+            for (int j0 = 0; j0 < ltotal; j0 += 32) {
+                const int j = j0 + lane;
+                int sl = 0;
+#pragma unroll
+                for (int step = 16; step >= 1; step >>= 1) {
+                    const int v = __shfl_sync(0xffffffffu, lincl, sl + step - 1);
+                    if (v <= j) sl += step;
+                }
+                sl = sl > 31 ? 31 : sl;
+                const int s_excl = __shfl_sync(0xffffffffu, lincl - nl, sl);
+                const uint32_t s_cm = __shfl_sync(0xffffffffu, cm, sl), s_got = __shfl_sync(0xffffffffu, got, sl);
+                const int s_nh = __shfl_sync(0xffffffffu, nh, sl), s_t = __shfl_sync(0xffffffffu, t, sl);
+                if (j >= ltotal || s_nh > LE_BCAP) continue;
+                const uint32_t o = o_first + (uint32_t)j;
+                if (o >= M.cap) {
+                    emb_set_status(st, EMB_ERR_CAPACITY);
+                    continue;
+                }
+                const int d = select64(s_cm, j - s_excl);
+                int tr = -1;
+                float q = -1.0f;
+                if ((s_got >> d) & 1u) {
+                    const uint2 hv = S.hit[S.best[d][sl]][sl];
+                    tr = (int)bin_ent[e0 + (hv.x & 0xFFFFFFu)];
+                    q = __uint_as_float(hv.y);
+                } else {
+                    emb_set_status(st, EMB_ERR_STATE);  // a fluid-to-solid link must cross the surface
+                }
+                M.o_cell[o] = (int32_t)(b * 64 + s_t);
+                M.o_dir[o] = (uint8_t)d;
+                M.o_q[o] = q;
+                M.o_tri[o] = tr;
             }
             __syncwarp();
         }
@@ -1085,12 +1194,21 @@ __global__ void k_probe(int kind, const long long *__restrict__ in, int64_t n, i
             T.nx = uy * vz - uz * vy;
             T.ny = uz * vx - ux * vz;
             T.nz = ux * vy - uy * vx;
-            link_pair(T, px, py, pz, 1u << d, h, [&](int dd, float qq) {
-                if (dd == d) {
-                    h_ = 1;
-                    q_ = qq;
-                }
-            });
+            uint32_t dm = 0;
+            link_pair<true>(
+                T, px, py, pz, 1u << d, h,
+                [&](int dd, float qq) {
+                    if (dd == d) {
+                        h_ = 1;
+                        q_ = qq;
+                    }
+                },
+                dm);
+            float qq;
+            if (((dm >> d) & 1u) && hit_segment(T, px, py, pz, d, h, &qq)) {
+                h_ = 1;
+                q_ = qq;
+            }
         }
     }
     hit[i] = h_;
