@@ -136,7 +136,7 @@ struct LeWarp {
     uint2 hit[LE_BCAP][32];  // per slot: (bin-local index | direction << 24, q bits)
     union {
         signed char best[27][32];  // resolution: per (direction, slot) the index of the nearest hit
-        uint2 hq[32];              // tile passes: queued pairs (tile index | cell << 5 | slot << 11, line hits)
+        uint2 hq[32];              // tile passes: queued pairs (tile index | cell << 5 | slot << 11 | wide << 16, line hits)
     };
     int hcnt[32];
     uint32_t cm[32];         // candidate directions of each slot's cell
@@ -371,6 +371,25 @@ __device__ __forceinline__ bool hit_segment(const TriT &T, long long px, long lo
     return true;
 }
 
+// The same for a line hit of the 64-bit path (coordinates below 2^25, so offsets fit 32
+// bits, |n| < 3 * 2^51 and c . n < 9 * 2^51): D = n . (A - P) in 128 bits.
+__device__ __noinline__ bool hit_segment_wide(const TriT &T, long long px, long long py, long long pz, int d,
+                                                 long long h, float *q)
+{
+    const long long nx = T.nx, ny = T.ny, nz = T.nz;
+    const i128 D = mul128(nx, (int)(T.ax - px)) + mul128(ny, (int)(T.ay - py)) + mul128(nz, (int)(T.az - pz));
+    int cx, cy, cz;
+    emb_dir(d, cx, cy, cz);
+    const long long nc = cx * nx + cy * ny + cz * nz;
+    const int sn = nc > 0 ? 1 : -1;
+    if (side_sign(D, nx, ny, nz) != sn) return false;                  // t <= 0
+    if (side_sign(D - mul128(h, nc), nx, ny, nz) != -sn) return false;  // t >= 1
+    const i128 N = sn > 0 ? D : -D;
+    const long long Mq = nc > 0 ? nc : -nc;
+    *q = __fdiv_rn(i128_to_float(N), (float)Mq * (float)h);
+    return true;
+}
+
 // Exact segment test for a pair whose vertices are not all within 2^14 of P
 // (128-bit plane offsets, 64-bit Pluecker products); returns t = N / (h M).
 __device__ __noinline__ bool pair_cross_wide(const TriT &T, long long px, long long py, long long pz, int cx, int cy,
@@ -400,14 +419,16 @@ __device__ __noinline__ bool pair_cross_wide(const TriT &T, long long px, long l
 // moments fit 32-bit integers and D fits 64 bits; otherwise the moments are formed
 // in 64 bits by widening products and D in 128 bits.  A zero Pluecker value sends
 // its direction through the exact per-direction test with the full tie-break.
-// With DEFER the narrow path does not test the segment ends of its line hits: it
-// returns them in `deferred` (directions whose line crosses the triangle; the caller
-// finishes them with hit_segment), so that a warp can test them 32 at a time.
+// With DEFER neither path tests the segment ends of its line hits: they come back in
+// `deferred` (directions whose line crosses the triangle), and `wide` says which path
+// found them; the caller finishes them with hit_segment or hit_segment_wide, so that a
+// warp can test them 32 at a time.
 template <bool DEFER, class Emit>
 __device__ __forceinline__ void link_pair(const TriT &T, long long px, long long py, long long pz, uint32_t ccm,
-                                          long long h, Emit emit, uint32_t &deferred)
+                                          long long h, Emit emit, uint32_t &deferred, bool &wide)
 {
     deferred = 0;
+    wide = false;
     const long long LIM = 1ll << 14;
     const long long l0 = T.lox - px, h0 = T.hix - px, l1 = T.loy - py, h1 = T.hiy - py,
                     l2 = T.loz - pz, h2 = T.hiz - pz;
@@ -516,6 +537,11 @@ __device__ __forceinline__ void link_pair(const TriT &T, long long px, long long
             if (((V1 ^ NC) | (V2 ^ NC) | (V3 ^ NC)) >= 0) line |= 1u << d;
         }
         uint32_t mm = (line | (line << 1)) & ccm;
+        if (DEFER) {
+            deferred = mm;
+            wide = true;
+            mm = 0;
+        }
         if (mm) {
             const i128 D = mul128(nx, ax) + mul128(ny, ay) + mul128(nz, az);
             while (mm) {
@@ -717,11 +743,13 @@ __global__ void __launch_bounds__(LE_WARPS * 32, LE_MINB) k_link_emit(const __gr
                         const uint32_t qm = __shfl_sync(0xffffffffu, qe.y, ei), qx = __shfl_sync(0xffffffffu, qe.x, ei);
                         if (g >= qt) continue;
                         const int d = select64(qm, g - qex);
-                        const int ti = (int)(qx & 31u), cell = (int)((qx >> 5) & 63u), slot = (int)(qx >> 11);
+                        const int ti = (int)(qx & 31u), cell = (int)((qx >> 5) & 63u), slot = (int)((qx >> 11) & 31u);
                         const long long px = X0 + (2 * (cell & 3) + 1) * half, py = Y0 + (2 * ((cell >> 2) & 3) + 1) * half,
                                         pz = Z0 + (2 * (cell >> 4) + 1) * half;
                         float q;
-                        if (!hit_segment(S.tile[ti], px, py, pz, d, h, &q)) continue;
+                        const bool ok = (qx >> 16) ? hit_segment_wide(S.tile[ti], px, py, pz, d, h, &q)
+                                                   : hit_segment(S.tile[ti], px, py, pz, d, h, &q);
+                        if (!ok) continue;
                         const int kk = atomicAdd(&S.hcnt[slot], 1);
                         if (kk < LE_BCAP)
                             S.hit[kk][slot] = make_uint2((e - e0 + (uint32_t)ti) | ((uint32_t)d << 24), __float_as_uint(q));
@@ -742,6 +770,7 @@ __global__ void __launch_bounds__(LE_WARPS * 32, LE_MINB) k_link_emit(const __gr
                     const unsigned long long pmi = ((unsigned long long)__shfl_sync(0xffffffffu, (unsigned)(pm >> 32), ti) << 32) |
                                                    (unsigned long long)__shfl_sync(0xffffffffu, (unsigned)pm, ti);
                     uint32_t dm = 0, qx = 0;
+                    bool wide = false;
                     if (gidx < total) {
                         const int cell = select64(pmi, gidx - excl_i);
                         const int slot = __popcll(cmask & ((1ull << cell) - 1ull));
@@ -757,8 +786,8 @@ __global__ void __launch_bounds__(LE_WARPS * 32, LE_MINB) k_link_emit(const __gr
                                 if (kk < LE_BCAP)
                                     S.hit[kk][slot] = make_uint2(local | ((uint32_t)d << 24), __float_as_uint(q));
                             },
-                            dm);
-                        qx = (uint32_t)ti | ((uint32_t)cell << 5) | ((uint32_t)slot << 11);
+                            dm, wide);
+                        qx = (uint32_t)ti | ((uint32_t)cell << 5) | ((uint32_t)slot << 11) | ((uint32_t)wide << 16);
                     }
                     const unsigned qb = __ballot_sync(0xffffffffu, dm != 0);
                     if (qn + __popc(qb) > 32) flush();
@@ -1195,6 +1224,7 @@ __global__ void k_probe(int kind, const long long *__restrict__ in, int64_t n, i
             T.ny = uz * vx - ux * vz;
             T.nz = ux * vy - uy * vx;
             uint32_t dm = 0;
+            bool wide = false;
             link_pair<true>(
                 T, px, py, pz, 1u << d, h,
                 [&](int dd, float qq) {
@@ -1203,9 +1233,10 @@ __global__ void k_probe(int kind, const long long *__restrict__ in, int64_t n, i
                         q_ = qq;
                     }
                 },
-                dm);
+                dm, wide);
             float qq;
-            if (((dm >> d) & 1u) && hit_segment(T, px, py, pz, d, h, &qq)) {
+            if (((dm >> d) & 1u) &&
+                (wide ? hit_segment_wide(T, px, py, pz, d, h, &qq) : hit_segment(T, px, py, pz, d, h, &qq))) {
                 h_ = 1;
                 q_ = qq;
             }
