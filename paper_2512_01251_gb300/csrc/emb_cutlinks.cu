@@ -96,20 +96,22 @@ __global__ void k_link_cand(const uint64_t *__restrict__ mask, const int32_t *__
 // form a 4x4x4 lattice, the set of cells passing that test is a sub-box, built as
 // a 64-bit mask with a few bit operations.  The surviving (triangle, cell) pairs
 // of a tile are spread over the 32 lanes with a prefix sum.  Per pair, with the
-// vertices relative to P, the moments m_i of the three edges and D = n . (A - P)
-// are formed once; the three Pluecker signs c . m_i against c . n then test the
-// lines of all 13 direction pairs (c and -c share the line) at once, and only a
-// hit line checks the ends of its candidate segments against the plane (D
-// against D - h n.c).  When every vertex lies within 2^14 of P the moments fit
-// 32-bit integers and D fits 64 bits; otherwise the moments are formed in 64 bits
-// by widening products and D in 128 bits (coarse frames, where h itself is 2^14 or
-// more, take this path).  A zero Pluecker value sends its direction through the
-// exact per-direction test with the full tie-break.  Crossings, with q already rounded, are appended to a
-// per-cell bucket; afterwards the owner lane of each cell keeps, per direction,
-// the nearest one (exact rational comparison when a link crosses more than one
-// face) and writes the links at the cell's offset in the table, which the
-// direction words fix whichever warp handles the cell.  A bucket that overflows
-// sends its cell through an exact per-cell scan of the whole bin instead.
+// vertices relative to P, the moments m_i of the three edges are formed once; the
+// three Pluecker signs c . m_i test the lines of all 13 direction pairs (c and -c
+// share the line) at once.  When every vertex lies within 2^14 of P the moments fit
+// 32-bit integers; otherwise they are formed in 64 bits by widening products
+// (coarse frames, where h itself is 2^14 or more, take this path).  A pair whose
+// lines hit is queued in the warp's shared memory (tile index, cell, hit
+// directions); the queue is drained 32 hits at a time, one hit per lane, which
+// checks the ends of the segment against the plane (D = n . (A - P) against
+// D - h n.c, in 64 bits, or 128 bits on the wide path) and rounds q.  A zero
+// Pluecker value sends its direction through the exact per-direction test with the
+// full tie-break at once.  Crossings are appended to a per-cell bucket; afterwards
+// the owner lane of each cell keeps, per direction, the nearest one (exact rational
+// comparison when a link crosses more than one face), and the warp writes the
+// chunk's links, which are consecutive in the table (the direction words fix each
+// cell's offset whichever warp handles it), one link per lane.  A bucket that
+// overflows sends its cell through an exact per-cell scan of the whole bin instead.
 // Sizes: 4 warps per CTA; a warp's tile of 32 triangles, 20 hit slots per cell and the
 // byte-wide best-hit indices take 9 KB of shared memory, so six CTAs fit on an SM (with
 // 80 registers a thread).  Fewer hit slots let more CTAs fit but send many more cells of
@@ -413,21 +415,19 @@ __device__ __noinline__ bool pair_cross_wide(const TriT &T, long long px, long l
     return true;
 }
 
-// All crossings of one (triangle, cell centre P) pair on the candidate directions ccm:
-// emit(d, q) for every direction d whose perturbed segment P -> P + h c_d crosses the
-// triangle, q = t rounded to float.  When every vertex lies within 2^14 of P the
-// moments fit 32-bit integers and D fits 64 bits; otherwise the moments are formed
-// in 64 bits by widening products and D in 128 bits.  A zero Pluecker value sends
-// its direction through the exact per-direction test with the full tie-break.
-// With DEFER neither path tests the segment ends of its line hits: they come back in
-// `deferred` (directions whose line crosses the triangle), and `wide` says which path
-// found them; the caller finishes them with hit_segment or hit_segment_wide, so that a
-// warp can test them 32 at a time.
-template <bool DEFER, class Emit>
+// The line tests of one (triangle, cell centre P) pair on the candidate directions
+// ccm.  The directions whose line crosses the triangle come back in `lines` (`wide`
+// says which path found them); the caller finishes each with the segment-end test
+// hit_segment or hit_segment_wide, so that a warp can run those 32 at a time.  When
+// every vertex lies within 2^14 of P the moments fit 32-bit integers; otherwise they
+// are formed in 64 bits by widening products.  A zero Pluecker value sends its
+// direction through the exact per-direction test with the full tie-break, and a
+// crossing found there is passed to emit(d, q) at once.
+template <class Emit>
 __device__ __forceinline__ void link_pair(const TriT &T, long long px, long long py, long long pz, uint32_t ccm,
-                                          long long h, Emit emit, uint32_t &deferred, bool &wide)
+                                          long long h, Emit emit, uint32_t &lines, bool &wide)
 {
-    deferred = 0;
+    lines = 0;
     wide = false;
     const long long LIM = 1ll << 14;
     const long long l0 = T.lox - px, h0 = T.hix - px, l1 = T.loy - py, h1 = T.hiy - py,
@@ -441,16 +441,13 @@ __device__ __forceinline__ void link_pair(const TriT &T, long long px, long long
         // c . n is NOT formed in 32 bits: for a corner direction it reaches 9 * 2^29 > 2^31.
         // The line test needs only the signs of V1, V2, V3 (n = m1 + m2 + m3, so c . n =
         // V1 + V2 + V3, which has their common sign when they agree and are nonzero, and a
-        // line parallel to the face cannot have three nonzero V of one sign); the crossing
-        // parameter takes c . n in 64 bits.  D = n . a < 3 * 2^31 * 2^14 < 2^47.
+        // line parallel to the face cannot have three nonzero V of one sign).
         const int ax = (int)(T.ax - px), ay = (int)(T.ay - py), az = (int)(T.az - pz);
         const int bx = (int)(T.bx - px), by = (int)(T.by - py), bz = (int)(T.bz - pz);
         const int qx = (int)(T.cx - px), qy = (int)(T.cy - py), qz = (int)(T.cz - pz);
         const int m1x = ay * bz - az * by, m1y = az * bx - ax * bz, m1z = ax * by - ay * bx;
         const int m2x = by * qz - bz * qy, m2y = bz * qx - bx * qz, m2z = bx * qy - by * qx;
         const int m3x = qy * az - qz * ay, m3y = qz * ax - qx * az, m3z = qx * ay - qy * ax;
-        const int nx = m1x + m2x + m3x, ny = m1y + m2y + m3y, nz = m1z + m2z + m3z;
-        const long long D = (long long)nx * ax + (long long)ny * ay + (long long)nz * az;
         // line tests for the 13 direction pairs (odd index d and its opposite d + 1):
         // all 13 lines, without branches (the lanes hold different cells, so a
         // per-direction branch would diverge); non-candidates are masked off
@@ -471,28 +468,10 @@ __device__ __forceinline__ void link_pair(const TriT &T, long long px, long long
             degen |= (ok & zero) << d;
             line |= (ok & (zero ^ 1u) & same) << d;
         }
-        // members of line-hit pairs that are candidates: the segment ends must straddle the plane
-        uint32_t mm = (line | (line << 1)) & ccm;
-        if (DEFER) {
-            deferred = mm;
-            mm = 0;
-        }
-        while (mm) {
-            const int d = __ffs(mm) - 1;
-            mm &= mm - 1;
-            int cx, cy, cz;
-            emb_dir(d, cx, cy, cz);
-            // |c . n| < 9 * 2^29 and h c . n < 2^18 * 2^33: both fit 64 bits
-            const long long nc = (long long)cx * nx + (long long)cy * ny + (long long)cz * nz;
-            const int sn = nc > 0 ? 1 : -1;
-            if (side_sign64(D, nx, ny, nz) != sn) continue;           // t <= 0
-            if (side_sign64(D - h * nc, nx, ny, nz) != -sn) continue;  // t >= 1
-            const long long N = sn > 0 ? D : -D, Mq = nc > 0 ? nc : -nc;
-            const float q = __fdiv_rn((float)N, (float)Mq * (float)h);
-            emit(d, q);
-        }
+        // members of line-hit pairs that are candidates (their segment ends are tested later)
+        lines = (line | (line << 1)) & ccm;
         // a zero Pluecker value: resolve the pair's directions exactly
-        mm = (degen | (degen << 1)) & ccm;
+        uint32_t mm = (degen | (degen << 1)) & ccm;
         while (mm) {
             const int d = __ffs(mm) - 1;
             mm &= mm - 1;
@@ -504,7 +483,7 @@ __device__ __forceinline__ void link_pair(const TriT &T, long long px, long long
         }
     } else {
         // coordinates are below 2^25, so offsets fit 32 bits: moments (below 2^51)
-        // and their signed sums in 64 bits from widening products, D in 128 bits
+        // and their signed sums in 64 bits from widening products
         const int ax = (int)(T.ax - px), ay = (int)(T.ay - py), az = (int)(T.az - pz);
         const int bx = (int)(T.bx - px), by = (int)(T.by - py), bz = (int)(T.bz - pz);
         const int qx = (int)(T.cx - px), qy = (int)(T.cy - py), qz = (int)(T.cz - pz);
@@ -536,30 +515,9 @@ __device__ __forceinline__ void link_pair(const TriT &T, long long px, long long
             }
             if (((V1 ^ NC) | (V2 ^ NC) | (V3 ^ NC)) >= 0) line |= 1u << d;
         }
-        uint32_t mm = (line | (line << 1)) & ccm;
-        if (DEFER) {
-            deferred = mm;
-            wide = true;
-            mm = 0;
-        }
-        if (mm) {
-            const i128 D = mul128(nx, ax) + mul128(ny, ay) + mul128(nz, az);
-            while (mm) {
-                const int d = __ffs(mm) - 1;
-                mm &= mm - 1;
-                int cx, cy, cz;
-                emb_dir(d, cx, cy, cz);
-                const long long nc = cx * nx + cy * ny + cz * nz;
-                const int sn = nc > 0 ? 1 : -1;
-                if (side_sign(D, nx, ny, nz) != sn) continue;                  // t <= 0
-                if (side_sign(D - mul128(h, nc), nx, ny, nz) != -sn) continue;  // t >= 1
-                const i128 N = sn > 0 ? D : -D;
-                const long long Mq = nc > 0 ? nc : -nc;
-                const float q = __fdiv_rn(i128_to_float(N), (float)Mq * (float)h);
-                emit(d, q);
-            }
-        }
-        mm = (degen | (degen << 1)) & ccm;
+        lines = (line | (line << 1)) & ccm;
+        wide = true;
+        uint32_t mm = (degen | (degen << 1)) & ccm;
         while (mm) {
             const int d = __ffs(mm) - 1;
             mm &= mm - 1;
@@ -779,7 +737,7 @@ __global__ void __launch_bounds__(LE_WARPS * 32, LE_MINB) k_link_emit(const __gr
                                         py = Y0 + (2 * ((cell >> 2) & 3) + 1) * half, pz = Z0 + (2 * (cell >> 4) + 1) * half;
                         const uint32_t ccm = S.cm[slot];
                         const uint32_t local = e - e0 + (uint32_t)ti;
-                        link_pair<true>(
+                        link_pair(
                             T, px, py, pz, ccm, h,
                             [&](int d, float q) {
                                 const int kk = atomicAdd(&S.hcnt[slot], 1);
@@ -1225,7 +1183,7 @@ __global__ void k_probe(int kind, const long long *__restrict__ in, int64_t n, i
             T.nz = ux * vy - uy * vx;
             uint32_t dm = 0;
             bool wide = false;
-            link_pair<true>(
+            link_pair(
                 T, px, py, pz, 1u << d, h,
                 [&](int dd, float qq) {
                     if (dd == d) {
