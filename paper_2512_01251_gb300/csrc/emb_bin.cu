@@ -18,10 +18,10 @@
 
 #include "emb_internal.cuh"
 
-__global__ void k_xfilter(const int4 *__restrict__ rec, int64_t T, LevelGeom g, uint32_t *__restrict__ flag)
+// Exact x-line filter of triangle t: 1 iff its yz-projection contains the centre of
+// some x-line of the level (perturbed orientation tests, Sec. 3.4 parity rule).
+__device__ __forceinline__ uint32_t xline_hit(const int4 *__restrict__ rec, int64_t t, const LevelGeom &g)
 {
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= T) return;
     int4 A = rec[3 * t], B = rec[3 * t + 1], C = rec[3 * t + 2];
     long long nx = ((long long)B.y - A.y) * ((long long)C.z - A.z) - ((long long)B.z - A.z) * ((long long)C.y - A.y);
     uint32_t hit = 0;
@@ -53,7 +53,42 @@ __global__ void k_xfilter(const int4 *__restrict__ rec, int64_t T, LevelGeom g, 
             }
         }
     }
-    flag[t] = hit;
+    return hit;
+}
+
+// Per-triangle filter flags (the ablation that keeps the list uncompacted).
+__global__ void k_xfilter(const int4 *__restrict__ rec, int64_t T, LevelGeom g, uint32_t *__restrict__ flag)
+{
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    flag[t] = xline_hit(rec, t, g);
+}
+
+// The filter as one bit per triangle: warp word t / 32 (bit t % 32) and its popcount.
+// The block size is a multiple of 32, so a warp covers triangles 32 w .. 32 w + 31.
+__global__ void k_xfilter_bits(const int4 *__restrict__ rec, int64_t T, LevelGeom g, uint32_t *__restrict__ word,
+                               uint32_t *__restrict__ wcnt)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t hit = t < T ? xline_hit(rec, t, g) : 0u;
+    const uint32_t m = __ballot_sync(0xffffffffu, hit != 0u);
+    if ((threadIdx.x & 31) == 0 && t < T) {
+        word[t >> 5] = m;
+        wcnt[t >> 5] = (uint32_t)__popc(m);
+    }
+}
+
+// Kept triangles in ascending order: triangle t (bit set) goes to the exclusive
+// prefix of its word plus the set bits below it; the kept count is stored at count.
+__global__ void k_compact_bits(const uint32_t *__restrict__ word, const uint32_t *__restrict__ wpos, int64_t T,
+                               uint32_t *__restrict__ flist, uint32_t *count)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    const uint32_t m = word[t >> 5];
+    const int lane = (int)(t & 31);
+    if ((m >> lane) & 1u) flist[wpos[t >> 5] + (uint32_t)__popc(m & ((1u << lane) - 1u))] = (uint32_t)t;
+    if (t == 0) *count = wpos[(T + 31) >> 5];
 }
 
 __global__ void k_compact(const uint32_t *__restrict__ flag, const uint32_t *__restrict__ pos, int64_t n,
@@ -196,6 +231,7 @@ __global__ void __launch_bounds__(EMB_WU_WARPS * 32) k_bin_pairs(const int4 *__r
     const uint32_t wtot = __shfl_sync(0xffffffffu, incl, 31);
     const int ox = (int)b0[0], oy = (int)b0[1], oz = (int)b0[2];
     const int onx = mine ? (int)(b1[0] - b0[0] + 1) : 1, ony = mine ? (int)(b1[1] - b0[1] + 1) : 1;
+    const uint32_t omx = emb_recip((uint32_t)onx), omy = emb_recip((uint32_t)ony);
     for (uint32_t s0 = 0; s0 < wtot; s0 += 32) {
         const uint32_t gi = s0 + lane;
         int lo = 0;
@@ -209,12 +245,13 @@ __global__ void __launch_bounds__(EMB_WU_WARPS * 32) k_bin_pairs(const int4 *__r
         const int bx0 = __shfl_sync(0xffffffffu, ox, ti), by0 = __shfl_sync(0xffffffffu, oy, ti),
                   bz0 = __shfl_sync(0xffffffffu, oz, ti), nbx = __shfl_sync(0xffffffffu, onx, ti),
                   nby = __shfl_sync(0xffffffffu, ony, ti);
+        const uint32_t mbx = __shfl_sync(0xffffffffu, omx, ti), mby = __shfl_sync(0xffffffffu, omy, ti);
         bool hit = false, need = false;
         int32_t id = -1;
         int bxi = 0, byi = 0, bzi = 0;
         if (gi < wtot) {
-            const uint32_t r = gi - first, cx = r % (uint32_t)nbx, rr = r / (uint32_t)nbx, cy = rr % (uint32_t)nby,
-                           cz = rr / (uint32_t)nby;
+            const uint32_t r = gi - first, rr = emb_div_recip(r, (uint32_t)nbx, mbx), cx = r - rr * (uint32_t)nbx,
+                           cz = emb_div_recip(rr, (uint32_t)nby, mby), cy = rr - cz * (uint32_t)nby;
             bxi = bx0 + (int)cx;
             byi = by0 + (int)cy;
             bzi = bz0 + (int)cz;
@@ -315,12 +352,29 @@ __global__ void __launch_bounds__(EMB_BIG_BLOCK) k_bin_pairs_big(const int4 *__r
 }
 
 // Step 1 (enqueue only): flag, pos, flist hold T + 1 uint32; the kept count ends at
-// pos[T]; tmp is scan scratch for T entries.
+// pos[T]; tmp is scan scratch for T entries.  The filter is kept as one bit per
+// triangle (flag[0, W) the W = ceil(T / 32) words, flag[W, 2W) their popcounts,
+// 2W <= T + 1), whose popcounts are scanned into pos[0, W]; the compaction then
+// reads the words instead of a 32-bit flag per triangle.
 emb_status emb_enq_filter(const int4 *rec, int64_t T, LevelGeom g, uint32_t *flag, uint32_t *pos, uint32_t *flist,
                           uint64_t *tmp, int block, cudaStream_t s, uint64_t expect)
 {
+    const int64_t W = (T + 31) / 32;
+    const int bs = block < 32 ? 32 : block - block % 32;
+    if (T > 0) EMB_LAUNCH((k_xfilter_bits), emb_grid(T, bs), bs, 0, s)(rec, T, g, flag, flag + W);
+    emb_status rc = emb_scan_into_expect(flag + W, pos, W, tmp, expect, s);
+    if (rc != EMB_OK) return rc;
+    if (T > 0) EMB_LAUNCH((k_compact_bits), emb_grid(T, 256), 256, 0, s)(flag, pos, T, flist, pos + T);
+    EMB_CUDA_TRY(cudaGetLastError());
+    return EMB_OK;
+}
+
+// The filter with a 32-bit flag per triangle kept in flag (the mode without compaction).
+static emb_status enq_filter_flags(const int4 *rec, int64_t T, LevelGeom g, uint32_t *flag, uint32_t *pos,
+                                   uint32_t *flist, uint64_t *tmp, int block, cudaStream_t s)
+{
     EMB_LAUNCH((k_xfilter), emb_grid(T, block), block, 0, s)(rec, T, g, flag);
-    emb_status rc = emb_scan_into_expect(flag, pos, T, tmp, expect, s);
+    emb_status rc = emb_scan_into_expect(flag, pos, T, tmp, EMB_NO_EXPECT, s);
     if (rc != EMB_OK) return rc;
     EMB_LAUNCH((k_compact), emb_grid(T, 256), 256, 0, s)(flag, pos, T, flist);
     EMB_CUDA_TRY(cudaGetLastError());
@@ -472,7 +526,7 @@ extern "C" emb_status emb_bin_ex(emb_mesh m, emb_forest f, int32_t level, int32_
     } else {
         // ablations: the filter flags kept per triangle without compaction, or no filter
         if (mode == EMB_BIN_FILTER_ONLY) {
-            rc = emb_enq_filter(m->rec, m->T, g, flag, pos, b->flist, tmp, 256, s);
+            rc = enq_filter_flags(m->rec, m->T, g, flag, pos, b->flist, tmp, 256, s);
             b->keep = flag;
             flag = nullptr;
         }

@@ -485,6 +485,17 @@ __device__ __forceinline__ void line_range(long long mn, long long mx, int lh, l
 // summed per-triangle candidates), and always in the finest-level binning, the
 // warp's (triangle, candidate block) pairs are spread evenly over its lanes instead.
 #define EMB_WU_WARPS 4
+// Division by a per-triangle divisor d >= 1 in the pair-spreading loops, through its
+// reciprocal m = ceil(2^32 / d) (emb_recip, once per triangle): q = floor(r m / 2^32)
+// is floor(r / d) or one more (r m / 2^32 lies in [r / d, r / d + r / 2^32)), and
+// the one multiply-compare takes the excess back; exact while r + d < 2^32.
+__device__ __forceinline__ uint32_t emb_recip(uint32_t d) { return d > 1u ? 0xFFFFFFFFu / d + 1u : 0u; }
+__device__ __forceinline__ uint32_t emb_div_recip(uint32_t r, uint32_t d, uint32_t m)
+{
+    uint32_t q = __umulhi(r, m);
+    q -= (uint32_t)(q * d > r);
+    return d > 1u ? q : r;
+}
 #define EMB_WU_MAX 2048
 
 struct WuTri {

@@ -144,13 +144,14 @@ __global__ void __launch_bounds__(EMB_WU_WARPS * 32, REFINE_MINB) k_refine(const
             // takes a union block; the blocks that exist and are not flagged yet are then
             // tested one at a time by the whole warp, each lane against its own triangle.
             const unsigned ux = (unsigned)nx, uxy = (unsigned)(nx * ny);
+            const unsigned mx = emb_recip(ux), mxy = emb_recip(uxy);
             for (unsigned c0 = 0; c0 < (unsigned)total; c0 += 32) {
                 const unsigned c = c0 + lane;
                 long long bx = 0, by = 0, bz = 0;
                 unsigned long long pos = 0;
                 int32_t id = -1;
                 if (c < (unsigned)total) {
-                    const unsigned cz = c / uxy, cr = c - cz * uxy, cy = cr / ux;
+                    const unsigned cz = emb_div_recip(c, uxy, mxy), cr = c - cz * uxy, cy = emb_div_recip(cr, ux, mx);
                     bx = u0[0] + (long long)(cr - cy * ux);
                     by = u0[1] + (long long)cy;
                     bz = u0[2] + (long long)cz;
@@ -189,6 +190,7 @@ __global__ void __launch_bounds__(EMB_WU_WARPS * 32, REFINE_MINB) k_refine(const
         const uint32_t wtot = __shfl_sync(0xffffffffu, incl, 31);
         const int ox = (int)b0[0], oy = (int)b0[1], oz = (int)b0[2];
         const int onx = mine ? (int)(b1[0] - b0[0] + 1) : 1, ony = mine ? (int)(b1[1] - b0[1] + 1) : 1;
+        const uint32_t omx = emb_recip((uint32_t)onx), omy = emb_recip((uint32_t)ony);
         for (uint32_t s0 = 0; s0 < wtot; s0 += 32) {
             const uint32_t gi = s0 + lane;
             int lo = 0;
@@ -202,9 +204,10 @@ __global__ void __launch_bounds__(EMB_WU_WARPS * 32, REFINE_MINB) k_refine(const
             const int bx0 = __shfl_sync(0xffffffffu, ox, ti), by0 = __shfl_sync(0xffffffffu, oy, ti),
                       bz0 = __shfl_sync(0xffffffffu, oz, ti), nbx = __shfl_sync(0xffffffffu, onx, ti),
                       nby = __shfl_sync(0xffffffffu, ony, ti);
+            const uint32_t mbx = __shfl_sync(0xffffffffu, omx, ti), mby = __shfl_sync(0xffffffffu, omy, ti);
             if (gi < wtot) {
-                const uint32_t r = gi - first, cx = r % (uint32_t)nbx, rr = r / (uint32_t)nbx, cy = rr % (uint32_t)nby,
-                               cz = rr / (uint32_t)nby;
+                const uint32_t r = gi - first, rr = emb_div_recip(r, (uint32_t)nbx, mbx), cx = r - rr * (uint32_t)nbx,
+                               cz = emb_div_recip(rr, (uint32_t)nby, mby), cy = rr - cz * (uint32_t)nby;
                 refine_block(S.A[ti], S.B[ti], S.C[ti], bx0 + (long long)cx, by0 + (long long)cy, bz0 + (long long)cz, g,
                              dil, lk, flags, fb);
             }
