@@ -113,9 +113,12 @@ __global__ void k_link_cand(const uint64_t *__restrict__ mask, const int32_t *__
 // cell's offset whichever warp handles it), one link per lane.  A bucket that
 // overflows sends its cell through an exact per-cell scan of the whole bin instead.
 // Sizes: 4 warps per CTA; a warp's tile of 32 triangles, 20 hit slots per cell and the
-// byte-wide best-hit indices take 9 KB of shared memory, so six CTAs fit on an SM (with
-// 80 registers a thread).  Fewer hit slots let more CTAs fit but send many more cells of
-// a D3Q27 workload through the per-cell rescan, which costs far more than it saves.
+// byte-wide best-hit indices (shared with the hit queue) take 9 KB of shared memory, so
+// six CTAs would fit on an SM.  The launch bound asks for five, which leaves 96
+// registers a thread: with the queue's shorter instruction stream the spills of the
+// 80-register build cost more than the sixth CTA gains (3.76 -> 3.43 ms on the 7.2M
+// step).  Fewer hit slots let more CTAs fit but send many more cells of a D3Q27
+// workload through the per-cell rescan, which costs far more than it saves.
 #define LE_WARPS 4
 #define LE_TILE 32
 #define LE_BCAP 20
@@ -531,7 +534,7 @@ __device__ __forceinline__ void link_pair(const TriT &T, long long px, long long
 }
 
 #ifndef LE_MINB
-#define LE_MINB 6
+#define LE_MINB 5
 #endif
 __global__ void __launch_bounds__(LE_WARPS * 32, LE_MINB) k_link_emit(const __grid_constant__ LinkTable tab,
                                                                 unsigned int *__restrict__ next, int *st)
