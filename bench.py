@@ -20,6 +20,7 @@ import json
 import math
 import os
 import statistics
+import select
 import subprocess
 import sys
 import time
@@ -201,12 +202,20 @@ class ClockSampler:
         self.p = None
 
     def start(self):
+        """Starts the sampler and returns once its first sample is out: nvidia-smi's own
+        start-up (driver queries of the device) then falls before the timed region, where it
+        stalled one step by about 7 ms."""
+        self.first = ""
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
                                        "--format=csv,noheader,nounits", "-lms", "200"],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.p = None
+            return
+        ready, _, _ = select.select([self.p.stdout], [], [], 10.0)
+        if ready:
+            self.first = self.p.stdout.readline()
 
     def stop(self):
         if self.p is None:
@@ -218,7 +227,7 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.p.kill()
             out, _ = self.p.communicate()
-        return parse_clock_samples(out)
+        return parse_clock_samples(self.first + (out or ""))
 
 
 def parse_clock_samples(text):
@@ -506,7 +515,8 @@ def run_ours(args):
     k = min(nst - 1, int(math.ceil(nst / 2 + 0.98 * math.sqrt(nst))))
     four = sum(groups.get(g_, 0.0) for g_ in ("bin", "voxelize", "refine_flags", "cutlinks_count", "cutlinks_emit"))
     line["step_ms_stats"] = dict(median=statistics.median(srt), min=srt[0], max=srt[-1],
-                                 ci95_median=[srt[j], srt[k]], n=nst)
+                                 ci95_median=[srt[j], srt[k]], n=nst,
+                                 in_order=[round(x, 3) for x in step_ms])
     line["four_calls"] = dict(ms=round(four, 4),
                              units_per_s=(64 * sum(level_blocks) + n_links) / (four / 1e3) if four else None)
     # the whole step against its roofline (the replay leg below adds the graph-replay time)

@@ -57,16 +57,41 @@ struct FlagBits {
     __device__ __forceinline__ void set(unsigned long long pos) const { atomicOr(w + (pos >> 6), 1ull << (pos & 63)); }
 };
 
+// Id of block (bx, by, bz) if it exists and is not flagged yet, else -1; pos receives
+// its dense position.  With both dense bitmaps (flagged bits and the level's rank
+// bitmap) the flagged word, the existence word and its rank prefix are independent
+// loads issued together, and the flag byte is not read: a flagged word read before
+// another SM set the bit only sends the block through the exact test once more, whose
+// flag store is idempotent.  Otherwise: the flagged bit, the lookup, the flag byte.
+__device__ __forceinline__ int32_t refine_candidate(const EmbLookup &lk, const FlagBits &fb,
+                                                    const uint8_t *__restrict__ flags, long long bx, long long by,
+                                                    long long bz, unsigned long long &pos)
+{
+    if (fb.w && lk.bits) {
+        pos = (unsigned long long)((bz * fb.nb + by) * fb.nb + bx);
+        if (!emb_ck(pos, (uint64_t)lk.nb * lk.nb * lk.nb, lk.st)) return -1;
+        const unsigned long long fw = fb.w[pos >> 6];
+        const uint64_t ew = __ldg(lk.bits + (pos >> 6));
+        const uint32_t pre = __ldg(lk.wpre + (pos >> 6));
+        const int sh = (int)(pos & 63);
+        if (((fw >> sh) & 1ull) || !((ew >> sh) & 1ull)) return -1;
+        const int32_t id = (int32_t)(pre + (uint32_t)__popcll(ew & ((1ull << sh) - 1ull)));
+        return emb_ck((uint64_t)id, (uint64_t)lk.n, lk.st) ? id : -1;
+    }
+    if (fb.w && fb.test(bx, by, bz, pos)) return -1;
+    const int32_t id = emb_lookup(lk, bx, by, bz);
+    if (id < 0 || *((volatile const uint8_t *)flags + id)) return -1;
+    return id;
+}
+
 // Flag block (bx, by, bz) if it exists, is not flagged yet and the triangle meets its dilated box.
 __device__ __forceinline__ void refine_block(const int4 &A, const int4 &B, const int4 &C, long long bx, long long by,
                                              long long bz, const LevelGeom &g, long long dil, const EmbLookup &lk,
                                              uint8_t *__restrict__ flags, const FlagBits &fb)
 {
     unsigned long long pos = 0;
-    if (fb.w && fb.test(bx, by, bz, pos)) return;
-    const int32_t id = emb_lookup(lk, bx, by, bz);
+    const int32_t id = refine_candidate(lk, fb, flags, bx, by, bz, pos);
     if (id < 0) return;
-    if (*((volatile uint8_t *)flags + id)) return;
     const long long lx = bx * g.W - dil, ly = by * g.W - dil, lz = bz * g.W - dil;
     const long long hx = lx + g.W + 2 * dil, hy = ly + g.W + 2 * dil, hz = lz + g.W + 2 * dil;
     if (emb_point_in_box(A, lx, ly, lz, hx, hy, hz) || emb_point_in_box(B, lx, ly, lz, hx, hy, hz) ||
@@ -155,10 +180,7 @@ __global__ void __launch_bounds__(EMB_WU_WARPS * 32, REFINE_MINB) k_refine(const
                     bx = u0[0] + (long long)(cr - cy * ux);
                     by = u0[1] + (long long)cy;
                     bz = u0[2] + (long long)cz;
-                    if (!(fb.w && fb.test(bx, by, bz, pos))) {  // the common case: one cached load
-                        id = emb_lookup(lk, bx, by, bz);
-                        if (id >= 0 && flags[id]) id = -1;
-                    }
+                    id = refine_candidate(lk, fb, flags, bx, by, bz, pos);
                 }
                 unsigned m = __ballot_sync(0xffffffffu, id >= 0);
                 while (m) {
