@@ -314,10 +314,12 @@ __device__ __forceinline__ int32_t emb_lookup(const EmbLookup &l, int64_t bx, in
     if (l.bits) {
         const int64_t lin = (bz * l.nb + by) * l.nb + bx;
         if (!emb_ck((uint64_t)lin, (uint64_t)l.nb * l.nb * l.nb, l.st)) return -1;
+        // the word and its rank prefix are independent loads: both issued before the test
         const uint64_t w = __ldg(l.bits + (lin >> 6));
+        const uint32_t pre = __ldg(l.wpre + (lin >> 6));
         const int sh = (int)(lin & 63);
         if (!((w >> sh) & 1ull)) return -1;
-        id = (int32_t)(__ldg(l.wpre + (lin >> 6)) + __popcll(w & ((1ull << sh) - 1ull)));
+        id = (int32_t)(pre + __popcll(w & ((1ull << sh) - 1ull)));
     } else {
         id = emb_hash_find(l.hkey, l.hval, l.hcap, emb_key(bx, by, bz));
     }
