@@ -327,6 +327,22 @@ __global__ void k_bits_set(const uint64_t *__restrict__ key, int64_t n, int64_t 
     atomicOr(bits + (lin >> 6), 1ull << (lin & 63));
 }
 
+// The bits of a child level whose block count, 8 x *nflags (at most cap), is still on
+// the device: threads past the count leave the bitmap alone.
+__global__ void k_bits_set_counted(const uint64_t *__restrict__ key, const uint32_t *__restrict__ nflags, int64_t cap,
+                                   int64_t nb, unsigned long long *__restrict__ bits)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t n = 8 * (int64_t)*nflags;
+    if (i >= n || i >= cap) return;
+    uint64_t k = key[i];
+    int64_t bx = (int64_t)(k & EMB_KEY_MASK), by = (int64_t)((k >> EMB_KEY_BITS) & EMB_KEY_MASK),
+            bz = (int64_t)(k >> (2 * EMB_KEY_BITS));
+    if (bx >= nb || by >= nb || bz >= nb) return;
+    int64_t lin = (bz * nb + by) * nb + bx;
+    atomicOr(bits + (lin >> 6), 1ull << (lin & 63));
+}
+
 __global__ void k_word_popc(const uint64_t *__restrict__ bits, int64_t nw, uint32_t *__restrict__ out)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -368,6 +384,92 @@ emb_status emb_enq_level_index(EmbLevel &lv, uint32_t *pc, uint64_t *tmp, cudaSt
     }
     EMB_CUDA_TRY(cudaGetLastError());
     return EMB_OK;
+}
+
+// The rank bitmap of level lv (which must have one) from keys whose count, 8 x *nflags
+// with at most cap keys, is read on the device: lets the host read the count back while
+// the index is being built.
+emb_status emb_build_index_counted(EmbLevel &lv, const uint32_t *nflags, int64_t cap, cudaStream_t s)
+{
+    const int64_t nw = emb_bitmap_words(lv.nb_axis);
+    if (nw == 0) return EMB_ERR_STATE;
+    if (lv.hkey) EMB_CUDA_TRY(cudaFreeAsync(lv.hkey, s));
+    if (lv.hval) EMB_CUDA_TRY(cudaFreeAsync(lv.hval, s));
+    if (lv.bits) EMB_CUDA_TRY(cudaFreeAsync(lv.bits, s));
+    if (lv.wpre) EMB_CUDA_TRY(cudaFreeAsync(lv.wpre, s));
+    lv.hkey = nullptr;
+    lv.hval = nullptr;
+    lv.hcap = 0;
+    uint32_t *pc = nullptr;
+    uint64_t *tmp = nullptr;
+    EMB_CUDA_TRY(emb_malloc_async(&lv.bits, nw * sizeof(uint64_t), s));
+    EMB_CUDA_TRY(emb_malloc_async(&lv.wpre, (nw + 1) * sizeof(uint32_t), s));
+    EMB_CUDA_TRY(emb_malloc_async(&pc, (nw + 1) * sizeof(uint32_t), s));
+    EMB_CUDA_TRY(emb_malloc_async(&tmp, emb_scan_tmp_words(nw) * sizeof(uint64_t), s));
+    EMB_CUDA_TRY(cudaMemsetAsync(lv.bits, 0, nw * sizeof(uint64_t), s));
+    if (cap > 0)
+        EMB_LAUNCH((k_bits_set_counted), emb_grid(cap, 256), 256, 0, s)(lv.key, nflags, cap, lv.nb_axis,
+                                                                           (unsigned long long *)lv.bits);
+    EMB_LAUNCH((k_word_popc), emb_grid(nw, 256), 256, 0, s)(lv.bits, nw, pc);
+    emb_status rc = emb_scan_into(pc, lv.wpre, nw, tmp, s);
+    EMB_CUDA_TRY(cudaFreeAsync(pc, s));
+    EMB_CUDA_TRY(cudaFreeAsync(tmp, s));
+    if (rc != EMB_OK) return rc;
+    EMB_CUDA_TRY(cudaGetLastError());
+    return EMB_OK;
+}
+
+// Pinned host words for small count read-backs, each with an event that marks when the
+// copy into it has landed (a slab shared by all forests; slots are reused after release).
+#define EMB_RB_SLOTS 1024
+static std::mutex g_rb_mu;
+static uint64_t *g_rb_host = nullptr;
+static cudaEvent_t g_rb_ev[EMB_RB_SLOTS];
+static int g_rb_dev[EMB_RB_SLOTS];
+static bool g_rb_used[EMB_RB_SLOTS];
+
+int emb_readback_acquire(uint64_t **h, cudaEvent_t *ev)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+    std::lock_guard<std::mutex> lk(g_rb_mu);
+    if (!g_rb_host) {
+        if (cudaHostAlloc((void **)&g_rb_host, EMB_RB_SLOTS * 64, cudaHostAllocPortable) != cudaSuccess) {
+            g_rb_host = nullptr;
+            return -1;
+        }
+        for (int i = 0; i < EMB_RB_SLOTS; ++i) {
+            g_rb_ev[i] = nullptr;
+            g_rb_dev[i] = -1;
+            g_rb_used[i] = false;
+        }
+    }
+    for (int i = 0; i < EMB_RB_SLOTS; ++i) {
+        if (g_rb_used[i]) continue;
+        if (g_rb_ev[i] && g_rb_dev[i] != dev) {
+            cudaEventDestroy(g_rb_ev[i]);
+            g_rb_ev[i] = nullptr;
+        }
+        if (!g_rb_ev[i]) {
+            if (cudaEventCreateWithFlags(&g_rb_ev[i], cudaEventDisableTiming) != cudaSuccess) {
+                g_rb_ev[i] = nullptr;
+                return -1;
+            }
+            g_rb_dev[i] = dev;
+        }
+        g_rb_used[i] = true;
+        *h = g_rb_host + 8 * i;
+        *ev = g_rb_ev[i];
+        return i;
+    }
+    return -1;  // all slots taken: the caller reads the count back the plain way
+}
+
+void emb_readback_release(int slot)
+{
+    if (slot < 0 || slot >= EMB_RB_SLOTS) return;
+    std::lock_guard<std::mutex> lk(g_rb_mu);
+    g_rb_used[slot] = false;
 }
 
 emb_status emb_build_hash(EmbLevel &lv, cudaStream_t s)

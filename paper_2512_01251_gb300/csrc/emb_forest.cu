@@ -117,6 +117,7 @@ extern "C" void emb_forest_destroy(emb_forest f)
     if (f->work) cudaFree(f->work);
     if (f->work_n) cudaFree(f->work_n);
     if (f->next) cudaFree(f->next);
+    emb_readback_release(f->rb_slot);
     delete f;
 }
 
@@ -172,19 +173,38 @@ extern "C" emb_status emb_forest_refine(emb_forest f, int32_t level, const uint8
     EMB_CUDA_TRY(emb_malloc_async(&tmp, emb_scan_tmp_words(P.n) * sizeof(uint64_t), s));
     emb_status rc = emb_enq_flag_ranks(P, d_flags, cnt, rank, tmp, s);
     if (rc != EMB_OK) return rc;
-    uint32_t F = 0;
-    EMB_CUDA_TRY(cudaMemcpyAsync(&F, rank + P.n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    EMB_CUDA_TRY(cudaStreamSynchronize(s));
-    C.n = 8 * (int64_t)F;
     C.nb_axis = P.nb_axis * 2;
-    EMB_CUDA_TRY(emb_malloc_async(&C.key, (C.n + 1) * sizeof(uint64_t), s));
-    rc = emb_enq_children(P, d_flags, rank, C.key, C.n, false, s);
-    if (rc != EMB_OK) return rc;
-    EMB_CUDA_TRY(cudaFreeAsync(cnt, s));
-    EMB_CUDA_TRY(cudaFreeAsync(rank, s));
-    EMB_CUDA_TRY(cudaFreeAsync(tmp, s));
-    rc = emb_build_hash(C, s);
-    if (rc != EMB_OK) return rc;
+    if (f->rb_slot < 0) f->rb_slot = emb_readback_acquire(&f->rb_h, &f->rb_ev);
+    if (emb_bitmap_words(C.nb_axis) > 0 && f->rb_slot >= 0) {
+        // The child level takes the rank bitmap: its keys (room for 8 per parent) and
+        // index are built from the flagged count on the device while that count comes
+        // back to the host, so the GPU is not left idle during the read-back.
+        EMB_CUDA_TRY(cudaMemcpyAsync(f->rb_h, rank + P.n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        EMB_CUDA_TRY(cudaEventRecord(f->rb_ev, s));
+        const int64_t cap = 8 * P.n;
+        EMB_CUDA_TRY(emb_malloc_async(&C.key, (cap + 1) * sizeof(uint64_t), s));
+        rc = emb_enq_children(P, d_flags, rank, C.key, cap, false, s);
+        if (rc == EMB_OK) rc = emb_build_index_counted(C, rank + P.n, cap, s);
+        EMB_CUDA_TRY(cudaFreeAsync(cnt, s));
+        EMB_CUDA_TRY(cudaFreeAsync(rank, s));
+        EMB_CUDA_TRY(cudaFreeAsync(tmp, s));
+        if (rc != EMB_OK) return rc;
+        EMB_CUDA_TRY(cudaEventSynchronize(f->rb_ev));
+        C.n = 8 * (int64_t)(*(volatile uint32_t *)f->rb_h);
+    } else {
+        uint32_t F = 0;
+        EMB_CUDA_TRY(cudaMemcpyAsync(&F, rank + P.n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        EMB_CUDA_TRY(cudaStreamSynchronize(s));
+        C.n = 8 * (int64_t)F;
+        EMB_CUDA_TRY(emb_malloc_async(&C.key, (C.n + 1) * sizeof(uint64_t), s));
+        rc = emb_enq_children(P, d_flags, rank, C.key, C.n, false, s);
+        if (rc != EMB_OK) return rc;
+        EMB_CUDA_TRY(cudaFreeAsync(cnt, s));
+        EMB_CUDA_TRY(cudaFreeAsync(rank, s));
+        EMB_CUDA_TRY(cudaFreeAsync(tmp, s));
+        rc = emb_build_hash(C, s);
+        if (rc != EMB_OK) return rc;
+    }
     f->top = level + 1;
     // a new finest level invalidates cached link candidates
     if (f->cand) {

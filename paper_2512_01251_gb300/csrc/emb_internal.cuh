@@ -136,6 +136,10 @@ struct emb_forest_s {
     int32_t cand_lattice = 0;
     int64_t n_links = -1;
     int device;
+    // pinned slot for reading the flagged count back while the child level is built
+    int rb_slot = -1;
+    uint64_t *rb_h = nullptr;
+    cudaEvent_t rb_ev = nullptr;
 };
 
 struct emb_bins_s {
@@ -199,6 +203,10 @@ int64_t emb_hash_capacity(int64_t n);
 int64_t emb_bitmap_words(int64_t nb);
 emb_status emb_enq_level_index(EmbLevel &lv, uint32_t *pc, uint64_t *tmp, cudaStream_t s);
 emb_status emb_build_hash(EmbLevel &lv, cudaStream_t s);
+emb_status emb_build_index_counted(EmbLevel &lv, const uint32_t *nflags, int64_t cap, cudaStream_t s);
+// A pinned host slot (8 words) and its event for a count read-back; -1 when none is free.
+int emb_readback_acquire(uint64_t **h, cudaEvent_t *ev);
+void emb_readback_release(int slot);
 emb_status emb_enq_neighbors(EmbLevel &lv, cudaStream_t s);
 emb_status emb_build_neighbors(EmbLevel &lv, cudaStream_t s);
 int emb_grid(int64_t n, int block);
