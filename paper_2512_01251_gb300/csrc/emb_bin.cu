@@ -163,7 +163,15 @@ __device__ __forceinline__ void bin_append(bool hit, int32_t id, uint32_t tri, i
     unsigned long long base = 0;
     if (lane == 0) base = atomicAdd(PL.n, (unsigned long long)__popc(hm));
     base = __shfl_sync(0xffffffffu, base, 0) + (unsigned long long)__popc(hm & ((1u << lane) - 1u));
-    if (hit) PL.put(base, (uint32_t)id, atomicAdd(cnt + id, 1u), tri);
+    if (hit) {
+        // lanes that hit the same block take their slots with one atomic
+        const unsigned grp = __match_any_sync(hm, id);
+        const int lead = __ffs(grp) - 1;
+        uint32_t first = 0;
+        if (lane == lead) first = atomicAdd(cnt + id, (uint32_t)__popc(grp));
+        first = __shfl_sync(grp, first, lead);
+        PL.put(base, (uint32_t)id, first + (uint32_t)__popc(grp & ((1u << lane) - 1u)), tri);
+    }
 }
 
 // Per warp: (triangle lane, bx, by, bz) and block id of pairs whose triangle has no vertex
@@ -540,6 +548,14 @@ extern "C" emb_status emb_bin_ex(emb_mesh m, emb_forest f, int32_t level, int32_
     if (flag) cudaFreeAsync(flag, s);
     cudaFreeAsync(pos, s);
     cudaFreeAsync(tmp, s);
+    // the counts travel to a pinned slot behind the bins, so that emb_bins_sync only
+    // waits for them instead of synchronising the stream
+    if (rc == EMB_OK) {
+        b->rb_slot = emb_readback_acquire(&b->rb_h, &b->rb_ev);
+        if (b->rb_slot >= 0 && (cudaMemcpyAsync(b->rb_h, b->dcount, 16, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                                cudaEventRecord(b->rb_ev, s) != cudaSuccess))
+            rc = EMB_ERR_CUDA;
+    }
     if (rc == EMB_OK && cudaGetLastError() != cudaSuccess) rc = EMB_ERR_CUDA;
     if (rc != EMB_OK) {
         emb_bins_destroy(b);
@@ -553,8 +569,13 @@ emb_status emb_bins_sync(emb_bins b)
 {
     if (b->known) return EMB_OK;
     unsigned char h[16];
-    EMB_CUDA_TRY(cudaMemcpyAsync(h, b->dcount, 16, cudaMemcpyDeviceToHost, b->s));
-    EMB_CUDA_TRY(cudaStreamSynchronize(b->s));
+    if (b->rb_slot >= 0) {
+        EMB_CUDA_TRY(cudaEventSynchronize(b->rb_ev));
+        memcpy(h, (const void *)b->rb_h, 16);
+    } else {
+        EMB_CUDA_TRY(cudaMemcpyAsync(h, b->dcount, 16, cudaMemcpyDeviceToHost, b->s));
+        EMB_CUDA_TRY(cudaStreamSynchronize(b->s));
+    }
     uint32_t nf = 0, np = 0;
     unsigned long long lreq = 0;
     memcpy(&nf, h, 4);
@@ -582,6 +603,7 @@ extern "C" void emb_bins_destroy(emb_bins b)
     void *bufs[] = {b->flist, b->off, b->ent, b->dcount, b->keep};
     for (void *p : bufs)
         if (p) cudaFreeAsync(p, b->s);
+    emb_readback_release(b->rb_slot);  // reused only once its event has completed
     delete b;
 }
 

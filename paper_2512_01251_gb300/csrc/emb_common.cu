@@ -427,6 +427,7 @@ static uint64_t *g_rb_host = nullptr;
 static cudaEvent_t g_rb_ev[EMB_RB_SLOTS];
 static int g_rb_dev[EMB_RB_SLOTS];
 static bool g_rb_used[EMB_RB_SLOTS];
+static bool g_rb_pending[EMB_RB_SLOTS];  // released, but its last copy may still be in flight
 
 int emb_readback_acquire(uint64_t **h, cudaEvent_t *ev)
 {
@@ -442,10 +443,15 @@ int emb_readback_acquire(uint64_t **h, cudaEvent_t *ev)
             g_rb_ev[i] = nullptr;
             g_rb_dev[i] = -1;
             g_rb_used[i] = false;
+            g_rb_pending[i] = false;
         }
     }
     for (int i = 0; i < EMB_RB_SLOTS; ++i) {
         if (g_rb_used[i]) continue;
+        if (g_rb_pending[i]) {
+            if (cudaEventQuery(g_rb_ev[i]) != cudaSuccess) continue;
+            g_rb_pending[i] = false;
+        }
         if (g_rb_ev[i] && g_rb_dev[i] != dev) {
             cudaEventDestroy(g_rb_ev[i]);
             g_rb_ev[i] = nullptr;
@@ -470,6 +476,7 @@ void emb_readback_release(int slot)
     if (slot < 0 || slot >= EMB_RB_SLOTS) return;
     std::lock_guard<std::mutex> lk(g_rb_mu);
     g_rb_used[slot] = false;
+    g_rb_pending[slot] = true;
 }
 
 emb_status emb_build_hash(EmbLevel &lv, cudaStream_t s)

@@ -158,6 +158,10 @@ struct emb_bins_s {
     // host copies, valid once `known` (emb_bins_sync)
     bool known = false;
     int64_t nf = 0, npairs = 0;
+    // pinned slot the counts are copied into as soon as the bins are enqueued
+    int rb_slot = -1;
+    uint64_t *rb_h = nullptr;
+    cudaEvent_t rb_ev = nullptr;
 };
 // Reads the counts of b back (synchronising b's stream) and, at the finest level,
 // redoes the bins with an exact pair list if the first one was too small.
