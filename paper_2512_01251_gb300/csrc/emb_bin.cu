@@ -78,17 +78,23 @@ __global__ void k_xfilter_bits(const int4 *__restrict__ rec, int64_t T, LevelGeo
     }
 }
 
-// Kept triangles in ascending order: triangle t (bit set) goes to the exclusive
-// prefix of its word plus the set bits below it; the kept count is stored at count.
+// Kept triangles in ascending order, one thread per filter word: the set bits of word
+// w go, in order, to the places from the exclusive prefix of its word; the kept count
+// is stored at count.
 __global__ void k_compact_bits(const uint32_t *__restrict__ word, const uint32_t *__restrict__ wpos, int64_t T,
                                uint32_t *__restrict__ flist, uint32_t *count)
 {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= T) return;
-    const uint32_t m = word[t >> 5];
-    const int lane = (int)(t & 31);
-    if ((m >> lane) & 1u) flist[wpos[t >> 5] + (uint32_t)__popc(m & ((1u << lane) - 1u))] = (uint32_t)t;
-    if (t == 0) *count = wpos[(T + 31) >> 5];
+    const int64_t W = (T + 31) >> 5;
+    const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= W) return;
+    uint32_t m = word[w];
+    uint32_t o = wpos[w];
+    while (m) {
+        const int b = __ffs(m) - 1;
+        m &= m - 1;
+        flist[o++] = (uint32_t)(32 * w + b);
+    }
+    if (w == 0) *count = wpos[W];
 }
 
 __global__ void k_compact(const uint32_t *__restrict__ flag, const uint32_t *__restrict__ pos, int64_t n,
@@ -372,7 +378,7 @@ emb_status emb_enq_filter(const int4 *rec, int64_t T, LevelGeom g, uint32_t *fla
     if (T > 0) EMB_LAUNCH((k_xfilter_bits), emb_grid(T, bs), bs, 0, s)(rec, T, g, flag, flag + W);
     emb_status rc = emb_scan_into_expect(flag + W, pos, W, tmp, expect, s);
     if (rc != EMB_OK) return rc;
-    if (T > 0) EMB_LAUNCH((k_compact_bits), emb_grid(T, 256), 256, 0, s)(flag, pos, T, flist, pos + T);
+    if (T > 0) EMB_LAUNCH((k_compact_bits), emb_grid(W, 256), 256, 0, s)(flag, pos, T, flist, pos + T);
     EMB_CUDA_TRY(cudaGetLastError());
     return EMB_OK;
 }

@@ -126,18 +126,22 @@ __global__ void k_vox(const int4 *__restrict__ rec, int64_t T, const uint32_t *_
                       const uint32_t *__restrict__ d_nf, const uint32_t *__restrict__ keep, LevelGeom g, EmbLookup lk,
                       VoxAcc acc, EmbBigQ Q, int *st)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    // nf: the planned count of a replay or the exact one; d_nf: the count this replay found
-    if (i >= nf || (d_nf && i >= (int64_t)*d_nf)) return;
-    const uint32_t t = flist[i];
-    if ((int64_t)t >= T) return;
-    if (keep && !keep[t]) return;  // filtered out, the list not compacted
-    VoxTri V;
-    if (!vox_setup(rec, t, g, V)) return;
-    const unsigned long long items = vox_items(V);
-    if (items > EMB_BIG_ITEMS && emb_bigq_push(Q, t, items)) return;
-    for (long long k = V.k0; k <= V.k1; ++k)
-        for (long long j = V.j0; j <= V.j1; ++j) vox_line(V, g, lk, j, k, acc, st);
+    // nf: the planned count of a replay, or T when the count is still on the device;
+    // d_nf: the count the filter found.  Grid-stride, so that a level with few kept
+    // triangles does not launch a thread per triangle of the mesh.
+    int64_t n = nf;
+    if (d_nf && (int64_t)*d_nf < n) n = (int64_t)*d_nf;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t t = flist[i];
+        if ((int64_t)t >= T) continue;
+        if (keep && !keep[t]) continue;  // filtered out, the list not compacted
+        VoxTri V;
+        if (!vox_setup(rec, t, g, V)) continue;
+        const unsigned long long items = vox_items(V);
+        if (items > EMB_BIG_ITEMS && emb_bigq_push(Q, t, items)) continue;
+        for (long long k = V.k0; k <= V.k1; ++k)
+            for (long long j = V.j0; j <= V.j1; ++j) vox_line(V, g, lk, j, k, acc, st);
+    }
 }
 
 // The queued chunks of large triangles, one warp per chunk (lines in j-major order).
@@ -213,7 +217,10 @@ emb_status emb_enq_voxelize(const int4 *rec, int64_t T, const uint32_t *flist, i
     if (nf > 0) {
         const EmbLookup lk = emb_lookup_of(lv);
         if (Q.cap) EMB_CUDA_TRY(cudaMemsetAsync(Q.n, 0, sizeof(unsigned long long), s));
-        EMB_LAUNCH((k_vox), emb_grid(nf, block), block, 0, s)(rec, T, flist, nf, d_nf, keep, g, lk, acc, Q, st);
+        int64_t grid = emb_grid(nf, block);
+        const int64_t full = (int64_t)emb_sm_count() * (2048 / block);  // one resident wave
+        if (grid > full) grid = full;
+        EMB_LAUNCH((k_vox), (int)grid, block, 0, s)(rec, T, flist, nf, d_nf, keep, g, lk, acc, Q, st);
         if (Q.cap) EMB_LAUNCH((k_vox_big), EMB_BIG_GRID, EMB_BIG_BLOCK, 0, s)(rec, g, lk, acc, Q, st);
     }
     EMB_LAUNCH((k_xscan), emb_grid(lv.n, 256), 256, 0, s)(lv.key, lv.n, s_acc, p_acc, t_acc, lv.mask);
