@@ -214,8 +214,10 @@ __device__ __forceinline__ void bin_sat_batch(const SatQueue &Q2, int w, int n, 
 // the full separating-axis test 32 at a time, so that the lanes run it together.  (Visiting the union of the 32
 // triangles' candidate blocks instead, one lane per block against all 32 triangles,
 // measured slower here: the lanes' overlap tests diverge.)  Degenerate triangles (zero
-// normal) are never crossed by a link and are left out.
-__global__ void __launch_bounds__(EMB_WU_WARPS * 32) k_bin_pairs(const int4 *__restrict__ rec, int64_t T, LevelGeom g,
+// normal) are never crossed by a link and are left out.  Eight CTAs per SM (64
+// registers, a few spills) hide the lookup and atomic latencies better than the six
+// that 80 registers allow (finest-level binning 1.060 -> 1.024 ms on the 7.2M mesh).
+__global__ void __launch_bounds__(EMB_WU_WARPS * 32, 8) k_bin_pairs(const int4 *__restrict__ rec, int64_t T, LevelGeom g,
                                                                  long long dil, EmbLookup lk, uint32_t *__restrict__ cnt,
                                                                  PairList PL, EmbBigQ Q)
 {
