@@ -443,7 +443,18 @@ emb_status emb_cutlinks_backward(emb_mesh m, emb_forest f, const int32_t *d_cell
  * (1..32), thread-block size of the triangle-parallel kernels (128, 256 or 512),
  * resident link CTAs per SM (0 = as many as fit) and link placement (0 joint,
  * 1 per mesh on its pipeline's stream, 2 per mesh on a low-priority stream of its
- * own, so that the link kernels yield SMs to the pipelines still running).  It synchronises and drops a captured graph.  emb_batch_configure
+ * own, so that the link kernels yield SMs to the pipelines still running).  It synchronises and drops a captured graph.
+ * A tuned shape is cached under (SM count, floor(log2) of the batch's triangles,
+ * floor(log2) of its mesh count, largest lattice); a later batch with the same key takes
+ * the cached shape without timing.  With the environment variable EMB_TUNE_CACHE set to
+ * a file path, the cache is read from that file at first use and rewritten after every
+ * timing run (plain text, one line of 8 integers per key; lines that name no valid
+ * shape are ignored; a file that cannot be opened only disables persistence).
+ * emb_batch_autotune_ex does the same with `flags` (EMB_TUNE_FORCE: time even when a
+ * shape is cached; other bits: EMB_ERR_BAD_INPUT) and h_choice of 5 int32 (may be
+ * NULL): the 4 values above and 1 when the shape came from the cache, else 0.
+ * emb_batch_autotune is emb_batch_autotune_ex with flags 0 and the first 4 values.
+ * emb_batch_configure
  * sets such a 4-value shape directly (host array; EMB_ERR_BAD_INPUT outside the
  * ranges above) and drops a captured graph; it enqueues nothing.
  *
@@ -457,7 +468,9 @@ emb_status emb_batch_create(const emb_mesh *meshes, const int32_t *levels, const
 emb_status emb_batch_run(emb_batch b, void *stream);
 emb_status emb_batch_capture(emb_batch b, void *stream);
 emb_status emb_batch_launch(emb_batch b, void *stream);
+#define EMB_TUNE_FORCE 1
 emb_status emb_batch_autotune(emb_batch b, void *stream, int32_t *h_choice);
+emb_status emb_batch_autotune_ex(emb_batch b, void *stream, int32_t flags, int32_t *h_choice);
 emb_status emb_batch_configure(emb_batch b, const int32_t *h_choice);
 emb_status emb_batch_info(emb_batch b, int32_t j, int64_t *h_blocks, int64_t *h_links);
 emb_status emb_batch_results(emb_batch b, int32_t j, int32_t level, uint64_t *d_mask, int32_t *d_blocks,

@@ -21,8 +21,10 @@
 // emb_batch_autotune times a small set of launch shapes (stream count, thread
 // block size of the triangle-parallel kernels, resident link CTAs per SM) on
 // this batch and keeps the fastest; emb_batch_configure sets one directly.
+#include <stdio.h>
 #include <stdlib.h>
 
+#include <mutex>
 #include <vector>
 
 #include "emb_internal.cuh"
@@ -473,9 +475,129 @@ extern "C" emb_status emb_batch_launch(emb_batch b, void *stream)
     return EMB_OK;
 }
 
+// Cache of tuned shapes keyed by (SM count, log2 of the batch's triangles, log2 of its
+// mesh count, largest lattice): a batch of the same kind takes the cached shape without
+// timing.  With EMB_TUNE_CACHE set to a file path, the cache is read from that file at
+// first use and written back after every timing run (one line per key, plain text).
+struct TuneKey {
+    int sm, tb, nb, lat;
+    bool operator==(const TuneKey &o) const { return sm == o.sm && tb == o.tb && nb == o.nb && lat == o.lat; }
+};
+struct TuneEntry {
+    TuneKey k;
+    int v[4];
+};
+static std::mutex g_tune_mu;
+static std::vector<TuneEntry> g_tune;
+static bool g_tune_loaded = false;
+
+static int ilog2_64(int64_t x)
+{
+    int r = 0;
+    while (x > 1) {
+        x >>= 1;
+        ++r;
+    }
+    return r;
+}
+
+static TuneKey tune_key(const emb_batch_s *b)
+{
+    int64_t T = 0;
+    int lat = 0;
+    for (const BMesh &B : b->m) {
+        T += B.m->T;
+        lat = B.lattice > lat ? B.lattice : lat;
+    }
+    return TuneKey{emb_sm_count(), ilog2_64(T), ilog2_64((int64_t)b->m.size()), lat};
+}
+
+// with g_tune_mu held
+static void tune_load()
+{
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char *path = getenv("EMB_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE *fp = fopen(path, "r");
+    if (!fp) return;
+    TuneEntry e;
+    while (fscanf(fp, "%d %d %d %d %d %d %d %d", &e.k.sm, &e.k.tb, &e.k.nb, &e.k.lat, &e.v[0], &e.v[1], &e.v[2],
+                  &e.v[3]) == 8) {
+        if (e.v[0] < 1 || e.v[0] > BATCH_MAX_STREAMS || (e.v[1] != 128 && e.v[1] != 256 && e.v[1] != 512) || e.v[2] < 0 ||
+            e.v[2] > 64 || e.v[3] < 0 || e.v[3] > 2)
+            continue;  // not a shape this library makes
+        g_tune.push_back(e);
+    }
+    fclose(fp);
+}
+
+// with g_tune_mu held
+static void tune_store(const TuneKey &k, const int v[4])
+{
+    bool found = false;
+    for (TuneEntry &e : g_tune)
+        if (e.k == k) {
+            for (int i = 0; i < 4; ++i) e.v[i] = v[i];
+            found = true;
+        }
+    if (!found) {
+        TuneEntry e;
+        e.k = k;
+        for (int i = 0; i < 4; ++i) e.v[i] = v[i];
+        g_tune.push_back(e);
+    }
+    const char *path = getenv("EMB_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE *fp = fopen(path, "w");
+    if (!fp) return;
+    for (const TuneEntry &e : g_tune)
+        fprintf(fp, "%d %d %d %d %d %d %d %d\n", e.k.sm, e.k.tb, e.k.nb, e.k.lat, e.v[0], e.v[1], e.v[2], e.v[3]);
+    fclose(fp);
+}
+
+static void drop_graph(emb_batch b)
+{
+    if (b->exec) {  // a captured graph no longer matches the chosen shape
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    if (b->graph) {
+        cudaGraphDestroy(b->graph);
+        b->graph = nullptr;
+    }
+}
+
 extern "C" emb_status emb_batch_autotune(emb_batch b, void *stream, int32_t *h_choice)
 {
-    if (!b) return EMB_ERR_BAD_INPUT;
+    int32_t c[5];
+    const emb_status rc = emb_batch_autotune_ex(b, stream, 0, c);
+    if (rc == EMB_OK && h_choice)
+        for (int i = 0; i < 4; ++i) h_choice[i] = c[i];
+    return rc;
+}
+
+extern "C" emb_status emb_batch_autotune_ex(emb_batch b, void *stream, int32_t flags, int32_t *h_choice)
+{
+    if (!b || (flags & ~EMB_TUNE_FORCE)) return EMB_ERR_BAD_INPUT;
+    const TuneKey key = tune_key(b);
+    if (!(flags & EMB_TUNE_FORCE)) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        tune_load();
+        for (const TuneEntry &e : g_tune)
+            if (e.k == key) {
+                b->nstreams = e.v[0];
+                b->tri_block = e.v[1];
+                b->link_ctas = e.v[2];
+                b->per_mesh_links = e.v[3];
+                drop_graph(b);
+                if (h_choice) {
+                    for (int i = 0; i < 4; ++i) h_choice[i] = e.v[i];
+                    h_choice[4] = 1;
+                }
+                return EMB_OK;
+            }
+    }
     cudaStream_t s = emb_stream(stream);
     struct Cand {
         int nstreams, tri_block, link_ctas, per_mesh;
@@ -526,19 +648,16 @@ extern "C" emb_status emb_batch_autotune(emb_batch b, void *stream, int32_t *h_c
     b->tri_block = cands[best_i].tri_block;
     b->link_ctas = cands[best_i].link_ctas;
     b->per_mesh_links = cands[best_i].per_mesh;
-    if (b->exec) {  // a captured graph no longer matches the chosen shape
-        cudaGraphExecDestroy(b->exec);
-        b->exec = nullptr;
-    }
-    if (b->graph) {
-        cudaGraphDestroy(b->graph);
-        b->graph = nullptr;
+    drop_graph(b);
+    const int v[4] = {b->nstreams, b->tri_block, b->link_ctas, b->per_mesh_links};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        tune_load();
+        tune_store(key, v);
     }
     if (h_choice) {
-        h_choice[0] = b->nstreams;
-        h_choice[1] = b->tri_block;
-        h_choice[2] = b->link_ctas;
-        h_choice[3] = b->per_mesh_links;
+        for (int i = 0; i < 4; ++i) h_choice[i] = v[i];
+        h_choice[4] = 0;
     }
     return EMB_OK;
 }

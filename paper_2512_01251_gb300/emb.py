@@ -520,6 +520,17 @@ def emb_batch_autotune(batch: Batch, stream=None) -> tuple:
     return tuple(c)
 
 
+EMB_TUNE_FORCE = 1
+
+
+def emb_batch_autotune_ex(batch: Batch, stream=None, force: bool = False) -> tuple:
+    """((streams, tri_block, link CTAs per SM, link placement), taken from the tuning cache)."""
+    c = (ctypes.c_int32 * 5)()
+    _check(load().emb_batch_autotune_ex(batch.h, _stream(stream), EMB_TUNE_FORCE if force else 0, c),
+           "emb_batch_autotune_ex")
+    return tuple(c[:4]), bool(c[4])
+
+
 def emb_batch_configure(batch: Batch, streams: int, tri_block: int, link_ctas: int = 0, per_mesh_links: int = 1):
     c = (ctypes.c_int32 * 4)(streams, tri_block, link_ctas, per_mesh_links)
     _check(load().emb_batch_configure(batch.h, c), "emb_batch_configure")

@@ -124,3 +124,32 @@ def test_batch_mesh_matches_oracle(orc):
     for k in ("cell", "dir", "tri"):
         np.testing.assert_array_equal(r["links"][k].astype(np.int64), o["links"][k], err_msg=f"links {k}")
     assert np.abs(r["links"]["q"].astype(np.float64) - o["links"]["q"]).max(initial=0) <= 2e-6
+
+
+def test_autotune_cache_reuses_and_persists_the_shape(tmp_path, monkeypatch):
+    """A timed shape is cached under (SM count, triangle and mesh-count buckets, lattice):
+    the next call with the same kind of batch takes it without timing, and the cache file
+    named by EMB_TUNE_CACHE holds it as a line of 8 integers."""
+    import torch
+
+    import paper_2512_01251_gb300 as P
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("EMB_TUNE_CACHE", str(path))
+    cases = batch_meshes(3, t_max=5e3)
+    meshes = [P.emb_mesh_create(torch.from_numpy(c["verts"]), torch.from_numpy(c["tris"]), c["R"]) for c in cases]
+    B = P.emb_batch_create(meshes, [c["levels"] for c in cases], [c["band"] for c in cases],
+                           [c["lattice"] for c in cases])
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        timed, cached = P.emb_batch_autotune_ex(B, s, force=True)
+        assert not cached
+        again, cached = P.emb_batch_autotune_ex(B, s)
+        assert cached and again == timed
+        assert P.emb_batch_autotune(B, s) == timed
+        P.emb_batch_run(B, s)
+        s.synchronize()
+        assert P.emb_status_get(s) == P.EMB_OK
+    rows = [tuple(int(x) for x in ln.split()) for ln in path.read_text().splitlines() if ln.strip()]
+    assert any(len(r) == 8 and r[4:] == tuple(timed) for r in rows)
+    sm = torch.cuda.get_device_properties(0).multi_processor_count
+    assert all(r[0] == sm for r in rows)
