@@ -458,13 +458,29 @@ emb_status emb_cutlinks_backward(emb_mesh m, emb_forest f, const int32_t *d_cell
  * sets such a 4-value shape directly (host array; EMB_ERR_BAD_INPUT outside the
  * ranges above) and drops a captured graph; it enqueues nothing.
  *
+ * emb_batch_create_ex is emb_batch_create with `headroom` percent (0..1000) of room in
+ * the replay's buffers (a replay whose buffers carry headroom; moving geometry, Sec. 5).
+ * Every planned count becomes a capacity of count x (1 + headroom/100) + 64: flagged
+ * blocks per refined level (8 child blocks each), bin entries, blocks with links and
+ * links.  A replay then accepts any counts up to those capacities: each level's block
+ * count is formed and read on the device, and a count above its capacity sets
+ * EMB_ERR_CAPACITY (the results are then incomplete, never out of bounds).  With
+ * headroom 0 the counts must match the plan exactly (EMB_ERR_STATE otherwise).
+ * emb_batch_counts: the blocks per level (levels[j] + 1 int64) and links of mesh j in
+ * the last replay (host arrays, either may be NULL); with headroom they are read from the
+ * device, which synchronises `stream`.
+ *
  * emb_batch_info: planned blocks per level (levels[j] + 1 int64) and link count of
- * mesh j (host).  emb_batch_results copies mesh j's results of the last replay into
- * caller buffers (any pointer may be NULL): the solid mask words and block
- * coordinates (bx, by, bz int32) of `level`, and the cut-link table. */
+ * mesh j (host): the capacities of a batch with headroom.  emb_batch_results copies mesh
+ * j's results of the last replay into caller buffers (any pointer may be NULL), as many
+ * as emb_batch_counts reports: the solid mask words and block coordinates (bx, by, bz
+ * int32) of `level`, and the cut-link table. */
 typedef struct emb_batch_s *emb_batch;
 emb_status emb_batch_create(const emb_mesh *meshes, const int32_t *levels, const int32_t *bands,
                             const int32_t *lattices, int32_t n, void *stream, emb_batch *out);
+emb_status emb_batch_create_ex(const emb_mesh *meshes, const int32_t *levels, const int32_t *bands,
+                               const int32_t *lattices, int32_t n, int32_t headroom, void *stream, emb_batch *out);
+emb_status emb_batch_counts(emb_batch b, int32_t j, void *stream, int64_t *h_blocks, int64_t *h_links);
 emb_status emb_batch_run(emb_batch b, void *stream);
 emb_status emb_batch_capture(emb_batch b, void *stream);
 emb_status emb_batch_launch(emb_batch b, void *stream);

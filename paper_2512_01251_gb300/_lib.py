@@ -60,6 +60,8 @@ SIGNATURES = {
     "emb_batch_launch": (I32, [P, P]),
     "emb_batch_autotune": (I32, [P, P, P]),
     "emb_batch_autotune_ex": (I32, [P, P, I32, P]),
+    "emb_batch_create_ex": (I32, [P, P, P, P, I32, I32, P, ctypes.POINTER(P)]),
+    "emb_batch_counts": (I32, [P, I32, P, P, P]),
     "emb_batch_configure": (I32, [P, P]),
     "emb_batch_info": (I32, [P, I32, P, PI64]),
     "emb_batch_results": (I32, [P, I32, I32, P, P, P, P, P, P, P]),

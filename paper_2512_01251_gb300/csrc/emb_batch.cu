@@ -67,6 +67,7 @@ struct BMesh {
     uint8_t *o_dir = nullptr;
     float *o_q = nullptr;
     int64_t pairs = 0, nwork = 0, links = 0;
+    uint32_t *d_n = nullptr;                        // with headroom: blocks of each level in this replay
     std::vector<void *> owned;
 };
 
@@ -83,6 +84,7 @@ struct emb_batch_s {
     // kernels, link CTAs per SM (0 = as many as fit), link placement (0 joint, 1 per
     // mesh on its pipeline's stream, 2 per mesh on a low-priority stream of its own)
     int nstreams = 8, tri_block = 256, link_ctas = 0, per_mesh_links = 1;
+    int headroom = 0;  // percent of room above the planned counts (0: the counts must match the plan)
     int device = 0;
 };
 
@@ -158,10 +160,31 @@ static emb_status plan_mesh(BMesh &B, cudaStream_t s)
     return rc;
 }
 
+// With headroom h percent, the planned counts become capacities of count (1 + h / 100)
+// plus 64: flagged blocks per refined level (so 8 x that many child blocks), bin
+// entries, blocks with links, links.  The replay then reads each level's block count
+// on the device (lv.d_n) and checks every count against its capacity.
+static void headroom_caps(BMesh &B, int headroom)
+{
+    auto cap = [&](int64_t x) { return x + (x * headroom + 99) / 100 + 64; };
+    for (int L = 0; L < B.Lf; ++L) {
+        B.L[L].F = cap(B.L[L].F);
+        B.L[L + 1].lv.n = 8 * B.L[L].F;
+    }
+    B.pairs = cap(B.pairs);
+    B.links = cap(B.links);
+    B.nwork = cap(B.nwork);
+}
+
 // Allocates every buffer of a replay of mesh B.
-static emb_status alloc_mesh(BMesh &B)
+static emb_status alloc_mesh(BMesh &B, int headroom)
 {
     const int64_t T = B.m->T;
+    if (headroom > 0) {
+        headroom_caps(B, headroom);
+        BTRY(balloc(B, &B.d_n, EMB_MAX_LEVELS));
+        for (int L = 1; L <= B.Lf; ++L) B.L[L].lv.d_n = B.d_n + L;
+    }
     int64_t nmax = 1, wmax = 1;
     for (int L = 0; L <= B.Lf; ++L) {
         EmbLevel &lv = B.L[L].lv;
@@ -222,35 +245,57 @@ static emb_status alloc_mesh(BMesh &B)
     return EMB_OK;
 }
 
+// d_n = 8 x the flagged count of the parent level, capped at the level's capacity
+// (EMB_ERR_CAPACITY when the flagged blocks need more).
+__global__ void k_level_count(const uint32_t *__restrict__ nflags, int64_t cap, uint32_t *__restrict__ d_n, int *st)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const uint64_t n = 8ull * *nflags;
+    if (n > (uint64_t)cap) emb_set_status(st, EMB_ERR_CAPACITY);
+    *d_n = (uint32_t)(n < (uint64_t)cap ? n : (uint64_t)cap);
+}
+
+// EMB_ERR_CAPACITY when the pair list asked for more entries than it holds.
+__global__ void k_list_check(const unsigned long long *__restrict__ list_n, uint64_t cap, int *st)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0 && *list_n > cap) emb_set_status(st, EMB_ERR_CAPACITY);
+}
+
 // Enqueues the pipeline of mesh B up to (not including) the link kernel, on stream s.
 static emb_status enqueue_mesh(BMesh &B, int tri_block, cudaStream_t s)
 {
     const int4 *rec = B.m->rec;
     const int64_t T = B.m->T;
+    const bool hr = B.d_n != nullptr;  // headroom: counts up to capacity, read on the device
+    int *st = emb_status_word();
+    if (!st) return EMB_ERR_CUDA;
     BTRY(emb_enq_root_keys(B.R, B.L[0].lv.key, s));
     BTRY(emb_enq_level_index(B.L[0].lv, B.pc, B.tmp, s));
     for (int L = 0; L <= B.Lf; ++L) {
         BLevel &BL = B.L[L];
         EmbLevel &lv = BL.lv;
         const LevelGeom g = level_geom(&B.geo, L);
-        BTRY(emb_enq_filter(rec, T, g, B.flag, B.pos, BL.flist, B.tmp, tri_block, s, (uint64_t)BL.nf));
-        BTRY(emb_enq_voxelize(rec, T, BL.flist, BL.nf, B.pos + T, nullptr, g, lv, B.s_acc, B.p_acc, B.t_acc, B.bq, tri_block, s));
+        BTRY(emb_enq_filter(rec, T, g, B.flag, B.pos, BL.flist, B.tmp, tri_block, s, hr ? EMB_NO_EXPECT : (uint64_t)BL.nf));
+        BTRY(emb_enq_voxelize(rec, T, BL.flist, hr ? T : BL.nf, B.pos + T, nullptr, g, lv, B.s_acc, B.p_acc, B.t_acc, B.bq,
+                              tri_block, s));
         if (L < B.Lf) {
             const long long dil = emb_refine_dilation(&B.geo, L, B.band);
             if (dil < 0) return EMB_ERR_RANGE;
             BTRY(emb_enq_refine(rec, T, g, dil, lv, BL.flags, B.fbits, B.bq, s));
-            BTRY(emb_enq_flag_ranks(lv, BL.flags, B.cnt, B.rank, B.tmp, s, (uint64_t)BL.F));
+            BTRY(emb_enq_flag_ranks(lv, BL.flags, B.cnt, B.rank, B.tmp, s, hr ? EMB_NO_EXPECT : (uint64_t)BL.F));
             EmbLevel &C = B.L[L + 1].lv;
+            if (hr) EMB_LAUNCH((k_level_count), 1, 32, 0, s)(B.rank + lv.n, C.n, B.d_n + L + 1, st);
             BTRY(emb_enq_children(lv, BL.flags, B.rank, C.key, C.n, true, s));
             BTRY(emb_enq_level_index(C, B.pc, B.tmp, s));
         } else {
             BTRY(emb_enq_bin_pairs(rec, T, g, lv, B.cnt, B.bin_off, B.list_bs, B.list_tri, B.list_n, (uint64_t)B.pairs,
-                                   B.tmp, B.bq, s, (uint64_t)B.pairs));
+                                   B.tmp, B.bq, s, hr ? EMB_NO_EXPECT : (uint64_t)B.pairs));
+            if (hr) EMB_LAUNCH((k_list_check), 1, 32, 0, s)(B.list_n, (uint64_t)B.pairs, st);
             BTRY(emb_enq_bin_scatter(B.list_bs, B.list_tri, B.list_n, (uint64_t)B.pairs, B.bin_off, B.bin_ent,
                                      (uint64_t)B.pairs, s));
             BTRY(emb_enq_neighbors(lv, s));
             BTRY(emb_enq_link_prep(lv, B.lattice, B.cand, B.cnt, B.rank, B.work_n, B.work, B.blk_off, B.tmp, s,
-                                   (uint64_t)B.nwork, (uint64_t)B.links));
+                                   hr ? EMB_NO_EXPECT : (uint64_t)B.nwork, hr ? EMB_NO_EXPECT : (uint64_t)B.links));
             BTRY(emb_enq_link_split(lv, B.work, B.work_n + lv.n, B.cand, B.blk_off, B.bin_off, B.witem, B.extra,
                                     B.extra_n, (uint32_t)emb_link_extra_capacity(lv.n), s));
         }
@@ -287,10 +332,20 @@ extern "C" void emb_batch_destroy(emb_batch b)
 extern "C" emb_status emb_batch_create(const emb_mesh *meshes, const int32_t *levels, const int32_t *bands,
                                        const int32_t *lattices, int32_t n, void *stream, emb_batch *out)
 {
-    if (!out || !meshes || !levels || !bands || !lattices || n < 1 || n > EMB_MAX_BATCH) return EMB_ERR_BAD_INPUT;
+    return emb_batch_create_ex(meshes, levels, bands, lattices, n, 0, stream, out);
+}
+
+extern "C" emb_status emb_batch_create_ex(const emb_mesh *meshes, const int32_t *levels, const int32_t *bands,
+                                          const int32_t *lattices, int32_t n, int32_t headroom, void *stream,
+                                          emb_batch *out)
+{
+    if (!out || !meshes || !levels || !bands || !lattices || n < 1 || n > EMB_MAX_BATCH || headroom < 0 ||
+        headroom > 1000)
+        return EMB_ERR_BAD_INPUT;
     *out = nullptr;
     cudaStream_t s = emb_stream(stream);
     emb_batch b = new emb_batch_s();
+    b->headroom = headroom;
     cudaGetDevice(&b->device);
     b->m.resize(n);
     emb_status rc = EMB_OK;
@@ -307,7 +362,7 @@ extern "C" emb_status emb_batch_create(const emb_mesh *meshes, const int32_t *le
         B.band = bands[j];
         B.lattice = lattices[j];
         rc = plan_mesh(B, s);
-        if (rc == EMB_OK) rc = alloc_mesh(B);
+        if (rc == EMB_OK) rc = alloc_mesh(B, b->headroom);
     }
     if (rc == EMB_OK && cudaMalloc(&b->next, sizeof(unsigned int)) != cudaSuccess) rc = EMB_ERR_CUDA;
     if (rc == EMB_OK) rc = emb_link_emit_init();  // kernel attributes are set outside of any capture
@@ -690,6 +745,35 @@ extern "C" emb_status emb_batch_info(emb_batch b, int32_t j, int64_t *h_blocks, 
     return EMB_OK;
 }
 
+// Counts of mesh j in the last replay: blocks per level and links.  With headroom they
+// are read from the device (this synchronises `stream`); otherwise they are the plan.
+static emb_status replay_counts(const BMesh &B, cudaStream_t s, int64_t *blocks, int64_t *links)
+{
+    for (int L = 0; L <= B.Lf; ++L) blocks[L] = B.L[L].lv.n;
+    *links = B.links;
+    if (!B.d_n) return EMB_OK;
+    uint32_t h[EMB_MAX_LEVELS + 1];
+    const EmbLevel &fin = B.L[B.Lf].lv;
+    if (B.Lf > 0) EMB_CUDA_TRY(cudaMemcpyAsync(h + 1, B.d_n + 1, B.Lf * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    EMB_CUDA_TRY(cudaMemcpyAsync(h + EMB_MAX_LEVELS, B.blk_off + fin.n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    EMB_CUDA_TRY(cudaStreamSynchronize(s));
+    for (int L = 1; L <= B.Lf; ++L) blocks[L] = h[L] < (uint64_t)B.L[L].lv.n ? h[L] : B.L[L].lv.n;
+    *links = h[EMB_MAX_LEVELS] < (uint64_t)B.links ? h[EMB_MAX_LEVELS] : B.links;
+    return EMB_OK;
+}
+
+extern "C" emb_status emb_batch_counts(emb_batch b, int32_t j, void *stream, int64_t *h_blocks, int64_t *h_links)
+{
+    if (!b || j < 0 || j >= (int32_t)b->m.size()) return EMB_ERR_BAD_INPUT;
+    const BMesh &B = b->m[j];
+    int64_t blocks[EMB_MAX_LEVELS], links = 0;
+    BTRY(replay_counts(B, emb_stream(stream), blocks, &links));
+    if (h_blocks)
+        for (int L = 0; L <= B.Lf; ++L) h_blocks[L] = blocks[L];
+    if (h_links) *h_links = links;
+    return EMB_OK;
+}
+
 extern "C" emb_status emb_batch_results(emb_batch b, int32_t j, int32_t level, uint64_t *d_mask, int32_t *d_blocks,
                                         int32_t *d_cell, uint8_t *d_dir, float *d_q, int32_t *d_tri, void *stream)
 {
@@ -697,7 +781,10 @@ extern "C" emb_status emb_batch_results(emb_batch b, int32_t j, int32_t level, u
     const BMesh &B = b->m[j];
     if (level < 0 || level > B.Lf) return EMB_ERR_BAD_INPUT;
     cudaStream_t s = emb_stream(stream);
-    const EmbLevel &lv = B.L[level].lv;
+    int64_t cnt_blocks[EMB_MAX_LEVELS], cnt_links = 0;
+    BTRY(replay_counts(B, s, cnt_blocks, &cnt_links));
+    EmbLevel lv = B.L[level].lv;  // a view: n becomes this replay's count
+    lv.n = cnt_blocks[level];
     if (d_mask && lv.n)
         EMB_CUDA_TRY(cudaMemcpyAsync(d_mask, lv.mask, lv.n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
     if (d_blocks && lv.n) {
@@ -709,7 +796,7 @@ extern "C" emb_status emb_batch_results(emb_batch b, int32_t j, int32_t level, u
         tmp.lv[level] = EmbLevel();  // not owned
         BTRY(rc);
     }
-    const size_t n = (size_t)B.links;
+    const size_t n = (size_t)cnt_links;
     if (d_cell && n) EMB_CUDA_TRY(cudaMemcpyAsync(d_cell, B.o_cell, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
     if (d_dir && n) EMB_CUDA_TRY(cudaMemcpyAsync(d_dir, B.o_dir, n, cudaMemcpyDeviceToDevice, s));
     if (d_q && n) EMB_CUDA_TRY(cudaMemcpyAsync(d_q, B.o_q, n * sizeof(float), cudaMemcpyDeviceToDevice, s));

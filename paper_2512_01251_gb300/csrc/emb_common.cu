@@ -297,10 +297,10 @@ emb_status emb_scan_u32(const uint32_t *d_in, uint32_t *d_out, int64_t n, uint64
 // level hash and neighbour table
 // ---------------------------------------------------------------------------
 __global__ void k_hash_insert(const uint64_t *__restrict__ key, int64_t n, uint64_t *hkey, int32_t *hval, int64_t hcap,
-                              int *st)
+                              int *st, const uint32_t *d_n)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= emb_count(n, d_n)) return;
     uint64_t k = key[i];
     uint64_t m = (uint64_t)hcap - 1, s = emb_hash_mix(k) & m;
     for (int64_t it = 0; it < hcap; ++it) {
@@ -315,10 +315,11 @@ __global__ void k_hash_insert(const uint64_t *__restrict__ key, int64_t n, uint6
     emb_set_status(st, EMB_ERR_STATE);  // table full: cannot happen with capacity >= 2n
 }
 
-__global__ void k_bits_set(const uint64_t *__restrict__ key, int64_t n, int64_t nb, unsigned long long *__restrict__ bits)
+__global__ void k_bits_set(const uint64_t *__restrict__ key, int64_t n, int64_t nb, unsigned long long *__restrict__ bits,
+                           const uint32_t *d_n)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= emb_count(n, d_n)) return;
     uint64_t k = key[i];
     int64_t bx = (int64_t)(k & EMB_KEY_MASK), by = (int64_t)((k >> EMB_KEY_BITS) & EMB_KEY_MASK),
             bz = (int64_t)(k >> (2 * EMB_KEY_BITS));
@@ -373,11 +374,12 @@ emb_status emb_enq_level_index(EmbLevel &lv, uint32_t *pc, uint64_t *tmp, cudaSt
     if (!(lv.bits && nw > 0)) {
         EMB_CUDA_TRY(cudaMemsetAsync(lv.hkey, 0xFF, lv.hcap * sizeof(uint64_t), s));
         if (lv.n > 0)
-            EMB_LAUNCH((k_hash_insert), emb_grid(lv.n, 256), 256, 0, s)(lv.key, lv.n, lv.hkey, lv.hval, lv.hcap, st);
+            EMB_LAUNCH((k_hash_insert), emb_grid(lv.n, 256), 256, 0, s)(lv.key, lv.n, lv.hkey, lv.hval, lv.hcap, st, lv.d_n);
     } else {
         EMB_CUDA_TRY(cudaMemsetAsync(lv.bits, 0, nw * sizeof(uint64_t), s));
         if (lv.n > 0)
-            EMB_LAUNCH((k_bits_set), emb_grid(lv.n, 256), 256, 0, s)(lv.key, lv.n, lv.nb_axis, (unsigned long long *)lv.bits);
+            EMB_LAUNCH((k_bits_set), emb_grid(lv.n, 256), 256, 0, s)(lv.key, lv.n, lv.nb_axis, (unsigned long long *)lv.bits,
+                                                                     lv.d_n);
         EMB_LAUNCH((k_word_popc), emb_grid(nw, 256), 256, 0, s)(lv.bits, nw, pc);
         emb_status rc = emb_scan_into(pc, lv.wpre, nw, tmp, s);
         if (rc != EMB_OK) return rc;
@@ -510,10 +512,11 @@ emb_status emb_build_hash(EmbLevel &lv, cudaStream_t s)
     return rc;
 }
 
-__global__ void k_neighbors(const uint64_t *__restrict__ key, int64_t n, int64_t nb, EmbLookup lk, int32_t *__restrict__ nbr)
+__global__ void k_neighbors(const uint64_t *__restrict__ key, int64_t n, int64_t nb, EmbLookup lk, int32_t *__restrict__ nbr,
+                            const uint32_t *d_n)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n * 26) return;
+    if (i >= emb_count(n, d_n) * 26) return;
     int64_t b = i / 26;
     int d = (int)(i % 26) + 1;
     uint64_t k = key[b];
@@ -530,7 +533,8 @@ __global__ void k_neighbors(const uint64_t *__restrict__ key, int64_t n, int64_t
 emb_status emb_enq_neighbors(EmbLevel &lv, cudaStream_t s)
 {
     if (lv.n > 0)
-        EMB_LAUNCH((k_neighbors), emb_grid(lv.n * 26, 256), 256, 0, s)(lv.key, lv.n, lv.nb_axis, emb_lookup_of(lv), lv.nbr);
+        EMB_LAUNCH((k_neighbors), emb_grid(lv.n * 26, 256), 256, 0, s)(lv.key, lv.n, lv.nb_axis, emb_lookup_of(lv), lv.nbr,
+                                                                               lv.d_n);
     EMB_CUDA_TRY(cudaGetLastError());
     return EMB_OK;
 }

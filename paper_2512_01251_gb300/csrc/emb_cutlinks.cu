@@ -43,10 +43,10 @@ __device__ __forceinline__ uint64_t shift_axis(uint64_t cur, uint64_t nxt, int a
 // a fluid cell with a solid neighbour is within one link of the surface, and the
 // refine rule makes every block within that reach exist.
 __global__ void k_link_cand(const uint64_t *__restrict__ mask, const int32_t *__restrict__ nbr, int64_t n, int lattice,
-                            uint64_t *__restrict__ cand, uint32_t *__restrict__ blk_cnt, int *st)
+                            uint64_t *__restrict__ cand, uint32_t *__restrict__ blk_cnt, int *st, const uint32_t *d_n)
 {
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= n) return;
+    if (b >= emb_count(n, d_n)) return;
     uint64_t W[27];  // mask words by offset code (ox+1) + 3(oy+1) + 9(oz+1)
     W[13] = mask[b];
 #pragma unroll
@@ -888,7 +888,7 @@ emb_status emb_enq_link_prep(const EmbLevel &lv, int lattice, uint64_t *cand, ui
     EMB_CUDA_TRY(cudaMemsetAsync(flag, 0, (lv.n + 1) * sizeof(uint32_t), s));
     if (lv.n > 0) {
         EMB_LAUNCH((k_link_cand), emb_grid(lv.n, 128), 128, 0, s)(lv.mask, lv.nbr, lv.n, lattice, cand, cnt,
-                                                                  emb_status_word());
+                                                                  emb_status_word(), lv.d_n);
         EMB_LAUNCH((k_nonempty), emb_grid(lv.n, 256), 256, 0, s)(cnt, lv.n, flag);
     }
     emb_status rc = emb_scan_into_expect(flag, work_n, lv.n, tmp, expect_work, s);

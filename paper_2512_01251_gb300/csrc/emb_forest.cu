@@ -132,13 +132,17 @@ emb_status emb_enq_flag_ranks(const EmbLevel &P, const uint8_t *d_flags, uint32_
     return emb_scan_into_expect(cnt, rank, P.n, tmp, expect, s);
 }
 
-// Keys [8 F, Cn) of a planned replay that flagged fewer blocks than its plan: the
-// in-range key 0, so that every later pass over the level stays in bounds (the
-// count check of the replay reports the difference).
+// Keys [8 F, Cn) of a planned replay that flagged fewer blocks than its buffers hold
+// (a replay with headroom, or one whose counts left its plan): a key above every real
+// key, so that the level's keys stay sorted for the binary searches over all Cn of
+// them; its coordinates (2^21 - 1 on every axis) fail the range checks of the passes
+// that decode keys, and the passes over blocks stop at the device count where there
+// is one.
+#define EMB_KEY_TAIL 0x7FFFFFFFFFFFFFFFull
 __global__ void k_key_tail(uint64_t *__restrict__ ckey, int64_t Cn, const uint32_t *__restrict__ nflags)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < Cn && i >= 8 * (int64_t)*nflags) ckey[i] = 0;
+    if (i < Cn && i >= 8 * (int64_t)*nflags) ckey[i] = EMB_KEY_TAIL;
 }
 
 emb_status emb_enq_children(const EmbLevel &P, const uint8_t *d_flags, const uint32_t *rank, uint64_t *ckey, int64_t Cn,

@@ -93,7 +93,15 @@ struct EmbLevel {
     uint64_t *bits = nullptr;
     uint32_t *wpre = nullptr;  // exclusive popcount prefix per 64-bit word
     int mask_valid = 0;
+    // a replay with headroom: n is the capacity, *d_n (device) the blocks of this replay;
+    // passes over the level's blocks stop at min(n, *d_n)
+    const uint32_t *d_n = nullptr;
 };
+
+__device__ __forceinline__ int64_t emb_count(int64_t n, const uint32_t *d_n)
+{
+    return d_n && (int64_t)*d_n < n ? (int64_t)*d_n : n;
+}
 
 #define EMB_BITMAP_MAX_BITS (1ll << 32)
 

@@ -189,9 +189,10 @@ __device__ __forceinline__ unsigned long long spread_lines(unsigned int p)
 
 __global__ void k_xscan(const uint64_t *__restrict__ key, int64_t n, const unsigned long long *__restrict__ s_acc,
                         const unsigned int *__restrict__ p_acc, const unsigned int *__restrict__ t_acc,
-                        uint64_t *__restrict__ mask)
+                        uint64_t *__restrict__ mask, const uint32_t *d_n)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    n = emb_count(n, d_n);
     if (i >= n) return;
     uint64_t row = key[i] >> EMB_KEY_BITS;
     if (i + 1 < n && (key[i + 1] >> EMB_KEY_BITS) == row) return;  // only the row's last (+x-most) block walks
@@ -223,7 +224,7 @@ emb_status emb_enq_voxelize(const int4 *rec, int64_t T, const uint32_t *flist, i
         EMB_LAUNCH((k_vox), (int)grid, block, 0, s)(rec, T, flist, nf, d_nf, keep, g, lk, acc, Q, st);
         if (Q.cap) EMB_LAUNCH((k_vox_big), EMB_BIG_GRID, EMB_BIG_BLOCK, 0, s)(rec, g, lk, acc, Q, st);
     }
-    EMB_LAUNCH((k_xscan), emb_grid(lv.n, 256), 256, 0, s)(lv.key, lv.n, s_acc, p_acc, t_acc, lv.mask);
+    EMB_LAUNCH((k_xscan), emb_grid(lv.n, 256), 256, 0, s)(lv.key, lv.n, s_acc, p_acc, t_acc, lv.mask, lv.d_n);
     EMB_CUDA_TRY(cudaGetLastError());
     return EMB_OK;
 }

@@ -488,17 +488,31 @@ def reembed_window(E: Embedding, verts: torch.Tensor, changed: tuple, band: int 
 # --------------------------------------------------------------------------- #
 # batches of meshes
 # --------------------------------------------------------------------------- #
-def emb_batch_create(meshes: list, levels: list, bands: list, lattices: list, stream=None) -> Batch:
+def emb_batch_create(meshes: list, levels: list, bands: list, lattices: list, stream=None, headroom: int = 0) -> Batch:
+    """Plan a batch; headroom (percent) gives the replay's buffers room above the planned
+    counts, so that geometry that moves can be replayed without a new plan."""
     n = len(meshes)
     arr = (ctypes.c_void_p * n)(*[m.h for m in meshes])
     lv = (ctypes.c_int32 * n)(*levels)
     bd = (ctypes.c_int32 * n)(*bands)
     lt = (ctypes.c_int32 * n)(*lattices)
     h = ctypes.c_void_p()
-    _check(load().emb_batch_create(arr, lv, bd, lt, n, _stream(stream), ctypes.byref(h)), "emb_batch_create")
+    if headroom:
+        _check(load().emb_batch_create_ex(arr, lv, bd, lt, n, int(headroom), _stream(stream), ctypes.byref(h)),
+               "emb_batch_create_ex")
+    else:
+        _check(load().emb_batch_create(arr, lv, bd, lt, n, _stream(stream), ctypes.byref(h)), "emb_batch_create")
     b = Batch(h, keep=tuple(meshes))
-    b.levels, b.lattices, b.n = list(levels), list(lattices), n
+    b.levels, b.lattices, b.n, b.headroom = list(levels), list(lattices), n, int(headroom)
     return b
+
+
+def emb_batch_counts(batch: Batch, j: int, stream=None):
+    """(blocks per level, links) of mesh j in the last replay."""
+    blocks = (ctypes.c_int64 * (batch.levels[j] + 1))()
+    links = ctypes.c_int64(0)
+    _check(load().emb_batch_counts(batch.h, int(j), _stream(stream), blocks, ctypes.byref(links)), "emb_batch_counts")
+    return list(blocks), links.value
 
 
 def emb_batch_run(batch: Batch, stream=None):
@@ -545,7 +559,7 @@ def emb_batch_info(batch: Batch, j: int):
 
 def emb_batch_results(batch: Batch, j: int, stream=None) -> dict:
     """Mesh j of the last replay: per level (blocks, masks), and its cut-link table."""
-    blocks, n = emb_batch_info(batch, j)
+    blocks, n = emb_batch_counts(batch, j, stream)
     out = dict(blocks=[], masks=[])
     for L, nb in enumerate(blocks):
         m = torch.empty(max(nb, 1), dtype=torch.int64, device="cuda")

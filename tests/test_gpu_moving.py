@@ -161,3 +161,52 @@ def test_batch_replay_reports_changed_counts_and_replans():
         assert P.emb_status_get(s) == P.EMB_OK
         got = _batch_result(P, B2, 0)
     _same(got, _result(P, _embed(P, v1, t0, R0, lv0, 19)), "re-planned mesh")
+
+
+def test_headroom_replay_follows_changed_counts_without_replanning():
+    """A batch planned with headroom replays a body that grows, shrinks and moves: its
+    block, bin and link counts change, the replay (also as one captured graph, launched
+    after each move) stays exact against the per-call path, and a body that outgrows the
+    capacities is reported as EMB_ERR_CAPACITY on the device, in bounds."""
+    import torch
+
+    import paper_2512_01251_gb300 as P
+    specs = [(icosphere(3, radius=0.15, centre=(0.5, 0.5, 0.5)), 8, 3),
+             (icosphere(3, radius=0.2, centre=(0.48, 0.52, 0.5)), 12, 2)]
+    meshes = [P.emb_mesh_create(torch.from_numpy(v), torch.from_numpy(t), R) for (v, t), R, _ in specs]
+    B = P.emb_batch_create(meshes, [lv for _, _, lv in specs], [2] * 2, [19] * 2, headroom=60)
+    planned = P.emb_batch_info(B, 0)
+    (v0, t0), R0, lv0 = specs[0]
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        P.emb_batch_capture(B, s)
+        seen = set()
+        for k, f in enumerate((1.0, 1.12, 0.9, 1.05)):
+            v1 = snap((v0 - 0.5) * f + 0.5 + np.array([0.01 * k, 0.0, -0.01 * k]))
+            P.emb_mesh_update(meshes[0], torch.from_numpy(v1), s)
+            if k % 2:
+                P.emb_batch_launch(B, s)  # the same graph for every count
+            else:
+                P.emb_batch_run(B, s)
+            s.synchronize()
+            assert P.emb_status_get(s) == P.EMB_OK, f
+            ref = _result(P, _embed(P, v1, t0, R0, lv0, 19))
+            _same(_batch_result(P, B, 0), ref, f"scale {f}")
+            blocks, links = P.emb_batch_counts(B, 0, s)
+            assert blocks == [len(b) for b in ref["blocks"]] and links == len(ref["links"]["q"])
+            seen.add((tuple(blocks), links))
+        assert len(seen) > 1  # the counts did change
+        (v, t), R, lv = specs[1]  # the other mesh did not move
+        _same(_batch_result(P, B, 1), _result(P, _embed(P, v, t, R, lv, 19)), "mesh 1")
+        # far beyond the capacities: reported, not faulted, and the context stays usable
+        v2 = snap((v0 - 0.5) * 2.2 + 0.5)
+        P.emb_mesh_update(meshes[0], torch.from_numpy(v2), s)
+        P.emb_batch_launch(B, s)
+        s.synchronize()
+        assert P.emb_status_get(s) == P.EMB_ERR_CAPACITY
+        P.emb_mesh_update(meshes[0], torch.from_numpy(snap(v0)), s)
+        P.emb_batch_run(B, s)
+        s.synchronize()
+        assert P.emb_status_get(s) == P.EMB_OK
+    assert P.emb_batch_info(B, 0) == planned
+    _same(_batch_result(P, B, 0), _result(P, _embed(P, snap(v0), t0, R0, lv0, 19)), "back to the start")
