@@ -211,7 +211,8 @@ emb_status emb_bins_copy(emb_bins b, uint32_t *d_filtered, uint32_t *d_off, uint
  * A segmented suffix-XOR of the line parities along each (y, z) row of blocks
  * then completes every line (the role of the external propagation of Alg. 4).
  * Writes one uint64 per level block (bit t = cell t solid) into d_solid_mask
- * (may be NULL) and keeps a copy in the forest.
+ * (may be NULL; device memory or page-locked host memory, EMB_ERR_BAD_INPUT for
+ * pageable memory) and keeps a copy in the forest.
  * Exact for any forest: a crossing inside a block position the level does not have
  * (a region left coarser) is carried along its row to the blocks on its left.
  * Errors: EMB_ERR_STATE (bins of another level, missing level). */
@@ -333,7 +334,11 @@ emb_status emb_cutlinks_count(emb_forest f, int32_t lattice, int64_t *h_count, v
  * receives the required size and the device status becomes EMB_ERR_CAPACITY.
  * A finest-level bin may hold at most 2^24 triangles (16,777,216 faces overlapping
  * one block); the links of a block with a larger bin are not written and the device
- * status becomes EMB_ERR_CAPACITY (refine further so that the bins shrink). */
+ * status becomes EMB_ERR_CAPACITY (refine further so that the bins shrink).
+ * The five output buffers may be device memory or page-locked host memory (e.g.
+ * cudaHostAlloc): the kernel then writes the table straight into host memory over the
+ * host link, with no copy after it.  Any other host memory (pageable) is refused with
+ * EMB_ERR_BAD_INPUT before anything is enqueued. */
 emb_status emb_cutlinks(emb_forest f, emb_bins b, int32_t lattice, int32_t *d_cell, uint8_t *d_dir,
                         float *d_q, int32_t *d_tri, int64_t capacity, int64_t *d_count, void *stream);
 

@@ -421,6 +421,30 @@ emb_status emb_build_index_counted(EmbLevel &lv, const uint32_t *nflags, int64_t
     return EMB_OK;
 }
 
+// The address a kernel uses for a caller's output buffer: device (or managed) memory as
+// it is, page-locked host memory through its device mapping (the kernel then writes
+// over the host link); pageable host memory, or an address the runtime does not know,
+// is refused before anything is enqueued.
+emb_status emb_device_view(void *p, void **dp)
+{
+    *dp = nullptr;
+    if (!p) return EMB_OK;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return EMB_ERR_BAD_INPUT;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) {
+        *dp = p;
+        return EMB_OK;
+    }
+    if (a.type == cudaMemoryTypeHost && a.devicePointer) {
+        *dp = a.devicePointer;
+        return EMB_OK;
+    }
+    return EMB_ERR_BAD_INPUT;
+}
+
 // Pinned host words for small count read-backs, each with an event that marks when the
 // copy into it has landed (a slab shared by all forests; slots are reused after release).
 #define EMB_RB_SLOTS 1024

@@ -1046,6 +1046,20 @@ extern "C" emb_status emb_cutlinks(emb_forest f, emb_bins b, int32_t lattice, in
 {
     if (!f || !b || (lattice != 19 && lattice != 27) || capacity < 0) return EMB_ERR_BAD_INPUT;
     if (b->f != f || b->level != f->max_level || f->top != f->max_level) return EMB_ERR_STATE;
+    {
+        // the outputs may be page-locked host memory: the kernel then writes the table
+        // straight over the host link, with no copy after it
+        void *v[5];
+        if (emb_device_view(d_cell, &v[0]) != EMB_OK || emb_device_view(d_dir, &v[1]) != EMB_OK ||
+            emb_device_view(d_q, &v[2]) != EMB_OK || emb_device_view(d_tri, &v[3]) != EMB_OK ||
+            emb_device_view(d_count, &v[4]) != EMB_OK)
+            return EMB_ERR_BAD_INPUT;
+        d_cell = (int32_t *)v[0];
+        d_dir = (uint8_t *)v[1];
+        d_q = (float *)v[2];
+        d_tri = (int32_t *)v[3];
+        d_count = (int64_t *)v[4];
+    }
     cudaStream_t s = emb_stream(stream);
     if (f->lv[f->max_level].n == 0) {
         // an empty finest level (nothing was refined down to it): no links

@@ -216,6 +216,9 @@ int64_t emb_bitmap_words(int64_t nb);
 emb_status emb_enq_level_index(EmbLevel &lv, uint32_t *pc, uint64_t *tmp, cudaStream_t s);
 emb_status emb_build_hash(EmbLevel &lv, cudaStream_t s);
 emb_status emb_build_index_counted(EmbLevel &lv, const uint32_t *nflags, int64_t cap, cudaStream_t s);
+// Device address of a caller output buffer (device memory, or page-locked host memory
+// through its mapping); EMB_ERR_BAD_INPUT for pageable memory.  NULL stays NULL.
+emb_status emb_device_view(void *p, void **dp);
 // A pinned host slot (8 words) and its event for a count read-back; -1 when none is free.
 int emb_readback_acquire(uint64_t **h, cudaEvent_t *ev);
 void emb_readback_release(int slot);

@@ -233,6 +233,8 @@ extern "C" emb_status emb_voxelize(emb_forest f, emb_bins b, int32_t level, uint
 {
     if (!f || !b) return EMB_ERR_BAD_INPUT;
     if (b->f != f || b->level != level || level < 0 || level > f->top) return EMB_ERR_STATE;
+    void *mask_out = nullptr;
+    if (emb_device_view(d_solid_mask, &mask_out) != EMB_OK) return EMB_ERR_BAD_INPUT;
     cudaStream_t s = emb_stream(stream);
     EmbLevel &lv = f->lv[level];
     LevelGeom g = level_geom(f, level);
@@ -254,8 +256,8 @@ extern "C" emb_status emb_voxelize(emb_forest f, emb_bins b, int32_t level, uint
                           g, lv, s_acc, p_acc, t_acc, Q, 128, s);
     emb_bigq_free(Q, s);
     if (rc != EMB_OK) return rc;
-    if (d_solid_mask)
-        EMB_CUDA_TRY(cudaMemcpyAsync(d_solid_mask, lv.mask, lv.n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+    if (mask_out)  // device memory, or page-locked host memory (an asynchronous copy over the host link)
+        EMB_CUDA_TRY(cudaMemcpyAsync(mask_out, lv.mask, lv.n * sizeof(uint64_t), cudaMemcpyDefault, s));
     EMB_CUDA_TRY(cudaFreeAsync(s_acc, s));
     EMB_CUDA_TRY(cudaFreeAsync(p_acc, s));
     EMB_CUDA_TRY(cudaFreeAsync(t_acc, s));

@@ -48,6 +48,16 @@ def _ptr(t: torch.Tensor | None):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _out_ptr(t: torch.Tensor | None):
+    """An output buffer: a CUDA tensor, or a host tensor that the library checks (it takes
+    page-locked host memory and refuses pageable memory)."""
+    if t is None:
+        return None
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
 def _stream(stream=None):
     s = stream if stream is not None else torch.cuda.current_stream()
     return ctypes.c_void_p(s.cuda_stream)
@@ -225,10 +235,13 @@ def emb_bins_copy(bins: Bins, forest: Forest | None = None, stream=None) -> dict
 
 def emb_voxelize(forest: Forest, bins: Bins, level: int, out: torch.Tensor | None = None, stream=None):
     """Solid mask words of `level` (int64 tensor holding the uint64 bit patterns)."""
+    n = emb_forest_num_blocks(forest, level)
     if out is None:
-        out = torch.empty(emb_forest_num_blocks(forest, level), dtype=torch.int64, device="cuda")
-    _check(load().emb_voxelize(forest.h, bins.h, int(level), _ptr(out), _stream(stream)), "emb_voxelize")
-    return out
+        out = torch.empty(n, dtype=torch.int64, device="cuda")
+    elif out.numel() < n:
+        raise EmbError(EMB_ERR_CAPACITY, "emb_voxelize: the output holds fewer words than the level has blocks")
+    _check(load().emb_voxelize(forest.h, bins.h, int(level), _out_ptr(out), _stream(stream)), "emb_voxelize")
+    return out[:n]
 
 
 def emb_voxelize_guard(forest: Forest, bins: Bins, out_solid: torch.Tensor | None = None,
@@ -280,8 +293,9 @@ def emb_cutlinks(forest: Forest, bins: Bins, lattice: int, capacity: int | None 
                    q=torch.empty(max(capacity, 1), dtype=torch.float32, device="cuda"),
                    tri=torch.empty(max(capacity, 1), dtype=torch.int32, device="cuda"),
                    count=torch.zeros(1, dtype=torch.int64, device="cuda"))
-    rc = load().emb_cutlinks(forest.h, bins.h, int(lattice), _ptr(out["cell"]), _ptr(out["dir"]), _ptr(out["q"]),
-                             _ptr(out["tri"]), int(capacity), _ptr(out["count"]), _stream(stream))
+    rc = load().emb_cutlinks(forest.h, bins.h, int(lattice), _out_ptr(out["cell"]), _out_ptr(out["dir"]),
+                             _out_ptr(out["q"]), _out_ptr(out["tri"]), int(capacity), _out_ptr(out["count"]),
+                             _stream(stream))
     _check(rc, "emb_cutlinks")
     n = capacity
     return {k: (v[:n] if k != "count" else v) for k, v in out.items()}
@@ -370,13 +384,17 @@ class Embedding:
 def embed(verts: torch.Tensor, tris: torch.Tensor, R: int, levels: int, band: int = 2, lattice: int = 19,
           check_watertight: bool = True, mesh: Mesh | None = None, keep_bins: bool = False,
           check_status: bool = True, stream=None, bin_mode: int = EMB_BIN_FILTER_COMPACT,
-          d_spec: float | None = None) -> Embedding:
+          d_spec: float | None = None, links_out: dict | None = None,
+          finest_mask_out: torch.Tensor | None = None) -> Embedding:
     """Embed a closed mesh into a forest with root R^3 blocks and levels 0..levels.
 
     Per level: emb_bin, emb_voxelize, then (below the finest level)
     emb_refine_flags and emb_forest_refine; at the finest level the cut-link
     table of `lattice` (19 or 27).  With d_spec, the refinement follows the
     paper's block-layer rules (emb_refine_flags_paper) instead of `band`.
+    links_out (cell, dir, q, tri int tensors and a count int64 tensor, each large enough)
+    and finest_mask_out receive the link table and the finest solid mask; they may be
+    page-locked host tensors, which the library then fills over the host link.
     """
     if mesh is None:
         mesh = emb_mesh_create(verts, tris, R, check_watertight, stream)
@@ -384,14 +402,20 @@ def embed(verts: torch.Tensor, tris: torch.Tensor, R: int, levels: int, band: in
     E = Embedding(mesh=mesh, forest=forest, levels=levels, lattice=lattice)
     for L in range(levels + 1):
         bins = emb_bin(mesh, forest, L, lattice, stream, mode=bin_mode)
-        E.masks.append(emb_voxelize(forest, bins, L, stream=stream))
+        E.masks.append(emb_voxelize(forest, bins, L, out=finest_mask_out if L == levels else None, stream=stream))
         if L < levels:
             fl = (emb_refine_flags(forest, bins, L, band, stream=stream) if d_spec is None
                   else emb_refine_flags_paper(forest, L, d_spec, stream=stream))
             E.flags.append(fl)
             emb_forest_refine(forest, L, fl, stream)
         else:
-            E.links = emb_cutlinks(forest, bins, lattice, stream=stream)
+            if links_out is None:
+                E.links = emb_cutlinks(forest, bins, lattice, stream=stream)
+            else:
+                n = emb_cutlinks_count(forest, lattice, stream)
+                if min(links_out[k].numel() for k in ("cell", "dir", "q", "tri")) < n:
+                    raise EmbError(EMB_ERR_CAPACITY, "embed: links_out holds fewer than the table's links")
+                E.links = emb_cutlinks(forest, bins, lattice, capacity=n, out=links_out, stream=stream)
         if keep_bins:
             E.bins.append(bins)
         else:
