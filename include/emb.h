@@ -478,8 +478,9 @@ emb_status emb_cutlinks_backward(emb_mesh m, emb_forest f, const int32_t *d_cell
  * emb_batch_info: planned blocks per level (levels[j] + 1 int64) and link count of
  * mesh j (host): the capacities of a batch with headroom.  emb_batch_results copies mesh
  * j's results of the last replay into caller buffers (any pointer may be NULL), as many
- * as emb_batch_counts reports: the solid mask words and block coordinates (bx, by, bz
- * int32) of `level`, and the cut-link table. */
+ * as emb_batch_counts reports (with headroom it reads them, synchronising `stream`): the
+ * solid mask words and block coordinates (bx, by, bz int32) of `level`, and the cut-link
+ * table. */
 typedef struct emb_batch_s *emb_batch;
 emb_status emb_batch_create(const emb_mesh *meshes, const int32_t *levels, const int32_t *bands,
                             const int32_t *lattices, int32_t n, void *stream, emb_batch *out);

@@ -432,9 +432,11 @@ __device__ __forceinline__ void link_pair(const TriT &T, long long px, long long
 {
     lines = 0;
     wide = false;
-    const long long LIM = 1ll << 14;
-    const long long l0 = T.lox - px, h0 = T.hix - px, l1 = T.loy - py, h1 = T.hiy - py,
-                    l2 = T.loz - pz, h2 = T.hiz - pz;
+    // coordinates and cell centres lie below 2^25: the offsets fit 32 bits
+    const int LIM = 1 << 14;
+    const int pxi = (int)px, pyi = (int)py, pzi = (int)pz;
+    const int l0 = T.lox - pxi, h0 = T.hix - pxi, l1 = T.loy - pyi, h1 = T.hiy - pyi, l2 = T.loz - pzi,
+              h2 = T.hiz - pzi;
     const bool narrow = l0 > -LIM && h0 < LIM && l1 > -LIM && h1 < LIM && l2 > -LIM && h2 < LIM;
     if (narrow) {
         // Every vertex offset a, b, q lies in (-2^14, 2^14), so in 32-bit integers:
@@ -647,16 +649,18 @@ __global__ void __launch_bounds__(LE_WARPS * 32, LE_MINB) k_link_emit(const __gr
                     s.nz = ux * vy - uy * vx;
                     S.tile[lane] = s;
                     // cell i (centre X0 + (2i+1) half) reaches the box iff lo - h <= centre <= hi + h
+                    // in 32 bits: coordinates and block origins lie below 2^25, h below 2^19
                     int r0[3], r1[3];
-                    const long long lo3[3] = {s.lox - X0, s.loy - Y0, s.loz - Z0};
-                    const long long hi3[3] = {s.hix - X0, s.hiy - Y0, s.hiz - Z0};
+                    const int hh = (int)h + (int)half;
+                    const int lo3[3] = {s.lox - (int)X0, s.loy - (int)Y0, s.loz - (int)Z0};
+                    const int hi3[3] = {s.hix - (int)X0, s.hiy - (int)Y0, s.hiz - (int)Z0};
 #pragma unroll
                     for (int d = 0; d < 3; ++d) {
-                        long long a_ = lo3[d] - h - half;  // ceil(a / h)
-                        long long c_ = hi3[d] + h - half;  // floor(c / h)
-                        long long i0_ = -((-a_) >> lh), i1_ = c_ >> lh;
-                        r0[d] = (int)(i0_ < 0 ? 0 : (i0_ > 4 ? 4 : i0_));
-                        r1[d] = (int)(i1_ > 3 ? 3 : (i1_ < -1 ? -1 : i1_));
+                        const int a_ = lo3[d] - hh;             // ceil(a / h)
+                        const int c_ = hi3[d] + (int)h - (int)half;  // floor(c / h)
+                        const int i0_ = -((-a_) >> lh), i1_ = c_ >> lh;
+                        r0[d] = i0_ < 0 ? 0 : (i0_ > 4 ? 4 : i0_);
+                        r1[d] = i1_ > 3 ? 3 : (i1_ < -1 ? -1 : i1_);
                     }
                     if (r0[0] <= r1[0] && r0[1] <= r1[1] && r0[2] <= r1[2]) {
                         const unsigned long long X = (unsigned long long)(((1u << (r1[0] + 1)) - 1u) & ~((1u << r0[0]) - 1u)) *
