@@ -642,11 +642,12 @@ __global__ void __launch_bounds__(LE_WARPS * 32, LE_MINB) k_link_emit(const __gr
                     s.lox = min(A.x, min(B.x, C.x)); s.hix = max(A.x, max(B.x, C.x));
                     s.loy = min(A.y, min(B.y, C.y)); s.hiy = max(A.y, max(B.y, C.y));
                     s.loz = min(A.z, min(B.z, C.z)); s.hiz = max(A.z, max(B.z, C.z));
-                    const long long ux = (long long)B.x - A.x, uy = (long long)B.y - A.y, uz = (long long)B.z - A.z;
-                    const long long vx = (long long)C.x - A.x, vy = (long long)C.y - A.y, vz = (long long)C.z - A.z;
-                    s.nx = uy * vz - uz * vy;
-                    s.ny = uz * vx - ux * vz;
-                    s.nz = ux * vy - uy * vx;
+                    // edge vectors in 32 bits (coordinates below 2^25), products widened to 64
+                    const int ux = B.x - A.x, uy = B.y - A.y, uz = B.z - A.z;
+                    const int vx = C.x - A.x, vy = C.y - A.y, vz = C.z - A.z;
+                    s.nx = (long long)uy * vz - (long long)uz * vy;
+                    s.ny = (long long)uz * vx - (long long)ux * vz;
+                    s.nz = (long long)ux * vy - (long long)uy * vx;
                     S.tile[lane] = s;
                     // cell i (centre X0 + (2i+1) half) reaches the box iff lo - h <= centre <= hi + h
                     // in 32 bits: coordinates and block origins lie below 2^25, h below 2^19
@@ -709,8 +710,9 @@ __global__ void __launch_bounds__(LE_WARPS * 32, LE_MINB) k_link_emit(const __gr
                         if (g >= qt) continue;
                         const int d = select64(qm, g - qex);
                         const int ti = (int)(qx & 31u), cell = (int)((qx >> 5) & 63u), slot = (int)((qx >> 11) & 31u);
-                        const long long px = X0 + (2 * (cell & 3) + 1) * half, py = Y0 + (2 * ((cell >> 2) & 3) + 1) * half,
-                                        pz = Z0 + (2 * (cell >> 4) + 1) * half;
+                        const int px = (int)X0 + (2 * (cell & 3) + 1) * (int)half,
+                                  py = (int)Y0 + (2 * ((cell >> 2) & 3) + 1) * (int)half,
+                                  pz = (int)Z0 + (2 * (cell >> 4) + 1) * (int)half;
                         float q;
                         const bool ok = (qx >> 16) ? hit_segment_wide(S.tile[ti], px, py, pz, d, h, &q)
                                                    : hit_segment(S.tile[ti], px, py, pz, d, h, &q);
@@ -740,8 +742,9 @@ __global__ void __launch_bounds__(LE_WARPS * 32, LE_MINB) k_link_emit(const __gr
                         const int cell = select64(pmi, gidx - excl_i);
                         const int slot = __popcll(cmask & ((1ull << cell) - 1ull));
                         const TriT &T = S.tile[ti];
-                        const long long px = X0 + (2 * (cell & 3) + 1) * half,
-                                        py = Y0 + (2 * ((cell >> 2) & 3) + 1) * half, pz = Z0 + (2 * (cell >> 4) + 1) * half;
+                        const int px = (int)X0 + (2 * (cell & 3) + 1) * (int)half,
+                                  py = (int)Y0 + (2 * ((cell >> 2) & 3) + 1) * (int)half,
+                                  pz = (int)Z0 + (2 * (cell >> 4) + 1) * (int)half;
                         const uint32_t ccm = S.cm[slot];
                         const uint32_t local = e - e0 + (uint32_t)ti;
                         link_pair(
