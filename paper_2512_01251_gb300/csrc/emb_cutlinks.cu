@@ -206,6 +206,26 @@ __device__ __forceinline__ int select64(unsigned long long m, int r)
     return pos;
 }
 
+
+// Position of the r-th (0-based) set bit of the 32-bit m (m has more than r set bits).
+__device__ __forceinline__ int select32(uint32_t m, int r)
+{
+    int pos = 0;
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1) {
+        const uint32_t lowm = m & ((1u << w) - 1u);
+        const int c = __popc(lowm);
+        if (r >= c) {
+            r -= c;
+            m >>= w;
+            pos += w;
+        } else {
+            m = lowm;
+        }
+    }
+    return pos;
+}
+
 // 32 x 32 bit-matrix transpose across a warp: lane r holds row r (bit c = entry
 // (r, c)); lane c receives column c (bit r = entry (r, c)).  Five stages, each
 // swapping the off-diagonal sub-blocks of the current size between lane pairs.
@@ -708,7 +728,7 @@ __global__ void __launch_bounds__(LE_WARPS * 32, LE_MINB) k_link_emit(const __gr
                         const int qex = __shfl_sync(0xffffffffu, qi - nq, ei);
                         const uint32_t qm = __shfl_sync(0xffffffffu, qe.y, ei), qx = __shfl_sync(0xffffffffu, qe.x, ei);
                         if (g >= qt) continue;
-                        const int d = select64(qm, g - qex);
+                        const int d = select32(qm, g - qex);
                         const int ti = (int)(qx & 31u), cell = (int)((qx >> 5) & 63u), slot = (int)((qx >> 11) & 31u);
                         const int px = (int)X0 + (2 * (cell & 3) + 1) * (int)half,
                                   py = (int)Y0 + (2 * ((cell >> 2) & 3) + 1) * (int)half,
@@ -832,7 +852,7 @@ __global__ void __launch_bounds__(LE_WARPS * 32, LE_MINB) k_link_emit(const __gr
                     emb_set_status(st, EMB_ERR_CAPACITY);
                     continue;
                 }
-                const int d = select64(s_cm, j - s_excl);
+                const int d = select32(s_cm, j - s_excl);
                 int tr = -1;
                 float q = -1.0f;
                 if ((s_got >> d) & 1u) {
