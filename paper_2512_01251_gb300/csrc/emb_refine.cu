@@ -101,6 +101,43 @@ __device__ __forceinline__ void refine_block(const int4 &A, const int4 &B, const
     }
 }
 
+
+// 32-bit forms of the per-block arithmetic: coordinates, block origins, widths and
+// dilations all lie below 2^25 in magnitude, block indices below 2^21.
+__device__ __forceinline__ void ref_range(int mn, int mx, int lW, int dil, int nb, int &b0, int &b1)
+{
+    b0 = -((-(mn - dil - (1 << lW))) >> lW);  // ceil
+    b1 = (mx + dil) >> lW;                    // floor
+    if (b0 < 0) b0 = 0;
+    if (b1 > nb - 1) b1 = nb - 1;
+}
+__device__ __forceinline__ bool ref_pt(const int4 &P, int lx, int ly, int lz, int hx, int hy, int hz)
+{
+    return P.x >= lx && P.x <= hx && P.y >= ly && P.y <= hy && P.z >= lz && P.z <= hz;
+}
+__device__ __forceinline__ bool ref_overlap(const WuTri &S, int j, int lx, int ly, int lz, int ux, int uy, int uz)
+{
+    if (S.lo[0][j] > ux || S.hi[0][j] < lx || S.lo[1][j] > uy || S.hi[1][j] < ly || S.lo[2][j] > uz || S.hi[2][j] < lz)
+        return false;
+    const int4 A = S.A[j], B = S.B[j], C = S.C[j];
+    return ref_pt(A, lx, ly, lz, ux, uy, uz) || ref_pt(B, lx, ly, lz, ux, uy, uz) || ref_pt(C, lx, ly, lz, ux, uy, uz) ||
+           emb_tri_box(A, B, C, lx, ly, lz, ux, uy, uz);
+}
+__device__ __forceinline__ void ref_block(const int4 &A, const int4 &B, const int4 &C, int bx, int by, int bz, int W,
+                                          int dil, const EmbLookup &lk, uint8_t *__restrict__ flags, const FlagBits &fb)
+{
+    unsigned long long pos = 0;
+    const int32_t id = refine_candidate(lk, fb, flags, bx, by, bz, pos);
+    if (id < 0) return;
+    const int lx = bx * W - dil, ly = by * W - dil, lz = bz * W - dil;
+    const int hx = lx + W + 2 * dil, hy = ly + W + 2 * dil, hz = lz + W + 2 * dil;
+    if (ref_pt(A, lx, ly, lz, hx, hy, hz) || ref_pt(B, lx, ly, lz, hx, hy, hz) || ref_pt(C, lx, ly, lz, hx, hy, hz) ||
+        emb_tri_box(A, B, C, lx, ly, lz, hx, hy, hz)) {
+        flags[id] = 1;
+        if (fb.w) fb.set(pos);
+    }
+}
+
 // Persistent warps over tiles of 32 consecutive triangles; each warp loads the
 // records of its next tile before it works on the current one, so that the loads
 // are in flight during the work (a warp otherwise spends most of its life after its
@@ -134,11 +171,12 @@ __global__ void __launch_bounds__(EMB_WU_WARPS * 32, REFINE_MINB) k_refine(const
                 nC = rec[3 * tn + 2];
             }
         }
-        long long b0[3] = {1ll << 40, 1ll << 40, 1ll << 40}, b1[3] = {-1, -1, -1};
+        const int dil32 = (int)dil, W32 = (int)g.W, nb32 = (int)g.nb;
+        int b0[3] = {0x7fffffff, 0x7fffffff, 0x7fffffff}, b1[3] = {-1, -1, -1};
         if (valid) {
-            emb_block_range(min(A.x, min(B.x, C.x)), max(A.x, max(B.x, C.x)), g.lW, dil, g.nb, b0[0], b1[0]);
-            emb_block_range(min(A.y, min(B.y, C.y)), max(A.y, max(B.y, C.y)), g.lW, dil, g.nb, b0[1], b1[1]);
-            emb_block_range(min(A.z, min(B.z, C.z)), max(A.z, max(B.z, C.z)), g.lW, dil, g.nb, b0[2], b1[2]);
+            ref_range(min(A.x, min(B.x, C.x)), max(A.x, max(B.x, C.x)), g.lW, dil32, nb32, b0[0], b1[0]);
+            ref_range(min(A.y, min(B.y, C.y)), max(A.y, max(B.y, C.y)), g.lW, dil32, nb32, b0[1], b1[1]);
+            ref_range(min(A.z, min(B.z, C.z)), max(A.z, max(B.z, C.z)), g.lW, dil32, nb32, b0[2], b1[2]);
         }
         __syncwarp();  // the previous tile's lanes are done with S
         S.A[lane] = A;
@@ -154,15 +192,19 @@ __global__ void __launch_bounds__(EMB_WU_WARPS * 32, REFINE_MINB) k_refine(const
         int u0[3], u1[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            u0[d] = __reduce_min_sync(0xffffffffu, (int)min(b0[d], (long long)0x7fffffff));
-            u1[d] = __reduce_max_sync(0xffffffffu, (int)b1[d]);
+            u0[d] = __reduce_min_sync(0xffffffffu, b0[d]);
+            u1[d] = __reduce_max_sync(0xffffffffu, b1[d]);
         }
         const long long nx = u1[0] - u0[0] + 1, ny = u1[1] - u0[1] + 1, nz = u1[2] - u0[2] + 1;
         if (nx <= 0 || ny <= 0 || nz <= 0) continue;
         const long long total = nx * ny * nz;
         // per-triangle candidates summed over the warp: the union pays off only when it is
         // much smaller (eight times: measured against two and four, and against sixteen)
-        const unsigned long long own = valid ? refine_items(b0, b1) : 0;
+        const unsigned long long own =
+            valid && b1[0] >= b0[0] && b1[1] >= b0[1] && b1[2] >= b0[2]
+                ? (unsigned long long)(b1[0] - b0[0] + 1) * (unsigned long long)(b1[1] - b0[1] + 1) *
+                      (unsigned long long)(b1[2] - b0[2] + 1)
+                : 0ull;
         const unsigned own_sum = __reduce_add_sync(0xffffffffu, (unsigned)min(own, 1ull << 20));
         if (total <= EMB_WU_MAX && 8 * total <= (long long)own_sum) {
             // total <= EMB_WU_MAX: decode the union index in 32-bit arithmetic.  Each lane
@@ -172,25 +214,25 @@ __global__ void __launch_bounds__(EMB_WU_WARPS * 32, REFINE_MINB) k_refine(const
             const unsigned mx = emb_recip(ux), mxy = emb_recip(uxy);
             for (unsigned c0 = 0; c0 < (unsigned)total; c0 += 32) {
                 const unsigned c = c0 + lane;
-                long long bx = 0, by = 0, bz = 0;
+                int bx = 0, by = 0, bz = 0;
                 unsigned long long pos = 0;
                 int32_t id = -1;
                 if (c < (unsigned)total) {
                     const unsigned cz = emb_div_recip(c, uxy, mxy), cr = c - cz * uxy, cy = emb_div_recip(cr, ux, mx);
-                    bx = u0[0] + (long long)(cr - cy * ux);
-                    by = u0[1] + (long long)cy;
-                    bz = u0[2] + (long long)cz;
+                    bx = u0[0] + (int)(cr - cy * ux);
+                    by = u0[1] + (int)cy;
+                    bz = u0[2] + (int)cz;
                     id = refine_candidate(lk, fb, flags, bx, by, bz, pos);
                 }
                 unsigned m = __ballot_sync(0xffffffffu, id >= 0);
                 while (m) {
                     const int src = __ffs(m) - 1;
                     m &= m - 1;
-                    const long long lx = __shfl_sync(0xffffffffu, bx, src) * g.W - dil,
-                                    ly = __shfl_sync(0xffffffffu, by, src) * g.W - dil,
-                                    lz = __shfl_sync(0xffffffffu, bz, src) * g.W - dil;
-                    const bool hit = wu_overlap(S, lane, lx, ly, lz, lx + g.W + 2 * dil, ly + g.W + 2 * dil,
-                                                lz + g.W + 2 * dil);
+                    const int lx = __shfl_sync(0xffffffffu, bx, src) * W32 - dil32,
+                              ly = __shfl_sync(0xffffffffu, by, src) * W32 - dil32,
+                              lz = __shfl_sync(0xffffffffu, bz, src) * W32 - dil32;
+                    const bool hit = ref_overlap(S, lane, lx, ly, lz, lx + W32 + 2 * dil32, ly + W32 + 2 * dil32,
+                                                 lz + W32 + 2 * dil32);
                     if (__any_sync(0xffffffffu, hit) && lane == src) {
                         flags[id] = 1;
                         if (fb.w) fb.set(pos);
@@ -230,8 +272,8 @@ __global__ void __launch_bounds__(EMB_WU_WARPS * 32, REFINE_MINB) k_refine(const
             if (gi < wtot) {
                 const uint32_t r = gi - first, rr = emb_div_recip(r, (uint32_t)nbx, mbx), cx = r - rr * (uint32_t)nbx,
                                cz = emb_div_recip(rr, (uint32_t)nby, mby), cy = rr - cz * (uint32_t)nby;
-                refine_block(S.A[ti], S.B[ti], S.C[ti], bx0 + (long long)cx, by0 + (long long)cy, bz0 + (long long)cz, g,
-                             dil, lk, flags, fb);
+                ref_block(S.A[ti], S.B[ti], S.C[ti], bx0 + (int)cx, by0 + (int)cy, bz0 + (int)cz, W32, dil32, lk, flags,
+                          fb);
             }
         }
     }
