@@ -56,6 +56,55 @@ __device__ __forceinline__ uint32_t xline_hit(const int4 *__restrict__ rec, int6
     return hit;
 }
 
+
+// The x-line filter's test in 32-bit arithmetic (coordinates below 2^25; the orientation
+// products widened to 64 bits), the same decisions as the 64-bit form.
+__device__ __forceinline__ int orient_yz32(int uy, int uz, int vy, int vz, int py, int pz)
+{
+    const int ey = vy - uy, ez = vz - uz;
+    const long long o = (long long)ey * (pz - uz) - (long long)ez * (py - uy);
+    if (o != 0) return o > 0 ? 1 : -1;
+    if (ez != 0) return ez > 0 ? -1 : 1;
+    return ey > 0 ? 1 : (ey < 0 ? -1 : 0);
+}
+__device__ __forceinline__ uint32_t xline_hit32(const int4 *__restrict__ rec, int64_t t, const LevelGeom &g)
+{
+    const int4 A = rec[3 * t], B = rec[3 * t + 1], C = rec[3 * t + 2];
+    const long long nx = (long long)(B.y - A.y) * (C.z - A.z) - (long long)(B.z - A.z) * (C.y - A.y);
+    if (nx == 0) return 0;
+    const int sx = nx > 0 ? 1 : -1;
+    const int lh = g.lh, half = (int)g.half, nc = (int)g.ncell;
+    const int mny = min(A.y, min(B.y, C.y)), mxy = max(A.y, max(B.y, C.y));
+    const int mnz = min(A.z, min(B.z, C.z)), mxz = max(A.z, max(B.z, C.z));
+    int j0 = -((-(mny - half)) >> lh), j1 = (mxy - half) >> lh;
+    int k0 = -((-(mnz - half)) >> lh), k1 = (mxz - half) >> lh;
+    j0 = j0 < 0 ? 0 : j0;
+    k0 = k0 < 0 ? 0 : k0;
+    j1 = j1 > nc - 1 ? nc - 1 : j1;
+    k1 = k1 > nc - 1 ? nc - 1 : k1;
+    if (j1 < j0 || k1 < k0) return 0;
+    // the line nearest the centroid first: it settles a large triangle in one test
+    int jc = ((A.y + B.y + C.y) >> lh) / 3, kc = ((A.z + B.z + C.z) >> lh) / 3;
+    jc = jc < j0 ? j0 : (jc > j1 ? j1 : jc);
+    kc = kc < k0 ? k0 : (kc > k1 ? k1 : kc);
+    {
+        const int py = (2 * jc + 1) * half, pz = (2 * kc + 1) * half;
+        if (orient_yz32(A.y, A.z, B.y, B.z, py, pz) == sx && orient_yz32(B.y, B.z, C.y, C.z, py, pz) == sx &&
+            orient_yz32(C.y, C.z, A.y, A.z, py, pz) == sx)
+            return 1;
+    }
+    for (int k = k0; k <= k1; ++k) {
+        const int pz = (2 * k + 1) * half;
+        for (int j = j0; j <= j1; ++j) {
+            const int py = (2 * j + 1) * half;
+            if (orient_yz32(A.y, A.z, B.y, B.z, py, pz) == sx && orient_yz32(B.y, B.z, C.y, C.z, py, pz) == sx &&
+                orient_yz32(C.y, C.z, A.y, A.z, py, pz) == sx)
+                return 1;
+        }
+    }
+    return 0;
+}
+
 // Per-triangle filter flags (the ablation that keeps the list uncompacted).
 __global__ void k_xfilter(const int4 *__restrict__ rec, int64_t T, LevelGeom g, uint32_t *__restrict__ flag)
 {
@@ -70,7 +119,7 @@ __global__ void k_xfilter_bits(const int4 *__restrict__ rec, int64_t T, LevelGeo
                                uint32_t *__restrict__ wcnt)
 {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t hit = t < T ? xline_hit(rec, t, g) : 0u;
+    const uint32_t hit = t < T ? xline_hit32(rec, t, g) : 0u;
     const uint32_t m = __ballot_sync(0xffffffffu, hit != 0u);
     if ((threadIdx.x & 31) == 0 && t < T) {
         word[t >> 5] = m;
@@ -126,6 +175,36 @@ __device__ __forceinline__ unsigned long long box_items(const long long b0[3], c
     if (b1[0] < b0[0] || b1[1] < b0[1] || b1[2] < b0[2]) return 0;
     return (unsigned long long)(b1[0] - b0[0] + 1) * (unsigned long long)(b1[1] - b0[1] + 1) *
            (unsigned long long)(b1[2] - b0[2] + 1);
+}
+
+
+// The pair kernel's set-up in 32-bit arithmetic (coordinates, block origins, widths and
+// dilations below 2^25 in magnitude; the degenerate test widens its products to 64 bits).
+__device__ __forceinline__ bool bin_setup32(const int4 *__restrict__ rec, int64_t t, int lW, int dil, int nb, int4 &A,
+                                            int4 &B, int4 &C, int b0[3], int b1[3])
+{
+    A = rec[3 * t];
+    B = rec[3 * t + 1];
+    C = rec[3 * t + 2];
+    const int ux = B.x - A.x, uy = B.y - A.y, uz = B.z - A.z;
+    const int vx = C.x - A.x, vy = C.y - A.y, vz = C.z - A.z;
+    if ((long long)uy * vz - (long long)uz * vy == 0 && (long long)uz * vx - (long long)ux * vz == 0 &&
+        (long long)ux * vy - (long long)uy * vx == 0)
+        return false;
+    const int mn[3] = {min(A.x, min(B.x, C.x)), min(A.y, min(B.y, C.y)), min(A.z, min(B.z, C.z))};
+    const int mx[3] = {max(A.x, max(B.x, C.x)), max(A.y, max(B.y, C.y)), max(A.z, max(B.z, C.z))};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        b0[d] = -((-(mn[d] - dil - (1 << lW))) >> lW);  // ceil
+        b1[d] = (mx[d] + dil) >> lW;                    // floor
+        if (b0[d] < 0) b0[d] = 0;
+        if (b1[d] > nb - 1) b1[d] = nb - 1;
+    }
+    return true;
+}
+__device__ __forceinline__ bool bin_pt32(const int4 &P, int lx, int ly, int lz, int hx, int hy, int hz)
+{
+    return P.x >= lx && P.x <= hx && P.y >= ly && P.y <= hy && P.z >= lz && P.z <= hz;
 }
 
 // Pair list of one binning pass: entry e is (block, slot in the block) and the triangle.
@@ -228,14 +307,19 @@ __global__ void __launch_bounds__(EMB_WU_WARPS * 32, 8) k_bin_pairs(const int4 *
     int qn = 0;  // pairs queued for the full overlap test (warp-uniform)
     const int64_t t0 = ((int64_t)blockIdx.x * EMB_WU_WARPS + w) * 32;
     const int64_t t = t0 + lane;
-    long long b0[3] = {1ll << 40, 1ll << 40, 1ll << 40}, b1[3] = {-1, -1, -1};
+    const int dil32 = (int)dil, W32 = (int)g.W;
+    int b0[3] = {0x7fffffff, 0x7fffffff, 0x7fffffff}, b1[3] = {-1, -1, -1};
     int4 A = make_int4(0, 0, 0, 0), B = A, C = A;
-    const bool valid = t < T && bin_setup(rec, t, g, dil, A, B, C, b0, b1);
+    const bool valid = t < T && bin_setup32(rec, t, g.lW, dil32, (int)g.nb, A, B, C, b0, b1);
     S.A[lane] = A;
     S.B[lane] = B;
     S.C[lane] = C;
     __syncwarp();
-    const unsigned long long own = valid ? box_items(b0, b1) : 0;
+    const unsigned long long own =
+        valid && b1[0] >= b0[0] && b1[1] >= b0[1] && b1[2] >= b0[2]
+            ? (unsigned long long)(b1[0] - b0[0] + 1) * (unsigned long long)(b1[1] - b0[1] + 1) *
+                  (unsigned long long)(b1[2] - b0[2] + 1)
+            : 0ull;
     const bool mine = valid && own > 0 && !(own > EMB_BIG_ITEMS && emb_bigq_push(Q, (uint32_t)t, own));
     const uint32_t k = mine ? (uint32_t)own : 0u;
     uint32_t incl = k;
@@ -273,12 +357,10 @@ __global__ void __launch_bounds__(EMB_WU_WARPS * 32, 8) k_bin_pairs(const int4 *
             bzi = bz0 + (int)cz;
             id = emb_lookup(lk, bxi, byi, bzi);
             if (id >= 0) {
-                const long long lx = (long long)bxi * g.W - dil, ly = (long long)byi * g.W - dil,
-                                lz = (long long)bzi * g.W - dil;
-                const long long hx = lx + g.W + 2 * dil, hy = ly + g.W + 2 * dil, hz = lz + g.W + 2 * dil;
-                hit = emb_point_in_box(S.A[ti], lx, ly, lz, hx, hy, hz) ||
-                      emb_point_in_box(S.B[ti], lx, ly, lz, hx, hy, hz) ||
-                      emb_point_in_box(S.C[ti], lx, ly, lz, hx, hy, hz);
+                const int lx = bxi * W32 - dil32, ly = byi * W32 - dil32, lz = bzi * W32 - dil32;
+                const int hx = lx + W32 + 2 * dil32, hy = ly + W32 + 2 * dil32, hz = lz + W32 + 2 * dil32;
+                hit = bin_pt32(S.A[ti], lx, ly, lz, hx, hy, hz) || bin_pt32(S.B[ti], lx, ly, lz, hx, hy, hz) ||
+                      bin_pt32(S.C[ti], lx, ly, lz, hx, hy, hz);
                 need = !hit;
             }
         }
