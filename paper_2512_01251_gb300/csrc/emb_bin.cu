@@ -19,46 +19,9 @@
 #include "emb_internal.cuh"
 
 // Exact x-line filter of triangle t: 1 iff its yz-projection contains the centre of
-// some x-line of the level (perturbed orientation tests, Sec. 3.4 parity rule).
-__device__ __forceinline__ uint32_t xline_hit(const int4 *__restrict__ rec, int64_t t, const LevelGeom &g)
-{
-    int4 A = rec[3 * t], B = rec[3 * t + 1], C = rec[3 * t + 2];
-    long long nx = ((long long)B.y - A.y) * ((long long)C.z - A.z) - ((long long)B.z - A.z) * ((long long)C.y - A.y);
-    uint32_t hit = 0;
-    if (nx != 0) {
-        int sx = nx > 0 ? 1 : -1;
-        long long j0, j1, k0, k1;
-        line_range(min(A.y, min(B.y, C.y)), max(A.y, max(B.y, C.y)), g.lh, g.half, g.ncell, j0, j1);
-        line_range(min(A.z, min(B.z, C.z)), max(A.z, max(B.z, C.z)), g.lh, g.half, g.ncell, k0, k1);
-        if (j1 >= j0 && k1 >= k0) {
-            // the line nearest the centroid first: it settles a large triangle in one test
-            long long jc = emb_floor_shr((long long)A.y + B.y + C.y, g.lh) / 3;
-            long long kc = emb_floor_shr((long long)A.z + B.z + C.z, g.lh) / 3;
-            jc = jc < j0 ? j0 : (jc > j1 ? j1 : jc);
-            kc = kc < k0 ? k0 : (kc > k1 ? k1 : kc);
-            const int py = (int)((2 * jc + 1) * g.half), pz = (int)((2 * kc + 1) * g.half);
-            if (emb_orient_yz(A.y, A.z, B.y, B.z, py, pz) == sx && emb_orient_yz(B.y, B.z, C.y, C.z, py, pz) == sx &&
-                emb_orient_yz(C.y, C.z, A.y, A.z, py, pz) == sx)
-                hit = 1;
-        }
-        for (long long k = k0; k <= k1 && !hit; ++k) {
-            int pz = (int)((2 * k + 1) * g.half);
-            for (long long j = j0; j <= j1; ++j) {
-                int py = (int)((2 * j + 1) * g.half);
-                if (emb_orient_yz(A.y, A.z, B.y, B.z, py, pz) == sx && emb_orient_yz(B.y, B.z, C.y, C.z, py, pz) == sx &&
-                    emb_orient_yz(C.y, C.z, A.y, A.z, py, pz) == sx) {
-                    hit = 1;
-                    break;
-                }
-            }
-        }
-    }
-    return hit;
-}
-
-
-// The x-line filter's test in 32-bit arithmetic (coordinates below 2^25; the orientation
-// products widened to 64 bits), the same decisions as the 64-bit form.
+// some x-line of the level (perturbed orientation tests, Sec. 3.4 parity rule).  In
+// 32-bit arithmetic: coordinates lie below 2^25, the orientation products are widened
+// to 64 bits.
 __device__ __forceinline__ int orient_yz32(int uy, int uz, int vy, int vz, int py, int pz)
 {
     const int ey = vy - uy, ez = vz - uz;
@@ -110,7 +73,7 @@ __global__ void k_xfilter(const int4 *__restrict__ rec, int64_t T, LevelGeom g, 
 {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= T) return;
-    flag[t] = xline_hit(rec, t, g);
+    flag[t] = xline_hit32(rec, t, g);
 }
 
 // The filter as one bit per triangle: warp word t / 32 (bit t % 32) and its popcount.
