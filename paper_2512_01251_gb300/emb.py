@@ -396,9 +396,9 @@ def embed(verts: torch.Tensor, tris: torch.Tensor, R: int, levels: int, band: in
     and finest_mask_out receive the link table and the finest solid mask; they may be
     page-locked host tensors, which the library then fills over the host link.
     """
+    forest = emb_forest_root(R, levels, stream)  # first: it runs while the mesh check reads back
     if mesh is None:
         mesh = emb_mesh_create(verts, tris, R, check_watertight, stream)
-    forest = emb_forest_root(R, levels, stream)
     E = Embedding(mesh=mesh, forest=forest, levels=levels, lattice=lattice)
     for L in range(levels + 1):
         bins = emb_bin(mesh, forest, L, lattice, stream, mode=bin_mode)
