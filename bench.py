@@ -327,7 +327,7 @@ def step_roofline(med, T, level_blocks, stats, n_links, tests, hbm_gbs, alu_tops
         if L < lf:
             add(f"refine_flags{L}", med.get(f"refine_flags{L}"), 48 * T + B)
             add(f"forest_refine{L}", med.get(f"forest_refine{L}"), 9 * B + 8 * level_blocks[L + 1])
-    cl_ms = (med.get("cutlinks_count") or 0.0) + (med.get("cutlinks_emit") or 0.0)
+    cl_ms = (med.get("cutlinks_prep") or 0.0) + (med.get("cutlinks_emit") or 0.0)
     Bf = level_blocks[lf]
     add("cutlinks", cl_ms, 27 * 8 * Bf + 4 * stats[lf][1] + 48 * stats[lf][0] + 13 * n_links,
         tests * KAPPA_SEG + n_links * KAPPA_Q)
@@ -366,6 +366,8 @@ def run_ours(args):
 
     names = ["mesh", "bin", "voxelize", "refine_flags", "forest_refine", "cutlinks"]
 
+    link_cap = [None]
+
     def step(timed=None):
         ev = []
 
@@ -392,9 +394,13 @@ def run_ours(args):
                 P.emb_forest_refine(forest, L, fl)
                 mark(f"forest_refine{L}")
             else:
-                n = P.emb_cutlinks_count(forest, lattice)
-                mark("cutlinks_count")
-                links = P.emb_cutlinks(forest, bins, lattice, capacity=n)
+                # the count stays on the device: the table's buffers take the previous
+                # step's count with headroom (the first step reads it back); the count
+                # is read after the step's last event
+                P.emb_cutlinks_prepare(forest, lattice)
+                mark("cutlinks_prep")
+                cap = link_cap[0] if link_cap[0] is not None else P.emb_cutlinks_count(forest, lattice)
+                links = P.emb_cutlinks(forest, bins, lattice, capacity=cap, sync=False)
                 mark("cutlinks_emit")
                 if timed is not None and timed.get("want_bins"):
                     timed["bins"] = P.emb_bins_copy(bins, forest)
@@ -403,6 +409,11 @@ def run_ours(args):
             bins.close()
         if timed is not None:
             timed["events"] = ev
+        n = int(links["count"].item())
+        if n > cap:
+            raise RuntimeError(f"link table of {n} links overflowed its {cap} slots")
+        link_cap[0] = n + n // 64 + 1024
+        links = {k: (v[:n] if k != "count" else v) for k, v in links.items()}
         return mesh, forest, masks, links, stats
 
     def units_of(forest, links):
@@ -517,7 +528,7 @@ def run_ours(args):
     nst = len(srt)
     j = max(0, int(math.floor(nst / 2 - 0.98 * math.sqrt(nst))))
     k = min(nst - 1, int(math.ceil(nst / 2 + 0.98 * math.sqrt(nst))))
-    four = sum(groups.get(g_, 0.0) for g_ in ("bin", "voxelize", "refine_flags", "cutlinks_count", "cutlinks_emit"))
+    four = sum(groups.get(g_, 0.0) for g_ in ("bin", "voxelize", "refine_flags", "cutlinks_prep", "cutlinks_emit"))
     line["step_ms_stats"] = dict(median=statistics.median(srt), min=srt[0], max=srt[-1],
                                  ci95_median=[srt[j], srt[k]], n=nst,
                                  in_order=[round(x, 3) for x in step_ms])
@@ -603,7 +614,7 @@ def fwd_bwd_leg(P, reps=10):
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         torch.cuda.synchronize()
         e0.record(stream)
-        P.emb_cutlinks(E.forest, fin, 19, capacity=n, out=L)
+        P.emb_cutlinks(E.forest, fin, 19, capacity=n, out=L, sync=False)
         P.emb_mex_force(E.forest, 19, L["cell"], L["dir"], L["q"], pop, out=F)
         e1.record(stream)
         P.emb_mex_force_backward(E.forest, 19, L["cell"], L["dir"], L["q"], pop, gF, out=gq)

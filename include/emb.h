@@ -325,13 +325,26 @@ emb_status emb_splice(emb_forest f, emb_forest w, int32_t y0, int32_t y1, int32_
  * Synchronises; the count is returned in *h_count. */
 emb_status emb_cutlinks_count(emb_forest f, int32_t lattice, int64_t *h_count, void *stream);
 
+/* The same work as emb_cutlinks_count (the finest level's neighbour table and the
+ * candidate cells of `lattice`), enqueued on `stream` without reading the count back:
+ * nothing synchronises.  A later emb_cutlinks on the same forest and lattice reuses
+ * it; emb_cutlinks_count afterwards only reads the count.  Errors: EMB_ERR_BAD_INPUT
+ * (lattice), EMB_ERR_STATE (finest level not voxelized). */
+emb_status emb_cutlinks_prepare(emb_forest f, int32_t lattice, void *stream);
+
 /* The flat link-length table (Sec. 3.4, "Link-Length Computation"): for every
  * cut link, d_cell = finest cell id, d_dir = direction, d_q = distance from the
  * cell centre to the nearest crossed face along the link divided by the link
  * length (in [0,1]), d_tri = that face's triangle id (lowest id on exact ties).
- * Ordered by (cell, dir).  `b` must be the bins of the finest level.  If the
- * count exceeds `capacity`, nothing is written, *d_count (device int64) still
- * receives the required size and the device status becomes EMB_ERR_CAPACITY.
+ * Ordered by (cell, dir).  `b` must be the bins of the finest level.  *d_count
+ * (device int64, may be NULL) receives the number of links.  The call reads nothing
+ * back unless the candidates have yet to be built (it then builds them without a
+ * read-back, as emb_cutlinks_prepare does): so the host does not wait for the GPU.
+ * If the count exceeds `capacity`: when the count is already known on the host
+ * (emb_cutlinks_count before), nothing is enqueued but the status and count writes,
+ * and EMB_ERR_CAPACITY is returned; otherwise the links at table positions below
+ * `capacity` are written, none past it, *d_count still receives the required size
+ * and the device status becomes EMB_ERR_CAPACITY (read it with emb_status_get).
  * A finest-level bin may hold at most 2^24 triangles (16,777,216 faces overlapping
  * one block); the links of a block with a larger bin are not written and the device
  * status becomes EMB_ERR_CAPACITY (refine further so that the bins shrink).

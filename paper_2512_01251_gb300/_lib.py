@@ -48,6 +48,7 @@ SIGNATURES = {
     "emb_refine_flags": (I32, [P, P, I32, I32, P, P]),
     "emb_refine_flags_paper": (I32, [P, I32, ctypes.c_double, P, P]),
     "emb_cutlinks_count": (I32, [P, I32, PI64, P]),
+    "emb_cutlinks_prepare": (I32, [P, I32, P]),
     "emb_cutlinks": (I32, [P, P, I32, P, P, P, P, I64, P, P]),
     "emb_mex_force": (I32, [P, I32, P, P, P, I64, P, I64, P, P]),
     "emb_mex_force_backward": (I32, [P, I32, P, P, P, I64, P, I64, P, P, P]),

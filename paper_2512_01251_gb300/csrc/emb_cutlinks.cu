@@ -879,6 +879,12 @@ __global__ void k_store_count(const uint32_t *__restrict__ blk_off, int64_t n, i
 
 __global__ void k_set_status(int *st, int code) { emb_set_status(st, code); }
 
+// EMB_ERR_CAPACITY when the block offsets count any link (a call with room for none).
+__global__ void k_count_check(const uint32_t *__restrict__ blk_off, int64_t n, int *st)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0 && blk_off[n] > 0) emb_set_status(st, EMB_ERR_CAPACITY);
+}
+
 __global__ void k_nonempty(const uint32_t *__restrict__ cnt, int64_t n, uint32_t *__restrict__ flag)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1027,11 +1033,22 @@ emb_status emb_enq_link_emit(const LinkTable &tab, unsigned int *next, int ctas_
     return EMB_OK;
 }
 
-static emb_status build_candidates(emb_forest f, int lattice, cudaStream_t s)
+// f->n_links: -1 no candidates; -2 candidates built, the link count still on the device
+// (blk_off[n]); >= 0 the count, read back.  With read_count the count is read back
+// (synchronising s); without it nothing is read back.
+#define EMB_LINKS_ON_DEVICE (-2)
+static emb_status build_candidates(emb_forest f, int lattice, cudaStream_t s, bool read_count)
 {
     int L = f->max_level;
     if (f->top != L || !f->lv[L].mask_valid) return EMB_ERR_STATE;
-    if (f->n_links >= 0 && f->cand_lattice == lattice && f->cand) return EMB_OK;
+    if ((f->n_links >= 0 || f->n_links == EMB_LINKS_ON_DEVICE) && f->cand_lattice == lattice && f->cand) {
+        if (f->n_links >= 0 || !read_count) return EMB_OK;
+        uint32_t total = 0;
+        EMB_CUDA_TRY(cudaMemcpyAsync(&total, f->blk_off + f->lv[L].n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        EMB_CUDA_TRY(cudaStreamSynchronize(s));
+        f->n_links = (int64_t)total;
+        return EMB_OK;
+    }
     EmbLevel &lv = f->lv[L];
     emb_status rc = emb_build_neighbors(lv, s);
     if (rc != EMB_OK) return rc;
@@ -1048,24 +1065,32 @@ static emb_status build_candidates(emb_forest f, int lattice, cudaStream_t s)
     EMB_CUDA_TRY(emb_malloc_async(&tmp, emb_scan_tmp_words(lv.n) * sizeof(uint64_t), s));
     rc = emb_enq_link_prep(lv, lattice, f->cand, cnt, flag, f->work_n, f->work, f->blk_off, tmp, s);
     if (rc != EMB_OK) return rc;
-    uint32_t total = 0;
-    EMB_CUDA_TRY(cudaMemcpyAsync(&total, f->blk_off + lv.n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    EMB_CUDA_TRY(cudaStreamSynchronize(s));
     EMB_CUDA_TRY(cudaFreeAsync(cnt, s));
     EMB_CUDA_TRY(cudaFreeAsync(flag, s));
     EMB_CUDA_TRY(cudaFreeAsync(tmp, s));
-    f->n_links = (int64_t)total;
     f->cand_lattice = lattice;
+    f->n_links = EMB_LINKS_ON_DEVICE;
+    if (!read_count) return EMB_OK;
+    uint32_t total = 0;
+    EMB_CUDA_TRY(cudaMemcpyAsync(&total, f->blk_off + lv.n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    EMB_CUDA_TRY(cudaStreamSynchronize(s));
+    f->n_links = (int64_t)total;
     return EMB_OK;
 }
 
 extern "C" emb_status emb_cutlinks_count(emb_forest f, int32_t lattice, int64_t *h_count, void *stream)
 {
     if (!f || !h_count || (lattice != 19 && lattice != 27)) return EMB_ERR_BAD_INPUT;
-    emb_status rc = build_candidates(f, lattice, emb_stream(stream));
+    emb_status rc = build_candidates(f, lattice, emb_stream(stream), true);
     if (rc != EMB_OK) return rc;
     *h_count = f->n_links;
     return EMB_OK;
+}
+
+extern "C" emb_status emb_cutlinks_prepare(emb_forest f, int32_t lattice, void *stream)
+{
+    if (!f || (lattice != 19 && lattice != 27)) return EMB_ERR_BAD_INPUT;
+    return build_candidates(f, lattice, emb_stream(stream), false);
 }
 
 extern "C" emb_status emb_cutlinks(emb_forest f, emb_bins b, int32_t lattice, int32_t *d_cell, uint8_t *d_dir, float *d_q,
@@ -1102,16 +1127,24 @@ extern "C" emb_status emb_cutlinks(emb_forest f, emb_bins b, int32_t lattice, in
     }
     int *st = emb_status_word();
     if (!st) return EMB_ERR_CUDA;
-    emb_status rc = build_candidates(f, lattice, s);
+    // without a count read back before (emb_cutlinks_count), the count stays on the
+    // device: the kernel writes no link past `capacity` and sets EMB_ERR_CAPACITY
+    emb_status rc = build_candidates(f, lattice, s, false);
     if (rc != EMB_OK) return rc;
     EmbLevel &lv = f->lv[f->max_level];
     if (d_count) EMB_LAUNCH((k_store_count), 1, 32, 0, s)(f->blk_off, lv.n, d_count);
-    if (f->n_links > capacity) {
+    if (f->n_links >= 0 && f->n_links > capacity) {
         EMB_LAUNCH((k_set_status), 1, 1, 0, s)(st, EMB_ERR_CAPACITY);
         EMB_CUDA_TRY(cudaGetLastError());
         return EMB_ERR_CAPACITY;
     }
     if (f->n_links == 0) return EMB_OK;
+    if (capacity == 0) {
+        // nothing may be written: the count on the device decides whether that is an error
+        EMB_LAUNCH((k_count_check), 1, 32, 0, s)(f->blk_off, lv.n, st);
+        EMB_CUDA_TRY(cudaGetLastError());
+        return EMB_OK;
+    }
     if (!d_cell || !d_dir || !d_q || !d_tri) return EMB_ERR_BAD_INPUT;
     LinkTable tab;
     tab.n = 1;

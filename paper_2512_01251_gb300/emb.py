@@ -63,6 +63,10 @@ def _stream(stream=None):
     return ctypes.c_void_p(s.cuda_stream)
 
 
+def _sync(stream=None):
+    (stream if stream is not None else torch.cuda.current_stream()).synchronize()
+
+
 class _Handle:
     _destroy = None
 
@@ -282,10 +286,24 @@ def emb_cutlinks_count(forest: Forest, lattice: int, stream=None) -> int:
     return out.value
 
 
+def emb_cutlinks_prepare(forest: Forest, lattice: int, stream=None) -> None:
+    """Enqueue the candidate cells of the link table without reading the count back."""
+    _check(load().emb_cutlinks_prepare(forest.h, int(lattice), _stream(stream)), "emb_cutlinks_prepare")
+
+
 def emb_cutlinks(forest: Forest, bins: Bins, lattice: int, capacity: int | None = None, out: dict | None = None,
-                 stream=None) -> dict:
-    """Cut-link table {cell int32, dir uint8, q float32, tri int32, count int64 (device)}."""
-    if capacity is None:
+                 stream=None, sync: bool = True) -> dict:
+    """Cut-link table {cell int32, dir uint8, q float32, tri int32, count int64}.
+
+    Without `capacity` the count is read back first (emb_cutlinks_count) and the
+    table is sized to it.  With `capacity` nothing is read back before the launch;
+    with `sync` the call then waits for the stream, reads the count and returns the
+    table cut to it (EmbError EMB_ERR_CAPACITY when it held more links than
+    `capacity`); without `sync` it returns the whole buffers at once and the caller
+    cuts them to out["count"] once the stream has passed the call.
+    """
+    exact = capacity is None
+    if exact:
         capacity = emb_cutlinks_count(forest, lattice, stream)
     if out is None:
         out = dict(cell=torch.empty(max(capacity, 1), dtype=torch.int32, device="cuda"),
@@ -297,7 +315,15 @@ def emb_cutlinks(forest: Forest, bins: Bins, lattice: int, capacity: int | None 
                              _out_ptr(out["q"]), _out_ptr(out["tri"]), int(capacity), _out_ptr(out["count"]),
                              _stream(stream))
     _check(rc, "emb_cutlinks")
-    n = capacity
+    if exact:
+        n = capacity
+    elif sync:
+        _sync(stream)
+        n = int(out["count"][0].item())
+        if n > capacity:
+            raise EmbError(EMB_ERR_CAPACITY, f"emb_cutlinks: {n} links, room for {capacity}")
+    else:
+        n = capacity
     return {k: (v[:n] if k != "count" else v) for k, v in out.items()}
 
 
@@ -412,10 +438,16 @@ def embed(verts: torch.Tensor, tris: torch.Tensor, R: int, levels: int, band: in
             if links_out is None:
                 E.links = emb_cutlinks(forest, bins, lattice, stream=stream)
             else:
-                n = emb_cutlinks_count(forest, lattice, stream)
-                if min(links_out[k].numel() for k in ("cell", "dir", "q", "tri")) < n:
-                    raise EmbError(EMB_ERR_CAPACITY, "embed: links_out holds fewer than the table's links")
-                E.links = emb_cutlinks(forest, bins, lattice, capacity=n, out=links_out, stream=stream)
+                # the buffers' size is the capacity: the count stays on the device
+                # until the table is written
+                cap = min(links_out[k].numel() for k in ("cell", "dir", "q", "tri"))
+                try:
+                    E.links = emb_cutlinks(forest, bins, lattice, capacity=cap, out=links_out, stream=stream)
+                except EmbError as e:
+                    if e.code == EMB_ERR_CAPACITY:
+                        emb_status_get(stream)  # the status the short table left
+                        raise EmbError(EMB_ERR_CAPACITY, "embed: links_out holds fewer than the table's links")
+                    raise
         if keep_bins:
             E.bins.append(bins)
         else:

@@ -103,6 +103,8 @@ def test_argument_errors_are_reported_before_any_device_work(lib):
     assert lib.emb_refine_flags_paper(fake, 0, -1.0, None, None) == BAD
     n = ctypes.c_int64(0)
     assert lib.emb_cutlinks_count(fake, 20, ctypes.byref(n), None) == BAD
+    assert lib.emb_cutlinks_prepare(fake, 20, None) == BAD
+    assert lib.emb_cutlinks_prepare(None, 19, None) == BAD
     assert lib.emb_cutlinks(None, None, 19, None, None, None, None, 0, None, None) == BAD
     assert lib.emb_lbm_step(fake, 19, None, None, None, 0, 2.5, fake, fake, fake, 64, 7, None) == BAD  # omega
     assert lib.emb_lbm_step(fake, 19, None, None, None, 0, 1.0, fake, fake, fake, 64, 8, None) == BAD  # phases
