@@ -140,7 +140,12 @@ void emb_forest_destroy(emb_forest f);
  * (z, y, x) order, plus their lookup index (a rank bitmap of the level's dense block
  * positions, or a hash where there are more than 2^32 of them).  This is the forest harness
  * (the paper delegates it to its AMR pipeline, Sec. 3.2 steps 1-8); it keeps no
- * ghost/interface metadata.  Synchronises once to read the child count.
+ * ghost/interface metadata.  Where the child level takes a rank bitmap the call
+ * returns without waiting: the child count travels to a pinned host slot behind the
+ * child keys, and the next call on this forest (any entry point that takes it) waits
+ * for it first, except emb_bin / emb_bin_ex, which first enqueue their x-line filter
+ * (it does not depend on the blocks), so that the GPU has work while the count
+ * travels.  With a hashed child level the call waits for the count itself.
  * Errors: EMB_ERR_STATE (level not the current finest, or beyond max_level). */
 emb_status emb_forest_refine(emb_forest f, int32_t level, const uint8_t *d_flags, void *stream);
 

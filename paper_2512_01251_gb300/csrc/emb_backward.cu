@@ -136,6 +136,7 @@ __global__ void k_mex_bwd(const int32_t *__restrict__ cell, const uint8_t *__res
 static emb_status mex_check(emb_forest f, int lattice, int64_t n, int64_t stride, cudaStream_t s)
 {
     if (!f || (lattice != 19 && lattice != 27) || n < 0) return EMB_ERR_BAD_INPUT;
+    EMB_SETTLE(f);
     int L = f->max_level;
     if (f->top != L || !f->lv[L].mask_valid) return EMB_ERR_STATE;
     if (stride < f->lv[L].n * 64) return EMB_ERR_BAD_INPUT;
@@ -255,6 +256,7 @@ extern "C" emb_status emb_mex_force_noalloc(emb_forest f, int32_t lattice, const
 {
     if (!f || (lattice != 19 && lattice != 27) || n < 0 || !d_F) return EMB_ERR_BAD_INPUT;
     if (n > 0 && (!d_cell || !d_dir || !d_q || !d_pop)) return EMB_ERR_BAD_INPUT;
+    EMB_SETTLE(f);
     const int L = f->max_level;
     if (f->top != L || !f->lv[L].mask_valid) return EMB_ERR_STATE;
     const EmbLevel &lv = f->lv[L];
@@ -386,6 +388,7 @@ extern "C" emb_status emb_cutlinks_backward(emb_mesh m, emb_forest f, const int3
                                             float *d_gverts, void *stream)
 {
     if (!m || !f || n < 0 || !d_gverts) return EMB_ERR_BAD_INPUT;
+    EMB_SETTLE(f);
     if (m->R != f->R || f->top != f->max_level) return EMB_ERR_STATE;
     if (n > 0 && (!d_cell || !d_dir || !d_q || !d_tri || !d_gq)) return EMB_ERR_BAD_INPUT;
     if (3 * n >= (1ll << 32)) return EMB_ERR_CAPACITY;

@@ -127,6 +127,7 @@ static emb_status plan_mesh(BMesh &B, cudaStream_t s)
             if (emb_malloc_async(&fl, n + 1, s) != cudaSuccess) rc = EMB_ERR_CUDA;
             if (rc == EMB_OK) rc = emb_refine_flags(f, b, L, B.band, fl, s);
             if (rc == EMB_OK) rc = emb_forest_refine(f, L, fl, s);
+            if (rc == EMB_OK) rc = emb_forest_settle(f);
             if (rc == EMB_OK) B.L[L].F = f->lv[L + 1].n / 8;
             cudaFreeAsync(fl, s);
         } else if (rc == EMB_OK) {

@@ -593,6 +593,8 @@ extern "C" emb_status emb_bin_ex(emb_mesh m, emb_forest f, int32_t level, int32_
         }
         if (rc == EMB_OK) EMB_LAUNCH((k_iota), emb_grid(m->T, 256), 256, 0, s)(b->flist, m->T, (uint32_t *)b->dcount);
     }
+    // a block count the forest still waits for is taken now, with the filter queued
+    if (rc == EMB_OK) rc = emb_forest_settle(f);
     // steps 2-9 at the finest level: CSR bins of link-relevant triangles per block
     if (rc == EMB_OK && level == f->max_level && lv.n > 0) {
         const uint64_t cap = (uint64_t)4 * m->T + (1 << 20);
@@ -663,6 +665,7 @@ extern "C" void emb_bins_destroy(emb_bins b)
 extern "C" emb_status emb_bins_stats(emb_bins b, int64_t *h_filtered, int64_t *h_pairs)
 {
     if (!b) return EMB_ERR_BAD_INPUT;
+    if (b) EMB_SETTLE(b->f);
     emb_status rc = emb_bins_sync(b);
     if (rc != EMB_OK) return rc;
     if (h_filtered) *h_filtered = b->nf;
@@ -673,6 +676,7 @@ extern "C" emb_status emb_bins_stats(emb_bins b, int64_t *h_filtered, int64_t *h
 extern "C" emb_status emb_bins_copy(emb_bins b, uint32_t *d_filtered, uint32_t *d_off, uint32_t *d_ent, void *stream)
 {
     if (!b) return EMB_ERR_BAD_INPUT;
+    if (b) EMB_SETTLE(b->f);
     emb_status rc = emb_bins_sync(b);
     if (rc != EMB_OK) return rc;
     cudaStream_t s = emb_stream(stream);

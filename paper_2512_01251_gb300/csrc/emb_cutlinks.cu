@@ -1081,6 +1081,7 @@ static emb_status build_candidates(emb_forest f, int lattice, cudaStream_t s, bo
 extern "C" emb_status emb_cutlinks_count(emb_forest f, int32_t lattice, int64_t *h_count, void *stream)
 {
     if (!f || !h_count || (lattice != 19 && lattice != 27)) return EMB_ERR_BAD_INPUT;
+    EMB_SETTLE(f);
     emb_status rc = build_candidates(f, lattice, emb_stream(stream), true);
     if (rc != EMB_OK) return rc;
     *h_count = f->n_links;
@@ -1090,6 +1091,7 @@ extern "C" emb_status emb_cutlinks_count(emb_forest f, int32_t lattice, int64_t 
 extern "C" emb_status emb_cutlinks_prepare(emb_forest f, int32_t lattice, void *stream)
 {
     if (!f || (lattice != 19 && lattice != 27)) return EMB_ERR_BAD_INPUT;
+    EMB_SETTLE(f);
     return build_candidates(f, lattice, emb_stream(stream), false);
 }
 
@@ -1097,6 +1099,7 @@ extern "C" emb_status emb_cutlinks(emb_forest f, emb_bins b, int32_t lattice, in
                                    int32_t *d_tri, int64_t capacity, int64_t *d_count, void *stream)
 {
     if (!f || !b || (lattice != 19 && lattice != 27) || capacity < 0) return EMB_ERR_BAD_INPUT;
+    EMB_SETTLE(f);
     if (b->f != f || b->level != f->max_level || f->top != f->max_level) return EMB_ERR_STATE;
     {
         // the outputs may be page-locked host memory: the kernel then writes the table

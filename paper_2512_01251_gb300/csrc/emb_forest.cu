@@ -161,9 +161,19 @@ emb_status emb_enq_root_keys(int64_t R, uint64_t *key, cudaStream_t s)
     return EMB_OK;
 }
 
+emb_status emb_forest_settle(emb_forest f)
+{
+    if (!f || f->n_pending < 0) return EMB_OK;
+    EMB_CUDA_TRY(cudaEventSynchronize(f->rb_ev));
+    f->lv[f->n_pending].n = 8 * (int64_t)(*(volatile uint32_t *)f->rb_h);
+    f->n_pending = -1;
+    return EMB_OK;
+}
+
 extern "C" emb_status emb_forest_refine(emb_forest f, int32_t level, const uint8_t *d_flags, void *stream)
 {
     if (!f) return EMB_ERR_BAD_INPUT;
+    EMB_SETTLE(f);
     if (level < 0 || level != f->top || level >= f->max_level) return EMB_ERR_STATE;
     if (!d_flags && f->lv[level].n > 0) return EMB_ERR_BAD_INPUT;
     cudaStream_t s = emb_stream(stream);
@@ -193,8 +203,11 @@ extern "C" emb_status emb_forest_refine(emb_forest f, int32_t level, const uint8
         EMB_CUDA_TRY(cudaFreeAsync(rank, s));
         EMB_CUDA_TRY(cudaFreeAsync(tmp, s));
         if (rc != EMB_OK) return rc;
-        EMB_CUDA_TRY(cudaEventSynchronize(f->rb_ev));
-        C.n = 8 * (int64_t)(*(volatile uint32_t *)f->rb_h);
+        // the count is stored when the forest is next used (emb_forest_settle): the
+        // caller may first queue work that does not need it, such as the next level's
+        // x-line filter, so that the GPU has it while the count travels
+        C.n = 0;
+        f->n_pending = level + 1;
     } else {
         uint32_t F = 0;
         EMB_CUDA_TRY(cudaMemcpyAsync(&F, rank + P.n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
@@ -234,12 +247,14 @@ extern "C" emb_status emb_forest_refine(emb_forest f, int32_t level, const uint8
 extern "C" emb_status emb_forest_num_blocks(emb_forest f, int32_t level, int64_t *h_out)
 {
     if (!f || !h_out || level < 0 || level >= EMB_MAX_LEVELS) return EMB_ERR_BAD_INPUT;
+    EMB_SETTLE(f);
     *h_out = level <= f->top ? f->lv[level].n : 0;
     return EMB_OK;
 }
 
 extern "C" emb_status emb_forest_blocks(emb_forest f, int32_t level, int32_t *d_out, void *stream)
 {
+    EMB_SETTLE(f);
     if (!f || level < 0 || level > f->top) return EMB_ERR_STATE;
     const EmbLevel &lv = f->lv[level];
     if (lv.n == 0) return EMB_OK;
@@ -251,6 +266,7 @@ extern "C" emb_status emb_forest_blocks(emb_forest f, int32_t level, int32_t *d_
 
 extern "C" emb_status emb_forest_neighbors(emb_forest f, int32_t level, int32_t *d_out, void *stream)
 {
+    EMB_SETTLE(f);
     if (!f || level < 0 || level > f->top) return EMB_ERR_STATE;
     EmbLevel &lv = f->lv[level];
     if (lv.n == 0) return EMB_OK;
@@ -264,6 +280,7 @@ extern "C" emb_status emb_forest_neighbors(emb_forest f, int32_t level, int32_t 
 
 extern "C" emb_status emb_forest_masks(emb_forest f, int32_t level, uint64_t *d_out, void *stream)
 {
+    EMB_SETTLE(f);
     if (!f || level < 0 || level > f->top || !f->lv[level].mask_valid) return EMB_ERR_STATE;
     const EmbLevel &lv = f->lv[level];
     if (lv.n == 0) return EMB_OK;

@@ -245,6 +245,7 @@ extern "C" emb_status emb_voxelize_guard(emb_forest f, emb_bins b, uint64_t *d_s
                                          void *stream)
 {
     if (!f || !b) return EMB_ERR_BAD_INPUT;
+    EMB_SETTLE(f);
     const int L = f->max_level;
     if (b->f != f || b->level != L || f->top != L) return EMB_ERR_STATE;
     EmbLevel &lv = f->lv[L];

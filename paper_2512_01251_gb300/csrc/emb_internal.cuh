@@ -148,6 +148,9 @@ struct emb_forest_s {
     int rb_slot = -1;
     uint64_t *rb_h = nullptr;
     cudaEvent_t rb_ev = nullptr;
+    // the level whose block count is still on its way to rb_h (-1: none); taken by
+    // emb_forest_settle, which every entry point that reads a forest calls first
+    int32_t n_pending = -1;
 };
 
 struct emb_bins_s {
@@ -199,6 +202,14 @@ static inline LevelGeom level_geom(const emb_forest_s *f, int L)
 // ---------------------------------------------------------------------------
 // small host helpers (defined in emb_common.cu)
 // ---------------------------------------------------------------------------
+// Waits for a block count emb_forest_refine left on its way back, and stores it
+// (emb_forest.cu).
+emb_status emb_forest_settle(emb_forest f);
+#define EMB_SETTLE(f_)                                         \
+    do {                                                       \
+        const emb_status rs_ = emb_forest_settle(f_);          \
+        if (rs_ != EMB_OK) return rs_;                         \
+    } while (0)
 // Scans: d_out gets n + 1 entries (exclusive sums, total at n).  emb_scan_u32
 // allocates its scratch and can read the total back (synchronising); emb_scan_into
 // only enqueues, with emb_scan_tmp_words(n) words of caller scratch.

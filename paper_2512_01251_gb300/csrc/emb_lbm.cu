@@ -131,6 +131,7 @@ extern "C" emb_status emb_lbm_step(emb_forest f, int32_t lattice, const int32_t 
     if (!f || (lattice != 19 && lattice != 27) || n_links < 0 || !(omega >= 0.0f && omega < 2.0f) || phases < 1 ||
         phases > 7)
         return EMB_ERR_BAD_INPUT;
+    EMB_SETTLE(f);
     const int L = f->max_level;
     if (f->top != L || !f->lv[L].mask_valid) return EMB_ERR_STATE;
     EmbLevel &lv = f->lv[L];

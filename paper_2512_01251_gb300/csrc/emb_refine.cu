@@ -362,6 +362,7 @@ extern "C" emb_status emb_refine_flags(emb_forest f, emb_bins b, int32_t level, 
                                        void *stream)
 {
     if (!f || !b || band < 1 || band > (1 << 20)) return EMB_ERR_BAD_INPUT;
+    EMB_SETTLE(f);
     if (b->f != f || level < 0 || level > f->top || level >= f->max_level) return EMB_ERR_STATE;
     const EmbLevel &lv = f->lv[level];
     if (lv.n == 0) return EMB_OK;
@@ -440,6 +441,7 @@ __global__ void k_pf_step(const int32_t *__restrict__ nbr, int64_t n, const uint
 extern "C" emb_status emb_refine_flags_paper(emb_forest f, int32_t level, double d_spec, uint8_t *d_flags, void *stream)
 {
     if (!f || !(d_spec >= 0.0) || d_spec > 1e6) return EMB_ERR_BAD_INPUT;
+    EMB_SETTLE(f);
     if (level < 0 || level != f->top || level >= f->max_level) return EMB_ERR_STATE;
     EmbLevel &lv = f->lv[level];
     if (!lv.mask_valid) return EMB_ERR_STATE;

@@ -166,6 +166,8 @@ extern "C" emb_status emb_splice(emb_forest f, emb_forest w, int32_t y0, int32_t
                                  void *stream)
 {
     if (!f || !w || !h_count || f_n < 0 || w_n < 0 || capacity < 0) return EMB_ERR_BAD_INPUT;
+    EMB_SETTLE(f);
+    EMB_SETTLE(w);
     if (f->R != w->R || f->max_level != w->max_level) return EMB_ERR_STATE;
     if (y0 < 0 || z0 < 0 || y1 > f->R || z1 > f->R || y0 >= y1 || z0 >= z1) return EMB_ERR_BAD_INPUT;
     const int Lf = f->max_level;

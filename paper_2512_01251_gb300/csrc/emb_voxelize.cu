@@ -232,6 +232,7 @@ emb_status emb_enq_voxelize(const int4 *rec, int64_t T, const uint32_t *flist, i
 extern "C" emb_status emb_voxelize(emb_forest f, emb_bins b, int32_t level, uint64_t *d_solid_mask, void *stream)
 {
     if (!f || !b) return EMB_ERR_BAD_INPUT;
+    EMB_SETTLE(f);
     if (b->f != f || b->level != level || level < 0 || level > f->top) return EMB_ERR_STATE;
     void *mask_out = nullptr;
     if (emb_device_view(d_solid_mask, &mask_out) != EMB_OK) return EMB_ERR_BAD_INPUT;
