@@ -536,29 +536,81 @@ emb_status emb_build_hash(EmbLevel &lv, cudaStream_t s)
     return rc;
 }
 
-__global__ void k_neighbors(const uint64_t *__restrict__ key, int64_t n, int64_t nb, EmbLookup lk, int32_t *__restrict__ nbr,
-                            const uint32_t *d_n)
+// Ids of the blocks at x - 1, x, x + 1 on row (y, z) of a rank-bitmap level into
+// out[0..2] (-1: no block, or outside the level).  The three positions are consecutive
+// bits, so they take at most two words and two rank prefixes.
+__device__ __forceinline__ void nbr_row3(const EmbLookup &lk, int64_t x, int64_t y, int64_t z, int32_t out[3])
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= emb_count(n, d_n) * 26) return;
-    int64_t b = i / 26;
-    int d = (int)(i % 26) + 1;
-    uint64_t k = key[b];
-    int64_t bx = (int64_t)(k & EMB_KEY_MASK), by = (int64_t)((k >> EMB_KEY_BITS) & EMB_KEY_MASK),
-            bz = (int64_t)(k >> (2 * EMB_KEY_BITS));
-    int cx, cy, cz;
-    emb_dir(d, cx, cy, cz);
-    int64_t x = bx + cx, y = by + cy, z = bz + cz;
-    int32_t r = -1;
-    if (x >= 0 && y >= 0 && z >= 0 && x < nb && y < nb && z < nb) r = emb_lookup(lk, x, y, z);
-    nbr[i] = r;
+    const int64_t nb = lk.nb;
+    out[0] = out[1] = out[2] = -1;
+    if (y < 0 || z < 0 || y >= nb || z >= nb) return;
+    const int64_t row = (z * nb + y) * nb;
+    const int64_t lo = x > 0 ? x - 1 : 0, hi = x + 1 < nb ? x + 1 : nb - 1;
+    const int64_t la = row + lo, lb = row + hi;
+    if (!emb_ck((uint64_t)lb, (uint64_t)nb * nb * nb, lk.st)) return;
+    const uint64_t wa = __ldg(lk.bits + (la >> 6)), wb = __ldg(lk.bits + (lb >> 6));
+    const uint32_t pa = __ldg(lk.wpre + (la >> 6)), pb = __ldg(lk.wpre + (lb >> 6));
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int64_t xx = x - 1 + k;
+        if (xx < lo || xx > hi) continue;
+        const int64_t l = row + xx;
+        const bool first = (l >> 6) == (la >> 6);
+        const uint64_t w = first ? wa : wb;
+        const int sh = (int)(l & 63);
+        if (!((w >> sh) & 1ull)) continue;
+        const int32_t id = (int32_t)((first ? pa : pb) + (uint32_t)__popcll(w & ((1ull << sh) - 1ull)));
+        out[k] = emb_ck((uint64_t)id, (uint64_t)lk.n, lk.st) ? id : -1;
+    }
+}
+
+// One thread per block: its 26 neighbours, found row by row (9 rows of 3 positions),
+// staged in shared memory so that the CTA writes its blocks' consecutive rows of the
+// table with coalesced stores.
+#define NBR_BLOCK 128
+__global__ void __launch_bounds__(NBR_BLOCK) k_neighbors(const uint64_t *__restrict__ key, int64_t n, int64_t nb,
+                                                          EmbLookup lk, int32_t *__restrict__ nbr, const uint32_t *d_n)
+{
+    __shared__ int32_t stage[NBR_BLOCK * 26];
+    const int64_t cnt = emb_count(n, d_n);
+    const int64_t b0 = (int64_t)blockIdx.x * NBR_BLOCK;
+    if (b0 >= cnt) return;  // the whole CTA
+    const int64_t b = b0 + threadIdx.x;
+    if (b < cnt) {
+        const uint64_t k = key[b];
+        const int64_t bx = (int64_t)(k & EMB_KEY_MASK), by = (int64_t)((k >> EMB_KEY_BITS) & EMB_KEY_MASK),
+                      bz = (int64_t)(k >> (2 * EMB_KEY_BITS));
+        int32_t id[27];  // by offset code (ox + 1) + 3 (oy + 1) + 9 (oz + 1)
+#pragma unroll
+        for (int r = 0; r < 9; ++r) {
+            const int oy = r % 3 - 1, oz = r / 3 - 1;
+            if (lk.bits) {
+                nbr_row3(lk, bx, by + oy, bz + oz, id + 3 * r);
+            } else {
+#pragma unroll
+                for (int ox = -1; ox <= 1; ++ox) {
+                    const int64_t x = bx + ox, y = by + oy, z = bz + oz;
+                    id[3 * r + ox + 1] = x >= 0 && y >= 0 && z >= 0 && x < nb && y < nb && z < nb ? emb_lookup(lk, x, y, z) : -1;
+                }
+            }
+        }
+#pragma unroll
+        for (int d = 1; d < 27; ++d) {
+            int cx, cy, cz;
+            emb_dir(d, cx, cy, cz);
+            stage[threadIdx.x * 26 + d - 1] = id[(cx + 1) + 3 * (cy + 1) + 9 * (cz + 1)];
+        }
+    }
+    __syncthreads();
+    const int m = (int)((cnt - b0 < NBR_BLOCK ? cnt - b0 : NBR_BLOCK) * 26);
+    for (int j = threadIdx.x; j < m; j += NBR_BLOCK) nbr[b0 * 26 + j] = stage[j];
 }
 
 emb_status emb_enq_neighbors(EmbLevel &lv, cudaStream_t s)
 {
     if (lv.n > 0)
-        EMB_LAUNCH((k_neighbors), emb_grid(lv.n * 26, 256), 256, 0, s)(lv.key, lv.n, lv.nb_axis, emb_lookup_of(lv), lv.nbr,
-                                                                               lv.d_n);
+        EMB_LAUNCH((k_neighbors), emb_grid(lv.n, NBR_BLOCK), NBR_BLOCK, 0, s)(lv.key, lv.n, lv.nb_axis, emb_lookup_of(lv),
+                                                                                    lv.nbr, lv.d_n);
     EMB_CUDA_TRY(cudaGetLastError());
     return EMB_OK;
 }
