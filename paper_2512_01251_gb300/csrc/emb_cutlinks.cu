@@ -41,50 +41,74 @@ __device__ __forceinline__ uint64_t shift_axis(uint64_t cur, uint64_t nxt, int a
 // Per finest block: word d-1 (d = 1 .. lattice-1) has bit t set iff cell t is fluid
 // and its neighbour along c_d is solid.  A missing neighbour block counts as fluid:
 // a fluid cell with a solid neighbour is within one link of the surface, and the
-// refine rule makes every block within that reach exist.
-__global__ void k_link_cand(const uint64_t *__restrict__ mask, const int32_t *__restrict__ nbr, int64_t n, int lattice,
-                            uint64_t *__restrict__ cand, uint32_t *__restrict__ blk_cnt, int *st, const uint32_t *d_n)
+// refine rule makes every block within that reach exist.  One thread per block; the
+// CTA reads its blocks' rows of the neighbour table and writes their rows of direction
+// words through shared memory, so that both go with coalesced accesses (rows of the
+// output are padded to 27 words there, against bank conflicts).
+#define CAND_BLOCK 128
+__global__ void __launch_bounds__(CAND_BLOCK) k_link_cand(const uint64_t *__restrict__ mask,
+                                                           const int32_t *__restrict__ nbr, int64_t n, int lattice,
+                                                           uint64_t *__restrict__ cand, uint32_t *__restrict__ blk_cnt,
+                                                           int *st, const uint32_t *d_n)
 {
-    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= emb_count(n, d_n)) return;
+    __shared__ uint64_t stage[CAND_BLOCK * 27];
+    int32_t *const srow = (int32_t *)stage;  // first the neighbour rows (26 ids a block)
+    const int64_t cnt = emb_count(n, d_n);
+    const int64_t b0 = (int64_t)blockIdx.x * CAND_BLOCK;
+    if (b0 >= cnt) return;  // the whole CTA
+    const int nloc = (int)(cnt - b0 < CAND_BLOCK ? cnt - b0 : CAND_BLOCK);
+    const int tid = threadIdx.x;
+    for (int j = tid; j < nloc * 26; j += CAND_BLOCK) srow[j] = nbr[b0 * 26 + j];
+    __syncthreads();
+    const int64_t b = b0 + tid;
     uint64_t W[27];  // mask words by offset code (ox+1) + 3(oy+1) + 9(oz+1)
-    W[13] = mask[b];
+    if (tid < nloc) {
+        W[13] = mask[b];
 #pragma unroll
-    for (int i = 1; i < 27; ++i) {
-        int cx, cy, cz;
-        emb_dir(i, cx, cy, cz);
-        const int32_t id = nbr[b * 26 + i - 1];
-        W[(cx + 1) + 3 * (cy + 1) + 9 * (cz + 1)] = id >= 0 && emb_ck((uint64_t)id, (uint64_t)n, st) ? mask[id] : 0ull;
-    }
-    const uint64_t fluid = ~W[13];
-    uint32_t count = 0;
-#pragma unroll
-    for (int d = 1; d < 27; ++d) {
-        if (d >= lattice) {
-            cand[b * 26 + d - 1] = 0;
-            continue;
+        for (int i = 1; i < 27; ++i) {
+            int cx, cy, cz;
+            emb_dir(i, cx, cy, cz);
+            const int32_t id = srow[tid * 26 + i - 1];
+            W[(cx + 1) + 3 * (cy + 1) + 9 * (cz + 1)] = id >= 0 && emb_ck((uint64_t)id, (uint64_t)n, st) ? mask[id] : 0ull;
         }
-        int cx, cy, cz;
-        emb_dir(d, cx, cy, cz);
-        // shift along x for every (y, z) block layer touched, then along y, then along z
-        uint64_t Y[2][2];
-#pragma unroll
-        for (int jy = 0; jy < 2; ++jy)
-#pragma unroll
-            for (int jz = 0; jz < 2; ++jz) {
-                const int oy = jy ? cy : 0, oz = jz ? cz : 0;
-                const uint64_t cur = W[1 + 3 * (oy + 1) + 9 * (oz + 1)];
-                Y[jy][jz] = cx ? shift_axis(cur, W[(cx + 1) + 3 * (oy + 1) + 9 * (oz + 1)], 0, cx) : cur;
-            }
-        uint64_t Z[2];
-#pragma unroll
-        for (int jz = 0; jz < 2; ++jz) Z[jz] = cy ? shift_axis(Y[0][jz], Y[1][jz], 1, cy) : Y[0][jz];
-        const uint64_t nb_solid = cz ? shift_axis(Z[0], Z[1], 2, cz) : Z[0];
-        const uint64_t c = fluid & nb_solid;
-        cand[b * 26 + d - 1] = c;
-        count += __popcll(c);
     }
-    blk_cnt[b] = count;
+    __syncthreads();  // the neighbour rows are overwritten below
+    if (tid < nloc) {
+        const uint64_t fluid = ~W[13];
+        uint32_t count = 0;
+#pragma unroll
+        for (int d = 1; d < 27; ++d) {
+            if (d >= lattice) {
+                stage[tid * 27 + d - 1] = 0;
+                continue;
+            }
+            int cx, cy, cz;
+            emb_dir(d, cx, cy, cz);
+            // shift along x for every (y, z) block layer touched, then along y, then along z
+            uint64_t Y[2][2];
+#pragma unroll
+            for (int jy = 0; jy < 2; ++jy)
+#pragma unroll
+                for (int jz = 0; jz < 2; ++jz) {
+                    const int oy = jy ? cy : 0, oz = jz ? cz : 0;
+                    const uint64_t cur = W[1 + 3 * (oy + 1) + 9 * (oz + 1)];
+                    Y[jy][jz] = cx ? shift_axis(cur, W[(cx + 1) + 3 * (oy + 1) + 9 * (oz + 1)], 0, cx) : cur;
+                }
+            uint64_t Z[2];
+#pragma unroll
+            for (int jz = 0; jz < 2; ++jz) Z[jz] = cy ? shift_axis(Y[0][jz], Y[1][jz], 1, cy) : Y[0][jz];
+            const uint64_t nb_solid = cz ? shift_axis(Z[0], Z[1], 2, cz) : Z[0];
+            const uint64_t c = fluid & nb_solid;
+            stage[tid * 27 + d - 1] = c;
+            count += __popcll(c);
+        }
+        blk_cnt[b] = count;
+    }
+    __syncthreads();
+    for (int j = tid; j < nloc * 26; j += CAND_BLOCK) {
+        const int r = j / 26;
+        cand[b0 * 26 + j] = stage[r * 27 + (j - r * 26)];
+    }
 }
 
 // One warp per work item: a finest block with links, or one part of a heavy block
@@ -920,7 +944,7 @@ emb_status emb_enq_link_prep(const EmbLevel &lv, int lattice, uint64_t *cand, ui
     EMB_CUDA_TRY(cudaMemsetAsync(cnt, 0, (lv.n + 1) * sizeof(uint32_t), s));
     EMB_CUDA_TRY(cudaMemsetAsync(flag, 0, (lv.n + 1) * sizeof(uint32_t), s));
     if (lv.n > 0) {
-        EMB_LAUNCH((k_link_cand), emb_grid(lv.n, 128), 128, 0, s)(lv.mask, lv.nbr, lv.n, lattice, cand, cnt,
+        EMB_LAUNCH((k_link_cand), emb_grid(lv.n, CAND_BLOCK), CAND_BLOCK, 0, s)(lv.mask, lv.nbr, lv.n, lattice, cand, cnt,
                                                                   emb_status_word(), lv.d_n);
         EMB_LAUNCH((k_nonempty), emb_grid(lv.n, 256), 256, 0, s)(cnt, lv.n, flag);
     }
