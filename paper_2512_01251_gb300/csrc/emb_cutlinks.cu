@@ -960,27 +960,49 @@ emb_status emb_enq_link_prep(const EmbLevel &lv, int lattice, uint64_t *cand, ui
 // into P = min(ceil(l nt / LE_SPLIT_COST), nbc, LE_SPLIT_MAX) parts of
 // ceil(nbc / P) consecutive cells.  The first part is the block's own item; the
 // others are appended to `extra`, and when that is full the block stays whole,
-// which changes the speed only.
+// which changes the speed only.  The lanes of a warp take their extra slots with one
+// atomic (a single counter taken once per heavy block serialised the kernel).
 __global__ void k_link_split(const uint32_t *__restrict__ work, const uint32_t *__restrict__ work_n,
                              const uint64_t *__restrict__ cand, const uint32_t *__restrict__ blk_off,
                              const uint32_t *__restrict__ bin_off, int64_t n, uint2 *__restrict__ witem,
                              uint2 *__restrict__ extra, unsigned long long *__restrict__ extra_n, uint32_t cap)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || i >= (int64_t)*work_n) return;
-    const uint32_t b = work[i];
-    uint64_t bm = 0;
-    for (int d = 0; d < 26; ++d) bm |= cand[(int64_t)b * 26 + d];
-    const uint32_t nbc = (uint32_t)__popcll(bm);
-    const unsigned long long l = blk_off[b + 1] - blk_off[b], nt = bin_off[b + 1] - bin_off[b];
-    unsigned long long P = (l * nt + LE_SPLIT_COST - 1) / LE_SPLIT_COST;
-    P = P < nbc ? P : nbc;
-    P = P < LE_SPLIT_MAX ? P : LE_SPLIT_MAX;
+    const int lane = threadIdx.x & 31;
+    const bool live = i < n && i < (int64_t)*work_n;
+    if (__ballot_sync(0xffffffffu, live) == 0u) return;  // the whole warp
+    const uint32_t b = live ? work[i] : 0u;
+    uint32_t nbc = 0;
+    unsigned long long P = 0;
+    if (live) {
+        uint64_t bm = 0;
+        for (int d = 0; d < 26; ++d) bm |= cand[(int64_t)b * 26 + d];
+        nbc = (uint32_t)__popcll(bm);
+        const unsigned long long l = blk_off[b + 1] - blk_off[b], nt = bin_off[b + 1] - bin_off[b];
+        P = (l * nt + LE_SPLIT_COST - 1) / LE_SPLIT_COST;
+        P = P < nbc ? P : nbc;
+        P = P < LE_SPLIT_MAX ? P : LE_SPLIT_MAX;
+    }
     uint32_t span = nbc;
     if (P > 1) {
         span = (uint32_t)((nbc + P - 1) / P);
         P = (nbc + span - 1) / span;  // no empty part
-        const unsigned long long base = atomicAdd(extra_n, P - 1);
+    }
+    // the warp's extra slots: one atomic, each lane's range from an exclusive prefix
+    const uint32_t want = P > 1 ? (uint32_t)(P - 1) : 0u;
+    uint32_t incl = want;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    unsigned long long wbase = 0;
+    if (lane == 31 && total > 0) wbase = atomicAdd(extra_n, (unsigned long long)total);
+    wbase = __shfl_sync(0xffffffffu, wbase, 31);
+    if (!live) return;
+    if (P > 1) {
+        const unsigned long long base = wbase + (incl - want);
         if (base + P - 1 > cap) {
             for (unsigned long long e = base; e < cap; ++e) extra[e] = make_uint2(EMB_BIG_NONE, 0u);
             span = nbc;
