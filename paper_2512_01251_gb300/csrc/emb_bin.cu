@@ -201,27 +201,6 @@ __device__ __forceinline__ void bin_block(const int4 &A, const int4 &B, const in
     PL.put(atomicAdd(PL.n, 1ull), (uint32_t)id, slot, t);
 }
 
-// Appends the pairs of the lanes with `hit` to the pair list (one list append per warp)
-// and takes each pair's slot in its block.
-__device__ __forceinline__ void bin_append(bool hit, int32_t id, uint32_t tri, int lane, uint32_t *__restrict__ cnt,
-                                           const PairList &PL)
-{
-    const unsigned hm = __ballot_sync(0xffffffffu, hit);
-    if (!hm) return;
-    unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(PL.n, (unsigned long long)__popc(hm));
-    base = __shfl_sync(0xffffffffu, base, 0) + (unsigned long long)__popc(hm & ((1u << lane) - 1u));
-    if (hit) {
-        // lanes that hit the same block take their slots with one atomic
-        const unsigned grp = __match_any_sync(hm, id);
-        const int lead = __ffs(grp) - 1;
-        uint32_t first = 0;
-        if (lane == lead) first = atomicAdd(cnt + id, (uint32_t)__popc(grp));
-        first = __shfl_sync(grp, first, lead);
-        PL.put(base, (uint32_t)id, first + (uint32_t)__popc(grp & ((1u << lane) - 1u)), tri);
-    }
-}
-
 // Per warp: (triangle lane, bx, by, bz) and block id of pairs whose triangle has no vertex
 // in the dilated block, waiting for the separating-axis test.
 struct SatQueue {
@@ -229,10 +208,55 @@ struct SatQueue {
     int32_t id[EMB_WU_WARPS][64];
 };
 
+// Per warp: pairs (block, slot; triangle) waiting to be appended to the pair list, so
+// that the list's one counter is taken once per 32 or more pairs instead of once per
+// round (a counter that every warp takes each round serialised the kernel).
+struct PairBuf {
+    uint2 bs[EMB_WU_WARPS][64];
+    uint32_t tri[EMB_WU_WARPS][64];
+};
+
+// Appends the buffered pairs of warp w to the list with one atomic; coalesced stores.
+__device__ __forceinline__ void pair_flush(PairBuf &PB, int w, int &bn, int lane, const PairList &PL)
+{
+    __syncwarp();
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(PL.n, (unsigned long long)bn);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (int j = lane; j < bn; j += 32) {
+        const uint2 v = PB.bs[w][j];
+        PL.put(base + (unsigned long long)j, v.x, v.y, PB.tri[w][j]);
+    }
+    __syncwarp();
+    bn = 0;
+}
+
+// bin_append through the warp's buffer: each pair takes its slot in its block at once
+// (lanes that hit the same block with one atomic); the buffer is flushed once it holds
+// 32 pairs or more (bn, warp-uniform, is below 32 on entry, so 64 entries suffice).
+__device__ __forceinline__ void bin_append_buf(bool hit, int32_t id, uint32_t tri, int lane, uint32_t *__restrict__ cnt,
+                                               PairBuf &PB, int w, int &bn, const PairList &PL)
+{
+    const unsigned hm = __ballot_sync(0xffffffffu, hit);
+    if (!hm) return;
+    if (hit) {
+        const unsigned grp = __match_any_sync(hm, id);
+        const int lead = __ffs(grp) - 1;
+        uint32_t first = 0;
+        if (lane == lead) first = atomicAdd(cnt + id, (uint32_t)__popc(grp));
+        first = __shfl_sync(grp, first, lead);
+        const int pos = bn + __popc(hm & ((1u << lane) - 1u));
+        PB.bs[w][pos] = make_uint2((uint32_t)id, first + (uint32_t)__popc(grp & ((1u << lane) - 1u)));
+        PB.tri[w][pos] = tri;
+    }
+    bn += __popc(hm);
+    if (bn >= 32) pair_flush(PB, w, bn, lane, PL);
+}
+
 // The separating-axis test of the first n queued pairs, one per lane.
 __device__ __forceinline__ void bin_sat_batch(const SatQueue &Q2, int w, int n, int lane, const WuTri &S, int64_t t0,
                                               const LevelGeom &g, long long dil, uint32_t *__restrict__ cnt,
-                                              const PairList &PL)
+                                              PairBuf &PB, int &bn, const PairList &PL)
 {
     bool hit = false;
     int32_t id = -1;
@@ -245,7 +269,7 @@ __device__ __forceinline__ void bin_sat_batch(const SatQueue &Q2, int w, int n, 
         const long long hx = lx + g.W + 2 * dil, hy = ly + g.W + 2 * dil, hz = lz + g.W + 2 * dil;
         hit = emb_tri_box(S.A[ti], S.B[ti], S.C[ti], lx, ly, lz, hx, hy, hz);
     }
-    bin_append(hit, id, (uint32_t)(t0 + ti), lane, cnt, PL);
+    bin_append_buf(hit, id, (uint32_t)(t0 + ti), lane, cnt, PB, w, bn, PL);
 }
 
 // The (triangle, candidate block) pairs of 32 consecutive triangles, spread evenly over
@@ -265,9 +289,11 @@ __global__ void __launch_bounds__(EMB_WU_WARPS * 32, 8) k_bin_pairs(const int4 *
 {
     __shared__ WuTri tiles[EMB_WU_WARPS];
     __shared__ SatQueue Q2;
+    __shared__ PairBuf PB;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WuTri &S = tiles[w];
     int qn = 0;  // pairs queued for the full overlap test (warp-uniform)
+    int bn = 0;  // pairs buffered for the list (warp-uniform)
     const int64_t t0 = ((int64_t)blockIdx.x * EMB_WU_WARPS + w) * 32;
     const int64_t t = t0 + lane;
     const int dil32 = (int)dil, W32 = (int)g.W;
@@ -327,7 +353,7 @@ __global__ void __launch_bounds__(EMB_WU_WARPS * 32, 8) k_bin_pairs(const int4 *
                 need = !hit;
             }
         }
-        bin_append(hit, id, (uint32_t)(t0 + ti), lane, cnt, PL);
+        bin_append_buf(hit, id, (uint32_t)(t0 + ti), lane, cnt, PB, w, bn, PL);
         // pairs that need the full overlap test wait until a whole warp's worth is queued
         const unsigned nm = __ballot_sync(0xffffffffu, need);
         if (need) {
@@ -338,7 +364,7 @@ __global__ void __launch_bounds__(EMB_WU_WARPS * 32, 8) k_bin_pairs(const int4 *
         qn += __popc(nm);
         __syncwarp();
         if (qn >= 32) {
-            bin_sat_batch(Q2, w, 32, lane, S, t0, g, dil, cnt, PL);
+            bin_sat_batch(Q2, w, 32, lane, S, t0, g, dil, cnt, PB, bn, PL);
             int4 e = make_int4(0, 0, 0, 0);
             int32_t idn = 0;
             if (lane < qn - 32) {
@@ -354,7 +380,8 @@ __global__ void __launch_bounds__(EMB_WU_WARPS * 32, 8) k_bin_pairs(const int4 *
             __syncwarp();
         }
     }
-    if (qn > 0) bin_sat_batch(Q2, w, qn, lane, S, t0, g, dil, cnt, PL);
+    if (qn > 0) bin_sat_batch(Q2, w, qn, lane, S, t0, g, dil, cnt, PB, bn, PL);
+    if (bn > 0) pair_flush(PB, w, bn, lane, PL);
 }
 
 // Decomposition of candidate index i of the box [b0, b1] (x fastest) and its step by 32.
