@@ -197,9 +197,29 @@ __global__ void k_xscan(const uint64_t *__restrict__ key, int64_t n, const unsig
     uint64_t row = key[i] >> EMB_KEY_BITS;
     if (i + 1 < n && (key[i + 1] >> EMB_KEY_BITS) == row) return;  // only the row's last (+x-most) block walks
     unsigned int acc = t_acc[i];  // crossings beyond the row's last block
-    for (int64_t j = i; j >= 0 && (key[j] >> EMB_KEY_BITS) == row; --j) {
-        mask[j] = s_acc[j] ^ spread_lines(acc);
-        acc ^= p_acc[j];
+    // the walk loads 8 blocks at a time (those past the row's first block are read and
+    // dropped), so that it waits on memory once per 8 blocks instead of once per block
+    for (int64_t j = i;; j -= 8) {
+        uint64_t kk[8];
+        unsigned long long ss[8];
+        unsigned int pp[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int64_t jj = j - u;
+            kk[u] = jj >= 0 ? key[jj] : ~0ull;  // ~0 >> EMB_KEY_BITS is no row
+            ss[u] = jj >= 0 ? s_acc[jj] : 0ull;
+            pp[u] = jj >= 0 ? p_acc[jj] : 0u;
+        }
+        bool end = false;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            end = end || (kk[u] >> EMB_KEY_BITS) != row;
+            if (!end) {
+                mask[j - u] = ss[u] ^ spread_lines(acc);
+                acc ^= pp[u];
+            }
+        }
+        if (end) break;
     }
 }
 
