@@ -231,9 +231,10 @@ __device__ __forceinline__ void pair_flush(PairBuf &PB, int w, int &bn, int lane
     bn = 0;
 }
 
-// bin_append through the warp's buffer: each pair takes its slot in its block at once
-// (lanes that hit the same block with one atomic); the buffer is flushed once it holds
-// 32 pairs or more (bn, warp-uniform, is below 32 on entry, so 64 entries suffice).
+// Appends the pairs of the lanes with `hit` through the warp's buffer: each pair takes
+// its slot in its block at once (lanes that hit the same block with one atomic); the
+// buffer is flushed once it holds 32 pairs or more (bn, warp-uniform, is below 32 on
+// entry, so 64 entries suffice).
 __device__ __forceinline__ void bin_append_buf(bool hit, int32_t id, uint32_t tri, int lane, uint32_t *__restrict__ cnt,
                                                PairBuf &PB, int w, int &bn, const PairList &PL)
 {
@@ -275,7 +276,7 @@ __device__ __forceinline__ void bin_sat_batch(const SatQueue &Q2, int w, int n, 
 // The (triangle, candidate block) pairs of 32 consecutive triangles, spread evenly over
 // the warp's lanes by a prefix sum of the lanes' candidate counts, so that every lane
 // tests one pair per round (a triangle with very many candidates goes to the chunk queue
-// instead), with one list append per warp and round.  A pair whose triangle has a vertex
+// instead), the pairs buffered per warp for the list.  A pair whose triangle has a vertex
 // in the dilated block is decided at once; the others wait in a per-warp queue and take
 // the full separating-axis test 32 at a time, so that the lanes run it together.  (Visiting the union of the 32
 // triangles' candidate blocks instead, one lane per block against all 32 triangles,
