@@ -291,7 +291,8 @@ def reduce_over_ranks(dist, total_ms: float, units: float, device: str):
     return float(tt.item()), float(uu.item())
 
 
-def step_roofline(med, T, level_blocks, stats, n_links, tests, hbm_gbs, alu_tops, step_ms, replay_ms=None):
+def step_roofline(med, T, level_blocks, stats, n_links, tests, hbm_gbs, alu_tops, step_ms, replay_ms=None,
+                  link_tris=None):
     """Roofline of the whole step: per call, T_roof = max(algorithmic bytes / HBM peak,
     algorithmic ops / ALU peak); summed over the calls of a step and divided by the
     measured step time.  Bytes per call (B = blocks of the level, T triangles, nf the
@@ -302,8 +303,10 @@ def step_roofline(med, T, level_blocks, stats, n_links, tests, hbm_gbs, alu_tops
       voxelize L        52 nf + 8 B + 32 B (kept records and ids, masks, line parities in and out)
       refine flags L    48 T + B
       forest refine L   9 B + 8 B_next (flags and keys in, child keys out)
-      cut links         27 x 8 B + 4 pairs + 48 nf + 13 links (mask words, bins, records,
-                        the table), ops = tests x KAPPA_SEG + links x KAPPA_Q
+      cut links         27 x 8 B + 4 pairs + 48 Tb + 13 links (mask words, bins, the records
+                        of the Tb distinct triangles of the finest bins, the table),
+                        ops = tests x KAPPA_SEG + links x KAPPA_Q (Tb = link_tris; the
+                        finest level's x-filter count when it is not given)
     Only the cut links carry an op count (the exact segment tests it must run); for the
     other calls the bytes bound is used, which makes their roofline time a lower bound."""
     lf = len(level_blocks) - 1
@@ -329,7 +332,8 @@ def step_roofline(med, T, level_blocks, stats, n_links, tests, hbm_gbs, alu_tops
             add(f"forest_refine{L}", med.get(f"forest_refine{L}"), 9 * B + 8 * level_blocks[L + 1])
     cl_ms = (med.get("cutlinks_prep") or 0.0) + (med.get("cutlinks_emit") or 0.0)
     Bf = level_blocks[lf]
-    add("cutlinks", cl_ms, 27 * 8 * Bf + 4 * stats[lf][1] + 48 * stats[lf][0] + 13 * n_links,
+    tb = stats[lf][0] if link_tris is None else link_tris
+    add("cutlinks", cl_ms, 27 * 8 * Bf + 4 * stats[lf][1] + 48 * tb + 13 * n_links,
         tests * KAPPA_SEG + n_links * KAPPA_Q)
     t_roof = sum(r["roof_ms"] for r in rows.values())
     out = dict(step_roof_ms=round(t_roof, 4), step_ms=round(step_ms, 4), step_frac=round(t_roof / step_ms, 4),
@@ -485,6 +489,8 @@ def run_ours(args):
     off = bins["off"].cpu().numpy().astype(np.int64)
     blk_links = np.bincount(links["cell"].cpu().numpy().astype(np.int64) // 64, minlength=len(off) - 1)
     tests = int((blk_links * np.diff(off)).sum())
+    # the triangles the link kernel stages: the distinct ones of the finest bins
+    link_tris = int(torch.unique(bins["ent"]).numel()) if bins["ent"].numel() else 0
     emit_ms = med["cutlinks_emit"]
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
     clk_mhz = (clk or {}).get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
@@ -536,7 +542,7 @@ def run_ours(args):
                              units_per_s=(64 * sum(level_blocks) + n_links) / (four / 1e3) if four else None)
     # the whole step against its roofline (the replay leg below adds the graph-replay time)
     roofline["step"] = step_roofline(med, T, level_blocks, stats, n_links, tests, hbm, alu_peak,
-                                     line["step_ms_stats"]["median"])
+                                     line["step_ms_stats"]["median"], link_tris=link_tris)
 
     if rank == 0 and not args.no_extras:
         legs = None if args.legs == "all" else set(args.legs.split(","))
@@ -563,7 +569,8 @@ def run_ours(args):
         if want("replay"):
             line["replay"] = replay_leg(P, verts, tris, w, lattice, line["ms_per_step"])
             line["roofline"]["step"] = step_roofline(med, T, level_blocks, stats, n_links, tests, hbm, alu_peak,
-                                                     line["step_ms_stats"]["median"], line["replay"]["ms"])
+                                                     line["step_ms_stats"]["median"], line["replay"]["ms"],
+                                                     link_tris=link_tris)
         if want("cpu_baseline"):
             units_b, secs_b = oracle_lines_full(v, t, w, lattice)
             units_a, secs_a = oracle_sample(v, t, w, lattice, 4, seed=7)

@@ -85,7 +85,7 @@ def test_oracle_slabs_partition_the_workload():
 def test_step_roofline_sums_the_calls():
     b = _bench()
     med = {"mesh": 0.3, "bin0": 0.5, "bin1": 1.0, "voxelize0": 0.1, "voxelize1": 0.2, "refine_flags0": 0.4,
-           "forest_refine0": 0.1, "cutlinks_count": 0.5, "cutlinks_emit": 4.0}
+           "forest_refine0": 0.1, "cutlinks_prep": 0.5, "cutlinks_emit": 4.0}
     r = b.step_roofline(med, 1000, [8, 64], [(500, 0), (400, 3000)], 20000, 10 ** 9, 6000.0, 40.0, 8.0, 6.0)
     assert set(r["per_call"]) == {"mesh", "bin0", "bin1", "voxelize0", "voxelize1", "refine_flags0", "forest_refine0",
                                   "cutlinks"}
@@ -93,3 +93,10 @@ def test_step_roofline_sums_the_calls():
     assert lk["bound"] == "alu" and abs(lk["roof_ms"] - (10 ** 9 * 48 + 20000 * 60) / 40e12 * 1e3) < 1e-3
     assert abs(r["step_roof_ms"] - sum(x["roof_ms"] for x in r["per_call"].values())) < 1e-3
     assert abs(r["step_frac"] - r["step_roof_ms"] / 8.0) < 1e-3 and abs(r["replay_frac"] - r["step_roof_ms"] / 6.0) < 1e-3
+    assert abs(lk["ms"] - 4.5) < 1e-9  # link preparation plus the table
+    # the link table's bytes count the records of the finest bins' distinct triangles
+    by = 27 * 8 * 64 + 4 * 3000 + 13 * 20000
+    assert lk["bytes"] == by + 48 * 400
+    r2 = b.step_roofline(med, 1000, [8, 64], [(500, 0), (400, 3000)], 20000, 10 ** 9, 6000.0, 40.0, 8.0, 6.0,
+                         link_tris=900)
+    assert r2["per_call"]["cutlinks"]["bytes"] == by + 48 * 900
