@@ -4,6 +4,7 @@ from __future__ import annotations
 import numpy as np
 import pytest
 
+from gpu_common import Q_TOL
 from synth import link_weights, populations, workload
 
 pytestmark = pytest.mark.gpu
@@ -16,6 +17,26 @@ def _cuda():
         pytest.skip("no CUDA device")
 
 
+def _gpu_table(E):
+    L = E.links
+    return dict(cell=L["cell"].cpu().numpy().astype(np.int64), dir=L["dir"].cpu().numpy().astype(np.int64),
+                q=L["q"].cpu().numpy().astype(np.float64), tri=L["tri"].cpu().numpy().astype(np.int64))
+
+
+def _same_as_oracle(E, o, levels):
+    """The GPU's finest blocks, mask and link table against the oracle's own (sorted-line
+    tier): blocks, mask words, cells, directions and triangles equal, q within Q_TOL."""
+    import paper_2512_01251_gb300 as P
+    np.testing.assert_array_equal(P.emb_forest_blocks(E.forest, levels).cpu().numpy().astype(np.int64),
+                                  o["blocks"][levels])
+    np.testing.assert_array_equal(E.masks[-1].cpu().numpy().view(np.uint64), o["masks"][levels])
+    g = _gpu_table(E)
+    for k in ("cell", "dir", "tri"):
+        np.testing.assert_array_equal(g[k], o["links"][k], err_msg=k)
+    assert np.abs(g["q"] - o["links"]["q"]).max() <= Q_TOL
+    return g
+
+
 def _setup(name, orc):
     import torch
 
@@ -23,12 +44,9 @@ def _setup(name, orc):
     w = workload(name)
     v, t = w.build_mesh()
     E = P.embed(torch.from_numpy(v), torch.from_numpy(t), w.R, w.levels, w.band, 19)
-    blocks_f = P.emb_forest_blocks(E.forest, w.levels).cpu().numpy().astype(np.int64)
-    mask_f = E.masks[-1].cpu().numpy().view(np.uint64)
-    L = E.links
-    lk = dict(cell=L["cell"].cpu().numpy().astype(np.int64), dir=L["dir"].cpu().numpy().astype(np.int64),
-              q=L["q"].cpu().numpy().astype(np.float64), tri=L["tri"].cpu().numpy().astype(np.int64))
-    return w, v, t, E, blocks_f, mask_f, lk
+    o = orc.embed_lines(v, t, w.R, w.levels, w.band, 19)
+    lk = _same_as_oracle(E, o, w.levels)
+    return w, v, t, E, o, lk
 
 
 @pytest.mark.parametrize("name", ["icosphere_320", "star_1k", "diff_112k"])
@@ -36,12 +54,16 @@ def test_force_and_adjoints_match_oracle(orc, name):
     import torch
 
     import paper_2512_01251_gb300 as P
-    w, v, t, E, blocks_f, mask_f, lk = _setup(name, orc)
+    w, v, t, E, o, lk = _setup(name, orc)
     L = E.links
+    blocks_f, mask_f, ol = o["blocks"][-1], o["masks"][-1], o["links"]
     ncell = len(blocks_f) * 64
     pop_np = populations(ncell, seed=w.extra.get("pop_seed", 20251206))
     pop = torch.from_numpy(pop_np).cuda()
-    partner = orc.partner_cells(w.R, w.levels, blocks_f, mask_f, lk["cell"], lk["dir"])
+    # partners from the oracle's own blocks and mask; the force and dF/dq references take
+    # the GPU's q (the table was just shown to be the oracle's within Q_TOL), so that the
+    # Bouzidi branch at q = 1/2 is decided on the same value on both sides
+    partner = orc.partner_cells(w.R, w.levels, blocks_f, mask_f, ol["cell"], ol["dir"])
 
     F = P.emb_mex_force(E.forest, 19, L["cell"], L["dir"], L["q"], pop).cpu().numpy().astype(np.float64)
     F_ref = orc.mex_force(lk, pop_np, partner)
@@ -57,8 +79,8 @@ def test_force_and_adjoints_match_oracle(orc, name):
     wk = link_weights(len(lk["q"]), seed=w.extra.get("w_seed", 20251207))
     gv = P.emb_cutlinks_backward(E.mesh, E.forest, L["cell"], L["dir"], L["q"], L["tri"],
                                  torch.from_numpy(wk).cuda()).cpu().numpy().astype(np.float64)
-    gv_ref = orc.grad_verts_from_gq(lk, wk.astype(np.float64), orc.int_coords(v, w.R), t, w.R, w.levels,
-                                    blocks_f, len(v))
+    # dL/dverts for L = sum_k w_k q_k on the oracle's own table (its q and triangles)
+    gv_ref = orc.grad_verts_from_gq(ol, wk.astype(np.float64), o["X"], t, w.R, w.levels, blocks_f, len(v))
     rel = np.linalg.norm(gv - gv_ref) / np.linalg.norm(gv_ref)
     assert rel <= 1e-4, rel
     assert np.abs(gv - gv_ref).max() <= 1e-4 * np.abs(gv_ref).max()
@@ -77,12 +99,14 @@ def test_autograd_chain_matches_composed_oracle(orc):
     F = mex_force(q, E, torch.from_numpy(pop_np).cuda())
     F[0].backward()
     g = verts.grad.cpu().numpy().astype(np.float64)
-    lk = dict(cell=E.links["cell"].cpu().numpy().astype(np.int64), dir=E.links["dir"].cpu().numpy().astype(np.int64),
-              q=E.links["q"].cpu().numpy().astype(np.float64), tri=E.links["tri"].cpu().numpy().astype(np.int64))
-    mask_f = E.masks[-1].cpu().numpy().view(np.uint64)
-    partner = orc.partner_cells(w.R, w.levels, blocks_f, mask_f, lk["cell"], lk["dir"])
+    o = orc.embed_lines(v, t, w.R, w.levels, w.band, 19)
+    lk = _same_as_oracle(E, o, w.levels)
+    ol = o["links"]
+    partner = orc.partner_cells(w.R, w.levels, o["blocks"][-1], o["masks"][-1], ol["cell"], ol["dir"])
+    # dF_x/dq with the branch at q = 1/2 decided on the GPU's q (as the kernel decides it),
+    # then dq/dverts on the oracle's own table
     gq = orc.mex_force_dq(lk, pop_np, partner)[:, 0]
-    ref = orc.grad_verts_from_gq(lk, gq, orc.int_coords(v, w.R), t, w.R, w.levels, blocks_f, len(v))
+    ref = orc.grad_verts_from_gq(ol, gq, o["X"], t, w.R, w.levels, o["blocks"][-1], len(v))
     assert np.linalg.norm(g - ref) <= 1e-4 * np.linalg.norm(ref)
 
 
