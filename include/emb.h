@@ -143,9 +143,10 @@ void emb_forest_destroy(emb_forest f);
  * ghost/interface metadata.  Where the child level takes a rank bitmap the call
  * returns without waiting: the child count travels to a pinned host slot behind the
  * child keys, and the next call on this forest (any entry point that takes it) waits
- * for it first, except emb_bin / emb_bin_ex, which first enqueue their x-line filter
- * (it does not depend on the blocks), so that the GPU has work while the count
- * travels.  With a hashed child level the call waits for the count itself.
+ * for it first, except emb_bin / emb_bin_ex: below the finest level they are the x-line
+ * filter alone (it does not depend on the blocks) and do not wait; at the finest level
+ * they wait after enqueueing the filter.  So the GPU has work while the count travels.
+ * With a hashed child level the call waits for the count itself.
  * Errors: EMB_ERR_STATE (level not the current finest, or beyond max_level). */
 emb_status emb_forest_refine(emb_forest f, int32_t level, const uint8_t *d_flags, void *stream);
 

@@ -621,8 +621,10 @@ extern "C" emb_status emb_bin_ex(emb_mesh m, emb_forest f, int32_t level, int32_
         }
         if (rc == EMB_OK) EMB_LAUNCH((k_iota), emb_grid(m->T, 256), 256, 0, s)(b->flist, m->T, (uint32_t *)b->dcount);
     }
-    // a block count the forest still waits for is taken now, with the filter queued
-    if (rc == EMB_OK) rc = emb_forest_settle(f);
+    // the finest level's bins need its exact block count: a count the forest still
+    // waits for is taken now, with the filter queued (below the finest level the bins are
+    // the filter alone, and the next call that needs the count takes it)
+    if (rc == EMB_OK && level == f->max_level) rc = emb_forest_settle(f);
     // steps 2-9 at the finest level: CSR bins of link-relevant triangles per block
     if (rc == EMB_OK && level == f->max_level && lv.n > 0) {
         const uint64_t cap = (uint64_t)4 * m->T + (1 << 20);
