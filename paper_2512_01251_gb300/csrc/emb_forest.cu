@@ -203,9 +203,9 @@ extern "C" emb_status emb_forest_refine(emb_forest f, int32_t level, const uint8
         EMB_CUDA_TRY(cudaFreeAsync(rank, s));
         EMB_CUDA_TRY(cudaFreeAsync(tmp, s));
         if (rc != EMB_OK) return rc;
-        // the count is stored when the forest is next used (emb_forest_settle): the
-        // caller may first queue work that does not need it, such as the next level's
-        // x-line filter, so that the GPU has it while the count travels
+        // the count is stored when a call first needs it (emb_forest_settle): work that
+        // does not need it, such as the next level's x-line filter, is queued first, so
+        // that the GPU has it while the count travels
         C.n = 0;
         f->n_pending = level + 1;
     } else {

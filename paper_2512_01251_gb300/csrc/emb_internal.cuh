@@ -149,7 +149,8 @@ struct emb_forest_s {
     uint64_t *rb_h = nullptr;
     cudaEvent_t rb_ev = nullptr;
     // the level whose block count is still on its way to rb_h (-1: none); taken by
-    // emb_forest_settle, which every entry point that reads a forest calls first
+    // emb_forest_settle, which every entry point that needs a forest's counts calls
+    // before it uses them
     int32_t n_pending = -1;
 };
 
